@@ -1,0 +1,279 @@
+"""CPU oracle for the trace-analysis path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``oracle.cpp`` (plain,
+single-threaded C++, written from the paper's definitions; see the header of
+that file for the section each function follows) through ctypes.  It shares no
+code with the CUDA path and never imports it.
+
+Parity pins live in ``tests/test_oracle_*.py``.  The per-group CV definitions
+(``cv_across``, ``cv_within``) are parity unpinned against the paper's printed
+numbers (the data behind Table IV is not available); their arithmetic is pinned
+by closed-form cases only.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK, INVALID, NOT_SORTED, BAD_CTX, BAD_CCT = 0, 1, 2, 3, 4
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "not_sorted", 3: "bad_ctx", 4: "bad_cct"}
+EXCL, INCL = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so (plain g++, no fast-math, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", _LIB + ".tmp", _SRC]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Input(C.Structure):
+    _fields_ = [("n_ranks", C.c_uint32), ("n_ctx", C.c_uint32), ("marker_ctx", C.c_uint32),
+                ("pad", C.c_uint32), ("n_records", C.c_uint64), ("rank_off", C.c_void_p),
+                ("ts", C.c_void_p), ("ctx", C.c_void_p), ("parent", C.c_void_p)]
+
+
+class CtxStats(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("present", C.c_uint32), ("argmax", C.c_uint32),
+                ("pad", C.c_uint32), ("min", C.c_uint64), ("max", C.c_uint64),
+                ("s1", C.c_uint64), ("s2_lo", C.c_uint64), ("s2_hi", C.c_uint64),
+                ("mean", C.c_double), ("std", C.c_double), ("cv", C.c_double),
+                ("balance", C.c_double)]
+
+
+class Outlier(C.Structure):
+    _fields_ = [("ctx", C.c_uint32), ("rank", C.c_uint32), ("z", C.c_double)]
+
+
+class SpeedupCtx(C.Structure):
+    _fields_ = [("A", C.c_uint64), ("B", C.c_uint64), ("G_lo", C.c_uint64), ("G_hi", C.c_uint64),
+                ("avg_mean", C.c_double), ("avg_max", C.c_double),
+                ("savings_per_iter", C.c_double), ("total_reduction", C.c_double),
+                ("share", C.c_double), ("cv_across", C.c_double), ("cv_within", C.c_double)]
+
+
+class SpeedupTotal(C.Structure):
+    _fields_ = [("i_star", C.c_uint32), ("pad", C.c_uint32), ("excluded_iterations", C.c_uint64),
+                ("sum_G_lo", C.c_uint64), ("sum_G_hi", C.c_uint64), ("t_app", C.c_uint64),
+                ("total_reduction", C.c_double), ("speedup_fraction", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.or_validate.restype = C.c_int
+        L.or_validate.argtypes = [C.POINTER(_Input)]
+        L.or_u128_to_double.restype = C.c_double
+        L.or_u128_to_double.argtypes = [C.c_uint64, C.c_uint64]
+        L.or_analyze.restype = C.c_void_p
+        L.or_analyze.argtypes = [C.POINTER(_Input), C.c_uint32, C.c_uint32, C.c_int, C.c_int,
+                                 C.POINTER(C.c_int)]
+        L.or_free.argtypes = [C.c_void_p]
+        L.or_tensor_sizes.argtypes = [C.c_void_p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
+        L.or_tensor_get.argtypes = [C.c_void_p] + [C.c_void_p] * 6
+        L.or_csr_nnz.restype = C.c_uint64
+        L.or_csr_nnz.argtypes = [C.c_void_p, C.c_int]
+        L.or_csr_get.argtypes = [C.c_void_p, C.c_int] + [C.c_void_p] * 4
+        L.or_span_get.argtypes = [C.c_void_p, C.c_void_p]
+        L.or_stats.restype = C.c_int
+        L.or_stats.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_uint32, C.c_void_p,
+                               C.c_uint32, C.c_uint32, C.c_uint32, C.c_void_p, C.c_void_p,
+                               C.c_uint64, C.POINTER(C.c_uint64), C.c_void_p]
+        L.or_topology.restype = C.c_int
+        L.or_topology.argtypes = ([C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_uint32,
+                                   C.c_uint32, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
+                                   C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32]
+                                  + [C.c_void_p] * 12)
+        L.or_speedup.restype = C.c_int
+        L.or_speedup.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
+                                 C.c_uint64, C.c_void_p, C.POINTER(SpeedupTotal)]
+        L.or_savings_from_averages.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
+                                               C.c_double, C.c_void_p, C.c_void_p,
+                                               C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _u32(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint32)
+
+
+class Traces:
+    """Host arrays of one experiment (kept alive for the oracle handle)."""
+
+    def __init__(self, rank_off, ts, ctx, parent, marker):
+        self.rank_off = np.ascontiguousarray(rank_off, dtype=np.uint64)
+        self.ts = np.ascontiguousarray(ts, dtype=np.uint64)
+        self.ctx = np.ascontiguousarray(ctx, dtype=np.uint32)
+        self.parent = np.ascontiguousarray(parent, dtype=np.uint32)
+        self.marker = int(marker)
+        self.R = len(self.rank_off) - 1
+        self.C = len(self.parent)
+        self.N = int(self.rank_off[-1]) if self.R >= 0 and len(self.rank_off) else 0
+
+    def struct(self):
+        s = _Input()
+        s.n_ranks, s.n_ctx, s.marker_ctx = self.R, self.C, self.marker
+        s.n_records = len(self.ts)
+        s.rank_off, s.ts = _p(self.rank_off), _p(self.ts)
+        s.ctx, s.parent = _p(self.ctx), _p(self.parent)
+        return s
+
+
+def validate(tr: Traces) -> int:
+    s = tr.struct()
+    return lib().or_validate(C.byref(s))
+
+
+def u128_to_double(v: int) -> float:
+    return lib().or_u128_to_double(v & (2**64 - 1), v >> 64)
+
+
+class Analysis:
+    """Oracle results for ranks [r0, r1) of one experiment."""
+
+    def __init__(self, tr: Traces, r0=0, r1=None, rows=True, incl=True, validate=True):
+        self.tr = tr
+        self.r0 = r0
+        self.r1 = tr.R if r1 is None else r1
+        s = tr.struct()
+        st = C.c_int(0)
+        want = (1 if rows else 0) | (2 if incl else 0)
+        self.h = lib().or_analyze(C.byref(s), r0, self.r1, want, 1 if validate else 0, C.byref(st))
+        self.status = st.value
+        if not self.h:
+            raise OracleError(self.status)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().or_free(h)
+            self.h = None
+
+    def tensor(self):
+        rows, nnz = C.c_uint64(0), C.c_uint64(0)
+        lib().or_tensor_sizes(self.h, C.byref(rows), C.byref(nnz))
+        n = self.r1 - self.r0
+        out = dict(row_off_of_rank=np.zeros(n + 1, np.uint64),
+                   entry_off=np.zeros(rows.value + 1, np.uint64),
+                   e_ctx=np.zeros(nnz.value, np.uint32), e_time=np.zeros(nnz.value, np.uint64),
+                   e_cnt=np.zeros(nnz.value, np.uint32), n_iter=np.zeros(n, np.uint32))
+        lib().or_tensor_get(self.h, _p(out["row_off_of_rank"]), _p(out["entry_off"]),
+                            _p(out["e_ctx"]), _p(out["e_time"]), _p(out["e_cnt"]),
+                            _p(out["n_iter"]))
+        return out
+
+    def csr(self, which=EXCL):
+        nnz = lib().or_csr_nnz(self.h, which)
+        n = self.r1 - self.r0
+        out = dict(off=np.zeros(n + 1, np.uint64), ctx=np.zeros(nnz, np.uint32),
+                   time=np.zeros(nnz, np.uint64), cnt=np.zeros(nnz, np.uint32))
+        lib().or_csr_get(self.h, which, _p(out["off"]), _p(out["ctx"]), _p(out["time"]),
+                         _p(out["cnt"]))
+        return out
+
+    def span(self):
+        out = np.zeros(self.r1 - self.r0, np.uint64)
+        lib().or_span_get(self.h, _p(out))
+        return out
+
+    def stats(self, metric=EXCL, ranks=None, ctxs=None, tau=(3, 1), cap=1 << 20, want_z=False):
+        ranks, ctxs = _u32(ranks), _u32(ctxs)
+        k = self.tr.C if ctxs is None else len(ctxs)
+        st = (CtxStats * max(k, 1))()
+        outl = (Outlier * max(cap, 1))()
+        n_out = C.c_uint64(0)
+        z = np.zeros(lib().or_csr_nnz(self.h, metric), np.float64) if want_z else None
+        s = lib().or_stats(self.h, metric, _p(ranks), 0 if ranks is None else len(ranks),
+                           _p(ctxs), 0 if ctxs is None else len(ctxs), tau[0], tau[1],
+                           C.cast(st, C.c_void_p), C.cast(outl, C.c_void_p), cap,
+                           C.byref(n_out), _p(z))
+        if s != OK:
+            raise OracleError(s)
+        stats = _structs_to_dict(st[:k], CtxStats)
+        m = min(n_out.value, cap)
+        outliers = dict(ctx=np.array([o.ctx for o in outl[:m]], np.uint32),
+                        rank=np.array([o.rank for o in outl[:m]], np.uint32),
+                        z=np.array([o.z for o in outl[:m]], np.float64))
+        return stats, outliers, n_out.value, z
+
+    def topology(self, ctx, node_of_rank, rack_of_node, chassis_of_node, n_racks, n_chassis,
+                 metric=EXCL, tau=(3, 1), min_ranks=1, ranks=None):
+        node_of_rank, rack_of_node = _u32(node_of_rank), _u32(rack_of_node)
+        chassis_of_node, ranks = _u32(chassis_of_node), _u32(ranks)
+        nn = len(rack_of_node)
+        o = dict(node_outliers=np.zeros(nn, np.uint32), node_sum=np.zeros(nn, np.uint64),
+                 node_ranks=np.zeros(nn, np.uint32), node_flag=np.zeros(nn, np.uint8),
+                 chassis_flagged=np.zeros(n_chassis, np.uint32),
+                 chassis_nodes=np.zeros(n_chassis, np.uint32),
+                 chassis_sum=np.zeros(n_chassis, np.uint64),
+                 rack_flagged=np.zeros(n_racks, np.uint32), rack_nodes=np.zeros(n_racks, np.uint32),
+                 rack_sum=np.zeros(n_racks, np.uint64), flagged_racks=np.zeros(n_racks, np.uint32))
+        nf = np.zeros(1, np.uint32)
+        s = lib().or_topology(self.h, metric, ctx, tau[0], tau[1], min_ranks, _p(ranks),
+                              0 if ranks is None else len(ranks), _p(node_of_rank), nn,
+                              _p(rack_of_node), n_racks, _p(chassis_of_node), n_chassis,
+                              _p(o["node_outliers"]), _p(o["node_sum"]), _p(o["node_ranks"]),
+                              _p(o["node_flag"]), _p(o["chassis_flagged"]),
+                              _p(o["chassis_nodes"]), _p(o["chassis_sum"]),
+                              _p(o["rack_flagged"]), _p(o["rack_nodes"]), _p(o["rack_sum"]),
+                              _p(o["flagged_racks"]), _p(nf))
+        if s != OK:
+            raise OracleError(s)
+        o["flagged_racks"] = o["flagged_racks"][: int(nf[0])]
+        return o
+
+    def speedup(self, ctxs, ranks=None, app_time_ns=0):
+        ctxs, ranks = _u32(ctxs), _u32(ranks)
+        per = (SpeedupCtx * len(ctxs))()
+        tot = SpeedupTotal()
+        s = lib().or_speedup(self.h, _p(ctxs), len(ctxs), _p(ranks),
+                             0 if ranks is None else len(ranks), app_time_ns,
+                             C.cast(per, C.c_void_p), C.byref(tot))
+        if s != OK:
+            raise OracleError(s)
+        d = _structs_to_dict(per[:], SpeedupCtx)
+        d["G"] = [int(lo) + (int(hi) << 64) for lo, hi in zip(d["G_lo"], d["G_hi"])]
+        t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "pad"}
+        t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
+        return d, t
+
+
+def savings_from_averages(avg_mean, avg_max, iterations, app_time):
+    a = np.ascontiguousarray(avg_mean, np.float64)
+    b = np.ascontiguousarray(avg_max, np.float64)
+    s = np.zeros(len(a)), np.zeros(len(a))
+    tot, frac = C.c_double(0), C.c_double(0)
+    lib().or_savings_from_averages(_p(a), _p(b), len(a), iterations, app_time, _p(s[0]),
+                                   _p(s[1]), C.byref(tot), C.byref(frac))
+    return s[0], s[1], tot.value, frac.value
+
+
+def _structs_to_dict(items, cls):
+    names = [f for f, _ in cls._fields_ if f != "pad"]
+    return {f: np.array([getattr(it, f) for it in items]) for f in names}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status):
+        super().__init__(f"oracle status {status} ({STATUS_NAMES.get(status, '?')})")
+        self.status = status
