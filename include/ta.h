@@ -1,0 +1,367 @@
+/*
+ * ta.h -- C ABI of the B300 trace-analysis library (libta.so).
+ *
+ * The library turns per-rank execution traces into the products the paper's
+ * analysis layer derives from them (arxiv 2605.03561):
+ *   - the rank x iteration x context tensor of exclusive time (Section V,
+ *     the tri-dimensional model; iterations re-materialised from traces),
+ *   - exclusive time per (rank, context) and inclusive time rolled up the
+ *     calling context tree (Section II-A, inclusive/exclusive costs),
+ *   - cross-rank statistics per context: min/max/mean/std, balance ratio,
+ *     coefficient of variation, argmax rank, z-score outliers (Section VI-A,
+ *     the group-by listing and Table IV; Section VI-B, outlier ranks),
+ *   - the node/chassis/rack rollup of outlier ranks (Section VI-B),
+ *   - the imbalance-derived potential speedup (Section VI-A, Table V).
+ *
+ * Every computation runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions
+ *   - Every call returns ta_status; no exception crosses the ABI.  After a
+ *     non-OK status, ta_last_error_message() (thread-local) says why.
+ *   - Inputs are borrowed: the library reads them during the call.
+ *   - Outputs go to caller-owned buffers whose memory kind (host or device) is
+ *     stated in the argument struct.  Every call below returns after its
+ *     device work is complete (it synchronises the context's stream), so both
+ *     host and device outputs are ready on return.
+ *   - Sizes use the two-call pattern: a call whose output arrays are NULL only
+ *     reports the sizes; too small a capacity returns TA_ERR_CAPACITY with
+ *     the required size filled in and writes nothing.
+ *   - Device memory the library needs is obtained from the allocator given to
+ *     ta_set_allocator() (default: cudaMallocAsync on the context's stream).
+ *   - Exactness: all times are integer nanoseconds (uint64).  Sums and moments
+ *     are exact integers (sum of squares in 128 bits); only the final mean,
+ *     std, cv, balance, z and speedup ratios are IEEE double, each a fixed
+ *     sequence of correctly rounded operations on exactly converted integers.
+ *     Loading requires R * (longest rank span) < 2^63 so that every such
+ *     integer fits (TA_ERR_INVALID_ARG otherwise).
+ */
+#ifndef TA_H
+#define TA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ta_status {
+  TA_OK = 0,
+  TA_ERR_INVALID_ARG = 1, /* bad pointer, size, subset, rank offsets, limits */
+  TA_ERR_NOT_SORTED = 2,  /* a rank's timestamps decrease                     */
+  TA_ERR_BAD_CTX = 3,     /* a sample's context id >= n_ctx                    */
+  TA_ERR_BAD_CCT = 4,     /* parent array: not exactly one root, parent out of
+                             range, or a cycle                                */
+  TA_ERR_OOM = 5,         /* device allocation failed                         */
+  TA_ERR_CAPACITY = 6,    /* caller buffer too small; required size filled in  */
+  TA_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up               */
+  TA_ERR_CUDA = 8,        /* CUDA runtime error                               */
+  TA_ERR_STATE = 9        /* call not valid in the object's current state     */
+} ta_status;
+
+#define TA_NO_PARENT 0xFFFFFFFFu
+
+typedef enum ta_mem_kind { TA_MEM_HOST = 0, TA_MEM_DEVICE = 1 } ta_mem_kind;
+typedef enum ta_metric { TA_EXCLUSIVE = 0, TA_INCLUSIVE = 1 } ta_metric;
+
+typedef struct ta_ctx ta_ctx;
+typedef struct ta_experiment ta_experiment;
+
+/* ------------------------------------------------------------ context ---- */
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).  The
+ * stream is borrowed and must outlive the context.  Errors: INVALID_ARG
+ * (out NULL), CUDA (no such device). */
+ta_status ta_create(int device, void* cuda_stream, ta_ctx** out);
+ta_status ta_destroy(ta_ctx* ctx);
+
+/* Device memory callbacks.  alloc(bytes, stream, user) returns device memory
+ * usable on `stream` or NULL; free(ptr, bytes, stream, user) releases it.
+ * Pass NULLs to restore the default (cudaMallocAsync / cudaFreeAsync). */
+typedef void* (*ta_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*ta_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+ta_status ta_set_allocator(ta_ctx* ctx, ta_alloc_fn alloc, ta_free_fn free_fn, void* user);
+
+/* Wait for all work issued on the context's stream. */
+ta_status ta_sync(ta_ctx* ctx);
+
+/* Thread-local text of the last error; never NULL. */
+const char* ta_last_error_message(void);
+const char* ta_status_string(ta_status s);
+
+/* Number of kernel launches the library has issued on this context so far. */
+uint64_t ta_kernel_launches(const ta_ctx* ctx);
+
+/* --------------------------------------------------------- ingestion ---- */
+
+/* Execution traces (Section II-A: per rank a time-ordered list of samples,
+ * each a timestamp and the calling context tree node it hit).
+ *   rank_off[R+1]  CSR offsets into ts/ctx; rank r owns samples
+ *                  [rank_off[r], rank_off[r+1]); rank_off[0] = 0,
+ *                  non-decreasing, rank_off[R] = n_records; a rank may be
+ *                  empty; a rank holds fewer than 2^32 samples.
+ *   ts[N]          uint64 ns, non-decreasing within a rank (ties allowed).
+ *   ctx[N]         uint32 context id < n_ctx.
+ *   parent[C]      calling context tree; exactly one root with
+ *                  parent = TA_NO_PARENT; every other parent < C; acyclic.
+ *   marker_ctx     iteration marker context (< C): an iteration starts at
+ *                  the first sample of every run of marker samples; samples
+ *                  before a rank's first marker form its prologue row.
+ *   mem_kind       where the four arrays live.
+ *   flags          TA_LOAD_BORROW: device ts/ctx are used in place (no copy)
+ *                  and must stay valid and unchanged until
+ *                  ta_experiment_free(); TA_LOAD_NO_INCLUSIVE: skip the
+ *                  inclusive rollup.
+ *   nnz_hint, rows_hint  optional first-try capacities of the tensor (0 =
+ *                  library default); a too-small hint only costs a re-run.
+ * A sample lasts until the next sample of its rank; a rank's last sample
+ * lasts 0 ns but still counts as one sample. */
+#define TA_LOAD_BORROW 1u
+#define TA_LOAD_NO_INCLUSIVE 2u
+
+typedef struct ta_trace_desc {
+  uint32_t n_ranks;
+  uint32_t n_ctx;
+  uint32_t marker_ctx;
+  uint32_t mem_kind;
+  uint64_t n_records;
+  const uint64_t* rank_off;
+  const uint64_t* ts;
+  const uint32_t* ctx;
+  const uint32_t* parent;
+  uint32_t flags;
+  uint32_t reserved;
+  uint64_t nnz_hint;
+  uint64_t rows_hint;
+} ta_trace_desc;
+
+/* Validate the traces (all of the rules above) and build the experiment's
+ * resident products on the device: per-rank spans and iteration counts, the
+ * iteration tensor, the exclusive CSR and (unless skipped) the inclusive CSR.
+ * Synchronous: returns after the device work, with the first error found in
+ * the order INVALID_ARG, BAD_CCT, BAD_CTX, NOT_SORTED (then OOM, TIMEOUT,
+ * CUDA).  Host inputs are copied to the device first.  The experiment is
+ * owned by the caller and released by ta_experiment_free(). */
+ta_status ta_load_traces(ta_ctx* ctx, const ta_trace_desc* d, ta_experiment** out);
+ta_status ta_experiment_free(ta_experiment* e);
+
+typedef struct ta_experiment_info {
+  uint32_t n_ranks, n_ctx, marker_ctx, max_depth; /* max_depth: deepest node */
+  uint64_t n_records;
+  uint64_t n_rows;       /* rows of the iteration tensor = R + sum n_iter   */
+  uint64_t tensor_nnz;   /* (rank, iteration, ctx) entries                  */
+  uint64_t excl_nnz;     /* (rank, ctx) entries of the exclusive CSR        */
+  uint64_t incl_nnz;     /* (rank, ctx) entries of the inclusive CSR (0 if skipped) */
+  uint64_t device_bytes; /* device memory held by the experiment           */
+} ta_experiment_info;
+ta_status ta_experiment_get_info(const ta_experiment* e, ta_experiment_info* info);
+
+/* ------------------------------------------------- iteration tensor ---- */
+
+/* The tri-dimensional model of Section V as CSR over (rank, iteration) rows.
+ * Rank r owns rows [row_off_of_rank[r], row_off_of_rank[r+1]): its prologue
+ * row (possibly empty) and then one row per iteration, n_iter[r] of them.
+ * Row k owns entries [entry_off[k], entry_off[k+1]), context-ascending, one
+ * per context with at least one sample in that row: e_time = summed sample
+ * durations (ns), e_cnt = samples.
+ *   n_iter[R], row_off_of_rank[R+1], entry_off[rows+1]  (rows_cap >= rows+1)
+ *   e_ctx, e_time, e_cnt [nnz]                          (nnz_cap >= nnz)
+ * Any array may be NULL to skip it; all NULL = sizes only. */
+typedef struct ta_tensor_out {
+  uint32_t mem_kind;
+  uint32_t reserved;
+  uint32_t* n_iter;
+  uint64_t* row_off_of_rank;
+  uint64_t* entry_off;
+  uint32_t* e_ctx;
+  uint64_t* e_time;
+  uint32_t* e_cnt;
+  uint64_t rows_cap; /* elements of entry_off                          */
+  uint64_t nnz_cap;  /* elements of e_ctx / e_time / e_cnt             */
+  uint64_t rows;     /* out                                            */
+  uint64_t nnz;      /* out                                            */
+} ta_tensor_out;
+ta_status ta_iteration_tensor(ta_experiment* e, ta_tensor_out* o);
+
+/* Per-(rank, context) CSR: rank r owns [off[r], off[r+1]), context-ascending.
+ * Exclusive: time and samples in that context (Section V, profiles collapse
+ * time).  Inclusive: the same summed over the context's subtree of the
+ * calling context tree; present for every ancestor of a present context. */
+typedef struct ta_csr_out {
+  uint32_t mem_kind;
+  uint32_t reserved;
+  uint64_t* off; /* [R+1] */
+  uint32_t* ctx;
+  uint64_t* time;
+  uint32_t* cnt;
+  uint64_t nnz_cap;
+  uint64_t nnz; /* out */
+} ta_csr_out;
+ta_status ta_exclusive(ta_experiment* e, ta_csr_out* o);
+ta_status ta_inclusive_rollup(ta_experiment* e, ta_csr_out* o);
+
+/* Zero-copy views of the resident products (device pointers owned by the
+ * experiment, valid until ta_experiment_free). */
+typedef struct ta_tensor_view {
+  const uint32_t* n_iter;
+  const uint64_t* row_off_of_rank;
+  const uint64_t* entry_off;
+  const uint32_t* e_ctx;
+  const uint64_t* e_time;
+  const uint32_t* e_cnt;
+  const uint64_t* span; /* [R] ts_last - ts_first (0 for an empty rank) */
+  uint64_t rows, nnz;
+} ta_tensor_view;
+typedef struct ta_csr_view {
+  const uint64_t* off;
+  const uint32_t* ctx;
+  const uint64_t* time;
+  const uint32_t* cnt;
+  uint64_t nnz;
+} ta_csr_view;
+ta_status ta_tensor_get_view(const ta_experiment* e, ta_tensor_view* v);
+ta_status ta_csr_get_view(const ta_experiment* e, uint32_t metric, ta_csr_view* v);
+
+/* ---------------------------------------------- cross-rank statistics ---- */
+
+/* Per context c over the rank set S (n = |S|; a rank without samples of c
+ * counts as x = 0 -- absent ranks are idle ranks):
+ *   n, present (ranks with >= 1 sample), min, max, argmax (lowest rank
+ *   attaining max), s1 = sum x, s2 = sum x^2 (128-bit: s2_hi:s2_lo),
+ *   mean = s1/n, std (ddof 1; 0 if n < 2), cv = std/mean (0 if mean = 0),
+ *   balance = mean/max (1 if max = 0)          (Section VI-A, Table IV).
+ * z-score of a present rank r: (n x_r - s1) / (n std) (0 if std = 0).
+ * Outlier: a present rank whose z exceeds tau = tau_num / tau_den, decided
+ * exactly in integers (no rounding) -- the high side only, slow ranks
+ * (Section VI-B).  Outliers are listed sorted by (ctx, rank).
+ *   ranks     sorted, unique rank ids, or NULL for all ranks;
+ *   ctxs      sorted, unique context ids, or NULL for all C;
+ *   mem_kind  of ranks/ctxs and of every output array. */
+typedef struct ta_stats_args {
+  uint32_t metric; /* ta_metric */
+  uint32_t mem_kind;
+  const uint32_t* ranks;
+  uint32_t n_ranks_subset;
+  uint32_t n_ctxs;
+  const uint32_t* ctxs;
+  uint32_t tau_num, tau_den; /* tau_den > 0 */
+} ta_stats_args;
+
+typedef struct ta_ctx_stats {
+  uint32_t n, present, argmax, reserved;
+  uint64_t min, max, s1, s2_lo, s2_hi;
+  double mean, std, cv, balance;
+} ta_ctx_stats;
+
+typedef struct ta_outlier {
+  uint32_t ctx, rank;
+  double z;
+} ta_outlier;
+
+/* stats[n_ctxs or C] in the order of ctxs; outliers[outlier_cap];
+ * z (optional) is laid out like the metric's CSR entries and receives the
+ * z-score of each entry of a rank in S and a requested context, 0 elsewhere.
+ * n_outliers is always set; if it exceeds outlier_cap the call returns
+ * TA_ERR_CAPACITY after writing stats and z (outliers unspecified). */
+typedef struct ta_stats_out {
+  ta_ctx_stats* stats;
+  ta_outlier* outliers;
+  uint64_t outlier_cap;
+  uint64_t n_outliers; /* out */
+  double* z;
+} ta_stats_out;
+ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_out* o);
+
+/* --------------------------------------------------- topology rollup ---- */
+
+/* Integer machine topology (Section VI-B: rank -> compute node via the
+ * profile metadata, node -> chassis and rack via its Slingshot coordinate).
+ * Chassis ids are global (not per rack). */
+typedef struct ta_topology {
+  uint32_t n_nodes, n_chassis, n_racks, mem_kind;
+  const uint32_t* node_of_rank;    /* [R]       */
+  const uint32_t* rack_of_node;    /* [n_nodes] */
+  const uint32_t* chassis_of_node; /* [n_nodes] */
+} ta_topology;
+
+/* One context: its outlier ranks over S (as in ta_context_stats), then per
+ * node: outlier ranks, sum of x over its ranks in S, ranks in S; a node is
+ * flagged when it has >= min_ranks (>= 1) outlier ranks; per chassis and per
+ * rack: flagged nodes, nodes, summed x; flagged_racks = racks with a flagged
+ * node, ascending. */
+typedef struct ta_topo_args {
+  uint32_t metric;
+  uint32_t ctx;
+  uint32_t tau_num, tau_den;
+  uint32_t min_ranks;
+  uint32_t n_ranks_subset;
+  const uint32_t* ranks; /* sorted unique or NULL; memory kind of ta_topo_out */
+} ta_topo_args;
+
+typedef struct ta_topo_out {
+  uint32_t mem_kind;
+  uint32_t n_flagged_racks; /* out */
+  uint32_t* node_outliers;   /* [n_nodes]   */
+  uint64_t* node_sum;        /* [n_nodes]   */
+  uint32_t* node_ranks;      /* [n_nodes]   */
+  uint8_t* node_flag;        /* [n_nodes]   */
+  uint32_t* chassis_flagged; /* [n_chassis] */
+  uint32_t* chassis_nodes;   /* [n_chassis] */
+  uint64_t* chassis_sum;     /* [n_chassis] */
+  uint32_t* rack_flagged;    /* [n_racks]   */
+  uint32_t* rack_nodes;      /* [n_racks]   */
+  uint64_t* rack_sum;        /* [n_racks]   */
+  uint32_t* flagged_racks;   /* [n_racks]   */
+} ta_topo_out;
+ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_topo_args* a,
+                             ta_topo_out* o);
+
+/* ------------------------------------------------- potential speedup ---- */
+
+/* Section VI-A, Table V.  For contexts K (sorted unique, e.g. the GPU
+ * kernels) over ranks S, using iterations i < I* = min over S of n_iter (the
+ * prologue and later iterations are excluded; excluded_iterations counts the
+ * latter).  With t[r][i][k] the tensor's time (0 if absent):
+ *   A_k = sum_i max_r t, B_k = sum_i sum_r t, G_k = n A_k - B_k (exact),
+ *   avg_mean = B_k / (n I*), avg_max = A_k / I*, savings_per_iter = G_k/(n I*),
+ *   total_reduction = G_k / n, share = B_k / sum B,
+ *   cv_across = mean over i of (std/mean over ranks of t[.][i][k]),
+ *   cv_within = mean over r in S of (std/mean over i < I* of t[r][.][k]),
+ * and totals: sum G, total reduction = sum G / n, t_app = app_time_ns or
+ * (if 0) the longest rank span in S, speedup_fraction = sum G / (n t_app).
+ * (Both CV sums run in ascending i / ascending r.) */
+typedef struct ta_speedup_args {
+  uint32_t mem_kind; /* of ctxs / ranks / outputs */
+  uint32_t n_ctxs;
+  const uint32_t* ctxs;
+  const uint32_t* ranks;
+  uint32_t n_ranks_subset;
+  uint32_t reserved;
+  uint64_t app_time_ns;
+} ta_speedup_args;
+
+typedef struct ta_speedup_ctx {
+  uint64_t A, B, G_lo, G_hi;
+  double avg_mean, avg_max, savings_per_iter, total_reduction, share, cv_across, cv_within;
+} ta_speedup_ctx;
+
+typedef struct ta_speedup_total {
+  uint32_t i_star, reserved;
+  uint64_t excluded_iterations;
+  uint64_t sum_G_lo, sum_G_hi;
+  uint64_t t_app;
+  double total_reduction;
+  double speedup_fraction;
+} ta_speedup_total;
+
+typedef struct ta_speedup_out {
+  ta_speedup_ctx* per_ctx;  /* [n_ctxs] */
+  ta_speedup_total* total;  /* [1]      */
+} ta_speedup_out;
+ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_speedup_out* o);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TA_H */
