@@ -1,0 +1,469 @@
+"""B300-native bulk trace analysis (arxiv 2605.03561, the hpcanalysis trace path).
+
+A thin ctypes binding over ``libta.so`` (C ABI in ``include/ta.h``).  Every
+step of the analysis runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch supplies device memory (the library allocates
+through torch's caching allocator) and the CUDA stream.  There is no CPU
+fallback: if the extension cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libta.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "ta.h")
+
+OK, INVALID_ARG, NOT_SORTED, BAD_CTX, BAD_CCT, OOM, CAPACITY, TIMEOUT, CUDA, STATE = range(10)
+MEM_HOST, MEM_DEVICE = 0, 1
+EXCLUSIVE, INCLUSIVE = 0, 1
+LOAD_BORROW, LOAD_NO_INCLUSIVE = 1, 2
+NO_PARENT = 0xFFFFFFFF
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "not_sorted", 3: "bad_ctx", 4: "bad_cct", 5: "oom",
+                6: "capacity", 7: "timeout", 8: "cuda", 9: "state"}
+
+P = C.c_void_p
+u32, u64 = C.c_uint32, C.c_uint64
+
+
+class TraceDesc(C.Structure):
+    _fields_ = [("n_ranks", u32), ("n_ctx", u32), ("marker_ctx", u32), ("mem_kind", u32),
+                ("n_records", u64), ("rank_off", P), ("ts", P), ("ctx", P), ("parent", P),
+                ("flags", u32), ("reserved", u32), ("nnz_hint", u64), ("rows_hint", u64)]
+
+
+class ExperimentInfo(C.Structure):
+    _fields_ = [("n_ranks", u32), ("n_ctx", u32), ("marker_ctx", u32), ("max_depth", u32),
+                ("n_records", u64), ("n_rows", u64), ("tensor_nnz", u64), ("excl_nnz", u64),
+                ("incl_nnz", u64), ("device_bytes", u64)]
+
+
+class TensorOut(C.Structure):
+    _fields_ = [("mem_kind", u32), ("reserved", u32), ("n_iter", P), ("row_off_of_rank", P),
+                ("entry_off", P), ("e_ctx", P), ("e_time", P), ("e_cnt", P), ("rows_cap", u64),
+                ("nnz_cap", u64), ("rows", u64), ("nnz", u64)]
+
+
+class CsrOut(C.Structure):
+    _fields_ = [("mem_kind", u32), ("reserved", u32), ("off", P), ("ctx", P), ("time", P),
+                ("cnt", P), ("nnz_cap", u64), ("nnz", u64)]
+
+
+class TensorView(C.Structure):
+    _fields_ = [("n_iter", P), ("row_off_of_rank", P), ("entry_off", P), ("e_ctx", P),
+                ("e_time", P), ("e_cnt", P), ("span", P), ("rows", u64), ("nnz", u64)]
+
+
+class CsrView(C.Structure):
+    _fields_ = [("off", P), ("ctx", P), ("time", P), ("cnt", P), ("nnz", u64)]
+
+
+class StatsArgs(C.Structure):
+    _fields_ = [("metric", u32), ("mem_kind", u32), ("ranks", P), ("n_ranks_subset", u32),
+                ("n_ctxs", u32), ("ctxs", P), ("tau_num", u32), ("tau_den", u32)]
+
+
+class CtxStats(C.Structure):
+    _fields_ = [("n", u32), ("present", u32), ("argmax", u32), ("reserved", u32), ("min", u64),
+                ("max", u64), ("s1", u64), ("s2_lo", u64), ("s2_hi", u64), ("mean", C.c_double),
+                ("std", C.c_double), ("cv", C.c_double), ("balance", C.c_double)]
+
+
+class Outlier(C.Structure):
+    _fields_ = [("ctx", u32), ("rank", u32), ("z", C.c_double)]
+
+
+class StatsOut(C.Structure):
+    _fields_ = [("stats", P), ("outliers", P), ("outlier_cap", u64), ("n_outliers", u64),
+                ("z", P)]
+
+
+class Topology(C.Structure):
+    _fields_ = [("n_nodes", u32), ("n_chassis", u32), ("n_racks", u32), ("mem_kind", u32),
+                ("node_of_rank", P), ("rack_of_node", P), ("chassis_of_node", P)]
+
+
+class TopoArgs(C.Structure):
+    _fields_ = [("metric", u32), ("ctx", u32), ("tau_num", u32), ("tau_den", u32),
+                ("min_ranks", u32), ("n_ranks_subset", u32), ("ranks", P)]
+
+
+class TopoOut(C.Structure):
+    _fields_ = [("mem_kind", u32), ("n_flagged_racks", u32), ("node_outliers", P),
+                ("node_sum", P), ("node_ranks", P), ("node_flag", P), ("chassis_flagged", P),
+                ("chassis_nodes", P), ("chassis_sum", P), ("rack_flagged", P),
+                ("rack_nodes", P), ("rack_sum", P), ("flagged_racks", P)]
+
+
+class SpeedupArgs(C.Structure):
+    _fields_ = [("mem_kind", u32), ("n_ctxs", u32), ("ctxs", P), ("ranks", P),
+                ("n_ranks_subset", u32), ("reserved", u32), ("app_time_ns", u64)]
+
+
+class SpeedupCtx(C.Structure):
+    _fields_ = [("A", u64), ("B", u64), ("G_lo", u64), ("G_hi", u64), ("avg_mean", C.c_double),
+                ("avg_max", C.c_double), ("savings_per_iter", C.c_double),
+                ("total_reduction", C.c_double), ("share", C.c_double),
+                ("cv_across", C.c_double), ("cv_within", C.c_double)]
+
+
+class SpeedupTotal(C.Structure):
+    _fields_ = [("i_star", u32), ("reserved", u32), ("excluded_iterations", u64),
+                ("sum_G_lo", u64), ("sum_G_hi", u64), ("t_app", u64),
+                ("total_reduction", C.c_double), ("speedup_fraction", C.c_double)]
+
+
+class SpeedupOut(C.Structure):
+    _fields_ = [("per_ctx", P), ("total", P)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_SIGS = {
+    "ta_create": (C.c_int, [C.c_int, P, C.POINTER(P)]),
+    "ta_destroy": (C.c_int, [P]),
+    "ta_set_allocator": (C.c_int, [P, ALLOC_FN, FREE_FN, P]),
+    "ta_sync": (C.c_int, [P]),
+    "ta_last_error_message": (C.c_char_p, []),
+    "ta_status_string": (C.c_char_p, [C.c_int]),
+    "ta_kernel_launches": (u64, [P]),
+    "ta_load_traces": (C.c_int, [P, C.POINTER(TraceDesc), C.POINTER(P)]),
+    "ta_experiment_free": (C.c_int, [P]),
+    "ta_experiment_get_info": (C.c_int, [P, C.POINTER(ExperimentInfo)]),
+    "ta_iteration_tensor": (C.c_int, [P, C.POINTER(TensorOut)]),
+    "ta_exclusive": (C.c_int, [P, C.POINTER(CsrOut)]),
+    "ta_inclusive_rollup": (C.c_int, [P, C.POINTER(CsrOut)]),
+    "ta_tensor_get_view": (C.c_int, [P, C.POINTER(TensorView)]),
+    "ta_csr_get_view": (C.c_int, [P, u32, C.POINTER(CsrView)]),
+    "ta_context_stats": (C.c_int, [P, C.POINTER(StatsArgs), C.POINTER(StatsOut)]),
+    "ta_topology_rollup": (C.c_int, [P, C.POINTER(Topology), C.POINTER(TopoArgs),
+                                     C.POINTER(TopoOut)]),
+    "ta_potential_speedup": (C.c_int, [P, C.POINTER(SpeedupArgs), C.POINTER(SpeedupOut)]),
+}
+
+_lib = None
+
+
+def declared_symbols():
+    """Names of the functions include/ta.h declares."""
+    with open(HEADER) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:ta_status|const char\*|uint64_t)\s+(ta_\w+)\s*\(",
+                                 text, re.M)))
+
+
+def lib():
+    """Load libta.so (building it first if needed); raises if unavailable."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            from . import build as _b
+            _b.build()
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class _CudaArray:
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, True),
+                                             version=3, strides=None)
+
+
+def device_array(ptr, n, dtype, device=0):
+    """Zero-copy torch view of n elements of library-owned device memory
+    (64-bit unsigned values are viewed as int64; reinterpret on the host)."""
+    torch = _torch()
+    typestr = {np.uint64: "<i8", np.uint32: "<i4", np.float64: "<f8"}[dtype]
+    return torch.as_tensor(_CudaArray(int(ptr), int(n), typestr), device=f"cuda:{device}")
+
+
+class TaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(s):
+    if s != OK:
+        raise TaError(s, lib().ta_last_error_message().decode())
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_dev(a):
+    return a is not None and not isinstance(a, np.ndarray) and a.is_cuda
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Context:
+    """A library context bound to a CUDA device and a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        torch = _torch()
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = P()
+        _check(lib().ta_create(device, self.stream.cuda_stream, C.byref(h)))
+        self.h = h
+        self._cb = None
+        if use_torch_allocator:
+            dev = device
+
+            def _alloc(n, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(n), dev, stream)
+                except Exception:
+                    return None
+
+            def _free(p, n, stream, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+            _check(lib().ta_set_allocator(self.h, self._cb[0], self._cb[1], None))
+
+    def launches(self) -> int:
+        return int(lib().ta_kernel_launches(self.h))
+
+    def sync(self):
+        _check(lib().ta_sync(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ta_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, rank_off, ts, ctx, parent, marker: int, borrow: bool = False,
+             inclusive: bool = True, nnz_hint: int = 0, rows_hint: int = 0) -> "Experiment":
+        return Experiment(self, rank_off, ts, ctx, parent, marker, borrow, inclusive, nnz_hint,
+                          rows_hint)
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Experiment:
+    """Resident analysis products of one trace set (see ta_load_traces)."""
+
+    def __init__(self, ctx: Context, rank_off, ts, cx, parent, marker, borrow=False,
+                 inclusive=True, nnz_hint=0, rows_hint=0):
+        self.ctx = ctx
+        dev = _is_dev(ts) or _is_dev(rank_off)
+        if dev:
+            torch = _torch()
+            rank_off = rank_off.contiguous()
+            ts, cx, parent = ts.contiguous(), cx.contiguous(), parent.contiguous()
+            assert rank_off.dtype == torch.uint64 and ts.dtype == torch.uint64
+            assert cx.dtype == torch.uint32 and parent.dtype == torch.uint32
+        else:
+            rank_off, ts, cx = _np(rank_off, np.uint64), _np(ts, np.uint64), _np(cx, np.uint32)
+            parent = _np(parent, np.uint32)
+        self._keep = (rank_off, ts, cx, parent) if borrow else None
+        d = TraceDesc()
+        d.n_ranks = rank_off.shape[0] - 1
+        d.n_ctx = parent.shape[0]
+        d.marker_ctx = int(marker)
+        d.mem_kind = MEM_DEVICE if dev else MEM_HOST
+        d.n_records = ts.shape[0]
+        d.rank_off, d.ts, d.ctx, d.parent = _ptr(rank_off), _ptr(ts), _ptr(cx), _ptr(parent)
+        d.flags = (LOAD_BORROW if borrow else 0) | (0 if inclusive else LOAD_NO_INCLUSIVE)
+        d.nnz_hint, d.rows_hint = nnz_hint, rows_hint
+        h = P()
+        _check(lib().ta_load_traces(ctx.h, C.byref(d), C.byref(h)))
+        self.h = h
+        self.R = int(d.n_ranks)
+        self.C = int(d.n_ctx)
+        self.has_incl = inclusive
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().ta_experiment_free(self.h)
+            self.h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = ExperimentInfo()
+        _check(lib().ta_experiment_get_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in ExperimentInfo._fields_}
+
+    # ---- products copied to host (numpy) or device (torch) -----------------
+    def _alloc(self, n, dtype, device):
+        if device:
+            torch = _torch()
+            tdt = {np.uint32: torch.uint32, np.uint64: torch.uint64, np.float64: torch.float64,
+                   np.uint8: torch.uint8}[dtype]
+            return torch.empty(max(n, 1), dtype=tdt, device=f"cuda:{self.ctx.device}")[:n]
+        return np.empty(n, dtype)
+
+    def tensor(self, device: bool = False) -> dict:
+        o = TensorOut()
+        _check(lib().ta_iteration_tensor(self.h, C.byref(o)))
+        rows, nnz = int(o.rows), int(o.nnz)
+        out = dict(n_iter=self._alloc(self.R, np.uint32, device),
+                   row_off_of_rank=self._alloc(self.R + 1, np.uint64, device),
+                   entry_off=self._alloc(rows + 1, np.uint64, device),
+                   e_ctx=self._alloc(nnz, np.uint32, device),
+                   e_time=self._alloc(nnz, np.uint64, device),
+                   e_cnt=self._alloc(nnz, np.uint32, device))
+        o = TensorOut()
+        o.mem_kind = MEM_DEVICE if device else MEM_HOST
+        for k, v in out.items():
+            setattr(o, k, _ptr(v))
+        o.rows_cap, o.nnz_cap = rows + 1, nnz
+        _check(lib().ta_iteration_tensor(self.h, C.byref(o)))
+        return out
+
+    def csr(self, metric=EXCLUSIVE, device: bool = False) -> dict:
+        fn = lib().ta_exclusive if metric == EXCLUSIVE else lib().ta_inclusive_rollup
+        o = CsrOut()
+        _check(fn(self.h, C.byref(o)))
+        nnz = int(o.nnz)
+        out = dict(off=self._alloc(self.R + 1, np.uint64, device),
+                   ctx=self._alloc(nnz, np.uint32, device),
+                   time=self._alloc(nnz, np.uint64, device), cnt=self._alloc(nnz, np.uint32, device))
+        o = CsrOut()
+        o.mem_kind = MEM_DEVICE if device else MEM_HOST
+        o.off, o.ctx, o.time, o.cnt = (_ptr(out[k]) for k in ("off", "ctx", "time", "cnt"))
+        o.nnz_cap = nnz
+        _check(fn(self.h, C.byref(o)))
+        return out
+
+    def tensor_view(self) -> TensorView:
+        v = TensorView()
+        _check(lib().ta_tensor_get_view(self.h, C.byref(v)))
+        return v
+
+    def span(self) -> np.ndarray:
+        """Per-rank span (ts_last - ts_first), read through the tensor view."""
+        v = self.tensor_view()
+        return device_array(v.span, self.R, np.uint64, self.ctx.device).cpu().numpy().view(np.uint64)
+
+    def stats(self, metric=EXCLUSIVE, ranks=None, ctxs=None, tau=(3, 1), outlier_cap=1 << 20,
+              want_z=False, device=False):
+        torch = _torch() if device else None
+        k = self.C if ctxs is None else len(ctxs)
+        a = StatsArgs()
+        a.metric, a.mem_kind = metric, MEM_DEVICE if device else MEM_HOST
+        if device:
+            rk = None if ranks is None else torch.as_tensor(np.asarray(ranks, np.uint32)).cuda()
+            cx = None if ctxs is None else torch.as_tensor(np.asarray(ctxs, np.uint32)).cuda()
+        else:
+            rk = None if ranks is None else _np(ranks, np.uint32)
+            cx = None if ctxs is None else _np(ctxs, np.uint32)
+        a.ranks, a.n_ranks_subset = _ptr(rk), 0 if ranks is None else len(ranks)
+        a.ctxs, a.n_ctxs = _ptr(cx), 0 if ctxs is None else len(ctxs)
+        a.tau_num, a.tau_den = tau
+        st = (CtxStats * max(k, 1))()
+        outl = (Outlier * max(outlier_cap, 1))()
+        nnz = 0
+        if want_z:
+            v = CsrView()
+            _check(lib().ta_csr_get_view(self.h, metric, C.byref(v)))
+            nnz = int(v.nnz)
+        z = np.zeros(max(nnz, 1), np.float64) if want_z else None
+        o = StatsOut()
+        if device:
+            dst = torch.empty(max(k, 1) * C.sizeof(CtxStats), dtype=torch.uint8, device="cuda")
+            dout = torch.empty(max(outlier_cap, 1) * C.sizeof(Outlier), dtype=torch.uint8,
+                               device="cuda")
+            dz = torch.zeros(max(nnz, 1), dtype=torch.float64, device="cuda") if want_z else None
+            o.stats, o.outliers, o.z = dst.data_ptr(), dout.data_ptr(), _ptr(dz)
+        else:
+            o.stats, o.outliers, o.z = C.addressof(st), C.addressof(outl), _ptr(z)
+        o.outlier_cap = outlier_cap
+        s = lib().ta_context_stats(self.h, C.byref(a), C.byref(o))
+        n_out = int(o.n_outliers)
+        if s not in (OK, CAPACITY):
+            _check(s)
+        if device:
+            C.memmove(st, dst.cpu().numpy().ctypes.data, max(k, 1) * C.sizeof(CtxStats))
+            C.memmove(outl, dout.cpu().numpy().ctypes.data, max(outlier_cap, 1) * C.sizeof(Outlier))
+            if want_z:
+                z = dz.cpu().numpy()
+        stats = {f: np.array([getattr(x, f) for x in st[:k]]) for f, _ in CtxStats._fields_
+                 if f != "reserved"}
+        m = min(n_out, outlier_cap) if s == OK else 0
+        outliers = dict(ctx=np.array([x.ctx for x in outl[:m]], np.uint32),
+                        rank=np.array([x.rank for x in outl[:m]], np.uint32),
+                        z=np.array([x.z for x in outl[:m]], np.float64))
+        if s == CAPACITY:
+            raise TaError(s, f"{n_out} outliers exceed capacity {outlier_cap}")
+        return stats, outliers, n_out, (z[:nnz] if want_z else None)
+
+    def topology(self, ctx, node_of_rank, rack_of_node, chassis_of_node, n_racks, n_chassis,
+                 metric=EXCLUSIVE, tau=(3, 1), min_ranks=1, ranks=None):
+        nn = len(rack_of_node)
+        t = Topology()
+        t.n_nodes, t.n_chassis, t.n_racks, t.mem_kind = nn, n_chassis, n_racks, MEM_HOST
+        arrs = [_np(node_of_rank, np.uint32), _np(rack_of_node, np.uint32),
+                _np(chassis_of_node, np.uint32)]
+        t.node_of_rank, t.rack_of_node, t.chassis_of_node = (_ptr(x) for x in arrs)
+        a = TopoArgs()
+        a.metric, a.ctx, a.tau_num, a.tau_den, a.min_ranks = metric, ctx, tau[0], tau[1], min_ranks
+        rk = None if ranks is None else _np(ranks, np.uint32)
+        a.ranks, a.n_ranks_subset = _ptr(rk), 0 if ranks is None else len(ranks)
+        out = dict(node_outliers=np.zeros(nn, np.uint32), node_sum=np.zeros(nn, np.uint64),
+                   node_ranks=np.zeros(nn, np.uint32), node_flag=np.zeros(nn, np.uint8),
+                   chassis_flagged=np.zeros(n_chassis, np.uint32),
+                   chassis_nodes=np.zeros(n_chassis, np.uint32),
+                   chassis_sum=np.zeros(n_chassis, np.uint64),
+                   rack_flagged=np.zeros(n_racks, np.uint32), rack_nodes=np.zeros(n_racks, np.uint32),
+                   rack_sum=np.zeros(n_racks, np.uint64), flagged_racks=np.zeros(n_racks, np.uint32))
+        o = TopoOut()
+        o.mem_kind = MEM_HOST
+        for k, v in out.items():
+            setattr(o, k, _ptr(v))
+        _check(lib().ta_topology_rollup(self.h, C.byref(t), C.byref(a), C.byref(o)))
+        out["flagged_racks"] = out["flagged_racks"][: int(o.n_flagged_racks)]
+        return out
+
+    def speedup(self, ctxs, ranks=None, app_time_ns=0):
+        cx = _np(ctxs, np.uint32)
+        rk = None if ranks is None else _np(ranks, np.uint32)
+        a = SpeedupArgs()
+        a.mem_kind, a.n_ctxs, a.ctxs = MEM_HOST, len(cx), _ptr(cx)
+        a.ranks, a.n_ranks_subset = _ptr(rk), 0 if ranks is None else len(ranks)
+        a.app_time_ns = app_time_ns
+        per = (SpeedupCtx * len(cx))()
+        tot = SpeedupTotal()
+        o = SpeedupOut()
+        o.per_ctx, o.total = C.addressof(per), C.addressof(tot)
+        _check(lib().ta_potential_speedup(self.h, C.byref(a), C.byref(o)))
+        d = {f: np.array([getattr(x, f) for x in per]) for f, _ in SpeedupCtx._fields_}
+        d["G"] = [int(lo) + (int(hi) << 64) for lo, hi in zip(d["G_lo"], d["G_hi"])]
+        t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
+        t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
+        return d, t

@@ -1,0 +1,559 @@
+// api.cu -- host implementation of the C ABI declared in include/ta.h:
+// contexts, device memory, ingestion orchestration, output copies and views.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ta.h"
+#include "ta_api_internal.h"
+
+using namespace ta;
+
+namespace {
+thread_local std::string g_err = "no error";
+}
+
+ta_status ta::fail(ta_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = std::string(ta_status_string(s)) + ": " + buf;
+  return s;
+}
+
+ta_status ta::cuda_fail(cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(TA_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ memory -----
+void* ta::dalloc(ta_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, (void*)c->stream, c->user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void ta::dfree(ta_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (c->free_fn) c->free_fn(p, bytes, (void*)c->stream, c->user);
+  else cudaFreeAsync(p, c->stream);
+}
+
+ta_status Pool::get(size_t bytes, void** out, const char* what) {
+  void* p = dalloc(ctx, bytes);
+  if (!p) return fail(TA_ERR_OOM, "device allocation of %zu bytes for %s failed", bytes, what);
+  items.push_back({p, bytes});
+  *out = p;
+  return TA_OK;
+}
+
+void Pool::release() {
+  for (auto& it : items) dfree(ctx, it.p, it.n);
+  items.clear();
+}
+
+ta_status ta::sync_check(ta_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return TA_OK;
+}
+
+ta_status ta::copy(ta_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (bytes == 0) return TA_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+  return TA_OK;
+}
+
+// Map device status bits to the first error in the documented order.
+ta_status ta::status_from_flags(u32 f, const char* where) {
+  if (f & F_INVALID) return fail(TA_ERR_INVALID_ARG, "%s: invalid argument", where);
+  if (f & F_BAD_CCT) return fail(TA_ERR_BAD_CCT, "%s: invalid calling context tree", where);
+  if (f & F_BAD_CTX) return fail(TA_ERR_BAD_CTX, "%s: context id >= n_ctx", where);
+  if (f & F_NOT_SORTED) return fail(TA_ERR_NOT_SORTED, "%s: timestamps decrease within a rank", where);
+  if (f & F_TIMEOUT) return fail(TA_ERR_TIMEOUT, "%s: device wait gave up", where);
+  if (f & F_INTERNAL) return fail(TA_ERR_CUDA, "%s: internal staging overflow", where);
+  return TA_OK;
+}
+
+// ------------------------------------------------------------ context ----
+extern "C" {
+
+const char* ta_status_string(ta_status s) {
+  switch (s) {
+    case TA_OK: return "TA_OK";
+    case TA_ERR_INVALID_ARG: return "TA_ERR_INVALID_ARG";
+    case TA_ERR_NOT_SORTED: return "TA_ERR_NOT_SORTED";
+    case TA_ERR_BAD_CTX: return "TA_ERR_BAD_CTX";
+    case TA_ERR_BAD_CCT: return "TA_ERR_BAD_CCT";
+    case TA_ERR_OOM: return "TA_ERR_OOM";
+    case TA_ERR_CAPACITY: return "TA_ERR_CAPACITY";
+    case TA_ERR_TIMEOUT: return "TA_ERR_TIMEOUT";
+    case TA_ERR_CUDA: return "TA_ERR_CUDA";
+    case TA_ERR_STATE: return "TA_ERR_STATE";
+  }
+  return "TA_ERR_UNKNOWN";
+}
+
+const char* ta_last_error_message(void) { return g_err.c_str(); }
+
+ta_status ta_create(int device, void* stream, ta_ctx** out) {
+  if (!out) return fail(TA_ERR_INVALID_ARG, "ta_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(TA_ERR_INVALID_ARG, "ta_create: no device %d", device);
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  ta_ctx* c = new ta_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return TA_OK;
+}
+
+ta_status ta_destroy(ta_ctx* c) {
+  if (!c) return TA_OK;
+  cudaStreamSynchronize(c->stream);
+  delete c;
+  return TA_OK;
+}
+
+ta_status ta_set_allocator(ta_ctx* c, ta_alloc_fn a, ta_free_fn f, void* user) {
+  if (!c) return fail(TA_ERR_INVALID_ARG, "ta_set_allocator: ctx is NULL");
+  if ((a == nullptr) != (f == nullptr))
+    return fail(TA_ERR_INVALID_ARG, "ta_set_allocator: give both callbacks or neither");
+  c->alloc = a;
+  c->free_fn = f;
+  c->user = user;
+  return TA_OK;
+}
+
+ta_status ta_sync(ta_ctx* c) {
+  if (!c) return fail(TA_ERR_INVALID_ARG, "ta_sync: ctx is NULL");
+  return sync_check(c, "ta_sync");
+}
+
+uint64_t ta_kernel_launches(const ta_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"
+
+// --------------------------------------------------------- experiment ----
+void ta_experiment::drop() {
+  for (auto& b : owned) dfree(ctx, b.p, b.n);
+  owned.clear();
+}
+
+ta_status ta_experiment::own(size_t bytes, void** out, const char* what) {
+  void* p = dalloc(ctx, bytes);
+  if (!p) return fail(TA_ERR_OOM, "device allocation of %zu bytes for %s failed", bytes, what);
+  owned.push_back({p, bytes});
+  device_bytes += bytes;
+  *out = p;
+  return TA_OK;
+}
+
+void ta_experiment::disown(void* p) {
+  for (size_t i = 0; i < owned.size(); ++i)
+    if (owned[i].p == p) {
+      dfree(ctx, p, owned[i].n);
+      device_bytes -= owned[i].n;
+      owned.erase(owned.begin() + i);
+      return;
+    }
+}
+
+#define TRY(x)                        \
+  do {                                \
+    ta_status _s = (x);               \
+    if (_s != TA_OK) return _s;       \
+  } while (0)
+
+namespace {
+
+// Tensor pass with exact-capacity retry.
+ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
+  const u64 N = e->N;
+  const u32 R = e->R;
+  TensorPlan P = plan_tensor(e->C, N, c->num_sms);
+  const u32 n_tiles = (u32)std::max<u64>(1, (N + P.tile - 1) / P.tile);
+  u32* tfr;
+  TRY(tmp.get((n_tiles + 1) * sizeof(u32), (void**)&tfr, "tile map"));
+  launch_tile_first_rank(L, e->rank_off, R, P.tile, n_tiles, tfr);
+  UnitStatus* ustat;
+  TRY(tmp.get((size_t)n_tiles * sizeof(UnitStatus), (void**)&ustat, "tile status"));
+  u64* meta;  // [0] counter|status, [1..2] totals
+  TRY(tmp.get(64, (void**)&meta, "tensor meta"));
+  u32* gbm = nullptr;
+  const u32 W = P.threads / 32;
+  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.grid * W * bm_words(e->C) * 4;
+  if (gbm_bytes) TRY(tmp.get(gbm_bytes, (void**)&gbm, "tensor bitmaps"));
+  u32 *gctx, *gcnt;
+  u64* gtime;
+  const size_t gn = (size_t)P.grid * P.gst_cap;
+  TRY(tmp.get(gn * 4, (void**)&gctx, "tensor stage"));
+  TRY(tmp.get(gn * 4, (void**)&gcnt, "tensor stage"));
+  TRY(tmp.get(gn * 8, (void**)&gtime, "tensor stage"));
+
+  const bool small = N <= (1u << 20);
+  u64 rows_cap = d->rows_hint ? d->rows_hint : (u64)R + (small ? N : N / 8) + 2;
+  u64 nnz_cap = d->nnz_hint ? d->nnz_hint : (small ? N : N / 2) + 16;
+  TRY(e->own(((u64)R + 1) * 8, (void**)&e->row_off, "row_off_of_rank"));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    TRY(e->own((rows_cap) * 8, (void**)&e->entry_off, "entry_off"));
+    TRY(e->own(nnz_cap * 4, (void**)&e->e_ctx, "e_ctx"));
+    TRY(e->own(nnz_cap * 8, (void**)&e->e_time, "e_time"));
+    TRY(e->own(nnz_cap * 4, (void**)&e->e_cnt, "e_cnt"));
+    cudaMemsetAsync(ustat, 0, (size_t)n_tiles * sizeof(UnitStatus), c->stream);
+    cudaMemsetAsync(meta, 0, 64, c->stream);
+    if (gbm) cudaMemsetAsync(gbm, 0, gbm_bytes, c->stream);
+    TensorArgs A;
+    A.rank_off = e->rank_off;
+    A.ts = e->ts;
+    A.ctx = e->ctxv;
+    A.R = R;
+    A.C = e->C;
+    A.m = e->m;
+    A.n_tiles = n_tiles;
+    A.N = N;
+    A.tfr = tfr;
+    A.unit_counter = (u32*)meta;
+    A.status = (u32*)meta + 1;
+    A.totals = meta + 1;
+    A.ustat = ustat;
+    A.row_off_of_rank = e->row_off;
+    A.entry_off = e->entry_off;
+    A.e_ctx = e->e_ctx;
+    A.e_time = e->e_time;
+    A.e_cnt = e->e_cnt;
+    A.rows_cap = rows_cap;
+    A.nnz_cap = nnz_cap;
+    A.gbm = gbm;
+    A.gst_ctx = gctx;
+    A.gst_time = gtime;
+    A.gst_cnt = gcnt;
+    A.gst_cap = P.gst_cap;
+    A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+    launch_tensor(L, P, A);
+    u64 h[3];
+    TRY(copy(c, h, meta, sizeof h));
+    TRY(sync_check(c, "iteration tensor"));
+    const u32 f = (u32)(h[0] >> 32);
+    TRY(status_from_flags(f, "ta_load_traces"));
+    e->rows = h[1];
+    e->nnz = h[2];
+    if (!(f & F_CAPACITY)) return TA_OK;
+    // Too small a first guess: free and retry with the exact sizes.
+    e->disown(e->entry_off);
+    e->disown(e->e_ctx);
+    e->disown(e->e_time);
+    e->disown(e->e_cnt);
+    rows_cap = e->rows + 1;
+    nnz_cap = std::max<u64>(e->nnz, 1);
+  }
+  return fail(TA_ERR_CUDA, "iteration tensor: capacity retry failed");
+}
+
+// Exclusive (mode 0) or inclusive (mode 1) per-rank CSR with retry.
+ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
+  const u32 R = e->R;
+  RankCsrPlan P = plan_rank_csr(R, e->C, c->num_sms);
+  UnitStatus* ustat;
+  TRY(tmp.get((size_t)P.n_units * sizeof(UnitStatus), (void**)&ustat, "unit status"));
+  u64* meta;
+  TRY(tmp.get(64, (void**)&meta, "csr meta"));
+  u32* gbm = nullptr;
+  const size_t gbm_bytes =
+      P.bm_in_smem ? 0 : (size_t)P.grid * (P.threads / 32) * bm_words(e->C) * 4;
+  if (gbm_bytes) TRY(tmp.get(gbm_bytes, (void**)&gbm, "csr bitmaps"));
+  u32 *gctx, *gcnt;
+  u64* gtime;
+  const size_t gn = (size_t)P.grid * P.gst_cap;
+  TRY(tmp.get(gn * 4, (void**)&gctx, "csr stage"));
+  TRY(tmp.get(gn * 4, (void**)&gcnt, "csr stage"));
+  TRY(tmp.get(gn * 8, (void**)&gtime, "csr stage"));
+  u64 cap;
+  if (mode == 0) cap = std::min<u64>(e->nnz, (u64)R * 160 + 4096);
+  else cap = std::min<u64>((u64)R * e->C, 3 * e->x.nnz + (u64)R * 64 + 4096);
+  cap = std::max<u64>(cap, 1);
+  Csr& out = mode == 0 ? e->x : e->in;
+  TRY(e->own(((u64)R + 1) * 8, (void**)&out.off, "csr off"));
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    TRY(e->own(cap * 4, (void**)&out.ctx, "csr ctx"));
+    TRY(e->own(cap * 8, (void**)&out.time, "csr time"));
+    TRY(e->own(cap * 4, (void**)&out.cnt, "csr cnt"));
+    cudaMemsetAsync(ustat, 0, (size_t)P.n_units * sizeof(UnitStatus), c->stream);
+    cudaMemsetAsync(meta, 0, 64, c->stream);
+    if (gbm) cudaMemsetAsync(gbm, 0, gbm_bytes, c->stream);
+    RankCsrArgs A;
+    std::memset(&A, 0, sizeof A);
+    A.mode = (u32)mode;
+    A.R = R;
+    A.C = e->C;
+    A.max_depth = e->max_depth;
+    A.row_off_of_rank = e->row_off;
+    A.entry_off = e->entry_off;
+    if (mode == 0) {
+      A.in_ctx = e->e_ctx;
+      A.in_time = e->e_time;
+      A.in_cnt = e->e_cnt;
+    } else {
+      A.in_off = e->x.off;
+      A.in_ctx = e->x.ctx;
+      A.in_time = e->x.time;
+      A.in_cnt = e->x.cnt;
+    }
+    A.parent = e->parent;
+    A.depth = e->depth;
+    A.unit_counter = (u32*)meta;
+    A.status = (u32*)meta + 1;
+    A.total = meta + 1;
+    A.ustat = ustat;
+    A.out_off = out.off;
+    A.out_ctx = out.ctx;
+    A.out_time = out.time;
+    A.out_cnt = out.cnt;
+    A.nnz_cap = cap;
+    A.gbm = gbm;
+    A.gst_ctx = gctx;
+    A.gst_time = gtime;
+    A.gst_cnt = gcnt;
+    A.gst_cap = P.gst_cap;
+    A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+    launch_rank_csr(L, P, A);
+    u64 h[2];
+    TRY(copy(c, h, meta, sizeof h));
+    TRY(sync_check(c, mode == 0 ? "exclusive" : "inclusive"));
+    const u32 f = (u32)(h[0] >> 32);
+    TRY(status_from_flags(f, mode == 0 ? "exclusive" : "inclusive"));
+    out.nnz = h[1];
+    if (!(f & F_CAPACITY)) return TA_OK;
+    e->disown(out.ctx);
+    e->disown(out.time);
+    e->disown(out.cnt);
+    cap = std::max<u64>(out.nnz, 1);
+  }
+  return fail(TA_ERR_CUDA, "per-rank CSR: capacity retry failed");
+}
+
+ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& tmp) {
+  Launch L{c->stream, c->num_sms, &c->launches};
+  const u32 R = d->n_ranks, C = d->n_ctx;
+  const u64 N = d->n_records;
+  const bool dev = d->mem_kind == TA_MEM_DEVICE;
+  TRY(e->own(((u64)R + 1) * 8, (void**)&e->rank_off, "rank_off"));
+  TRY(copy(c, e->rank_off, d->rank_off, ((u64)R + 1) * 8));
+  TRY(e->own((u64)C * 4, (void**)&e->parent, "parent"));
+  TRY(copy(c, e->parent, d->parent, (u64)C * 4));
+  if (dev && (d->flags & TA_LOAD_BORROW)) {
+    e->ts = d->ts;
+    e->ctxv = d->ctx;
+  } else {
+    u64* ts;
+    u32* cx;
+    TRY(e->own(N * 8, (void**)&ts, "ts"));
+    TRY(e->own(N * 4, (void**)&cx, "ctx"));
+    TRY(copy(c, ts, d->ts, N * 8));
+    TRY(copy(c, cx, d->ctx, N * 4));
+    e->ts = ts;
+    e->ctxv = cx;
+    e->owns_traces = true;
+  }
+  TRY(e->own((u64)R * 8, (void**)&e->span, "span"));
+  TRY(e->own((u64)C * 4, (void**)&e->depth, "depth"));
+  TRY(e->own((u64)R * 4 + 4, (void**)&e->n_iter, "n_iter"));
+  u64* meta;  // [0] status|pad, [1] max_span, [2] roots|max_depth
+  TRY(tmp.get(64, (void**)&meta, "load meta"));
+  u32* scratch;
+  TRY(tmp.get((u64)C * 16, (void**)&scratch, "tree scratch"));
+  cudaMemsetAsync(meta, 0, 64, c->stream);
+  u32* status = (u32*)meta;
+  launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status);
+  launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status);
+  u64 h[3];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, "validation"));
+  const u32 f = (u32)h[0];
+  if (f & F_INVALID) return fail(TA_ERR_INVALID_ARG, "rank offsets are not a valid CSR of n_records samples "
+                                                     "(rank_off[0] = 0, non-decreasing, rank_off[R] = N, < 2^32 per rank)");
+  const u32 roots = (u32)h[2], maxd = (u32)(h[2] >> 32);
+  if ((f & F_BAD_CCT) || roots != 1)
+    return fail(TA_ERR_BAD_CCT, "parent array: %u roots, parents in range: %s, acyclic: %s", roots,
+                (f & F_BAD_CCT) ? "no or cycle" : "yes", (f & F_BAD_CCT) ? "?" : "yes");
+  if ((unsigned __int128)h[1] * R >= ((unsigned __int128)1 << 63))
+    return fail(TA_ERR_INVALID_ARG, "R * longest rank span = %u * %llu >= 2^63 (exact moments)", R,
+                (unsigned long long)h[1]);
+  e->max_depth = maxd;
+  e->max_span = h[1];
+  TRY(build_tensor(e, d, tmp));
+  launch_n_iter(L, e->row_off, R, e->n_iter);
+  TRY(build_rank_csr(e, 0, tmp));
+  if (!(d->flags & TA_LOAD_NO_INCLUSIVE)) {
+    TRY(build_rank_csr(e, 1, tmp));
+    e->has_incl = true;
+  }
+  if (e->owns_traces) {  // raw traces are not needed after ingestion
+    e->disown((void*)e->ts);
+    e->disown((void*)e->ctxv);
+    e->ts = nullptr;
+    e->ctxv = nullptr;
+  }
+  return sync_check(c, "ta_load_traces");
+}
+
+}  // namespace
+
+extern "C" {
+
+ta_status ta_load_traces(ta_ctx* c, const ta_trace_desc* d, ta_experiment** out) {
+  if (!c || !d || !out) return fail(TA_ERR_INVALID_ARG, "ta_load_traces: NULL argument");
+  *out = nullptr;
+  if (d->n_ranks == 0) return fail(TA_ERR_INVALID_ARG, "n_ranks = 0");
+  if (d->n_ranks == 0xFFFFFFFFu) return fail(TA_ERR_INVALID_ARG, "n_ranks too large");
+  if (d->n_ctx == 0) return fail(TA_ERR_INVALID_ARG, "n_ctx = 0");
+  if (d->marker_ctx >= d->n_ctx) return fail(TA_ERR_INVALID_ARG, "marker_ctx >= n_ctx");
+  if (d->mem_kind != TA_MEM_HOST && d->mem_kind != TA_MEM_DEVICE)
+    return fail(TA_ERR_INVALID_ARG, "mem_kind");
+  if (!d->rank_off || !d->parent) return fail(TA_ERR_INVALID_ARG, "rank_off / parent NULL");
+  if (d->n_records > 0 && (!d->ts || !d->ctx)) return fail(TA_ERR_INVALID_ARG, "ts / ctx NULL");
+  if (d->n_ctx > 0x7FFFFFFFu) return fail(TA_ERR_INVALID_ARG, "n_ctx too large");
+  cudaSetDevice(c->device);
+  ta_experiment* e = new ta_experiment();
+  e->ctx = c;
+  e->R = d->n_ranks;
+  e->C = d->n_ctx;
+  e->m = d->marker_ctx;
+  e->N = d->n_records;
+  Pool tmp{c, {}};
+  ta_status s = load_impl(c, d, e, tmp);
+  cudaStreamSynchronize(c->stream);
+  tmp.release();
+  if (s != TA_OK) {
+    std::string keep = g_err;
+    e->drop();
+    cudaStreamSynchronize(c->stream);
+    delete e;
+    g_err = keep;
+    return s;
+  }
+  *out = e;
+  return TA_OK;
+}
+
+ta_status ta_experiment_free(ta_experiment* e) {
+  if (!e) return TA_OK;
+  cudaStreamSynchronize(e->ctx->stream);
+  e->drop();
+  cudaStreamSynchronize(e->ctx->stream);
+  delete e;
+  return TA_OK;
+}
+
+ta_status ta_experiment_get_info(const ta_experiment* e, ta_experiment_info* i) {
+  if (!e || !i) return fail(TA_ERR_INVALID_ARG, "ta_experiment_get_info: NULL argument");
+  i->n_ranks = e->R;
+  i->n_ctx = e->C;
+  i->marker_ctx = e->m;
+  i->max_depth = e->max_depth;
+  i->n_records = e->N;
+  i->n_rows = e->rows;
+  i->tensor_nnz = e->nnz;
+  i->excl_nnz = e->x.nnz;
+  i->incl_nnz = e->has_incl ? e->in.nnz : 0;
+  i->device_bytes = e->device_bytes;
+  return TA_OK;
+}
+
+ta_status ta_iteration_tensor(ta_experiment* e, ta_tensor_out* o) {
+  if (!e || !o) return fail(TA_ERR_INVALID_ARG, "ta_iteration_tensor: NULL argument");
+  ta_ctx* c = e->ctx;
+  o->rows = e->rows;
+  o->nnz = e->nnz;
+  if (o->entry_off && o->rows_cap < e->rows + 1)
+    return fail(TA_ERR_CAPACITY, "entry_off needs %llu elements", (unsigned long long)e->rows + 1);
+  if ((o->e_ctx || o->e_time || o->e_cnt) && o->nnz_cap < e->nnz)
+    return fail(TA_ERR_CAPACITY, "entries need %llu elements", (unsigned long long)e->nnz);
+  if (o->n_iter) TRY(copy(c, o->n_iter, e->n_iter, (u64)e->R * 4));
+  if (o->row_off_of_rank) TRY(copy(c, o->row_off_of_rank, e->row_off, ((u64)e->R + 1) * 8));
+  if (o->entry_off) TRY(copy(c, o->entry_off, e->entry_off, (e->rows + 1) * 8));
+  if (o->e_ctx) TRY(copy(c, o->e_ctx, e->e_ctx, e->nnz * 4));
+  if (o->e_time) TRY(copy(c, o->e_time, e->e_time, e->nnz * 8));
+  if (o->e_cnt) TRY(copy(c, o->e_cnt, e->e_cnt, e->nnz * 4));
+  return sync_check(c, "ta_iteration_tensor");
+}
+
+static ta_status csr_out(ta_experiment* e, const Csr& s, ta_csr_out* o, const char* what) {
+  ta_ctx* c = e->ctx;
+  o->nnz = s.nnz;
+  if ((o->ctx || o->time || o->cnt) && o->nnz_cap < s.nnz)
+    return fail(TA_ERR_CAPACITY, "%s needs %llu entries", what, (unsigned long long)s.nnz);
+  if (o->off) TRY(copy(c, o->off, s.off, ((u64)e->R + 1) * 8));
+  if (o->ctx) TRY(copy(c, o->ctx, s.ctx, s.nnz * 4));
+  if (o->time) TRY(copy(c, o->time, s.time, s.nnz * 8));
+  if (o->cnt) TRY(copy(c, o->cnt, s.cnt, s.nnz * 4));
+  return sync_check(c, what);
+}
+
+ta_status ta_exclusive(ta_experiment* e, ta_csr_out* o) {
+  if (!e || !o) return fail(TA_ERR_INVALID_ARG, "ta_exclusive: NULL argument");
+  return csr_out(e, e->x, o, "ta_exclusive");
+}
+
+ta_status ta_inclusive_rollup(ta_experiment* e, ta_csr_out* o) {
+  if (!e || !o) return fail(TA_ERR_INVALID_ARG, "ta_inclusive_rollup: NULL argument");
+  if (!e->has_incl) return fail(TA_ERR_STATE, "inclusive rollup was skipped at load");
+  return csr_out(e, e->in, o, "ta_inclusive_rollup");
+}
+
+ta_status ta_tensor_get_view(const ta_experiment* e, ta_tensor_view* v) {
+  if (!e || !v) return fail(TA_ERR_INVALID_ARG, "ta_tensor_get_view: NULL argument");
+  v->n_iter = e->n_iter;
+  v->row_off_of_rank = e->row_off;
+  v->entry_off = e->entry_off;
+  v->e_ctx = e->e_ctx;
+  v->e_time = e->e_time;
+  v->e_cnt = e->e_cnt;
+  v->span = e->span;
+  v->rows = e->rows;
+  v->nnz = e->nnz;
+  return TA_OK;
+}
+
+ta_status ta_csr_get_view(const ta_experiment* e, uint32_t metric, ta_csr_view* v) {
+  if (!e || !v) return fail(TA_ERR_INVALID_ARG, "ta_csr_get_view: NULL argument");
+  if (metric > 1) return fail(TA_ERR_INVALID_ARG, "metric");
+  if (metric == 1 && !e->has_incl) return fail(TA_ERR_STATE, "inclusive rollup was skipped at load");
+  const Csr& s = metric == 0 ? e->x : e->in;
+  v->off = s.off;
+  v->ctx = s.ctx;
+  v->time = s.time;
+  v->cnt = s.cnt;
+  v->nnz = s.nnz;
+  return TA_OK;
+}
+
+}  // extern "C"

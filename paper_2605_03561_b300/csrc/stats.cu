@@ -1,0 +1,907 @@
+// stats.cu -- cross-rank statistics, outliers, topology rollup and the
+// potential-speedup estimate (Sections VI-A and VI-B; Tables IV and V).
+//
+// Integer partials (present, min, max, sum, 128-bit sum of squares) are exact
+// and order-independent; the FP64 values are computed from them once, by the
+// same fixed sequence of correctly rounded operations for every context.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <type_traits>
+#include <vector>
+
+#include "ta.h"
+#include "ta_api_internal.h"
+
+using namespace ta;
+
+#define TRY(x)                  \
+  do {                          \
+    ta_status _s = (x);         \
+    if (_s != TA_OK) return _s; \
+  } while (0)
+
+namespace {
+
+__device__ __forceinline__ u32 rank_at(const u32* S, u32 i) { return S ? S[i] : i; }
+
+// sorted, unique, < limit
+__global__ void k_check_sorted(const u32* __restrict__ v, u32 n, u32 limit, u32* status) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (v[i] >= limit || (i > 0 && v[i] <= v[i - 1])) flag(status, F_INVALID);
+}
+
+// slot_of_ctx[ctxs[i]] = i (ctxs NULL: identity over C).
+__global__ void k_slot_map(const u32* __restrict__ ctxs, u32 n, u32 C, u32* slot_of_ctx) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ctxs) {
+    if (i < n && ctxs[i] < C) slot_of_ctx[ctxs[i]] = i;
+  } else if (i < C) {
+    slot_of_ctx[i] = i;
+  }
+}
+
+__global__ void k_fill_u64(u64* p, u64 n, u64 v) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+struct Partials {
+  u32* present;
+  u64* mn;
+  u64* mx;
+  u64* s1;
+  u64* s2lo;
+  u64* s2hi;
+  u32* argmax;
+  double* sd;
+  u64* Mlo;
+  u64* Mhi;
+};
+
+// Per-CTA hash table of context slots in shared memory, flushed to the
+// global partials once per CTA (low contention on popular contexts).
+constexpr int HCAP = 1024;
+constexpr int STATS_NT = 256;
+
+__global__ void __launch_bounds__(STATS_NT)
+    k_stats_partial(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
+                    const u32* __restrict__ ctx, const u64* __restrict__ time,
+                    const u32* __restrict__ slot_of_ctx, Partials P) {
+  __shared__ u32 hkey[HCAP];
+  __shared__ u32 hpres[HCAP];
+  __shared__ unsigned long long hmn[HCAP], hmx[HCAP], hs1[HCAP], hs2lo[HCAP], hs2hi[HCAP];
+  for (int h = threadIdx.x; h < HCAP; h += STATS_NT) {
+    hkey[h] = NONE32;
+    hpres[h] = 0;
+    hmn[h] = ~0ull;
+    hmx[h] = 0;
+    hs1[h] = 0;
+    hs2lo[h] = 0;
+    hs2hi[h] = 0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const u32 gw = (blockIdx.x * STATS_NT + threadIdx.x) >> 5;
+  const u32 nw = (gridDim.x * STATS_NT) >> 5;
+  for (u32 i = gw; i < n; i += nw) {
+    const u32 r = rank_at(S, i);
+    const u64 E0 = off[r], E1 = off[r + 1];
+    for (u64 j = E0 + lane; j < E1; j += 32) {
+      const u32 slot = slot_of_ctx[ctx[j]];
+      if (slot == NONE32) continue;
+      const u64 x = time[j];
+      const u128 x2 = (u128)x * x;
+      u32 h = (slot * 2654435761u) >> (32 - 10);
+      int found = -1;
+      for (int probe = 0; probe < 64; ++probe) {
+        const u32 k = hkey[h];
+        if (k == slot) {
+          found = (int)h;
+          break;
+        }
+        if (k == NONE32) {
+          const u32 old = atomicCAS(&hkey[h], NONE32, slot);
+          if (old == NONE32 || old == slot) {
+            found = (int)h;
+            break;
+          }
+        }
+        h = (h + 1) & (HCAP - 1);
+      }
+      if (found >= 0) {
+        atomicAdd(&hpres[found], 1u);
+        atomicMin(&hmn[found], (unsigned long long)x);
+        atomicMax(&hmx[found], (unsigned long long)x);
+        atomicAdd(&hs1[found], (unsigned long long)x);
+        atomic_add_u128((u64*)&hs2lo[found], (u64*)&hs2hi[found], x2);
+      } else {
+        atomicAdd(&P.present[slot], 1u);
+        atomicMin((unsigned long long*)&P.mn[slot], (unsigned long long)x);
+        atomicMax((unsigned long long*)&P.mx[slot], (unsigned long long)x);
+        atomicAdd((unsigned long long*)&P.s1[slot], (unsigned long long)x);
+        atomic_add_u128(&P.s2lo[slot], &P.s2hi[slot], x2);
+      }
+    }
+  }
+  __syncthreads();
+  for (int h = threadIdx.x; h < HCAP; h += STATS_NT) {
+    const u32 slot = hkey[h];
+    if (slot == NONE32) continue;
+    atomicAdd(&P.present[slot], hpres[h]);
+    atomicMin((unsigned long long*)&P.mn[slot], hmn[h]);
+    atomicMax((unsigned long long*)&P.mx[slot], hmx[h]);
+    atomicAdd((unsigned long long*)&P.s1[slot], hs1[h]);
+    atomic_add_u128(&P.s2lo[slot], &P.s2hi[slot], ((u128)hs2hi[h] << 64) | hs2lo[h]);
+  }
+}
+
+// Per slot: mean, std (ddof 1), cv, balance from the exact partials.
+__global__ void k_stats_finalize(u32 n_slots, u64 n, const u32* S, Partials P,
+                                 ta_ctx_stats* out) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const u32 present = P.present[s];
+  const u64 mx = P.mx[s], s1 = P.s1[s];
+  const u128 S2 = ((u128)P.s2hi[s] << 64) | P.s2lo[s];
+  const u128 M = (u128)n * S2 - (u128)s1 * s1;
+  const double mean = u64_to_f64(s1) / u64_to_f64(n);
+  const double sd = (n < 2) ? 0.0 : sqrt(u128_to_f64(M) / u64_to_f64(n * (n - 1)));
+  ta_ctx_stats st;
+  st.n = (u32)n;
+  st.present = present;
+  st.argmax = 0;
+  st.reserved = 0;
+  st.min = (present < n) ? 0ull : P.mn[s];
+  st.max = mx;
+  st.s1 = s1;
+  st.s2_lo = (u64)S2;
+  st.s2_hi = (u64)(S2 >> 64);
+  st.mean = mean;
+  st.std = sd;
+  st.cv = (mean == 0.0) ? 0.0 : sd / mean;
+  st.balance = (mx == 0) ? 1.0 : mean / u64_to_f64(mx);
+  out[s] = st;
+  P.sd[s] = sd;
+  P.Mlo[s] = (u64)M;
+  P.Mhi[s] = (u64)(M >> 64);
+  P.argmax[s] = (mx == 0) ? rank_at(S, 0) : NONE32;
+}
+
+// Argmax (lowest rank attaining max), z-scores and the exact outlier rule.
+__global__ void k_stats_z(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
+                          const u32* __restrict__ ctx, const u64* __restrict__ time,
+                          const u32* __restrict__ slot_of_ctx, Partials P, u32 tn, u32 td,
+                          double* z_out, u64* keys, double* zs, u64 cap,
+                          unsigned long long* n_out, uint8_t* rank_flag) {
+  const int lane = threadIdx.x & 31;
+  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  for (u32 i = gw; i < n; i += nw) {
+    const u32 r = rank_at(S, i);
+    const u64 E0 = off[r], E1 = off[r + 1];
+    for (u64 j = E0 + lane; j < E1; j += 32) {
+      const u32 c = ctx[j];
+      const u32 slot = slot_of_ctx[c];
+      if (slot == NONE32) continue;
+      const u64 x = time[j];
+      const u64 mx = P.mx[slot];
+      if (mx > 0 && x == mx) atomicMin(&P.argmax[slot], r);
+      const u64 s1 = P.s1[slot];
+      const u128 M = ((u128)P.Mhi[slot] << 64) | P.Mlo[slot];
+      const long long D = (long long)((u64)n * x) - (long long)s1;
+      const double z = (n < 2 || M == 0) ? 0.0 : i64_to_f64(D) / (u64_to_f64(n) * P.sd[slot]);
+      if (z_out) z_out[j] = z;
+      if (is_outlier(D, n, M, tn, td)) {
+        const unsigned long long q = atomicAdd(n_out, 1ull);
+        if (q < cap) {
+          keys[q] = ((u64)c << 32) | r;
+          zs[q] = z;
+        }
+        if (rank_flag) rank_flag[r] = 1;
+      }
+    }
+  }
+}
+
+__global__ void k_stats_argmax(u32 n_slots, const u32* argmax, ta_ctx_stats* out) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n_slots) out[s].argmax = argmax[s];
+}
+
+// ---- sort of (key, z) pairs by key: bitonic, in shared memory when small --
+constexpr int SORT_SMEM = 2048;
+
+__device__ __forceinline__ void cmp_swap(u64* k, double* v, u32 i, u32 j, bool up) {
+  const u64 a = k[i], b = k[j];
+  if ((a > b) == up) {
+    k[i] = b;
+    k[j] = a;
+    const double t = v[i];
+    v[i] = v[j];
+    v[j] = t;
+  }
+}
+
+__global__ void k_sort_small(u64* keys, double* vals, u32 n) {
+  __shared__ u64 sk[SORT_SMEM];
+  __shared__ double sv[SORT_SMEM];
+  u32 P = 1;
+  while (P < n) P <<= 1;
+  for (u32 i = threadIdx.x; i < P; i += blockDim.x) {
+    sk[i] = i < n ? keys[i] : ~0ull;
+    sv[i] = i < n ? vals[i] : 0.0;
+  }
+  __syncthreads();
+  for (u32 k = 2; k <= P; k <<= 1)
+    for (u32 j = k >> 1; j > 0; j >>= 1) {
+      for (u32 i = threadIdx.x; i < P; i += blockDim.x) {
+        const u32 l = i ^ j;
+        if (l > i) cmp_swap(sk, sv, i, l, (i & k) == 0);
+      }
+      __syncthreads();
+    }
+  for (u32 i = threadIdx.x; i < n; i += blockDim.x) {
+    keys[i] = sk[i];
+    vals[i] = sv[i];
+  }
+}
+
+__global__ void k_sort_step(u64* keys, double* vals, u64 P, u64 j, u64 k) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P) return;
+  const u64 l = i ^ j;
+  if (l > i) {
+    const bool up = (i & k) == 0;
+    const u64 a = keys[i], b = keys[l];
+    if ((a > b) == up) {
+      keys[i] = b;
+      keys[l] = a;
+      const double t = vals[i];
+      vals[i] = vals[l];
+      vals[l] = t;
+    }
+  }
+}
+
+__global__ void k_write_outliers(const u64* keys, const double* zs, u64 n, ta_outlier* out) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  ta_outlier o;
+  o.ctx = (u32)(keys[i] >> 32);
+  o.rank = (u32)keys[i];
+  o.z = zs[i];
+  out[i] = o;
+}
+
+inline unsigned blocks(u64 n, int nt = 256) { return (unsigned)std::max<u64>(1, (n + nt - 1) / nt); }
+
+// Sort n (key, z) pairs held in buffers of at least next_pow2(n) entries.
+void sort_pairs(const Launch& L, u64* keys, double* vals, u64 n) {
+  if (n <= 1) return;
+  if (n <= SORT_SMEM) {
+    k_sort_small<<<1, 1024, 0, L.stream>>>(keys, vals, (u32)n);
+    L.count();
+    return;
+  }
+  u64 P = 1;
+  while (P < n) P <<= 1;
+  k_fill_u64<<<blocks(P - n), 256, 0, L.stream>>>(keys + n, P - n, ~0ull);
+  L.count();
+  for (u64 k = 2; k <= P; k <<= 1)
+    for (u64 j = k >> 1; j > 0; j >>= 1) {
+      k_sort_step<<<blocks(P), 256, 0, L.stream>>>(keys, vals, P, j, k);
+      L.count();
+    }
+}
+
+const Csr* metric_csr(const ta_experiment* e, u32 metric) {
+  if (metric == TA_EXCLUSIVE) return &e->x;
+  if (metric == TA_INCLUSIVE && e->has_incl) return &e->in;
+  return nullptr;
+}
+
+// Device copy of a caller array (or the caller's device pointer itself).
+template <class T>
+ta_status to_device(ta_ctx* c, Pool& tmp, const T* src, u64 n, u32 kind, const T** out,
+                    const char* what) {
+  if (!src) {
+    *out = nullptr;
+    return TA_OK;
+  }
+  if (kind == TA_MEM_DEVICE) {
+    *out = src;
+    return TA_OK;
+  }
+  T* d;
+  TRY(tmp.get_n(std::max<u64>(n, 1), &d, what));
+  TRY(copy(c, d, src, n * sizeof(T)));
+  *out = d;
+  return TA_OK;
+}
+
+// Validate a sorted-unique subset on the device.
+ta_status check_subset(ta_ctx* c, const Launch& L, const u32* dv, u32 n, u32 limit, u32* status,
+                       const char* what) {
+  if (!dv) return TA_OK;
+  cudaMemsetAsync(status, 0, 4, c->stream);
+  k_check_sorted<<<blocks(n), 256, 0, L.stream>>>(dv, n, limit, status);
+  L.count();
+  u32 h = 0;
+  TRY(copy(c, &h, status, 4));
+  TRY(sync_check(c, what));
+  if (h) return fail(TA_ERR_INVALID_ARG, "%s must be sorted, unique and in range", what);
+  return TA_OK;
+}
+
+struct StatsRun {
+  u32 n_slots = 0;
+  u64 n = 0;
+  Partials P{};
+  ta_ctx_stats* stats = nullptr;  // device [n_slots]
+  u64* keys = nullptr;
+  double* zs = nullptr;
+  u64 n_out = 0;
+  u64 kept = 0;
+};
+
+// Everything of ta_context_stats on device buffers.
+ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 n,
+                    const u32* dK, u32 nk, u32 tn, u32 td, u64 cap, double* z_out,
+                    uint8_t* rank_flag, StatsRun& R) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
+  const Csr* m = metric_csr(e, metric);
+  R.n = n;
+  R.n_slots = dK ? nk : e->C;
+  const u32 ns = R.n_slots;
+  u32* slot_of_ctx;
+  TRY(tmp.get_n(e->C, &slot_of_ctx, "slot map"));
+  cudaMemsetAsync(slot_of_ctx, 0xFF, (size_t)e->C * 4, c->stream);
+  k_slot_map<<<blocks(dK ? nk : e->C), 256, 0, L.stream>>>(dK, nk, e->C, slot_of_ctx);
+  L.count();
+  Partials& P = R.P;
+  TRY(tmp.get_n(ns, &P.present, "partials"));
+  TRY(tmp.get_n(ns, &P.mn, "partials"));
+  TRY(tmp.get_n(ns, &P.mx, "partials"));
+  TRY(tmp.get_n(ns, &P.s1, "partials"));
+  TRY(tmp.get_n(ns, &P.s2lo, "partials"));
+  TRY(tmp.get_n(ns, &P.s2hi, "partials"));
+  TRY(tmp.get_n(ns, &P.argmax, "partials"));
+  TRY(tmp.get_n(ns, &P.sd, "partials"));
+  TRY(tmp.get_n(ns, &P.Mlo, "partials"));
+  TRY(tmp.get_n(ns, &P.Mhi, "partials"));
+  TRY(tmp.get_n(ns, &R.stats, "stats"));
+  cudaMemsetAsync(P.present, 0, (size_t)ns * 4, c->stream);
+  cudaMemsetAsync(P.mn, 0xFF, (size_t)ns * 8, c->stream);
+  cudaMemsetAsync(P.mx, 0, (size_t)ns * 8, c->stream);
+  cudaMemsetAsync(P.s1, 0, (size_t)ns * 8, c->stream);
+  cudaMemsetAsync(P.s2lo, 0, (size_t)ns * 8, c->stream);
+  cudaMemsetAsync(P.s2hi, 0, (size_t)ns * 8, c->stream);
+  const u64 kcap = std::max<u64>(1, cap);
+  u64 P2 = 1;
+  while (P2 < kcap) P2 <<= 1;
+  TRY(tmp.get_n(P2, &R.keys, "outlier keys"));
+  TRY(tmp.get_n(P2, &R.zs, "outlier z"));
+  unsigned long long* n_out;
+  TRY(tmp.get_n(1, &n_out, "outlier count"));
+  cudaMemsetAsync(n_out, 0, 8, c->stream);
+  if (z_out) cudaMemsetAsync(z_out, 0, m->nnz * 8, c->stream);
+  const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + 7) / 8)));
+  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P);
+  k_stats_finalize<<<blocks(ns), 256, 0, L.stream>>>(ns, n, dS, P, R.stats);
+  k_stats_z<<<grid, 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P, tn, td,
+                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag);
+  k_stats_argmax<<<blocks(ns), 256, 0, L.stream>>>(ns, P.argmax, R.stats);
+  L.count(4);
+  u64 h = 0;
+  TRY(copy(c, &h, n_out, 8));
+  TRY(sync_check(c, "context statistics"));
+  R.n_out = h;
+  R.kept = std::min<u64>(h, cap);
+  if (R.kept > 1 && h <= cap) sort_pairs(L, R.keys, R.zs, R.kept);
+  return TA_OK;
+}
+
+// ------------------------------------------------------------- topology --
+__global__ void k_topo_check(const u32* node_of_rank, u32 R, u32 nn, const u32* rack, u32 nr,
+                             const u32* chassis, u32 nc, u32* status) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < R && node_of_rank[i] >= nn) flag(status, F_INVALID);
+  if (i < nn && (rack[i] >= nr || chassis[i] >= nc)) flag(status, F_INVALID);
+}
+
+__device__ __forceinline__ u64 csr_lookup(const u64* off, const u32* ctx, const u64* time, u32 r,
+                                          u32 c) {
+  u64 lo = off[r], hi = off[r + 1];
+  while (lo < hi) {
+    const u64 mid = (lo + hi) / 2;
+    if (ctx[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < off[r + 1] && ctx[lo] == c) ? time[lo] : 0ull;
+}
+
+__global__ void k_topo_nodes(const u32* S, u32 n, const u64* off, const u32* ctx, const u64* time,
+                             u32 c, const uint8_t* rank_flag, const u32* node_of_rank,
+                             u32* node_out, unsigned long long* node_sum, u32* node_ranks) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u32 r = rank_at(S, i);
+  const u32 nd = node_of_rank[r];
+  const u64 x = csr_lookup(off, ctx, time, r, c);
+  if (rank_flag[r]) atomicAdd(&node_out[nd], 1u);
+  atomicAdd(&node_sum[nd], (unsigned long long)x);
+  atomicAdd(&node_ranks[nd], 1u);
+}
+
+__global__ void k_topo_up(u32 nn, const u32* node_out, const unsigned long long* node_sum,
+                          u32 min_ranks, const u32* rack, const u32* chassis, uint8_t* node_flag,
+                          u32* ch_flag, u32* ch_nodes, unsigned long long* ch_sum, u32* rk_flag,
+                          u32* rk_nodes, unsigned long long* rk_sum) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const u32 f = node_out[i] >= min_ranks ? 1u : 0u;
+  node_flag[i] = (uint8_t)f;
+  const u32 ch = chassis[i], rk = rack[i];
+  atomicAdd(&ch_flag[ch], f);
+  atomicAdd(&ch_nodes[ch], 1u);
+  atomicAdd(&ch_sum[ch], node_sum[i]);
+  atomicAdd(&rk_flag[rk], f);
+  atomicAdd(&rk_nodes[rk], 1u);
+  atomicAdd(&rk_sum[rk], node_sum[i]);
+}
+
+// One block: racks with a flagged node, ascending.
+__global__ void k_topo_racks(u32 nr, const u32* rk_flag, u32* flagged, u32* count) {
+  __shared__ u32 s_scan[32];
+  __shared__ u32 s_base;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (u32 b0 = 0; b0 < nr; b0 += blockDim.x) {
+    const u32 i = b0 + threadIdx.x;
+    const u32 f = (i < nr && rk_flag[i] > 0) ? 1u : 0u;
+    const u32 x = warp_incl_scan(f, lane);
+    if (lane == 31) s_scan[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      const u32 nw = blockDim.x / 32;
+      u32 y = lane < (int)nw ? s_scan[lane] : 0u;
+      y = warp_incl_scan(y, lane);
+      if (lane < (int)nw) s_scan[lane] = y;
+    }
+    __syncthreads();
+    const u32 pos = s_base + (warp > 0 ? s_scan[warp - 1] : 0u) + x - f;
+    if (f) flagged[pos] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) s_base += s_scan[blockDim.x / 32 - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count = s_base;
+}
+
+// -------------------------------------------------------------- speedup --
+__global__ void k_sp_istar(const u32* S, u32 n, const u32* n_iter, const u64* span, u32* istar,
+                           unsigned long long* sum_iter, unsigned long long* max_span) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u32 r = rank_at(S, i);
+  atomicMin(istar, n_iter[r]);
+  atomicAdd(sum_iter, (unsigned long long)n_iter[r]);
+  atomicMax(max_span, (unsigned long long)span[r]);
+}
+
+constexpr int SP_NT = 256;
+constexpr u32 SP_SMEM_CELLS = 4096;  // 32 B each
+
+// Cells (i, k) for i < I*, k in [k0, k0 + nkc): sum, max, 128-bit sum of
+// squares over ranks; per (rank, k) the within-rank CV term over i < I*.
+__global__ void __launch_bounds__(SP_NT)
+    k_sp_rows(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
+              const u64* e_time, const u32* kmap, u32 k0, u32 nkc, u32 nk, u32 I,
+              bool cells_in_smem, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi,
+              double* cvw) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  constexpr int W = SP_NT / 32;
+  u64* rk = (u64*)sm;  // per warp: sum[nkc], sqlo[nkc], sqhi[nkc]
+  u64* c_sum = rk + (size_t)W * 3 * nkc;
+  u64* c_max = c_sum + (cells_in_smem ? (size_t)I * nkc : 0);
+  u64* c_sqlo = c_max + (cells_in_smem ? (size_t)I * nkc : 0);
+  u64* c_sqhi = c_sqlo + (cells_in_smem ? (size_t)I * nkc : 0);
+  const u32 ncell = I * nkc;
+  if (cells_in_smem)
+    for (u32 q = threadIdx.x; q < ncell; q += SP_NT) c_sum[q] = c_max[q] = c_sqlo[q] = c_sqhi[q] = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64* my_sum = rk + (size_t)warp * 3 * nkc;
+  u64* my_lo = my_sum + nkc;
+  u64* my_hi = my_lo + nkc;
+  for (u32 q = lane; q < 3 * nkc; q += 32) my_sum[q] = 0;
+  __syncthreads();
+  u64* ts_ = cells_in_smem ? c_sum : g_sum;
+  u64* tm_ = cells_in_smem ? c_max : g_max;
+  u64* tl_ = cells_in_smem ? c_sqlo : g_sqlo;
+  u64* th_ = cells_in_smem ? c_sqhi : g_sqhi;
+  const u32 gw = blockIdx.x * W + warp, nw = gridDim.x * W;
+  for (u32 ri = gw; ri < n; ri += nw) {
+    const u32 r = rank_at(S, ri);
+    const u64 row0 = row_off[r] + 1;  // skip the prologue row
+    for (u32 i = 0; i < I; ++i) {
+      const u64 E0 = entry_off[row0 + i], E1 = entry_off[row0 + i + 1];
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 k = kmap[e_ctx[j]];
+        if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
+        const u32 kk = k - k0;
+        const u64 t = e_time[j];
+        const u128 t2 = (u128)t * t;
+        const u64 q = cells_in_smem ? (u64)i * nkc + kk : (u64)i * nk + k0 + kk;
+        atomicAdd((unsigned long long*)&ts_[q], (unsigned long long)t);
+        atomicMax((unsigned long long*)&tm_[q], (unsigned long long)t);
+        atomic_add_u128(&tl_[q], &th_[q], t2);
+        my_sum[kk] += t;  // one entry per context per row: lanes hit distinct kk
+        const u64 lo = my_lo[kk] + (u64)t2;
+        my_hi[kk] += (u64)(t2 >> 64) + (lo < my_lo[kk] ? 1ull : 0ull);
+        my_lo[kk] = lo;
+      }
+      __syncwarp();
+    }
+    for (u32 kk = lane; kk < nkc; kk += 32) {
+      const u64 s = my_sum[kk];
+      const u128 q = ((u128)my_hi[kk] << 64) | my_lo[kk];
+      double term = 0.0;
+      if (I > 0) {
+        const double mean = u64_to_f64(s) / u64_to_f64(I);
+        const double sd = (I < 2) ? 0.0
+                                  : sqrt(u128_to_f64((u128)I * q - (u128)s * s) /
+                                         u64_to_f64((u64)I * (I - 1)));
+        term = (mean == 0.0) ? 0.0 : sd / mean;
+      }
+      cvw[(u64)ri * nk + k0 + kk] = term;
+      my_sum[kk] = 0;
+      my_lo[kk] = 0;
+      my_hi[kk] = 0;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  if (cells_in_smem) {
+    for (u32 q = threadIdx.x; q < ncell; q += SP_NT) {
+      const u32 i = q / nkc, kk = q % nkc;
+      const u64 gq = (u64)i * nk + k0 + kk;
+      if (c_sum[q]) atomicAdd((unsigned long long*)&g_sum[gq], (unsigned long long)c_sum[q]);
+      if (c_max[q]) atomicMax((unsigned long long*)&g_max[gq], (unsigned long long)c_max[q]);
+      if (c_sqlo[q] | c_sqhi[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)c_sqhi[q] << 64) | c_sqlo[q]);
+    }
+  }
+}
+
+// One thread per context: sums in ascending iteration / rank order.
+__global__ void k_sp_final_k(u32 nk, u32 n, u32 I, const u64* g_sum, const u64* g_max,
+                             const u64* g_sqlo, const u64* g_sqhi, const double* cvw,
+                             ta_speedup_ctx* per) {
+  const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  u64 A = 0, B = 0;
+  double across = 0.0;
+  for (u32 i = 0; i < I; ++i) {
+    const u64 q = (u64)i * nk + k;
+    const u64 sum = g_sum[q], mx = g_max[q];
+    const u128 sq = ((u128)g_sqhi[q] << 64) | g_sqlo[q];
+    A += mx;
+    B += sum;
+    const double mean = u64_to_f64(sum) / u64_to_f64(n);
+    const double sd = (n < 2) ? 0.0
+                              : sqrt(u128_to_f64((u128)n * sq - (u128)sum * sum) /
+                                     u64_to_f64((u64)n * (n - 1)));
+    across += (mean == 0.0) ? 0.0 : sd / mean;
+  }
+  double within = 0.0;
+  if (I > 0)
+    for (u32 ri = 0; ri < n; ++ri) within += cvw[(u64)ri * nk + k];
+  const u128 G = (u128)n * A - B;
+  ta_speedup_ctx p;
+  p.A = A;
+  p.B = B;
+  p.G_lo = (u64)G;
+  p.G_hi = (u64)(G >> 64);
+  if (I == 0) {
+    p.avg_mean = p.avg_max = p.savings_per_iter = 0.0;
+    p.cv_across = p.cv_within = 0.0;
+  } else {
+    p.avg_mean = u64_to_f64(B) / u128_to_f64((u128)n * I);
+    p.avg_max = u64_to_f64(A) / u64_to_f64(I);
+    p.savings_per_iter = u128_to_f64(G) / u128_to_f64((u128)n * I);
+    p.cv_across = across / u64_to_f64(I);
+    p.cv_within = within / u64_to_f64(n);
+  }
+  p.total_reduction = u128_to_f64(G) / u64_to_f64(n);
+  p.share = 0.0;
+  per[k] = p;
+}
+
+__global__ void k_sp_total(u32 nk, u32 n, u32 I, u64 excluded, u64 t_app, ta_speedup_ctx* per,
+                           ta_speedup_total* tot) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  u128 sumB = 0, sumG = 0;
+  for (u32 k = 0; k < nk; ++k) {
+    sumB += per[k].B;
+    sumG += ((u128)per[k].G_hi << 64) | per[k].G_lo;
+  }
+  for (u32 k = 0; k < nk; ++k)
+    per[k].share = (sumB == 0) ? 0.0 : u64_to_f64(per[k].B) / u128_to_f64(sumB);
+  ta_speedup_total t;
+  t.i_star = I;
+  t.reserved = 0;
+  t.excluded_iterations = excluded;
+  t.sum_G_lo = (u64)sumG;
+  t.sum_G_hi = (u64)(sumG >> 64);
+  t.t_app = t_app;
+  t.total_reduction = u128_to_f64(sumG) / u64_to_f64(n);
+  t.speedup_fraction = (t_app == 0) ? 0.0 : u128_to_f64(sumG) / u128_to_f64((u128)n * t_app);
+  *tot = t;
+}
+
+}  // namespace
+
+extern "C" {
+
+ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_out* o) {
+  if (!e || !a || !o) return fail(TA_ERR_INVALID_ARG, "ta_context_stats: NULL argument");
+  if (a->metric > 1) return fail(TA_ERR_INVALID_ARG, "metric");
+  if (!metric_csr(e, a->metric)) return fail(TA_ERR_STATE, "inclusive rollup was skipped at load");
+  if (a->tau_den == 0) return fail(TA_ERR_INVALID_ARG, "tau_den = 0");
+  if (a->mem_kind > 1) return fail(TA_ERR_INVALID_ARG, "mem_kind");
+  if (a->ranks && a->n_ranks_subset == 0) return fail(TA_ERR_INVALID_ARG, "empty rank subset");
+  if (!o->stats) return fail(TA_ERR_INVALID_ARG, "stats output is NULL");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  Pool tmp{c, {}};
+  struct Rel {
+    Pool& p;
+    ~Rel() {
+      cudaStreamSynchronize(p.ctx->stream);
+      p.release();
+    }
+  } rel{tmp};
+  const u32 n = a->ranks ? a->n_ranks_subset : e->R;
+  const u32 nk = a->ctxs ? a->n_ctxs : e->C;
+  const u32 *dS, *dK;
+  TRY(to_device(c, tmp, a->ranks, a->ranks ? n : 0, a->mem_kind, &dS, "rank subset"));
+  TRY(to_device(c, tmp, a->ctxs, a->ctxs ? nk : 0, a->mem_kind, &dK, "ctx subset"));
+  u32* status;
+  TRY(tmp.get_n(1, &status, "status"));
+  TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
+  TRY(check_subset(c, L, dK, nk, e->C, status, "ctx subset"));
+  const Csr* m = metric_csr(e, a->metric);
+  double* dz = nullptr;
+  if (o->z) {
+    if (a->mem_kind == TA_MEM_DEVICE) dz = o->z;
+    else TRY(tmp.get_n(std::max<u64>(m->nnz, 1), &dz, "z"));
+  }
+  StatsRun R;
+  TRY(stats_run(e, tmp, a->metric, dS, n, dK, a->ctxs ? nk : 0, a->tau_num, a->tau_den,
+                o->outlier_cap, dz, nullptr, R));
+  o->n_outliers = R.n_out;
+  const bool fits = R.n_out <= o->outlier_cap;
+  ta_outlier* dout = nullptr;
+  if (fits && R.kept > 0 && o->outliers) {
+    if (a->mem_kind == TA_MEM_DEVICE) dout = o->outliers;
+    else TRY(tmp.get_n(R.kept, &dout, "outliers"));
+    k_write_outliers<<<blocks(R.kept), 256, 0, L.stream>>>(R.keys, R.zs, R.kept, dout);
+    L.count();
+    if (a->mem_kind == TA_MEM_HOST) TRY(copy(c, o->outliers, dout, R.kept * sizeof(ta_outlier)));
+  }
+  TRY(copy(c, o->stats, R.stats, (size_t)R.n_slots * sizeof(ta_ctx_stats)));
+  if (o->z && a->mem_kind == TA_MEM_HOST) TRY(copy(c, o->z, dz, m->nnz * 8));
+  TRY(sync_check(c, "ta_context_stats"));
+  if (!fits)
+    return fail(TA_ERR_CAPACITY, "%llu outliers, capacity %llu",
+                (unsigned long long)R.n_out, (unsigned long long)o->outlier_cap);
+  return TA_OK;
+}
+
+ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_topo_args* a,
+                             ta_topo_out* o) {
+  if (!e || !t || !a || !o) return fail(TA_ERR_INVALID_ARG, "ta_topology_rollup: NULL argument");
+  if (a->metric > 1 || !metric_csr(e, a->metric))
+    return fail(a->metric > 1 ? TA_ERR_INVALID_ARG : TA_ERR_STATE, "metric");
+  if (a->ctx >= e->C) return fail(TA_ERR_INVALID_ARG, "ctx >= n_ctx");
+  if (a->min_ranks == 0) return fail(TA_ERR_INVALID_ARG, "min_ranks = 0");
+  if (a->tau_den == 0) return fail(TA_ERR_INVALID_ARG, "tau_den = 0");
+  if (!t->node_of_rank || !t->rack_of_node || !t->chassis_of_node || t->n_nodes == 0 ||
+      t->n_racks == 0 || t->n_chassis == 0)
+    return fail(TA_ERR_INVALID_ARG, "topology arrays");
+  if (a->ranks && a->n_ranks_subset == 0) return fail(TA_ERR_INVALID_ARG, "empty rank subset");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  Pool tmp{c, {}};
+  struct Rel {
+    Pool& p;
+    ~Rel() {
+      cudaStreamSynchronize(p.ctx->stream);
+      p.release();
+    }
+  } rel{tmp};
+  const u32 n = a->ranks ? a->n_ranks_subset : e->R;
+  const u32 nn = t->n_nodes, nc = t->n_chassis, nr = t->n_racks;
+  const u32 *dS, *dnode, *drack, *dch;
+  TRY(to_device(c, tmp, a->ranks, a->ranks ? n : 0, o->mem_kind, &dS, "rank subset"));
+  TRY(to_device(c, tmp, t->node_of_rank, e->R, t->mem_kind, &dnode, "node_of_rank"));
+  TRY(to_device(c, tmp, t->rack_of_node, nn, t->mem_kind, &drack, "rack_of_node"));
+  TRY(to_device(c, tmp, t->chassis_of_node, nn, t->mem_kind, &dch, "chassis_of_node"));
+  u32* status;
+  TRY(tmp.get_n(1, &status, "status"));
+  TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
+  cudaMemsetAsync(status, 0, 4, c->stream);
+  k_topo_check<<<blocks(std::max(e->R, nn)), 256, 0, L.stream>>>(dnode, e->R, nn, drack, nr, dch,
+                                                                  nc, status);
+  L.count();
+  u32 hs = 0;
+  TRY(copy(c, &hs, status, 4));
+  TRY(sync_check(c, "topology check"));
+  if (hs) return fail(TA_ERR_INVALID_ARG, "topology ids out of range");
+  uint8_t* rank_flag;
+  TRY(tmp.get_n(e->R, &rank_flag, "rank flags"));
+  cudaMemsetAsync(rank_flag, 0, e->R, c->stream);
+  u32* dk;
+  TRY(tmp.get_n(1, &dk, "ctx"));
+  TRY(copy(c, dk, &a->ctx, 4));
+  StatsRun R;
+  TRY(stats_run(e, tmp, a->metric, dS, n, dk, 1, a->tau_num, a->tau_den, 0, nullptr, rank_flag, R));
+  // outputs on the device (staged when the caller wants host memory)
+  const bool dev = o->mem_kind == TA_MEM_DEVICE;
+  u32 *no, *nrk, *cf, *cn, *rf, *rn, *fr, *cnt;
+  unsigned long long *nsum, *csum, *rsum;
+  uint8_t* nf;
+  auto pick = [&](auto* user, auto** out, u64 cnt_, const char* w) -> ta_status {
+    using T = std::remove_pointer_t<std::remove_reference_t<decltype(*out)>>;
+    if (dev && user) {
+      *out = (T*)user;
+      return TA_OK;
+    }
+    return tmp.get_n(std::max<u64>(cnt_, 1), out, w);
+  };
+  TRY(pick(o->node_outliers, &no, nn, "node outliers"));
+  TRY(pick((unsigned long long*)o->node_sum, &nsum, nn, "node sum"));
+  TRY(pick(o->node_ranks, &nrk, nn, "node ranks"));
+  TRY(pick(o->node_flag, &nf, nn, "node flag"));
+  TRY(pick(o->chassis_flagged, &cf, nc, "chassis"));
+  TRY(pick(o->chassis_nodes, &cn, nc, "chassis"));
+  TRY(pick((unsigned long long*)o->chassis_sum, &csum, nc, "chassis"));
+  TRY(pick(o->rack_flagged, &rf, nr, "rack"));
+  TRY(pick(o->rack_nodes, &rn, nr, "rack"));
+  TRY(pick((unsigned long long*)o->rack_sum, &rsum, nr, "rack"));
+  TRY(pick(o->flagged_racks, &fr, nr, "flagged racks"));
+  TRY(tmp.get_n(1, &cnt, "count"));
+  cudaMemsetAsync(no, 0, (size_t)nn * 4, c->stream);
+  cudaMemsetAsync(nsum, 0, (size_t)nn * 8, c->stream);
+  cudaMemsetAsync(nrk, 0, (size_t)nn * 4, c->stream);
+  cudaMemsetAsync(cf, 0, (size_t)nc * 4, c->stream);
+  cudaMemsetAsync(cn, 0, (size_t)nc * 4, c->stream);
+  cudaMemsetAsync(csum, 0, (size_t)nc * 8, c->stream);
+  cudaMemsetAsync(rf, 0, (size_t)nr * 4, c->stream);
+  cudaMemsetAsync(rn, 0, (size_t)nr * 4, c->stream);
+  cudaMemsetAsync(rsum, 0, (size_t)nr * 8, c->stream);
+  const Csr* m = metric_csr(e, a->metric);
+  k_topo_nodes<<<blocks(n), 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, a->ctx, rank_flag,
+                                                dnode, no, nsum, nrk);
+  k_topo_up<<<blocks(nn), 256, 0, L.stream>>>(nn, no, nsum, a->min_ranks, drack, dch, nf, cf, cn,
+                                              csum, rf, rn, rsum);
+  k_topo_racks<<<1, 256, 0, L.stream>>>(nr, rf, fr, cnt);
+  L.count(3);
+  u32 nfr = 0;
+  TRY(copy(c, &nfr, cnt, 4));
+  if (!dev) {
+    if (o->node_outliers) TRY(copy(c, o->node_outliers, no, (size_t)nn * 4));
+    if (o->node_sum) TRY(copy(c, o->node_sum, nsum, (size_t)nn * 8));
+    if (o->node_ranks) TRY(copy(c, o->node_ranks, nrk, (size_t)nn * 4));
+    if (o->node_flag) TRY(copy(c, o->node_flag, nf, nn));
+    if (o->chassis_flagged) TRY(copy(c, o->chassis_flagged, cf, (size_t)nc * 4));
+    if (o->chassis_nodes) TRY(copy(c, o->chassis_nodes, cn, (size_t)nc * 4));
+    if (o->chassis_sum) TRY(copy(c, o->chassis_sum, csum, (size_t)nc * 8));
+    if (o->rack_flagged) TRY(copy(c, o->rack_flagged, rf, (size_t)nr * 4));
+    if (o->rack_nodes) TRY(copy(c, o->rack_nodes, rn, (size_t)nr * 4));
+    if (o->rack_sum) TRY(copy(c, o->rack_sum, rsum, (size_t)nr * 8));
+    if (o->flagged_racks) TRY(copy(c, o->flagged_racks, fr, (size_t)nr * 4));
+  }
+  TRY(sync_check(c, "ta_topology_rollup"));
+  o->n_flagged_racks = nfr;
+  return TA_OK;
+}
+
+ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_speedup_out* o) {
+  if (!e || !a || !o) return fail(TA_ERR_INVALID_ARG, "ta_potential_speedup: NULL argument");
+  if (!a->ctxs || a->n_ctxs == 0) return fail(TA_ERR_INVALID_ARG, "empty context set");
+  if (a->ranks && a->n_ranks_subset == 0) return fail(TA_ERR_INVALID_ARG, "empty rank subset");
+  if (!o->per_ctx || !o->total) return fail(TA_ERR_INVALID_ARG, "outputs NULL");
+  if (a->mem_kind > 1) return fail(TA_ERR_INVALID_ARG, "mem_kind");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  Pool tmp{c, {}};
+  struct Rel {
+    Pool& p;
+    ~Rel() {
+      cudaStreamSynchronize(p.ctx->stream);
+      p.release();
+    }
+  } rel{tmp};
+  const u32 n = a->ranks ? a->n_ranks_subset : e->R;
+  const u32 nk = a->n_ctxs;
+  const u32 *dS, *dK;
+  TRY(to_device(c, tmp, a->ranks, a->ranks ? n : 0, a->mem_kind, &dS, "rank subset"));
+  TRY(to_device(c, tmp, a->ctxs, nk, a->mem_kind, &dK, "ctx set"));
+  u32* status;
+  TRY(tmp.get_n(1, &status, "status"));
+  TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
+  TRY(check_subset(c, L, dK, nk, e->C, status, "ctx set"));
+  u64* meta;  // [0] istar, [1] sum n_iter, [2] max span
+  TRY(tmp.get_n(4, &meta, "speedup meta"));
+  cudaMemsetAsync(meta, 0, 32, c->stream);
+  cudaMemsetAsync(meta, 0xFF, 4, c->stream);
+  k_sp_istar<<<blocks(n), 256, 0, L.stream>>>(dS, n, e->n_iter, e->span, (u32*)meta,
+                                              (unsigned long long*)meta + 1,
+                                              (unsigned long long*)meta + 2);
+  L.count();
+  u64 h[3];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, "speedup I*"));
+  const u32 I = (u32)h[0];
+  const u64 excluded = h[1] - (u64)n * I;
+  const u64 t_app = a->app_time_ns ? a->app_time_ns : h[2];
+  u32* kmap;
+  TRY(tmp.get_n(e->C, &kmap, "kmap"));
+  cudaMemsetAsync(kmap, 0xFF, (size_t)e->C * 4, c->stream);
+  k_slot_map<<<blocks(nk), 256, 0, L.stream>>>(dK, nk, e->C, kmap);
+  L.count();
+  const u64 ncell = std::max<u64>(1, (u64)I * nk);
+  u64 *gs, *gm, *gl, *gh;
+  double* cvw;
+  TRY(tmp.get_n(ncell, &gs, "cells"));
+  TRY(tmp.get_n(ncell, &gm, "cells"));
+  TRY(tmp.get_n(ncell, &gl, "cells"));
+  TRY(tmp.get_n(ncell, &gh, "cells"));
+  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw, "cv terms"));
+  cudaMemsetAsync(gs, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
+  // chunk the context set so that a chunk's cells fit in shared memory
+  u32 nkc = std::min<u32>(std::min<u32>(nk, 256), I > 0 ? std::max<u32>(1, SP_SMEM_CELLS / I) : 256);
+  const bool smem_cells = (u64)I * nkc <= SP_SMEM_CELLS;
+  const int W = SP_NT / 32;
+  const size_t smem = ((size_t)W * 3 * nkc + (smem_cells ? (size_t)4 * I * nkc : 0)) * 8;
+  if (smem > 200 * 1024) return fail(TA_ERR_INVALID_ARG, "speedup: too many contexts per chunk");
+  cudaFuncSetAttribute(k_sp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = std::max(1, std::min<int>(c->num_sms * 2, (int)((n + W - 1) / W)));
+  for (u32 k0 = 0; I > 0 && k0 < nk; k0 += nkc) {
+    const u32 cnk = std::min(nkc, nk - k0);
+    k_sp_rows<<<grid, SP_NT, smem, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
+                                               e->e_time, kmap, k0, cnk, nk, I, smem_cells, gs, gm,
+                                               gl, gh, cvw);
+    L.count();
+  }
+  ta_speedup_ctx* dper;
+  ta_speedup_total* dtot;
+  if (a->mem_kind == TA_MEM_DEVICE) {
+    dper = o->per_ctx;
+    dtot = o->total;
+  } else {
+    TRY(tmp.get_n(nk, &dper, "per ctx"));
+    TRY(tmp.get_n(1, &dtot, "total"));
+  }
+  k_sp_final_k<<<blocks(nk, 64), 64, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, cvw, dper);
+  k_sp_total<<<1, 1, 0, L.stream>>>(nk, n, I, excluded, t_app, dper, dtot);
+  L.count(2);
+  if (a->mem_kind == TA_MEM_HOST) {
+    TRY(copy(c, o->per_ctx, dper, (size_t)nk * sizeof(ta_speedup_ctx)));
+    TRY(copy(c, o->total, dtot, sizeof(ta_speedup_total)));
+  }
+  return sync_check(c, "ta_potential_speedup");
+}
+
+}  // extern "C"

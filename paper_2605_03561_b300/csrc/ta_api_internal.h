@@ -1,0 +1,85 @@
+// ta_api_internal.h -- the objects behind the opaque handles of ta.h.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ta.h"
+#include "ta_internal.h"
+
+struct ta_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  ta_alloc_fn alloc = nullptr;
+  ta_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  unsigned long long launches = 0;
+};
+
+namespace ta {
+
+struct Block {
+  void* p;
+  size_t n;
+};
+
+struct Csr {
+  u64* off = nullptr;
+  u32* ctx = nullptr;
+  u64* time = nullptr;
+  u32* cnt = nullptr;
+  u64 nnz = 0;
+};
+
+// Per-call temporaries, released after the call's last synchronisation.
+struct Pool {
+  ta_ctx* ctx;
+  std::vector<Block> items;
+  ta_status get(size_t bytes, void** out, const char* what);
+  template <class T>
+  ta_status get_n(size_t n, T** out, const char* what) {
+    return get(n * sizeof(T), (void**)out, what);
+  }
+  void release();
+};
+
+ta_status fail(ta_status s, const char* fmt, ...);
+ta_status cuda_fail(cudaError_t e, const char* what);
+void* dalloc(ta_ctx* c, size_t bytes);
+void dfree(ta_ctx* c, void* p, size_t bytes);
+ta_status sync_check(ta_ctx* c, const char* what);
+ta_status copy(ta_ctx* c, void* dst, const void* src, size_t bytes);
+ta_status status_from_flags(u32 f, const char* where);
+
+}  // namespace ta
+
+struct ta_experiment {
+  ta_ctx* ctx = nullptr;
+  ta::u32 R = 0, C = 0, m = 0, max_depth = 0;
+  ta::u64 N = 0, max_span = 0;
+  // inputs on the device (ts/ctx released after ingestion unless borrowed)
+  ta::u64* rank_off = nullptr;
+  ta::u32* parent = nullptr;
+  const ta::u64* ts = nullptr;
+  const ta::u32* ctxv = nullptr;
+  bool owns_traces = false;
+  // resident products
+  ta::u32* depth = nullptr;
+  ta::u64* span = nullptr;
+  ta::u32* n_iter = nullptr;
+  ta::u64* row_off = nullptr;
+  ta::u64* entry_off = nullptr;
+  ta::u32* e_ctx = nullptr;
+  ta::u64* e_time = nullptr;
+  ta::u32* e_cnt = nullptr;
+  ta::u64 rows = 0, nnz = 0;
+  ta::Csr x, in;
+  bool has_incl = false;
+  ta::u64 device_bytes = 0;
+  std::vector<ta::Block> owned;
+
+  ta_status own(size_t bytes, void** out, const char* what);
+  void disown(void* p);
+  void drop();
+};

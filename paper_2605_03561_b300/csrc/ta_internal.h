@@ -1,0 +1,102 @@
+// ta_internal.h -- host-side declarations shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ta_dev.cuh"
+
+namespace ta {
+
+struct Launch {
+  cudaStream_t stream;
+  int num_sms;
+  unsigned long long* launches;  // counter of kernel launches
+  void count(int k = 1) const { *launches += (unsigned long long)k; }
+};
+
+// ------------------------------------------------------------- ingest ----
+struct TensorArgs {
+  const u64* rank_off;
+  const u64* ts;
+  const u32* ctx;
+  u32 R, C, m, n_tiles;
+  u64 N;
+  const u32* tfr;  // [n_tiles + 1] first rank starting at or after tile start
+  u32* unit_counter;
+  UnitStatus* ustat;  // [n_tiles]
+  u64* row_off_of_rank;
+  u64* entry_off;
+  u32* e_ctx;
+  u64* e_time;
+  u32* e_cnt;
+  u64 rows_cap, nnz_cap;
+  u64* totals;  // [2] rows, nnz
+  u32* gbm;     // global bitmaps (per CTA x warp) when not in shared memory
+  u32* gst_ctx;
+  u64* gst_time;
+  u32* gst_cnt;
+  u32 gst_cap;  // per CTA
+  u32 bm_in_smem;
+  u32* status;
+};
+
+struct TensorPlan {
+  int tile, threads, grid;
+  size_t smem;
+  bool bm_in_smem;
+  u32 gst_cap;
+};
+TensorPlan plan_tensor(u32 C, u64 N, int num_sms);
+void launch_tensor(const Launch& L, const TensorPlan& P, const TensorArgs& A);
+
+void launch_rank_off(const Launch& L, const u64* rank_off, u32 R, u64 N, const u64* ts,
+                     u64* span, u64* max_span, u32* status);
+void launch_tile_first_rank(const Launch& L, const u64* rank_off, u32 R, u32 tile, u32 n_tiles,
+                            u32* tfr);
+// parent[C] -> depth[C], *max_depth; scratch: 4*C u32.
+void launch_cct(const Launch& L, const u32* parent, u32 C, u32* depth, u32* max_depth,
+                u32* roots, u32* scratch, u32* status);
+void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_iter);
+
+// Per-rank CSR of distinct contexts (mode 0: exclusive from the tensor,
+// mode 1: inclusive from the exclusive CSR).
+struct RankCsrArgs {
+  u32 mode, R, C, max_depth;
+  // mode 0 input: tensor
+  const u64* row_off_of_rank;
+  const u64* entry_off;
+  // mode 1 input: exclusive CSR offsets
+  const u64* in_off;
+  const u32* in_ctx;
+  const u64* in_time;
+  const u32* in_cnt;
+  const u32* parent;
+  const u32* depth;
+  u32* unit_counter;
+  UnitStatus* ustat;
+  u64* out_off;
+  u32* out_ctx;
+  u64* out_time;
+  u32* out_cnt;
+  u64 nnz_cap;
+  u64* total;  // [1]
+  u32* gbm;
+  u32* gst_ctx;
+  u64* gst_time;
+  u32* gst_cnt;
+  u32 gst_cap;
+  u32 bm_in_smem;
+  u32* status;
+};
+struct RankCsrPlan {
+  int threads, grid;
+  size_t smem;
+  bool bm_in_smem;
+  u32 gst_cap;
+  u32 n_units;
+};
+RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
+void launch_rank_csr(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+
+}  // namespace ta

@@ -1,0 +1,164 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Small and medium cases compare every output element by element; they span
+many 1024-sample tiles with ragged tails, rows that cross tiles, empty and
+degenerate ranks, and contexts far apart in the tree."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_03561_b300 as ta
+from paper_2605_03561_b300 import synth
+from paper_2605_03561_b300.synth import edge
+from gpu_helpers import (check_products, check_speedup, check_stats, check_topology,
+                         load_both, simple_topology)
+
+pytestmark = pytest.mark.gpu
+
+NONE = 0xFFFFFFFF
+
+
+def _hand(golden_dir):
+    with open(os.path.join(golden_dir, "hand_example.json")) as f:
+        g = json.load(f)
+    lens = [len(r["ts"]) for r in g["ranks"]]
+    ro = np.concatenate([[0], np.cumsum(lens)]).astype(np.uint64)
+    return dict(rank_off=ro, ts=np.array(sum((r["ts"] for r in g["ranks"]), []), np.uint64),
+                ctx=np.array(sum((r["ctx"] for r in g["ranks"]), []), np.uint32),
+                parent=np.array(g["parent"], np.uint32), marker=g["marker"]), g
+
+
+def test_hand_example(golden_dir):
+    d, g = _hand(golden_dir)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    st, _ = check_stats(a, e, ta.EXCLUSIVE, ctxs=[2])
+    assert st["std"][0] == pytest.approx(g["stats_excl_ctx2"]["std"], rel=1e-15)
+    check_stats(a, e, ta.INCLUSIVE)
+    gp, gt = check_speedup(a, e, [1, 2])
+    assert gt["speedup_fraction"] == pytest.approx(g["speedup_ctx_1_2"]["speedup_fraction"],
+                                                   rel=1e-15)
+
+
+@pytest.mark.parametrize("name", edge.EDGE_CASES)
+def test_edge_cases(name):
+    d = edge.case(name, 1)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE, tau=(1, 1))
+    check_stats(a, e, ta.INCLUSIVE, tau=(2, 1))
+    ctxs = sorted(set(int(c) for c in d["ctx"][:50]))
+    if ctxs:
+        check_speedup(a, e, ctxs)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small(seed):
+    d = edge.case("random_small", seed)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE, tau=(1, 1))
+    check_stats(a, e, ta.INCLUSIVE, tau=(1, 2))
+    check_speedup(a, e, list(range(tr.C)))
+    topo = simple_topology(tr.R, 2, 2, 1)
+    check_topology(a, e, int(d["ctx"][0]) if len(d["ctx"]) else 0, topo, tau=(1, 1))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_medium(seed):
+    d = edge.case("random_medium", seed)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    rng = np.random.default_rng(seed)
+    ranks = np.unique(rng.integers(0, tr.R, size=max(1, tr.R // 2))).astype(np.uint32)
+    check_stats(a, e, ta.EXCLUSIVE, tau=(2, 1))
+    check_stats(a, e, ta.INCLUSIVE, ranks=ranks, tau=(3, 2))
+    ctxs = np.unique(d["ctx"][: 200]).astype(np.uint32)
+    check_speedup(a, e, ctxs, ranks=ranks)
+
+
+def test_capacity_retry_paths():
+    """First-try capacities that are far too small are recovered exactly."""
+    d = edge.case("random_medium", 3)
+    tr, a, e = load_both(d, nnz_hint=7, rows_hint=3)
+    check_products(tr, a, e)
+
+
+def test_borrowed_device_input():
+    import torch
+    d = edge.case("random_medium", 4)
+    tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+    a = oracle.Analysis(tr)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(d[k])).cuda()
+           for k in ("rank_off", "ts", "ctx", "parent")}
+    from gpu_helpers import context
+    e = context().load(dev["rank_off"], dev["ts"], dev["ctx"], dev["parent"], d["marker"],
+                       borrow=True)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE)
+
+
+@pytest.mark.parametrize("preset,R", [(0, 8), (1, 64), (2, 96), (3, 1500)])
+def test_generated_configs(preset, R):
+    """The structured generator at reduced rank counts (full trace lengths)."""
+    cfg = synth.preset(preset, seed=11, n_ranks=R)
+    g = synth.generate(cfg)
+    tr, a, e = load_both(g)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE)
+    check_stats(a, e, ta.INCLUSIVE, tau=(2, 1))
+    truth = synth.truth(cfg, g["info"])
+    kset = np.unique(truth["segment_ctx"]).astype(np.uint32)
+    check_speedup(a, e, kset)
+    topo = synth.topology(cfg, g["info"])
+    comm = truth["segment_ctx"][truth["comm_segment"].astype(bool)]
+    check_topology(a, e, int(comm[0]), topo, tau=(2, 1))
+
+
+def test_validation_errors():
+    base = edge.case("random_small", 2)
+    from gpu_helpers import context
+
+    def load(d):
+        try:
+            context().load(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+            return ta.OK
+        except ta.TaError as err:
+            return err.status
+
+    def variant(kind):
+        d = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in base.items()}
+        nz = [r for r in range(len(d["rank_off"]) - 1) if d["rank_off"][r + 1] - d["rank_off"][r] >= 2]
+        b = int(d["rank_off"][nz[0]])
+        if kind == "not_sorted":
+            d["ts"][b + 1] = d["ts"][b] - 1 if d["ts"][b] > 0 else 0
+            d["ts"][b] = d["ts"][b] + 5
+        elif kind == "bad_ctx":
+            d["ctx"][b] = len(d["parent"])
+        elif kind == "two_roots":
+            d["parent"] = d["parent"].copy()
+            nonroot = np.nonzero(d["parent"] != NONE)[0]
+            d["parent"][nonroot[0]] = NONE
+        elif kind == "cycle":
+            C = len(d["parent"])
+            d["parent"] = np.array([NONE] + [(v % (C - 1)) + 1 for v in range(1, C)], np.uint32)
+        elif kind == "rank_off":
+            d["rank_off"][1] = d["rank_off"][-1] + 1
+        elif kind == "marker":
+            d["marker"] = len(d["parent"])
+        return d
+
+    for kind, code in [("not_sorted", ta.NOT_SORTED), ("bad_ctx", ta.BAD_CTX),
+                       ("two_roots", ta.BAD_CCT), ("cycle", ta.BAD_CCT),
+                       ("rank_off", ta.INVALID_ARG), ("marker", ta.INVALID_ARG)]:
+        d = variant(kind)
+        tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+        if kind in ("not_sorted", "bad_ctx", "two_roots", "cycle", "rank_off"):
+            assert oracle.validate(tr) == code, kind
+        assert load(d) == code, kind
+    # the context is still usable afterwards
+    tr, a, e = load_both(base)
+    check_products(tr, a, e)
