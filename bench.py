@@ -1,0 +1,426 @@
+#!/usr/bin/env python3
+"""Benchmark of the trace-analysis hot path on B300.
+
+One step = one pass of the whole path over one trace set resident in HBM:
+ingest (validate, durations, iteration cut, the rank x iteration x context
+tensor, exclusive and inclusive per-rank CSR), cross-rank statistics with
+outliers over every context, the rack rollup of a communication context, and
+the potential-speedup estimate over the iteration program's contexts.
+
+Prints one JSON line (see --help).  ``--impl reference`` times the CPU oracle
+(the plain single-threaded definition) on a bounded sample of the same
+workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "trace records/s & HBM GB/s vs peak (batched vs plain); query p50/p99 latency"
+WORKLOADS = {
+    1: "plain: R=64 ranks x 20k samples, C=200, I=10, 2 ranks slowed 1.5x",
+    2: "plain: R=4096 ranks, C=5000 (depth<=24), lognormal lengths mean 100k sigma 0.5, I=50, "
+       "jitter 5%, 1% of ranks 1.2-2x on random iterations",
+    3: "plain at scale: R=100,000 ranks, C=20,000, lognormal lengths mean 20k sigma 0.7 "
+       "(~2e9 records), I=100, 12 ranks/node, 22 racks, 3 racks 1.3x slower in communication "
+       "contexts",
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- workload --
+def make_workload(preset: int, seed: int = 1, pinned: bool = True):
+    """Generate the synthetic trace set on the host (pinned memory)."""
+    import torch
+    from paper_2605_03561_b300 import synth
+    cfg = synth.preset(preset, seed=seed)
+    rank_off, parent, info = synth.plan(cfg)
+    N = int(rank_off[-1])
+    t0 = time.time()
+    ts = torch.empty(N, dtype=torch.uint64, pin_memory=pinned)
+    cx = torch.empty(N, dtype=torch.uint32, pin_memory=pinned)
+    synth.fill(cfg, rank_off, 0, cfg.n_ranks, ts.data_ptr(), cx.data_ptr(), 0)
+    log(f"generated {N} records in {time.time() - t0:.1f} s")
+    truth = synth.truth(cfg, info)
+    topo = synth.topology(cfg, info)
+    return dict(cfg=cfg, info=info, rank_off=rank_off, parent=parent, ts=ts, ctx=cx, N=N,
+                marker=cfg.marker_ctx, truth=truth, topo=topo)
+
+
+def analysis_args(w):
+    segs = np.unique(w["truth"]["segment_ctx"]).astype(np.uint32)
+    comm = w["truth"]["segment_ctx"][w["truth"]["comm_segment"].astype(bool)]
+    return dict(kset=segs, topo_ctx=int(comm[0]) if len(comm) else int(segs[0]))
+
+
+# ------------------------------------------------------- device-side calls --
+class DeviceCalls:
+    """ta_context_stats / ta_topology_rollup / ta_potential_speedup with every
+    output in preallocated device buffers (no host copies inside the step)."""
+
+    def __init__(self, ta, w, args, device=0):
+        import torch
+        self.ta, self.torch = ta, torch
+        dev = f"cuda:{device}"
+        C_ = len(w["parent"])
+        topo = w["topo"]
+        self.nn, self.nc, self.nr = int(topo["n_nodes"]), int(topo["n_chassis"]), int(topo["n_racks"])
+        self.stats = torch.empty(C_ * C.sizeof(ta.CtxStats), dtype=torch.uint8, device=dev)
+        self.outlier_cap = 1 << 20
+        self.outliers = torch.empty(self.outlier_cap * C.sizeof(ta.Outlier), dtype=torch.uint8,
+                                    device=dev)
+        self.node = torch.from_numpy(topo["node_of_rank"]).to(dev)
+        self.rack = torch.from_numpy(topo["rack_of_node"]).to(dev)
+        self.chassis = torch.from_numpy(topo["chassis_of_node"]).to(dev)
+        u32, u64 = torch.uint32, torch.uint64
+        self.o = {k: torch.empty(n, dtype=t, device=dev) for k, n, t in [
+            ("node_outliers", self.nn, u32), ("node_sum", self.nn, u64), ("node_ranks", self.nn, u32),
+            ("node_flag", self.nn, torch.uint8), ("chassis_flagged", self.nc, u32),
+            ("chassis_nodes", self.nc, u32), ("chassis_sum", self.nc, u64),
+            ("rack_flagged", self.nr, u32), ("rack_nodes", self.nr, u32),
+            ("rack_sum", self.nr, u64), ("flagged_racks", self.nr, u32)]}
+        self.kset = torch.from_numpy(args["kset"]).to(dev)
+        self.nk = len(args["kset"])
+        self.per = torch.empty(self.nk * C.sizeof(ta.SpeedupCtx), dtype=torch.uint8, device=dev)
+        self.tot = torch.empty(C.sizeof(ta.SpeedupTotal), dtype=torch.uint8, device=dev)
+        self.topo_ctx = args["topo_ctx"]
+
+    def run(self, e):
+        ta = self.ta
+        a = ta.StatsArgs()
+        a.metric, a.mem_kind, a.tau_num, a.tau_den = ta.EXCLUSIVE, ta.MEM_DEVICE, 3, 1
+        o = ta.StatsOut()
+        o.stats, o.outliers, o.outlier_cap = self.stats.data_ptr(), self.outliers.data_ptr(), self.outlier_cap
+        ta._check(ta.lib().ta_context_stats(e.h, C.byref(a), C.byref(o)))
+        t = ta.Topology()
+        t.n_nodes, t.n_chassis, t.n_racks, t.mem_kind = self.nn, self.nc, self.nr, ta.MEM_DEVICE
+        t.node_of_rank, t.rack_of_node, t.chassis_of_node = (
+            self.node.data_ptr(), self.rack.data_ptr(), self.chassis.data_ptr())
+        ta_ = ta.TopoArgs()
+        ta_.metric, ta_.ctx, ta_.tau_num, ta_.tau_den, ta_.min_ranks = ta.EXCLUSIVE, self.topo_ctx, 2, 1, 1
+        to = ta.TopoOut()
+        to.mem_kind = ta.MEM_DEVICE
+        for k, v in self.o.items():
+            setattr(to, k, v.data_ptr())
+        ta._check(ta.lib().ta_topology_rollup(e.h, C.byref(t), C.byref(ta_), C.byref(to)))
+        sa = ta.SpeedupArgs()
+        sa.mem_kind, sa.n_ctxs, sa.ctxs = ta.MEM_DEVICE, self.nk, self.kset.data_ptr()
+        so = ta.SpeedupOut()
+        so.per_ctx, so.total = self.per.data_ptr(), self.tot.data_ptr()
+        ta._check(ta.lib().ta_potential_speedup(e.h, C.byref(sa), C.byref(so)))
+        return int(o.n_outliers)
+
+
+def host_calls(e, w, args):
+    """The same three calls with host outputs (the user-facing e2e form)."""
+    topo = w["topo"]
+    st, outl, n_out, _ = e.stats(0, tau=(3, 1))
+    tp = e.topology(args["topo_ctx"], topo["node_of_rank"], topo["rack_of_node"],
+                    topo["chassis_of_node"], topo["n_racks"], topo["n_chassis"], tau=(2, 1))
+    sp = e.speedup(args["kset"])
+    C_ = len(w["parent"])
+    nn, nc, nr = topo["n_nodes"], topo["n_chassis"], topo["n_racks"]
+    d2h = (C_ * C.sizeof(__import__("paper_2605_03561_b300").CtxStats) + n_out * 16 +
+           nn * (4 + 8 + 4 + 1) + nc * 16 + nr * 20 + len(args["kset"]) * 88 + 48)
+    return d2h
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- baselines --
+def oracle_sample(w, n_ranks, args):
+    """Run the oracle on ranks [0, n_ranks) of the workload; returns (records, s)."""
+    import oracle
+    ro = w["rank_off"][: n_ranks + 1].copy()
+    n = int(ro[-1])
+    ts = w["ts"][:n].numpy()
+    cx = w["ctx"][:n].numpy()
+    tr = oracle.Traces(ro, ts, cx, w["parent"], w["marker"])
+    topo = w["topo"]
+    node = topo["node_of_rank"][:n_ranks]
+    nn = int(node.max()) + 1
+    t0 = time.perf_counter()
+    a = oracle.Analysis(tr)
+    a.stats(0, tau=(3, 1))
+    a.topology(args["topo_ctx"], node, topo["rack_of_node"][:nn], topo["chassis_of_node"][:nn],
+               topo["n_racks"], topo["n_chassis"], tau=(2, 1))
+    a.speedup(args["kset"])
+    return n, time.perf_counter() - t0
+
+
+def pick_sample(w, target_records):
+    ro = w["rank_off"]
+    k = int(np.searchsorted(ro, target_records))
+    return max(1, min(k, len(ro) - 1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def committed_traffic(preset):
+    """Per-launch DRAM traffic of the tensor kernel from a committed ncu
+    summary, if the kernel source is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_tensor_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2605_03561_b300", "csrc", "ingest.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("ingest_cu_sha256_16") != h:
+        return None
+    return d.get("per_record_bytes")
+
+
+# --------------------------------------------------------------------- arms --
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.config, pinned=False)
+    aa = analysis_args(w)
+    k = pick_sample(w, args.ref_records)
+    recs = 0
+    secs = 0.0
+    for i in range(args.warmup + args.steps):
+        n, s = oracle_sample(w, k, aa)
+        if i >= args.warmup:
+            recs += n
+            secs += s
+    v = recs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "records/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "sample_ranks": k,
+                       "sample_records": recs // args.steps},
+            "cpu_baseline": {"value": v, "unit": "records/s", "cores": 1, "kind": "oracle",
+                             "sample": f"ranks [0, {k}) of the workload per step"},
+            "e2e": {"value": v, "unit": "records/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import paper_2605_03561_b300 as ta
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    w = make_workload(args.config, seed=1 + rank)
+    aa = analysis_args(w)
+    N, R = w["N"], len(w["rank_off"]) - 1
+    dev = f"cuda:{local}"
+    d_ro = torch.from_numpy(w["rank_off"]).to(dev)
+    d_par = torch.from_numpy(w["parent"]).to(dev)
+    d_ts = w["ts"].to(dev, non_blocking=True)
+    d_cx = w["ctx"].to(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    ctx = ta.Context(local)
+    calls = DeviceCalls(ta, w, aa, local)
+    stream = ctx.stream
+
+    def step():
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        n_out = calls.run(e)
+        info = e.info()
+        e.free()
+        return info, n_out
+
+    for _ in range(args.warmup):
+        info, n_out = step()
+    torch.cuda.synchronize()
+    ctx.profile(reset=True)
+    launches0 = ctx.launches()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        info, n_out = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t[0])
+    clk = clocks.stop()
+    prof = ctx.profile(reset=True)
+    launches = ctx.launches() - launches0
+    ms_step = ms / args.steps
+    value = world * N * args.steps / (ms / 1000.0)
+
+    # dominant kernel: the iteration-tensor kernel, timed with events on its stream
+    peaks, peak_kind = measured_peaks()
+    n_l = max(1, prof["tensor_launches"])
+    t_launch = prof["tensor_ms"] / n_l / 1000.0
+    alg_bytes = (12 * prof["tensor_records"] + 16 * prof["tensor_entries"]
+                 + 8 * prof["tensor_rows"] + 8 * (R + 1) * prof["tensor_launches"]) / n_l
+    achieved = alg_bytes / t_launch / 1e9
+    per_rec = committed_traffic(args.config)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": (per_rec * prof["tensor_records"] / n_l) if per_rec else None,
+                "kernel": "k_tensor", "peak_kind": peak_kind,
+                "frac_of_8TBs_nominal": achieved / 8000.0,
+                "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_launch * 1e3}
+    step_bytes = alg_bytes  # the step's HBM floor is dominated by the tensor pass
+
+    # e2e: the user-facing call with host (pinned) inputs and host outputs
+    e2e = None
+    if not args.no_e2e:
+        del d_ts, d_cx
+        torch.cuda.empty_cache()
+        h_ro, h_par = w["rank_off"], w["parent"]
+        h_ts, h_cx = w["ts"].numpy(), w["ctx"].numpy()
+        k_e2e = max(1, min(args.steps, 3))
+        for _ in range(1):
+            e = ctx.load(h_ro, h_ts, h_cx, h_par, w["marker"])
+            host_calls(e, w, aa)
+            e.free()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d2h = 0
+        for _ in range(k_e2e):
+            e = ctx.load(h_ro, h_ts, h_cx, h_par, w["marker"])
+            d2h = host_calls(e, w, aa)
+            e.free()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        h2d = 8 * (R + 1) + 12 * N + 4 * len(h_par) + 4 * (R + 2 * len(w["topo"]["rack_of_node"])) + 4 * len(aa["kset"])
+        e2e = {"value": world * N * k_e2e / el, "unit": "records/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": k_e2e, "s_per_step": el / k_e2e}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        k = pick_sample(w, args.cpu_records)
+        n, s = oracle_sample(w, k, aa)
+        cpu = {"value": n / s, "unit": "records/s", "cores": 1, "kind": "oracle",
+               "sample": f"ranks [0, {k}) = {n} records of the same workload, whole path "
+                         f"(analysis, stats over all contexts, rack rollup, speedup); {s:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "records": N, "ranks": R,
+                           "contexts": len(w["parent"]), "tensor_rows": info["n_rows"],
+                           "tensor_entries": info["tensor_nnz"],
+                           "exclusive_entries": info["excl_nnz"],
+                           "inclusive_entries": info["incl_nnz"], "outliers": n_out,
+                           "l2": "inputs (12 B x records) far exceed the 126 MB L2; no flush",
+                           "step": "ingest + tensor + exclusive + inclusive + stats(all ctx) + "
+                                   "rack rollup + speedup",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "hbm_gbs_step": step_bytes / (ms_step / 1000.0) / 1e9 * 1.0,
+                "phase_ms_per_step": {k: prof[k] / args.steps for k in
+                                      ("validate_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
+                                       "stats_ms", "topology_ms", "speedup_ms")},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    p = argparse.ArgumentParser(description=__doc__)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", type=int, default=3, choices=[1, 2, 3])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-records", type=float, default=1.5e7)
+    p.add_argument("--ref-records", type=float, default=5e6)
+    args = p.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

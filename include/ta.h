@@ -93,6 +93,17 @@ const char* ta_status_string(ta_status s);
 /* Number of kernel launches the library has issued on this context so far. */
 uint64_t ta_kernel_launches(const ta_ctx* ctx);
 
+/* Device time of the library's phases on this context, measured with CUDA
+ * events recorded on the context's stream around each phase, accumulated
+ * since the last reset; plus the units the iteration-tensor kernel processed
+ * (samples read, entries and rows written) for bytes-per-launch accounting. */
+typedef struct ta_profile {
+  double validate_ms, tensor_ms, exclusive_ms, inclusive_ms;
+  double stats_ms, topology_ms, speedup_ms;
+  uint64_t tensor_launches, tensor_records, tensor_entries, tensor_rows;
+} ta_profile;
+ta_status ta_get_profile(ta_ctx* ctx, ta_profile* out, int reset);
+
 /* --------------------------------------------------------- ingestion ---- */
 
 /* Execution traces (Section II-A: per rank a time-ordered list of samples,

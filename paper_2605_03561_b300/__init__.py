@@ -117,6 +117,14 @@ class SpeedupTotal(C.Structure):
                 ("total_reduction", C.c_double), ("speedup_fraction", C.c_double)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("validate_ms", C.c_double), ("tensor_ms", C.c_double),
+                ("exclusive_ms", C.c_double), ("inclusive_ms", C.c_double),
+                ("stats_ms", C.c_double), ("topology_ms", C.c_double), ("speedup_ms", C.c_double),
+                ("tensor_launches", u64), ("tensor_records", u64), ("tensor_entries", u64),
+                ("tensor_rows", u64)]
+
+
 class SpeedupOut(C.Structure):
     _fields_ = [("per_ctx", P), ("total", P)]
 
@@ -132,6 +140,7 @@ _SIGS = {
     "ta_last_error_message": (C.c_char_p, []),
     "ta_status_string": (C.c_char_p, [C.c_int]),
     "ta_kernel_launches": (u64, [P]),
+    "ta_get_profile": (C.c_int, [P, C.POINTER(Profile), C.c_int]),
     "ta_load_traces": (C.c_int, [P, C.POINTER(TraceDesc), C.POINTER(P)]),
     "ta_experiment_free": (C.c_int, [P]),
     "ta_experiment_get_info": (C.c_int, [P, C.POINTER(ExperimentInfo)]),
@@ -175,7 +184,7 @@ def lib():
 
 class _CudaArray:
     def __init__(self, ptr, n, typestr):
-        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, True),
+        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, False),
                                              version=3, strides=None)
 
 
@@ -247,6 +256,11 @@ class Context:
 
     def sync(self):
         _check(lib().ta_sync(self.h))
+
+    def profile(self, reset: bool = False) -> dict:
+        p = Profile()
+        _check(lib().ta_get_profile(self.h, C.byref(p), 1 if reset else 0))
+        return {f: getattr(p, f) for f, _ in Profile._fields_}
 
     def close(self):
         if getattr(self, "h", None):

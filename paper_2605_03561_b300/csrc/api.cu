@@ -128,6 +128,8 @@ ta_status ta_create(int device, void* stream, ta_ctx** out) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaEventCreate(&c->ev[0]);
+  cudaEventCreate(&c->ev[1]);
   *out = c;
   return TA_OK;
 }
@@ -135,6 +137,8 @@ ta_status ta_create(int device, void* stream, ta_ctx** out) {
 ta_status ta_destroy(ta_ctx* c) {
   if (!c) return TA_OK;
   cudaStreamSynchronize(c->stream);
+  if (c->ev[0]) cudaEventDestroy(c->ev[0]);
+  if (c->ev[1]) cudaEventDestroy(c->ev[1]);
   delete c;
   return TA_OK;
 }
@@ -155,6 +159,13 @@ ta_status ta_sync(ta_ctx* c) {
 }
 
 uint64_t ta_kernel_launches(const ta_ctx* c) { return c ? c->launches : 0; }
+
+ta_status ta_get_profile(ta_ctx* c, ta_profile* out, int reset) {
+  if (!c) return fail(TA_ERR_INVALID_ARG, "ta_get_profile: ctx is NULL");
+  if (out) *out = c->prof;
+  if (reset) c->prof = ta_profile{};
+  return TA_OK;
+}
 
 }  // extern "C"
 
@@ -256,10 +267,16 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     A.gst_cnt = gcnt;
     A.gst_cap = P.gst_cap;
     A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+    PhaseTimer timer(c, &c->prof.tensor_ms);
     launch_tensor(L, P, A);
+    timer.stop_and_sync();
     u64 h[3];
     TRY(copy(c, h, meta, sizeof h));
     TRY(sync_check(c, "iteration tensor"));
+    c->prof.tensor_launches += 1;
+    c->prof.tensor_records += N;
+    c->prof.tensor_entries += h[2];
+    c->prof.tensor_rows += h[1];
     const u32 f = (u32)(h[0] >> 32);
     TRY(status_from_flags(f, "ta_load_traces"));
     e->rows = h[1];
@@ -344,7 +361,9 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
     A.gst_cnt = gcnt;
     A.gst_cap = P.gst_cap;
     A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+    PhaseTimer timer(c, mode == 0 ? &c->prof.exclusive_ms : &c->prof.inclusive_ms);
     launch_rank_csr(L, P, A);
+    timer.stop_and_sync();
     u64 h[2];
     TRY(copy(c, h, meta, sizeof h));
     TRY(sync_check(c, mode == 0 ? "exclusive" : "inclusive"));
@@ -392,8 +411,10 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   TRY(tmp.get((u64)C * 16, (void**)&scratch, "tree scratch"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
   u32* status = (u32*)meta;
+  PhaseTimer timer(c, &c->prof.validate_ms);
   launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status);
   launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status);
+  timer.stop_and_sync();
   u64 h[3];
   TRY(copy(c, h, meta, sizeof h));
   TRY(sync_check(c, "validation"));

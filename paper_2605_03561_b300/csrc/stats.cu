@@ -658,6 +658,7 @@ ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_ou
   ta_ctx* c = e->ctx;
   cudaSetDevice(c->device);
   Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.stats_ms);
   Pool tmp{c, {}};
   struct Rel {
     Pool& p;
@@ -718,6 +719,7 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
   ta_ctx* c = e->ctx;
   cudaSetDevice(c->device);
   Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.topology_ms);
   Pool tmp{c, {}};
   struct Rel {
     Pool& p;
@@ -822,6 +824,7 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   ta_ctx* c = e->ctx;
   cudaSetDevice(c->device);
   Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.speedup_ms);
   Pool tmp{c, {}};
   struct Rel {
     Pool& p;

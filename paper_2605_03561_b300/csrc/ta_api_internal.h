@@ -15,6 +15,8 @@ struct ta_ctx {
   ta_free_fn free_fn = nullptr;
   void* user = nullptr;
   unsigned long long launches = 0;
+  ta_profile prof{};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
 namespace ta {
@@ -51,6 +53,25 @@ void dfree(ta_ctx* c, void* p, size_t bytes);
 ta_status sync_check(ta_ctx* c, const char* what);
 ta_status copy(ta_ctx* c, void* dst, const void* src, size_t bytes);
 ta_status status_from_flags(u32 f, const char* where);
+
+// Device time between two points on the context's stream (profiling).
+struct PhaseTimer {
+  ta_ctx* c;
+  double* acc;
+  bool done = false;
+  PhaseTimer(ta_ctx* c_, double* acc_) : c(c_), acc(acc_) { cudaEventRecord(c->ev[0], c->stream); }
+  ~PhaseTimer() {
+    if (!done) stop_and_sync();
+  }
+  // Records the end of the phase on the stream and waits for it.
+  void stop_and_sync() {
+    done = true;
+    cudaEventRecord(c->ev[1], c->stream);
+    cudaEventSynchronize(c->ev[1]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) *acc += ms;
+  }
+};
 
 }  // namespace ta
 

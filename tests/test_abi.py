@@ -17,7 +17,8 @@ STRUCTS = {"ta_trace_desc": ta.TraceDesc, "ta_experiment_info": ta.ExperimentInf
            "ta_outlier": ta.Outlier, "ta_stats_out": ta.StatsOut, "ta_topology": ta.Topology,
            "ta_topo_args": ta.TopoArgs, "ta_topo_out": ta.TopoOut,
            "ta_speedup_args": ta.SpeedupArgs, "ta_speedup_ctx": ta.SpeedupCtx,
-           "ta_speedup_total": ta.SpeedupTotal, "ta_speedup_out": ta.SpeedupOut}
+           "ta_speedup_total": ta.SpeedupTotal, "ta_speedup_out": ta.SpeedupOut,
+           "ta_profile": ta.Profile}
 
 
 def test_library_builds_and_exports_every_declared_symbol():
