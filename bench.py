@@ -44,11 +44,13 @@ def log(*a):
 
 
 # ----------------------------------------------------------------- workload --
-def make_workload(preset: int, seed: int = 1, pinned: bool = True):
+def make_workload(preset: int, seed: int = 1, pinned: bool = True, ranks: int = 0):
     """Generate the synthetic trace set on the host (pinned memory)."""
     import torch
     from paper_2605_03561_b300 import synth
     cfg = synth.preset(preset, seed=seed)
+    if ranks:
+        cfg.n_ranks = ranks
     rank_off, parent, info = synth.plan(cfg)
     N = int(rank_off[-1])
     t0 = time.time()
@@ -249,7 +251,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = make_workload(args.config, pinned=False)
+    w = make_workload(args.config, pinned=False, ranks=args.ranks)
     aa = analysis_args(w)
     k = pick_sample(w, args.ref_records)
     recs = 0
@@ -264,7 +266,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * secs / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "sample_ranks": k,
+            "config": {"workload": WORKLOADS[args.config] + (f" (ranks={args.ranks})" if args.ranks else ""), "sample_ranks": k,
                        "sample_records": recs // args.steps},
             "cpu_baseline": {"value": v, "unit": "records/s", "cores": 1, "kind": "oracle",
                              "sample": f"ranks [0, {k}) of the workload per step"},
@@ -283,7 +285,7 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("gloo")
     torch.cuda.set_device(local)
-    w = make_workload(args.config, seed=1 + rank)
+    w = make_workload(args.config, seed=1 + rank, ranks=args.ranks)
     aa = analysis_args(w)
     N, R = w["N"], len(w["rank_off"]) - 1
     dev = f"cuda:{local}"
@@ -384,7 +386,8 @@ def run_gpu(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "u64", "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.config], "records": N, "ranks": R,
+                "config": {"workload": WORKLOADS[args.config] + (f" (ranks={args.ranks})" if args.ranks else ""),
+                           "records": N, "ranks": R,
                            "contexts": len(w["parent"]), "tensor_rows": info["n_rows"],
                            "tensor_entries": info["tensor_nnz"],
                            "exclusive_entries": info["excl_nnz"],
@@ -395,7 +398,7 @@ def run_gpu(args):
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "hbm_gbs_step": step_bytes / (ms_step / 1000.0) / 1e9 * 1.0,
                 "phase_ms_per_step": {k: prof[k] / args.steps for k in
-                                      ("validate_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
+                                      ("validate_ms", "tensor_count_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk}
@@ -411,9 +414,11 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=3, choices=[1, 2, 3])
+    p.add_argument("--ranks", type=int, default=0,
+                   help="override the rank count (smaller cases for profiling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-records", type=float, default=1.5e7)
+    p.add_argument("--cpu-records", type=float, default=1.5e8)
     p.add_argument("--ref-records", type=float, default=5e6)
     args = p.parse_args()
     if args.impl == "reference":

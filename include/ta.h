@@ -98,7 +98,10 @@ uint64_t ta_kernel_launches(const ta_ctx* ctx);
  * since the last reset; plus the units the iteration-tensor kernel processed
  * (samples read, entries and rows written) for bytes-per-launch accounting. */
 typedef struct ta_profile {
-  double validate_ms, tensor_ms, exclusive_ms, inclusive_ms;
+  double validate_ms;
+  double tensor_count_ms; /* tensor count pass + tile scan                 */
+  double tensor_ms;       /* tensor write pass (the dominant kernel)       */
+  double exclusive_ms, inclusive_ms;
   double stats_ms, topology_ms, speedup_ms;
   uint64_t tensor_launches, tensor_records, tensor_entries, tensor_rows;
 } ta_profile;

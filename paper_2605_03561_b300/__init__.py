@@ -118,7 +118,8 @@ class SpeedupTotal(C.Structure):
 
 
 class Profile(C.Structure):
-    _fields_ = [("validate_ms", C.c_double), ("tensor_ms", C.c_double),
+    _fields_ = [("validate_ms", C.c_double), ("tensor_count_ms", C.c_double),
+                ("tensor_ms", C.c_double),
                 ("exclusive_ms", C.c_double), ("inclusive_ms", C.c_double),
                 ("stats_ms", C.c_double), ("topology_ms", C.c_double), ("speedup_ms", C.c_double),
                 ("tensor_launches", u64), ("tensor_records", u64), ("tensor_entries", u64),

@@ -202,181 +202,168 @@ void ta_experiment::disown(void* p) {
 
 namespace {
 
-// Tensor pass with exact-capacity retry.
+// Tensor: count pass, scan of per-tile counts, exact allocation, write pass.
 ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
+  (void)d;
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const u64 N = e->N;
   const u32 R = e->R;
   TensorPlan P = plan_tensor(e->C, N, c->num_sms);
-  const u32 n_tiles = (u32)std::max<u64>(1, (N + P.tile - 1) / P.tile);
-  u32* tfr;
-  TRY(tmp.get((n_tiles + 1) * sizeof(u32), (void**)&tfr, "tile map"));
-  launch_tile_first_rank(L, e->rank_off, R, P.tile, n_tiles, tfr);
-  UnitStatus* ustat;
-  TRY(tmp.get((size_t)n_tiles * sizeof(UnitStatus), (void**)&ustat, "tile status"));
-  u64* meta;  // [0] counter|status, [1..2] totals
+  const u64 n_tiles = std::max<u64>(1, (N + P.tile - 1) / P.tile);
+  TensorArgs A;
+  std::memset(&A, 0, sizeof A);
+  TRY(tmp.get_n(n_tiles + 1, (u32**)&A.tfr, "tile map"));
+  launch_tile_first_rank(L, e->rank_off, R, P.tile, (u32)n_tiles, (u32*)A.tfr);
+  TRY(tmp.get_n(n_tiles, &A.tile_rows, "tile rows"));
+  TRY(tmp.get_n(n_tiles, &A.tile_ents, "tile entries"));
+  TRY(tmp.get_n(n_tiles, &A.tile_row_off, "tile row offsets"));
+  TRY(tmp.get_n(n_tiles, &A.tile_ent_off, "tile entry offsets"));
+  u64* meta;  // [0] status, [1..2] totals
   TRY(tmp.get(64, (void**)&meta, "tensor meta"));
-  u32* gbm = nullptr;
+  TRY(tmp.get_n(2 * scan_scratch_elems(n_tiles), &A.scan_scratch, "tile scan"));
+  cudaMemsetAsync(meta, 0, 64, c->stream);
   const u32 W = P.threads / 32;
   const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.grid * W * bm_words(e->C) * 4;
-  if (gbm_bytes) TRY(tmp.get(gbm_bytes, (void**)&gbm, "tensor bitmaps"));
-  u32 *gctx, *gcnt;
-  u64* gtime;
-  const size_t gn = (size_t)P.grid * P.gst_cap;
-  TRY(tmp.get(gn * 4, (void**)&gctx, "tensor stage"));
-  TRY(tmp.get(gn * 4, (void**)&gcnt, "tensor stage"));
-  TRY(tmp.get(gn * 8, (void**)&gtime, "tensor stage"));
-
-  const bool small = N <= (1u << 20);
-  u64 rows_cap = d->rows_hint ? d->rows_hint : (u64)R + (small ? N : N / 8) + 2;
-  u64 nnz_cap = d->nnz_hint ? d->nnz_hint : (small ? N : N / 2) + 16;
-  TRY(e->own(((u64)R + 1) * 8, (void**)&e->row_off, "row_off_of_rank"));
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    TRY(e->own((rows_cap) * 8, (void**)&e->entry_off, "entry_off"));
-    TRY(e->own(nnz_cap * 4, (void**)&e->e_ctx, "e_ctx"));
-    TRY(e->own(nnz_cap * 8, (void**)&e->e_time, "e_time"));
-    TRY(e->own(nnz_cap * 4, (void**)&e->e_cnt, "e_cnt"));
-    cudaMemsetAsync(ustat, 0, (size_t)n_tiles * sizeof(UnitStatus), c->stream);
-    cudaMemsetAsync(meta, 0, 64, c->stream);
-    if (gbm) cudaMemsetAsync(gbm, 0, gbm_bytes, c->stream);
-    TensorArgs A;
-    A.rank_off = e->rank_off;
-    A.ts = e->ts;
-    A.ctx = e->ctxv;
-    A.R = R;
-    A.C = e->C;
-    A.m = e->m;
-    A.n_tiles = n_tiles;
-    A.N = N;
-    A.tfr = tfr;
-    A.unit_counter = (u32*)meta;
-    A.status = (u32*)meta + 1;
-    A.totals = meta + 1;
-    A.ustat = ustat;
-    A.row_off_of_rank = e->row_off;
-    A.entry_off = e->entry_off;
-    A.e_ctx = e->e_ctx;
-    A.e_time = e->e_time;
-    A.e_cnt = e->e_cnt;
-    A.rows_cap = rows_cap;
-    A.nnz_cap = nnz_cap;
-    A.gbm = gbm;
-    A.gst_ctx = gctx;
-    A.gst_time = gtime;
-    A.gst_cnt = gcnt;
-    A.gst_cap = P.gst_cap;
-    A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
-    PhaseTimer timer(c, &c->prof.tensor_ms);
-    launch_tensor(L, P, A);
-    timer.stop_and_sync();
-    u64 h[3];
-    TRY(copy(c, h, meta, sizeof h));
-    TRY(sync_check(c, "iteration tensor"));
-    c->prof.tensor_launches += 1;
-    c->prof.tensor_records += N;
-    c->prof.tensor_entries += h[2];
-    c->prof.tensor_rows += h[1];
-    const u32 f = (u32)(h[0] >> 32);
-    TRY(status_from_flags(f, "ta_load_traces"));
-    e->rows = h[1];
-    e->nnz = h[2];
-    if (!(f & F_CAPACITY)) return TA_OK;
-    // Too small a first guess: free and retry with the exact sizes.
-    e->disown(e->entry_off);
-    e->disown(e->e_ctx);
-    e->disown(e->e_time);
-    e->disown(e->e_cnt);
-    rows_cap = e->rows + 1;
-    nnz_cap = std::max<u64>(e->nnz, 1);
+  if (gbm_bytes) {
+    TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "tensor bitmaps"));
+    cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
   }
-  return fail(TA_ERR_CUDA, "iteration tensor: capacity retry failed");
+  const size_t gn = (size_t)P.grid * W * P.gst_cap;
+  TRY(tmp.get_n(gn, &A.gst_ctx, "tensor stage"));
+  TRY(tmp.get_n(gn, &A.gst_cnt, "tensor stage"));
+  TRY(tmp.get_n(gn, &A.gst_time, "tensor stage"));
+  A.rank_off = e->rank_off;
+  A.ts = e->ts;
+  A.ctx = e->ctxv;
+  A.R = R;
+  A.C = e->C;
+  A.m = e->m;
+  A.n_tiles = n_tiles;
+  A.N = N;
+  A.status = (u32*)meta;
+  A.totals = meta + 1;
+  A.gst_cap = P.gst_cap;
+  A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+  {
+    PhaseTimer timer(c, &c->prof.tensor_count_ms);
+    launch_tensor_count(L, P, A);
+    launch_tile_scan(L, A);
+    timer.stop_and_sync();
+  }
+  u64 h[3];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, "iteration tensor (count)"));
+  TRY(status_from_flags((u32)h[0], "ta_load_traces"));
+  e->rows = h[1];
+  e->nnz = h[2];
+  TRY(e->own((u64)(R + 1) * 8, (void**)&e->row_off, "row_off_of_rank"));
+  TRY(e->own((e->rows + 1) * 8, (void**)&e->entry_off, "entry_off"));
+  TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&e->e_ctx, "e_ctx"));
+  TRY(e->own(std::max<u64>(e->nnz, 1) * 8, (void**)&e->e_time, "e_time"));
+  TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&e->e_cnt, "e_cnt"));
+  TRY(copy(c, e->row_off + R, &e->rows, 8));
+  TRY(copy(c, e->entry_off + e->rows, &e->nnz, 8));
+  A.row_off_of_rank = e->row_off;
+  A.entry_off = e->entry_off;
+  A.e_ctx = e->e_ctx;
+  A.e_time = e->e_time;
+  A.e_cnt = e->e_cnt;
+  {
+    PhaseTimer timer(c, &c->prof.tensor_ms);
+    launch_tensor_write(L, P, A);
+    timer.stop_and_sync();
+  }
+  u64 f = 0;
+  TRY(copy(c, &f, meta, 8));
+  TRY(sync_check(c, "iteration tensor (write)"));
+  TRY(status_from_flags((u32)f, "ta_load_traces"));
+  c->prof.tensor_launches += 1;
+  c->prof.tensor_records += N;
+  c->prof.tensor_entries += e->nnz;
+  c->prof.tensor_rows += e->rows;
+  return TA_OK;
 }
 
-// Exclusive (mode 0) or inclusive (mode 1) per-rank CSR with retry.
+// Exclusive (mode 0) or inclusive (mode 1) per-rank CSR: count, scan, exact
+// allocation, write.
 ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const u32 R = e->R;
   RankCsrPlan P = plan_rank_csr(R, e->C, c->num_sms);
-  UnitStatus* ustat;
-  TRY(tmp.get((size_t)P.n_units * sizeof(UnitStatus), (void**)&ustat, "unit status"));
+  RankCsrArgs A;
+  std::memset(&A, 0, sizeof A);
   u64* meta;
   TRY(tmp.get(64, (void**)&meta, "csr meta"));
-  u32* gbm = nullptr;
+  cudaMemsetAsync(meta, 0, 64, c->stream);
   const size_t gbm_bytes =
       P.bm_in_smem ? 0 : (size_t)P.grid * (P.threads / 32) * bm_words(e->C) * 4;
-  if (gbm_bytes) TRY(tmp.get(gbm_bytes, (void**)&gbm, "csr bitmaps"));
-  u32 *gctx, *gcnt;
-  u64* gtime;
-  const size_t gn = (size_t)P.grid * P.gst_cap;
-  TRY(tmp.get(gn * 4, (void**)&gctx, "csr stage"));
-  TRY(tmp.get(gn * 4, (void**)&gcnt, "csr stage"));
-  TRY(tmp.get(gn * 8, (void**)&gtime, "csr stage"));
-  u64 cap;
-  if (mode == 0) cap = std::min<u64>(e->nnz, (u64)R * 160 + 4096);
-  else cap = std::min<u64>((u64)R * e->C, 3 * e->x.nnz + (u64)R * 64 + 4096);
-  cap = std::max<u64>(cap, 1);
+  if (gbm_bytes) {
+    TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "csr bitmaps"));
+    cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
+  }
+  const size_t gn = (size_t)P.grid * (P.threads / 32) * P.gst_cap;
+  TRY(tmp.get_n(gn, &A.gst_ctx, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_cnt, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_time, "csr stage"));
+  if (mode == 1) {
+    TRY(tmp.get_n(gn, &A.gst_dep, "csr stage"));
+    TRY(tmp.get_n(gn, &A.gst_par, "csr stage"));
+  }
+  TRY(tmp.get_n((u64)R, &A.out_cnt, "csr counts"));
+  TRY(tmp.get_n(scan_scratch_elems(R), &A.scan_scratch, "csr scan"));
   Csr& out = mode == 0 ? e->x : e->in;
   TRY(e->own(((u64)R + 1) * 8, (void**)&out.off, "csr off"));
-  for (int attempt = 0; attempt < 2; ++attempt) {
-    TRY(e->own(cap * 4, (void**)&out.ctx, "csr ctx"));
-    TRY(e->own(cap * 8, (void**)&out.time, "csr time"));
-    TRY(e->own(cap * 4, (void**)&out.cnt, "csr cnt"));
-    cudaMemsetAsync(ustat, 0, (size_t)P.n_units * sizeof(UnitStatus), c->stream);
-    cudaMemsetAsync(meta, 0, 64, c->stream);
-    if (gbm) cudaMemsetAsync(gbm, 0, gbm_bytes, c->stream);
-    RankCsrArgs A;
-    std::memset(&A, 0, sizeof A);
-    A.mode = (u32)mode;
-    A.R = R;
-    A.C = e->C;
-    A.max_depth = e->max_depth;
-    A.row_off_of_rank = e->row_off;
-    A.entry_off = e->entry_off;
-    if (mode == 0) {
-      A.in_ctx = e->e_ctx;
-      A.in_time = e->e_time;
-      A.in_cnt = e->e_cnt;
-    } else {
-      A.in_off = e->x.off;
-      A.in_ctx = e->x.ctx;
-      A.in_time = e->x.time;
-      A.in_cnt = e->x.cnt;
-    }
-    A.parent = e->parent;
-    A.depth = e->depth;
-    A.unit_counter = (u32*)meta;
-    A.status = (u32*)meta + 1;
-    A.total = meta + 1;
-    A.ustat = ustat;
-    A.out_off = out.off;
-    A.out_ctx = out.ctx;
-    A.out_time = out.time;
-    A.out_cnt = out.cnt;
-    A.nnz_cap = cap;
-    A.gbm = gbm;
-    A.gst_ctx = gctx;
-    A.gst_time = gtime;
-    A.gst_cnt = gcnt;
-    A.gst_cap = P.gst_cap;
-    A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
-    PhaseTimer timer(c, mode == 0 ? &c->prof.exclusive_ms : &c->prof.inclusive_ms);
-    launch_rank_csr(L, P, A);
-    timer.stop_and_sync();
-    u64 h[2];
-    TRY(copy(c, h, meta, sizeof h));
-    TRY(sync_check(c, mode == 0 ? "exclusive" : "inclusive"));
-    const u32 f = (u32)(h[0] >> 32);
-    TRY(status_from_flags(f, mode == 0 ? "exclusive" : "inclusive"));
-    out.nnz = h[1];
-    if (!(f & F_CAPACITY)) return TA_OK;
-    e->disown(out.ctx);
-    e->disown(out.time);
-    e->disown(out.cnt);
-    cap = std::max<u64>(out.nnz, 1);
+  A.mode = (u32)mode;
+  A.R = R;
+  A.C = e->C;
+  A.max_depth = e->max_depth;
+  A.row_off_of_rank = e->row_off;
+  A.entry_off = e->entry_off;
+  if (mode == 0) {
+    A.in_ctx = e->e_ctx;
+    A.in_time = e->e_time;
+    A.in_cnt = e->e_cnt;
+  } else {
+    A.in_off = e->x.off;
+    A.in_ctx = e->x.ctx;
+    A.in_time = e->x.time;
+    A.in_cnt = e->x.cnt;
   }
-  return fail(TA_ERR_CUDA, "per-rank CSR: capacity retry failed");
+  A.parent = e->parent;
+  A.depth = e->depth;
+  A.out_off = out.off;
+  A.total = meta + 1;
+  A.status = (u32*)meta;
+  A.gst_cap = P.gst_cap;
+  A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+  double* acc = mode == 0 ? &c->prof.exclusive_ms : &c->prof.inclusive_ms;
+  {
+    PhaseTimer timer(c, acc);
+    launch_rank_count(L, P, A);
+    timer.stop_and_sync();
+  }
+  u64 h[2];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, mode == 0 ? "exclusive (count)" : "inclusive (count)"));
+  out.nnz = h[1];
+  const u64 n = std::max<u64>(out.nnz, 1);
+  TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
+  TRY(e->own(n * 8, (void**)&out.time, "csr time"));
+  TRY(e->own(n * 4, (void**)&out.cnt, "csr cnt"));
+  A.out_ctx = out.ctx;
+  A.out_time = out.time;
+  A.out_cnt_e = out.cnt;
+  {
+    PhaseTimer timer(c, acc);
+    launch_rank_write(L, P, A);
+    timer.stop_and_sync();
+  }
+  u64 f = 0;
+  TRY(copy(c, &f, meta, 8));
+  TRY(sync_check(c, mode == 0 ? "exclusive" : "inclusive"));
+  return status_from_flags((u32)f, mode == 0 ? "exclusive" : "inclusive");
 }
 
 ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& tmp) {

@@ -150,22 +150,82 @@ void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_it
 }
 
 // ---------------------------------------------------------------------------
-// Staging of aggregated entries: shared memory first, a per-CTA global region
-// when a tile's rows do not fit (sized so that it cannot overflow).
-constexpr u32 GBIT = 0x80000000u;
+// The iteration tensor (Section V): two passes over warp tiles, no waiting.
+//
+// A tile is TW consecutive samples; it owns the rows (rank prologues and
+// iterations) that START inside it and reads past its end to finish its last
+// row.  Every warp takes tiles grid-stride and streams a tile 128 samples at a
+// time (4 per lane, 16-byte vector loads, the next step prefetched while the
+// current one is processed): rank starts and marker-run starts cut rows; each
+// run head of a row sets its context's bit in the warp's two-level bitmap.
+//   count pass (contexts only): per tile, rows and distinct entries (bitmap
+//     popcount per row); also validates context ids.
+//   a device scan of the per-tile counts gives every tile its row and entry
+//     offsets and the exact output sizes.
+//   write pass (contexts and timestamps): validates timestamp order; per row a
+//     prefix over the bitmap ranks its contexts in ascending order, a second
+//     pass over the row's samples (cache-resident, consecutive equal contexts
+//     merged in registers first) accumulates time and count at those ranks in
+//     shared memory, and the row is written straight to its final place.
+// No tile ever waits for another, so uneven tiles (long rows, rank
+// boundaries) cost only their own work.
+namespace {
 
-__device__ __forceinline__ u32 stage_alloc(u32 n, u32* top, u32* gtop, u32 cap, u32 gcap,
-                                           u32* status, bool* ok) {
-  *ok = true;
-  const u32 o = atomicAdd(top, n);
-  if (o + n <= cap) return o;
-  const u32 g = atomicAdd(gtop, n);
-  if (g + n > gcap) {
-    flag(status, F_INTERNAL);
-    *ok = false;
-    return GBIT;
+constexpr u32 TW = 1024;   // samples per tile
+constexpr u32 STEP = 128;  // samples per warp step (4 per lane)
+constexpr u32 RS = 128;    // staged entries per warp in shared memory
+
+struct WarpSmem {
+  static constexpr u32 mask_off = 0;               // u32[36] rank-start mask
+  static constexpr u32 time_off = 4 * 36 + 16;     // u64[RS] (8-byte aligned)
+  static constexpr u32 ctx_off = time_off + 8 * RS;
+  static constexpr u32 cnt_off = ctx_off + 4 * RS;
+  static constexpr u32 bm_off = cnt_off + 4 * RS;  // bitmap words (16-byte aligned)
+  static constexpr u32 fixed_count = 4 * 36 + 16;  // count pass: mask only
+  static constexpr u32 fixed_write = bm_off;
+};
+
+struct Step {
+  u32 c[4];
+  u64 t[4];
+};
+
+// Load samples q0 + 4 lane + j (j < 4); contexts always, timestamps if want_ts.
+__device__ __forceinline__ void load_step(const TensorArgs& A, u64 q0, int lane, bool want_ts,
+                                          Step& s) {
+  const u64 q = q0 + 4 * (u64)lane;
+  if (q + 3 < A.N) {
+    const uint4 cv = *reinterpret_cast<const uint4*>(A.ctx + q);
+    s.c[0] = cv.x;
+    s.c[1] = cv.y;
+    s.c[2] = cv.z;
+    s.c[3] = cv.w;
+    if (want_ts) {
+      const ulonglong2 t0 = *reinterpret_cast<const ulonglong2*>(A.ts + q);
+      const ulonglong2 t1 = *reinterpret_cast<const ulonglong2*>(A.ts + q + 2);
+      s.t[0] = t0.x;
+      s.t[1] = t0.y;
+      s.t[2] = t1.x;
+      s.t[3] = t1.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      s.c[j] = (q + j < A.N) ? A.ctx[q + j] : NONE32;
+      if (want_ts) s.t[j] = (q + j < A.N) ? A.ts[q + j] : 0ull;
+    }
   }
-  return g | GBIT;
+}
+
+// Distinct contexts of the row in the bitmap (count pass).
+__device__ __forceinline__ u32 bm_count_warp(const Bm& b, int lane) {
+  u32 sum = 0;
+  for (u32 g = 0; g < b.W2; g += 32) {
+    const u32 w2 = g + lane;
+    const u32 bits = (w2 < b.W2) ? vld(&b.L2[w2]) : 0u;
+    for (u32 x = bits; x; x &= x - 1) sum += __popc(vld(&b.L1[w2 * 32 + __ffs(x) - 1]));
+  }
+  return __reduce_add_sync(FULL, sum);
 }
 
 struct Stage {
@@ -174,588 +234,558 @@ struct Stage {
   u32* cnt;
 };
 
-__device__ __forceinline__ Stage stage_at(u32 soff, const Stage& sm, const Stage& gl) {
-  Stage s;
-  if (soff & GBIT) {
-    const u32 o = soff & ~GBIT;
-    s.ctx = gl.ctx + o;
-    s.time = gl.time + o;
-    s.cnt = gl.cnt + o;
-  } else {
-    s.ctx = sm.ctx + soff;
-    s.time = sm.time + soff;
-    s.cnt = sm.cnt + soff;
+// Write pass: rank, accumulate and write the row [s, e) at entry eo.
+__device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Stage& sm,
+                                         const Stage& gl, u64 s, u64 e, bool e_rs, u64 eo,
+                                         int lane) {
+  __syncwarp();
+  const u32 nnz = bm_prefix_warp(bm, lane);
+  const Stage st = (nnz <= RS) ? sm : gl;
+  for (u32 k = lane; k < nnz; k += 32) {
+    st.time[k] = 0;
+    st.cnt[k] = 0;
   }
-  return s;
+  __syncwarp();
+  const u32 C = A.C;
+  for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
+    Step x;
+    load_step(A, g0, lane, true, x);
+    const u64 q = g0 + 4 * (u64)lane;
+    u64 t_after = __shfl_down_sync(FULL, x.t[0], 1);  // first timestamp of the next lane
+    if (lane == 31 && q + 4 < e) t_after = A.ts[q + 4];
+    u32 rc = NONE32, rn = 0;
+    u64 rt = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const u64 qj = q + j;
+      if (qj < s || qj >= e) continue;
+      u64 tn;
+      if (qj + 1 < e) tn = (j < 3) ? x.t[j + 1] : t_after;
+      else tn = e_rs ? x.t[j] : A.ts[e];
+      const u64 d = tn >= x.t[j] ? tn - x.t[j] : 0;
+      const u32 c = x.c[j] < C ? x.c[j] : 0u;
+      if (c == rc) {
+        rt += d;
+        ++rn;
+      } else {
+        if (rn) {
+          const u32 k = bm_rank(bm, rc);
+          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)rt);
+          atomicAdd(&st.cnt[k], rn);
+          st.ctx[k] = rc;
+        }
+        rc = c;
+        rt = d;
+        rn = 1;
+      }
+    }
+    if (rn) {
+      const u32 k = bm_rank(bm, rc);
+      atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)rt);
+      atomicAdd(&st.cnt[k], rn);
+      st.ctx[k] = rc;
+    }
+  }
+  __syncwarp();
+  for (u32 k = lane; k < nnz; k += 32) {
+    const u64 g = eo + k;
+    A.e_ctx[g] = vld(&st.ctx[k]);
+    A.e_time[g] = vld(&st.time[k]);
+    A.e_cnt[g] = vld(&st.cnt[k]);
+  }
+  bm_clear_warp(bm, lane);
+  __syncwarp();
+  return nnz;
 }
 
-// ---------------------------------------------------------------------------
-// The iteration tensor (Section V): one persistent kernel over tiles of T
-// consecutive samples, claimed in order.  A tile owns the rows (rank prologues
-// and iterations) that START inside it and reads past its end to finish its
-// last row.  Per tile:
-//   0. load samples to shared memory; validate contexts and timestamp order;
-//      durations; rank starts; marker-run starts; prefix counts -> local rows
-//   1. rows of at most LONG samples: one warp each, sorted distinct-context
-//      aggregation with the warp's two-level bitmap
-//   2. longer rows (and the row that runs past the tile): the whole CTA
-//   3. prefix of entries; decoupled look-back gives the global row / entry
-//      offsets; 4. write rows, rank offsets and entries.
-template <int T, int NT>
-__global__ void __launch_bounds__(NT) k_tensor(const TensorArgs A) {
-  constexpr int W = NT / 32;
-  constexpr int PER = T / NT;
-  constexpr u32 CAP = T;
-  constexpr u32 LONG = 1024;
-  static_assert(T % NT == 0 && T <= 32768, "tile shape");
+}  // namespace
+
+template <int NW, bool WRITE>
+__global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
-  u64* dur_s = (u64*)sm;                      // [T + 2] ts, then durations
-  u32* ctx_s = (u32*)(dur_s + T + 2);         // [T]
-  u32* nrs_s = ctx_s + T;                     // [T + 4] rank starts per position
-  uint16_t* d_pos = (uint16_t*)(nrs_s + T + 4);  // [T] data-row start position
-  uint16_t* d_mspre = d_pos + T;              // [T] marker starts before it
-  u32* d_nrspre = (u32*)(d_mspre + T);        // [T] rank starts before it
-  u32* d_nnz = d_nrspre + T;                  // [T] entries, then entry prefix
-  u32* d_soff = d_nnz + T;                    // [T] stage offset
-  Stage ss;
-  ss.ctx = d_soff + T;                        // [CAP]
-  ss.cnt = ss.ctx + CAP;                      // [CAP]
-  ss.time = (u64*)(ss.cnt + CAP);             // [CAP]
-  u32* bm_sm = (u32*)(ss.time + CAP);
-
-  __shared__ u64 s_scan[W];
-  __shared__ u32 s_tile, s_rs_lo, s_rs_hi, s_prevc, s_rank_at_b, s_ndata, s_ms_total, s_nend;
-  __shared__ u32 s_stage_top, s_gtop, s_cnnz, s_csoff;
-  __shared__ unsigned long long s_q;
-  __shared__ u64 s_nrs_total, s_pre_rows, s_pre_ents;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
-  u32* const bm_cta_base =
-      A.bm_in_smem ? bm_sm : A.gbm + (u64)blockIdx.x * W * bmw;
-  const Bm bm = bm_at(bm_cta_base + (u64)warp * bmw, A.C);
-  const Bm bm0 = bm_at(bm_cta_base, A.C);
+  const u32 fixed = WRITE ? WarpSmem::fixed_write : WarpSmem::fixed_count;
+  const u32 wbytes = fixed + (A.bm_in_smem ? bmw * 4 : 0);
+  unsigned char* ws = sm + (size_t)warp * wbytes;
+  const u64 gw = (u64)blockIdx.x * NW + warp;
+  const u64 G = (u64)gridDim.x * NW;
+  u32* mask = (u32*)(ws + WarpSmem::mask_off);
+  const Bm bm = bm_at(A.bm_in_smem ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
   if (A.bm_in_smem)
-    for (u32 i = tid; i < W * bmw; i += NT) bm_sm[i] = 0;
-  Stage gs;
-  gs.ctx = A.gst_ctx + (u64)blockIdx.x * A.gst_cap;
-  gs.time = A.gst_time + (u64)blockIdx.x * A.gst_cap;
-  gs.cnt = A.gst_cnt + (u64)blockIdx.x * A.gst_cap;
+    for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
+  Stage sst, gst;
+  if (WRITE) {
+    sst.time = (u64*)(ws + WarpSmem::time_off);
+    sst.ctx = (u32*)(ws + WarpSmem::ctx_off);
+    sst.cnt = (u32*)(ws + WarpSmem::cnt_off);
+    gst.time = A.gst_time + gw * A.gst_cap;
+    gst.ctx = A.gst_ctx + gw * A.gst_cap;
+    gst.cnt = A.gst_cnt + gw * A.gst_cap;
+  }
+  __syncwarp();
   const u32 m = A.m, C = A.C;
+  const u64 N = A.N;
 
-  for (;;) {
-    if (tid == 0) {
-      s_tile = atomicAdd(A.unit_counter, 1u);
-      s_q = ~0ull;
-      s_stage_top = 0;
-      s_gtop = 0;
-    }
-    __syncthreads();
-    const u32 t = s_tile;
-    if (t >= A.n_tiles) break;
-    const u64 a = (u64)t * T;
-    const u64 b = min(a + (u64)T, A.N);
-    const u32 nrec = (u32)(b - a);
+  for (u64 t = gw; t < A.n_tiles; t += G) {
+    const u64 a = t * TW;
+    const u64 b = min(a + (u64)TW, N);
     const bool last = (t == A.n_tiles - 1);
-
-    // ---- 0. load, validate, durations, row starts --------------------------
-    if (tid == 0) {
-      const u32 hi = A.tfr[t + 1];
-      s_rs_lo = A.tfr[t];
-      s_rs_hi = hi;
-      s_prevc = a > 0 ? A.ctx[a - 1] : NONE32;
-      s_rank_at_b = (!last && hi < A.R && A.rank_off[hi] == b) ? 1u : 0u;
-      dur_s[nrec] = (b < A.N) ? A.ts[b] : 0ull;
+    const u32 lo = A.tfr[t], hi = A.tfr[t + 1];
+    const u64 qrank = (hi < A.R) ? A.rank_off[hi] : N;  // first rank start >= b (or N)
+    u32 carry = (a > 0) ? A.ctx[a - 1] : NONE32;
+    u64 PR = 0, PE = 0;
+    if (WRITE) {
+      PR = A.tile_row_off[t];
+      PE = A.tile_ent_off[t];
     }
-    for (u32 i = tid; i < T + 4; i += NT) nrs_s[i] = 0;
-    for (u32 i = tid; i < nrec; i += NT) {
-      ctx_s[i] = A.ctx[a + i];
-      dur_s[i] = A.ts[a + i];
+    for (u32 i = lane; i < 36; i += 32) mask[i] = 0;
+    __syncwarp();
+    for (u32 r = lo + lane; r < hi; r += 32) {
+      const u32 p = (u32)(A.rank_off[r] - a);
+      atomicOr(&mask[p >> 5], 1u << (p & 31));
     }
-    __syncthreads();
-    const u32 rs_lo = s_rs_lo, rs_hi = s_rs_hi;
-    for (u32 r = rs_lo + tid; r < rs_hi; r += NT) atomicAdd(&nrs_s[(u32)(A.rank_off[r] - a)], 1u);
-    __syncthreads();
+    __syncwarp();
 
-    u64 v[PER], du[PER];
-    u32 cl[PER];
-    {
-      u32 fl = 0;
-      const u32 prevc = s_prevc;
-      const bool rab = s_rank_at_b != 0;
+    u32 rank_ptr = lo, rows_local = 0, fl = 0;
+    u64 cum = 0;
+    bool row_open = false;
+    u64 row_s = 0;
+    Step cur;
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const u32 i = tid * PER + k;
-        v[k] = 0;
-        du[k] = 0;
-        cl[k] = 0;
-        if (i < nrec) {
-          const u32 c = ctx_s[i];
-          u32 cc = c;
-          if (c >= C) {
-            fl |= F_BAD_CTX;
-            cc = 0;
+    for (int j = 0; j < 4; ++j) {
+      cur.c[j] = NONE32;
+      cur.t[j] = 0;
+    }
+    load_step(A, a, lane, WRITE && a < b, cur);
+    for (u64 q0 = a;; q0 += STEP) {
+      const bool tile_step = q0 < b;
+      if (!tile_step && !row_open) break;
+      const u64 lim = tile_step ? b : qrank;
+      if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
+        if (row_open) {
+          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, lim, true, PE + cum, lane);
+          else {
+            __syncwarp();
+            cum += bm_count_warp(bm, lane);
+            bm_clear_warp(bm, lane);
+            __syncwarp();
           }
-          const u32 pc = i > 0 ? ctx_s[i - 1] : prevc;
-          const u32 nr = nrs_s[i];
-          const bool nxt = (i + 1 < nrec) ? (nrs_s[i + 1] > 0) : ((b == A.N) || rab);
-          if (!nxt) {
-            const u64 t0 = dur_s[i], t1 = dur_s[i + 1];
-            if (t1 < t0) fl |= F_NOT_SORTED;
-            else du[k] = t1 - t0;
+        }
+        row_open = false;
+        break;
+      }
+      Step nx;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        nx.c[j] = NONE32;
+        nx.t[j] = 0;
+      }
+      const u64 q1 = q0 + STEP;
+      if (q1 < N) load_step(A, q1, lane, WRITE && q1 < b, nx);
+      const u64 q = q0 + 4 * (u64)lane;
+      // samples of this step that exist (tile steps: below b; continuation:
+      // below the next rank start)
+      const u32 nvalid = (u32)min(lim - q0, (u64)STEP);
+      const u32 pos0 = 4u * (u32)lane;
+      u32 pc[4];
+      pc[0] = __shfl_up_sync(FULL, cur.c[3], 1);
+      if (lane == 0) pc[0] = carry;
+      pc[1] = cur.c[0];
+      pc[2] = cur.c[1];
+      pc[3] = cur.c[2];
+      carry = __shfl_sync(FULL, cur.c[3], 31);
+      const u32 rel = (u32)(q - a);
+      // rank-start bits of this lane's 4 samples (positions rel .. rel + 3)
+      const u32 rs4 = tile_step ? ((mask[rel >> 5] >> (rel & 31)) & 0xFu) : 0u;
+      u32 ms4 = 0, valid4 = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool valid = pos0 + j < nvalid;
+        valid4 |= (valid ? 1u : 0u) << j;
+        const bool ms = cur.c[j] == m && (pc[j] != m || ((rs4 >> j) & 1u));
+        ms4 |= (ms ? 1u : 0u) << j;
+      }
+      ms4 &= valid4;
+      if (tile_step) {
+        if (!WRITE) {
+          u32 cmax = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if ((valid4 >> j) & 1u) cmax = max(cmax, cur.c[j]);
+          if (cmax >= C) fl |= F_BAD_CTX;
+        } else {
+          // timestamp order within ranks: sample i+1 must not be earlier
+          // unless a rank starts at i+1
+          const u32 rs_next_lane = __shfl_down_sync(FULL, rs4, 1) & 1u;
+          u64 t_after = __shfl_down_sync(FULL, cur.t[0], 1);
+          const u64 nx_t0 = __shfl_sync(FULL, nx.t[0], 0);  // all lanes (nx is always set)
+          u32 rsn = (rs4 >> 1) | (rs_next_lane << 3);  // rank start at rel + j + 1
+          if (lane == 31) {
+            if (q + 4 < N) t_after = (q1 < b) ? nx_t0 : A.ts[q + 4];
+            const u32 r4 = rel + 4;
+            const bool r4s = (q + 4 >= N) ? true
+                             : (r4 < TW) ? (((mask[r4 >> 5] >> (r4 & 31)) & 1u) != 0)
+                                         : (qrank == b);
+            rsn = (rsn & 7u) | ((r4s ? 1u : 0u) << 3);
           }
-          const u32 ms = (c == m && (nr > 0 || pc != m)) ? 1u : 0u;
-          v[k] = ((u64)nr << 32) | ((nr + ms > 0) ? (1ull << 16) : 0ull) | ms;
-          cl[k] = cc;
-        }
-      }
-      if (fl) flag(A.status, fl);
-    }
-    u64 tsum = 0;
 #pragma unroll
-    for (int k = 0; k < PER; ++k) tsum += v[k];
-    u64 TOT;
-    u64 run = block_excl_scan<NT>(tsum, s_scan, &TOT);
+          for (int j = 0; j < 4; ++j) {
+            if (!((valid4 >> j) & 1u) || ((rsn >> j) & 1u)) continue;
+            if (q + j + 1 >= N) continue;
+            const u64 tn = (j < 3) ? cur.t[j + 1] : t_after;
+            if (tn < cur.t[j]) fl |= F_NOT_SORTED;
+          }
+        }
+      }
+      const u32 st4_any = (rs4 & valid4) | ms4;
+      if (!__any_sync(FULL, st4_any != 0)) {
+        // fast path: no row starts in this step; mark the run heads of the
+        // open row
+        if (row_open) {
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const u32 i = tid * PER + k;
-      if (i < nrec) {
-        dur_s[i] = du[k];
-        ctx_s[i] = cl[k];
-        if (v[k] & (1ull << 16)) {
-          const u32 di = (u32)((run >> 16) & 0xFFFFu);
-          d_pos[di] = (uint16_t)i;
-          d_mspre[di] = (uint16_t)(run & 0xFFFFu);
-          d_nrspre[di] = (u32)(run >> 32);
+          for (int j = 0; j < 4; ++j)
+            if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) bm_set(bm, cur.c[j] < C ? cur.c[j] : 0u);
         }
-      }
-      run += v[k];
-    }
-    if (tid == 0) {
-      s_ndata = (u32)((TOT >> 16) & 0xFFFFu);
-      s_ms_total = (u32)(TOT & 0xFFFFu);
-      s_nrs_total = TOT >> 32;
-      s_nend = last ? nrs_s[nrec] : 0u;
-    }
-    __syncthreads();
-    const u32 nd = s_ndata;
-
-    // ---- end of the tile's last row: first row start at or after b --------
-    u64 e = b;
-    bool lz = true;  // the last row ends at a rank boundary (last sample 0 ns)
-    if (nd > 0 && b < A.N) {
-      const u64 qrank = (rs_hi < A.R) ? A.rank_off[rs_hi] : A.N;
-      e = qrank;
-      for (u64 q0 = b; q0 < qrank; q0 += NT) {
-        const u64 q = q0 + tid;
-        bool hit = false;
-        if (q < qrank) hit = (A.ctx[q] == m) && (A.ctx[q - 1] != m);
-        if (hit) atomicMin(&s_q, (unsigned long long)q);
-        if (__syncthreads_or(hit)) break;
-      }
-      if (s_q != ~0ull) {
-        e = s_q;
-        lz = false;
-      }
-    }
-    const u64 e_rel = e - a;
-
-    // ---- 1. short rows, one warp each --------------------------------------
-    for (u32 d = warp; d < nd; d += W) {
-      const u32 s = d_pos[d];
-      const u64 te = (d + 1 < nd) ? (u64)d_pos[d + 1] : e_rel;
-      if (te > nrec || te - s > LONG) continue;
-      const u32 tt = (u32)te;
-      for (u32 j = s + lane; j < tt; j += 32) {
-        const u32 c = ctx_s[j];
-        if (j == s || ctx_s[j - 1] != c) bm_set(bm, c);
-      }
-      __syncwarp();
-      const u32 nnz = bm_prefix_warp(bm, lane);
-      u32 soff = 0;
-      bool ok = true;
-      if (lane == 0) soff = stage_alloc(nnz, &s_stage_top, &s_gtop, CAP, A.gst_cap, A.status, &ok);
-      soff = __shfl_sync(FULL, soff, 0);
-      ok = __shfl_sync(FULL, ok, 0);
-      const Stage st = stage_at(soff, ss, gs);
-      if (ok) {
-        for (u32 k = lane; k < nnz; k += 32) {
-          st.time[k] = 0;
-          st.cnt[k] = 0;
-        }
-        __syncwarp();
-        for (u32 j = s + lane; j < tt; j += 32) {
-          const u32 c = ctx_s[j];
-          const u32 k = bm_rank(bm, c);
-          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)dur_s[j]);
-          atomicAdd(&st.cnt[k], 1u);
-          st.ctx[k] = c;
-        }
-      }
-      __syncwarp();
-      bm_clear_warp(bm, lane);
-      __syncwarp();
-      if (lane == 0) {
-        d_nnz[d] = ok ? nnz : 0u;
-        d_soff[d] = soff;
-      }
-    }
-    __syncthreads();
-
-    // ---- 2. long rows and the row that continues past the tile: whole CTA --
-    for (u32 d = 0; d < nd; ++d) {
-      const u32 s = d_pos[d];
-      const u64 te = (d + 1 < nd) ? (u64)d_pos[d + 1] : e_rel;
-      if (!(te > nrec || te - s > LONG)) continue;
-      for (u64 j = s + tid; j < te; j += NT) {
-        u32 c = (j < nrec) ? ctx_s[j] : A.ctx[a + j];
-        if (c >= C) c = 0;
-        bool head = (j == s);
-        if (!head) {
-          u32 cp = (j - 1 < nrec) ? ctx_s[j - 1] : A.ctx[a + j - 1];
-          if (cp >= C) cp = 0;
-          head = cp != c;
-        }
-        if (head) bm_set(bm0, c);
-      }
-      __syncthreads();
-      if (warp == 0) {
-        const u32 nnz = bm_prefix_warp(bm0, lane);
-        if (lane == 0) {
-          bool ok = true;
-          const u32 so = stage_alloc(nnz, &s_stage_top, &s_gtop, CAP, A.gst_cap, A.status, &ok);
-          s_cnnz = ok ? nnz : 0u;
-          s_csoff = so;
-        }
-      }
-      __syncthreads();
-      const u32 nnz = s_cnnz;
-      const Stage st = stage_at(s_csoff, ss, gs);
-      for (u32 k = tid; k < nnz; k += NT) {
-        st.time[k] = 0;
-        st.cnt[k] = 0;
-      }
-      __syncthreads();
-      if (nnz > 0) {
-        for (u64 j = s + tid; j < te; j += NT) {
-          u32 c;
-          u64 dd;
-          if (j < nrec) {
-            c = ctx_s[j];
-            dd = dur_s[j];
-          } else {
-            const u64 gj = a + j;
-            c = A.ctx[gj];
-            if (c >= C) c = 0;
-            const u64 t0 = A.ts[gj];
-            if (j + 1 < te) {
-              const u64 t1 = A.ts[gj + 1];
-              dd = t1 >= t0 ? t1 - t0 : 0;
-            } else if (lz) {
-              dd = 0;
-            } else {
-              const u64 t1 = A.ts[a + te];
-              dd = t1 >= t0 ? t1 - t0 : 0;
+        if (q1 >= b && b == N) {  // the last tile: rows end at N
+          if (row_open) {
+            if (WRITE) cum += write_row(A, bm, sst, gst, row_s, N, true, PE + cum, lane);
+            else {
+              __syncwarp();
+              cum += bm_count_warp(bm, lane);
+              bm_clear_warp(bm, lane);
+              __syncwarp();
             }
           }
-          const u32 k = bm_rank(bm0, c);
-          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)dd);
-          atomicAdd(&st.cnt[k], 1u);
-          st.ctx[k] = c;
+          row_open = false;
+          break;
         }
+        cur = nx;
+        continue;
       }
-      __syncthreads();
-      if (warp == 0) bm_clear_warp(bm0, lane);
-      if (tid == 0) {
-        d_nnz[d] = nnz;
-        d_soff[d] = s_csoff;
-      }
-      __syncthreads();
-    }
-
-    // ---- 3. entry prefix over the tile's data rows ---------------------------
-    u64 EL;
-    {
-      u32 vals[PER];
-      u64 nsum = 0;
+      u32 cc[4];
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const u32 di = tid * PER + k;
-        vals[k] = di < nd ? d_nnz[di] : 0u;
-        nsum += vals[k];
-      }
-      u64 r2 = block_excl_scan<NT>(nsum, s_scan, &EL);
+      for (int j = 0; j < 4; ++j) cc[j] = cur.c[j] < C ? cur.c[j] : 0u;
+      const u32 st4 = st4_any;
+      u32 seg_lo = 0, from = 0;
+      bool stop = false;
+      for (;;) {
+        u32 mypos = 255;
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const u32 di = tid * PER + k;
-        if (di < nd) d_nnz[di] = (u32)r2;
-        r2 += vals[k];
-      }
-    }
-
-    // ---- look-back: global row / entry offsets --------------------------------
-    const u64 RL = s_nrs_total + s_ms_total + s_nend;
-    if (tid == 0) {
-      u64 pr, pe;
-      lookback(A.ustat, t, RL, EL, &pr, &pe, A.status);
-      s_pre_rows = pr;
-      s_pre_ents = pe;
-      if (last) {
-        const u64 rows = pr + RL, nnz = pe + EL;
-        A.totals[0] = rows;
-        A.totals[1] = nnz;
-        A.row_off_of_rank[A.R] = rows;
-        if (rows + 1 > A.rows_cap || nnz > A.nnz_cap) flag(A.status, F_CAPACITY);
-        else A.entry_off[rows] = nnz;
-      }
-    }
-    __syncthreads();
-    const u64 PR = s_pre_rows, PE = s_pre_ents;
-
-    // ---- 4. outputs ----------------------------------------------------------
-    for (u32 d = warp; d < nd; d += W) {
-      const u32 pos = d_pos[d];
-      const u32 nrs = nrs_s[pos];
-      const u32 ms = (u32)((d + 1 < nd) ? d_mspre[d + 1] : s_ms_total) - d_mspre[d];
-      const u64 row0 = PR + d_nrspre[d] + d_mspre[d];
-      const u64 eo = PE + d_nnz[d];
-      const u32 nrow = nrs + ms;
-      for (u32 k = lane; k < nrow; k += 32)
-        if (row0 + k < A.rows_cap) A.entry_off[row0 + k] = eo;
-      for (u32 k = lane; k < nrs; k += 32)
-        A.row_off_of_rank[rs_lo + d_nrspre[d] + k] = row0 + k;
-      const u32 nnz = (u32)(((d + 1 < nd) ? (u64)d_nnz[d + 1] : EL) - d_nnz[d]);
-      const Stage st = stage_at(d_soff[d], ss, gs);
-      for (u32 k = lane; k < nnz; k += 32) {
-        const u64 g = eo + k;
-        if (g < A.nnz_cap) {
-          A.e_ctx[g] = vld(&st.ctx[k]);
-          A.e_time[g] = vld(&st.time[k]);
-          A.e_cnt[g] = vld(&st.cnt[k]);
+        for (int j = 3; j >= 0; --j) {
+          const u32 pos = 4 * lane + j;
+          if (((st4 >> j) & 1u) && pos >= from) mypos = pos;
         }
+        const u32 nxt = __reduce_min_sync(FULL, mypos);
+        const u32 end = nxt < STEP ? nxt : STEP;
+        if (row_open) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const u32 pos = pos0 + j;
+            if (((valid4 >> j) & 1u) && pos >= seg_lo && pos < end)
+              if (q + j == row_s || pc[j] != cur.c[j]) bm_set(bm, cc[j]);
+          }
+        }
+        if (nxt >= STEP) break;
+        const u64 p = q0 + nxt;
+        const u32 src = nxt >> 2, bj = nxt & 3;
+        const bool p_rs = (__shfl_sync(FULL, rs4, src) >> bj) & 1u;
+        const bool p_ms = (__shfl_sync(FULL, ms4, src) >> bj) & 1u;
+        if (row_open) {
+          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, p, p_rs, PE + cum, lane);
+          else {
+            __syncwarp();
+            cum += bm_count_warp(bm, lane);
+            bm_clear_warp(bm, lane);
+            __syncwarp();
+          }
+        }
+        if (!tile_step) {  // the continuation found the end of the row
+          row_open = false;
+          stop = true;
+          break;
+        }
+        u32 nrs = 0, r0 = rank_ptr;
+        if (p_rs) {
+          u32 rp = rank_ptr;
+          if (lane == 0)
+            while (rp < hi && A.rank_off[rp] == p) ++rp;
+          rp = __shfl_sync(FULL, rp, 0);
+          nrs = rp - rank_ptr;
+          rank_ptr = rp;
+        }
+        const u32 nrow = nrs + (p_ms ? 1u : 0u);
+        if (WRITE) {
+          const u64 row0 = PR + rows_local;
+          for (u32 k = lane; k < nrow; k += 32) A.entry_off[row0 + k] = PE + cum;
+          for (u32 k = lane; k < nrs; k += 32) A.row_off_of_rank[r0 + k] = row0 + k;
+        }
+        rows_local += nrow;
+        row_open = true;
+        row_s = p;
+        seg_lo = nxt;
+        from = nxt + 1;
       }
-    }
-    if (last) {  // empty ranks that start at N
-      const u32 ne = s_nend;
-      const u64 row0 = PR + s_nrs_total + s_ms_total;
-      for (u32 k = tid; k < ne; k += NT) {
-        if (row0 + k < A.rows_cap) A.entry_off[row0 + k] = PE + EL;
-        A.row_off_of_rank[A.R - ne + k] = row0 + k;
+      if (stop) break;
+      if (q1 >= b && b == N) {  // the last tile: rows end at N
+        if (row_open) {
+          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, N, true, PE + cum, lane);
+          else {
+            __syncwarp();
+            cum += bm_count_warp(bm, lane);
+            bm_clear_warp(bm, lane);
+            __syncwarp();
+          }
+        }
+        row_open = false;
+        break;
       }
+      cur = nx;
     }
-    __syncthreads();
+    fl = __reduce_or_sync(FULL, fl);
+    if (lane == 0 && fl) flag(A.status, fl);
+    const u32 n_end = last ? hi - rank_ptr : 0u;  // empty ranks starting at N
+    if (WRITE) {
+      const u64 row0 = PR + rows_local;
+      for (u32 k = lane; k < n_end; k += 32) {
+        A.entry_off[row0 + k] = PE + cum;
+        A.row_off_of_rank[A.R - n_end + k] = row0 + k;
+      }
+    } else if (lane == 0) {
+      A.tile_rows[t] = rows_local + n_end;
+      A.tile_ents[t] = cum;
+    }
+    __syncwarp();
   }
 }
 
-constexpr int TENSOR_T = 1024;
-constexpr int TENSOR_NT = 256;
+constexpr int TENSOR_NW = 8;
 
-static size_t tensor_smem_base(int T) {
-  const int CAP = T;
-  return (size_t)8 * (T + 2) + 4 * T + 4 * (T + 4) + 2 * T + 2 * T + 3 * 4 * T + 16 * (size_t)CAP;
+static void set_smem(const void* k, size_t smem) {
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 TensorPlan plan_tensor(u32 C, u64 N, int num_sms) {
   TensorPlan P;
-  P.tile = TENSOR_T;
-  P.threads = TENSOR_NT;
-  const size_t base = tensor_smem_base(TENSOR_T);
-  const size_t bm = (size_t)(TENSOR_NT / 32) * bm_words(C) * 4;
-  P.bm_in_smem = base + bm <= 110 * 1024;
-  P.smem = base + (P.bm_in_smem ? bm : 0);
-  auto kern = k_tensor<TENSOR_T, TENSOR_NT>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TENSOR_NT, P.smem);
-  if (occ < 1) occ = 1;
-  const u64 n_tiles = std::max<u64>(1, (N + TENSOR_T - 1) / TENSOR_T);
-  P.grid = (int)std::min<u64>((u64)num_sms * occ, n_tiles);
-  P.gst_cap = TENSOR_T + C;
+  P.tile = TW;
+  P.threads = TENSOR_NW * 32;
+  const size_t bm = (size_t)bm_words(C) * 4;
+  P.bm_in_smem = WarpSmem::fixed_write + bm <= 12 * 1024;
+  P.smem_count = (WarpSmem::fixed_count + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
+  P.smem = (WarpSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
+  set_smem((const void*)k_tensor_pass<TENSOR_NW, false>, P.smem_count);
+  set_smem((const void*)k_tensor_pass<TENSOR_NW, true>, P.smem);
+  int o1 = 0, o2 = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_tensor_pass<TENSOR_NW, false>, P.threads,
+                                                P.smem_count);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_tensor_pass<TENSOR_NW, true>, P.threads,
+                                                P.smem);
+  const int occ = std::max(1, std::min(o1, o2));
+  const u64 n_tiles = std::max<u64>(1, (N + TW - 1) / TW);
+  P.grid = (int)std::min<u64>((u64)num_sms * occ, (n_tiles + TENSOR_NW - 1) / TENSOR_NW);
+  P.gst_cap = C;
   return P;
 }
 
-void launch_tensor(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  k_tensor<TENSOR_T, TENSOR_NT><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
+  k_tensor_pass<TENSOR_NW, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  L.count();
+}
+
+void launch_tile_scan(const Launch& L, const TensorArgs& A) {
+  const u64 ns = scan_scratch_elems(A.n_tiles);
+  scan_exclusive(L, A.tile_rows, A.n_tiles, A.tile_row_off, A.totals, A.scan_scratch);
+  scan_exclusive(L, A.tile_ents, A.n_tiles, A.tile_ent_off, A.totals + 1, A.scan_scratch + ns);
+}
+
+void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
+  k_tensor_pass<TENSOR_NW, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
   L.count();
 }
 
 // ---------------------------------------------------------------------------
-// Per-rank CSR of distinct contexts.  Work unit = W consecutive ranks (one
-// per warp), claimed in order; look-back over units gives output offsets.
-//  mode 0 (exclusive, Section V): union of the rank's tensor rows, summed.
+// Per-rank CSR of distinct contexts, one warp per rank (grid-stride), in two
+// passes with a scan between them (no rank waits for another):
+//  mode 0 (exclusive, Section V): the union of the rank's tensor rows, summed.
 //  mode 1 (inclusive, Sections II-A / VI-B): the ancestor closure of the
-//    rank's exclusive contexts, values rolled up level by level from the
-//    deepest level to the root (every node of depth d adds into its parent
-//    before any node of depth d-1 is read).
-template <int NT>
-__global__ void __launch_bounds__(NT) k_rank_csr(const RankCsrArgs A) {
-  constexpr int W = NT / 32;
-  constexpr u32 CAP = 4096;
+//    rank's exclusive contexts; values rolled up level by level from the
+//    rank's deepest level to the root (every node of depth d adds into its
+//    parent before any node of depth d-1 is read: a level-synchronous sweep).
+// count pass: distinct contexts per rank -> out_cnt[r].  write pass: offsets
+// from the scan; rank, accumulate (and sweep) in shared memory; write.
+namespace {
+
+constexpr u32 RSR = 256;  // staged entries per warp in shared memory
+
+struct RankSmem {
+  static constexpr u32 time_off = 0;                 // u64[RSR]
+  static constexpr u32 ctx_off = 8 * RSR;            // u32[RSR]
+  static constexpr u32 cnt_off = ctx_off + 4 * RSR;  // u32[RSR]
+  static constexpr u32 dep_off = cnt_off + 4 * RSR;  // u32[RSR] (inclusive)
+  static constexpr u32 par_off = dep_off + 4 * RSR;  // u32[RSR] (inclusive)
+  static constexpr u32 fixed_write = par_off + 4 * RSR;
+};
+
+struct RStage {
+  u64* time;
+  u32* ctx;
+  u32* cnt;
+  u32* dep;
+  u32* par;
+};
+
+}  // namespace
+
+template <int NW, int MODE, bool WRITE>
+__global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
-  Stage ss;
-  ss.time = (u64*)sm;
-  ss.ctx = (u32*)(ss.time + CAP);
-  ss.cnt = ss.ctx + CAP;
-  u32* bm_sm = ss.cnt + CAP;
-  __shared__ u32 s_unit, s_top, s_gtop;
-  __shared__ u32 s_nnz[W], s_soff[W];
-  __shared__ u64 s_eoff[W];
-  __shared__ u64 s_pre;
-
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
-  u32* const bm_cta_base = A.bm_in_smem ? bm_sm : A.gbm + (u64)blockIdx.x * W * bmw;
-  const Bm bm = bm_at(bm_cta_base + (u64)warp * bmw, A.C);
+  const u32 fixed = WRITE ? RankSmem::fixed_write : 0u;
+  const u32 wbytes = fixed + (A.bm_in_smem ? bmw * 4 : 0);
+  unsigned char* ws = sm + (size_t)warp * wbytes;
+  const u64 gw = (u64)blockIdx.x * NW + warp;
+  const u64 G = (u64)gridDim.x * NW;
+  const Bm bm = bm_at(A.bm_in_smem ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
   if (A.bm_in_smem)
-    for (u32 i = tid; i < W * bmw; i += NT) bm_sm[i] = 0;
-  Stage gs;
-  gs.ctx = A.gst_ctx + (u64)blockIdx.x * A.gst_cap;
-  gs.time = A.gst_time + (u64)blockIdx.x * A.gst_cap;
-  gs.cnt = A.gst_cnt + (u64)blockIdx.x * A.gst_cap;
-  const u32 n_units = (A.R + W - 1) / W;
-
-  for (;;) {
-    if (tid == 0) {
-      s_unit = atomicAdd(A.unit_counter, 1u);
-      s_top = 0;
-      s_gtop = 0;
+    for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
+  RStage ss, gs;
+  if (WRITE) {
+    ss.time = (u64*)(ws + RankSmem::time_off);
+    ss.ctx = (u32*)(ws + RankSmem::ctx_off);
+    ss.cnt = (u32*)(ws + RankSmem::cnt_off);
+    ss.dep = (u32*)(ws + RankSmem::dep_off);
+    ss.par = (u32*)(ws + RankSmem::par_off);
+    const u64 gbase = gw * (u64)A.gst_cap;
+    gs.time = A.gst_time + gbase;
+    gs.ctx = A.gst_ctx + gbase;
+    gs.cnt = A.gst_cnt + gbase;
+    gs.dep = A.gst_dep + gbase;
+    gs.par = A.gst_par + gbase;
+  }
+  __syncwarp();
+  for (u64 r = gw; r < A.R; r += G) {
+    u64 E0, E1;
+    if (MODE == 0) {
+      E0 = A.entry_off[A.row_off_of_rank[r]];
+      E1 = A.entry_off[A.row_off_of_rank[r + 1]];
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 c = A.in_ctx[j];
+        if (!bm_has(bm, c)) bm_set(bm, c);
+      }
+    } else {
+      E0 = A.in_off[r];
+      E1 = A.in_off[r + 1];
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        u32 c = A.in_ctx[j];
+        for (u32 step = 0; c != NONE32 && step <= A.max_depth; ++step) {
+          if (bm_test_set(bm, c)) break;
+          c = A.parent[c];
+        }
+      }
     }
-    __syncthreads();
-    const u32 g = s_unit;
-    if (g >= n_units) break;
-    const u32 r = g * W + warp;
-    u32 nnz = 0, soff = 0;
-    if (r < A.R) {
-      u64 E0, E1;
-      const u32* in_ctx = A.in_ctx;
-      if (A.mode == 0) {
-        E0 = A.entry_off[A.row_off_of_rank[r]];
-        E1 = A.entry_off[A.row_off_of_rank[r + 1]];
-        for (u64 j = E0 + lane; j < E1; j += 32) {
-          const u32 c = in_ctx[j];
-          if (!bm_has(bm, c)) bm_set(bm, c);
-        }
-      } else {
-        E0 = A.in_off[r];
-        E1 = A.in_off[r + 1];
-        for (u64 j = E0 + lane; j < E1; j += 32) {
-          u32 c = in_ctx[j];
-          for (u32 step = 0; c != NONE32 && step <= A.max_depth; ++step) {
-            if (bm_test_set(bm, c)) break;
-            c = A.parent[c];
-          }
-        }
-      }
-      __syncwarp();
-      nnz = bm_prefix_warp(bm, lane);
-      bool ok = true;
-      if (lane == 0) soff = stage_alloc(nnz, &s_top, &s_gtop, CAP, A.gst_cap, A.status, &ok);
-      soff = __shfl_sync(FULL, soff, 0);
-      ok = __shfl_sync(FULL, ok, 0);
-      const Stage st = stage_at(soff, ss, gs);
-      if (ok) {
-        for (u32 k = lane; k < nnz; k += 32) {
-          st.time[k] = 0;
-          st.cnt[k] = 0;
-        }
-        __syncwarp();
-        if (A.mode == 0) {
-          for (u64 j = E0 + lane; j < E1; j += 32) {
-            const u32 c = in_ctx[j];
-            const u32 k = bm_rank(bm, c);
-            atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)A.in_time[j]);
-            atomicAdd(&st.cnt[k], A.in_cnt[j]);
-            st.ctx[k] = c;
-          }
-        } else {
-          bm_enumerate_warp(bm, st.ctx, lane);
-          for (u64 j = E0 + lane; j < E1; j += 32) {
-            const u32 k = bm_rank(bm, in_ctx[j]);
-            st.time[k] = A.in_time[j];
-            st.cnt[k] = A.in_cnt[j];
-          }
-          __syncwarp();
-          for (u32 d = A.max_depth; d >= 1; --d) {
-            for (u32 k = lane; k < nnz; k += 32) {
-              const u32 c = vld(&st.ctx[k]);
-              if (A.depth[c] == d) {
-                const u32 kp = bm_rank(bm, A.parent[c]);
-                atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
-                atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
-              }
-            }
-            __syncwarp();
-          }
-        }
-      } else {
-        nnz = 0;
-      }
-      __syncwarp();
+    __syncwarp();
+    if (!WRITE) {
+      const u32 n = bm_count_warp(bm, lane);
+      if (lane == 0) A.out_cnt[r] = n;
       bm_clear_warp(bm, lane);
       __syncwarp();
+      continue;
     }
-    if (lane == 0) {
-      s_nnz[warp] = nnz;
-      s_soff[warp] = soff;
+    const u32 nnz = bm_prefix_warp(bm, lane);
+    const RStage st = nnz <= RSR ? ss : gs;
+    for (u32 k = lane; k < nnz; k += 32) {
+      st.time[k] = 0;
+      st.cnt[k] = 0;
     }
-    __syncthreads();
-    if (warp == 0) {
-      const u32 x = lane < W ? s_nnz[lane] : 0u;
-      const u64 incl = warp_incl_scan((u64)x, lane);
-      if (lane < W) s_eoff[lane] = incl - x;
-      const u64 tot = __shfl_sync(FULL, incl, 31);
-      if (lane == 0) {
-        u64 pre, dummy;
-        lookback(A.ustat, g, tot, 0, &pre, &dummy, A.status);
-        s_pre = pre;
-        if (g == n_units - 1) {
-          A.total[0] = pre + tot;
-          A.out_off[A.R] = pre + tot;
-          if (pre + tot > A.nnz_cap) flag(A.status, F_CAPACITY);
+    __syncwarp();
+    if (MODE == 0) {
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 c = A.in_ctx[j];
+        const u32 k = bm_rank(bm, c);
+        atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)A.in_time[j]);
+        atomicAdd(&st.cnt[k], A.in_cnt[j]);
+        st.ctx[k] = c;
+      }
+    } else {
+      bm_enumerate_warp(bm, st.ctx, lane);
+      __syncwarp();
+      u32 maxd = 0;
+      for (u32 k = lane; k < nnz; k += 32) {
+        const u32 c = st.ctx[k];
+        const u32 d = A.depth[c];
+        st.dep[k] = d;
+        st.par[k] = d > 0 ? bm_rank(bm, A.parent[c]) : NONE32;
+        maxd = max(maxd, d);
+      }
+      maxd = __reduce_max_sync(FULL, maxd);
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 k = bm_rank(bm, A.in_ctx[j]);
+        st.time[k] = A.in_time[j];
+        st.cnt[k] = A.in_cnt[j];
+      }
+      __syncwarp();
+      for (u32 d = maxd; d >= 1; --d) {
+        for (u32 k = lane; k < nnz; k += 32) {
+          if (st.dep[k] == d) {
+            const u32 kp = st.par[k];
+            atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
+            atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
+          }
         }
+        __syncwarp();
       }
     }
-    __syncthreads();
-    if (r < A.R) {
-      const u64 eo = s_pre + s_eoff[warp];
-      if (lane == 0) A.out_off[r] = eo;
-      const Stage st = stage_at(s_soff[warp], ss, gs);
-      const u32 n = s_nnz[warp];
-      for (u32 k = lane; k < n; k += 32) {
-        const u64 gk = eo + k;
-        if (gk < A.nnz_cap) {
-          A.out_ctx[gk] = vld(&st.ctx[k]);
-          A.out_time[gk] = vld(&st.time[k]);
-          A.out_cnt[gk] = vld(&st.cnt[k]);
-        }
-      }
+    __syncwarp();
+    const u64 eo = A.out_off[r];
+    for (u32 k = lane; k < nnz; k += 32) {
+      A.out_ctx[eo + k] = vld(&st.ctx[k]);
+      A.out_time[eo + k] = vld(&st.time[k]);
+      A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
     }
-    __syncthreads();
+    bm_clear_warp(bm, lane);
+    __syncwarp();
   }
 }
 
-constexpr int RANK_NT = 256;
+constexpr int RANK_NW = 8;
 
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms) {
   RankCsrPlan P;
-  P.threads = RANK_NT;
-  const size_t base = (size_t)4096 * 16;
-  const size_t bm = (size_t)(RANK_NT / 32) * bm_words(C) * 4;
-  P.bm_in_smem = base + bm <= 110 * 1024;
-  P.smem = base + (P.bm_in_smem ? bm : 0);
-  auto kern = k_rank_csr<RANK_NT>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P.smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, RANK_NT, P.smem);
-  if (occ < 1) occ = 1;
-  P.n_units = (R + RANK_NT / 32 - 1) / (RANK_NT / 32);
-  P.grid = (int)std::min<u64>((u64)num_sms * occ, P.n_units);
-  P.gst_cap = (RANK_NT / 32) * C;
+  P.threads = RANK_NW * 32;
+  const size_t bm = (size_t)bm_words(C) * 4;
+  P.bm_in_smem = RankSmem::fixed_write + bm <= 16 * 1024;
+  P.smem_count = (P.bm_in_smem ? bm : 0) * RANK_NW;
+  P.smem = (RankSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * RANK_NW;
+  const void* ks[4] = {(const void*)k_rank_pass<RANK_NW, 0, false>,
+                       (const void*)k_rank_pass<RANK_NW, 0, true>,
+                       (const void*)k_rank_pass<RANK_NW, 1, false>,
+                       (const void*)k_rank_pass<RANK_NW, 1, true>};
+  int occ = 1 << 20;
+  for (int i = 0; i < 4; ++i) {
+    const size_t s = (i & 1) ? P.smem : P.smem_count;
+    cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s);
+    int o = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ks[i], P.threads, s);
+    occ = std::min(occ, std::max(o, 1));
+  }
+  P.n_units = R;
+  P.grid = (int)std::min<u64>((u64)num_sms * occ, ((u64)R + RANK_NW - 1) / RANK_NW);
+  P.gst_cap = C;
   return P;
 }
 
-void launch_rank_csr(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
-  k_rank_csr<RANK_NT><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
+  if (A.mode == 0) k_rank_pass<RANK_NW, 0, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  else k_rank_pass<RANK_NW, 1, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  L.count();
+  scan_exclusive(L, A.out_cnt, A.R, A.out_off, A.total, A.scan_scratch);
+  cudaMemcpyAsync(A.out_off + A.R, A.total, 8, cudaMemcpyDeviceToDevice, L.stream);
+}
+
+void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
+  if (A.mode == 0) k_rank_pass<RANK_NW, 0, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+  else k_rank_pass<RANK_NW, 1, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
   L.count();
 }
 

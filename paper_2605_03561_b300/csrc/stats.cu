@@ -494,86 +494,114 @@ __global__ void k_sp_istar(const u32* S, u32 n, const u32* n_iter, const u64* sp
   atomicMax(max_span, (unsigned long long)span[r]);
 }
 
-constexpr int SP_NT = 256;
-constexpr u32 SP_SMEM_CELLS = 4096;  // 32 B each
+constexpr int SP_NW = 8;
+constexpr u32 SP_KC = 256;    // contexts per within-rank chunk (per-warp accumulators)
+constexpr u32 SP_CELLS = 128; // (iteration, context) cells per warp
 
-// Cells (i, k) for i < I*, k in [k0, k0 + nkc): sum, max, 128-bit sum of
-// squares over ranks; per (rank, k) the within-rank CV term over i < I*.
-__global__ void __launch_bounds__(SP_NT)
-    k_sp_rows(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
-              const u64* e_time, const u32* kmap, u32 k0, u32 nkc, u32 nk, u32 I,
-              bool cells_in_smem, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi,
-              double* cvw) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  constexpr int W = SP_NT / 32;
-  u64* rk = (u64*)sm;  // per warp: sum[nkc], sqlo[nkc], sqhi[nkc]
-  u64* c_sum = rk + (size_t)W * 3 * nkc;
-  u64* c_max = c_sum + (cells_in_smem ? (size_t)I * nkc : 0);
-  u64* c_sqlo = c_max + (cells_in_smem ? (size_t)I * nkc : 0);
-  u64* c_sqhi = c_sqlo + (cells_in_smem ? (size_t)I * nkc : 0);
-  const u32 ncell = I * nkc;
-  if (cells_in_smem)
-    for (u32 q = threadIdx.x; q < ncell; q += SP_NT) c_sum[q] = c_max[q] = c_sqlo[q] = c_sqhi[q] = 0;
+// (a) Within-rank CV terms: one warp per rank of S; over iterations i < I*,
+// per context k in [k0, k0 + nkc): sum and 128-bit sum of squares of
+// t[r][i][k] in warp-private shared memory, then the CV term of (r, k).
+__global__ void __launch_bounds__(SP_NW * 32)
+    k_sp_within(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
+                const u64* e_time, const u32* kmap, u32 k0, u32 nkc, u32 nk, u32 I, double* cvw) {
+  __shared__ unsigned long long s_sum[SP_NW][SP_KC], s_lo[SP_NW][SP_KC], s_hi[SP_NW][SP_KC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u64* my_sum = rk + (size_t)warp * 3 * nkc;
-  u64* my_lo = my_sum + nkc;
-  u64* my_hi = my_lo + nkc;
-  for (u32 q = lane; q < 3 * nkc; q += 32) my_sum[q] = 0;
-  __syncthreads();
-  u64* ts_ = cells_in_smem ? c_sum : g_sum;
-  u64* tm_ = cells_in_smem ? c_max : g_max;
-  u64* tl_ = cells_in_smem ? c_sqlo : g_sqlo;
-  u64* th_ = cells_in_smem ? c_sqhi : g_sqhi;
-  const u32 gw = blockIdx.x * W + warp, nw = gridDim.x * W;
+  unsigned long long* my_sum = s_sum[warp];
+  unsigned long long* my_lo = s_lo[warp];
+  unsigned long long* my_hi = s_hi[warp];
+  for (u32 q = lane; q < nkc; q += 32) my_sum[q] = my_lo[q] = my_hi[q] = 0;
+  __syncwarp();
+  const u32 gw = blockIdx.x * SP_NW + warp, nw = gridDim.x * SP_NW;
   for (u32 ri = gw; ri < n; ri += nw) {
     const u32 r = rank_at(S, ri);
     const u64 row0 = row_off[r] + 1;  // skip the prologue row
-    for (u32 i = 0; i < I; ++i) {
-      const u64 E0 = entry_off[row0 + i], E1 = entry_off[row0 + i + 1];
-      for (u64 j = E0 + lane; j < E1; j += 32) {
-        const u32 k = kmap[e_ctx[j]];
-        if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
-        const u32 kk = k - k0;
-        const u64 t = e_time[j];
-        const u128 t2 = (u128)t * t;
-        const u64 q = cells_in_smem ? (u64)i * nkc + kk : (u64)i * nk + k0 + kk;
-        atomicAdd((unsigned long long*)&ts_[q], (unsigned long long)t);
-        atomicMax((unsigned long long*)&tm_[q], (unsigned long long)t);
-        atomic_add_u128(&tl_[q], &th_[q], t2);
-        my_sum[kk] += t;  // one entry per context per row: lanes hit distinct kk
-        const u64 lo = my_lo[kk] + (u64)t2;
-        my_hi[kk] += (u64)(t2 >> 64) + (lo < my_lo[kk] ? 1ull : 0ull);
-        my_lo[kk] = lo;
-      }
-      __syncwarp();
+    const u64 E0 = entry_off[row0], E1 = entry_off[row0 + I];
+    for (u64 j = E0 + lane; j < E1; j += 32) {
+      const u32 k = kmap[e_ctx[j]];
+      if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
+      const u32 kk = k - k0;
+      const u64 t = e_time[j];
+      atomicAdd(&my_sum[kk], (unsigned long long)t);
+      atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t * t);
     }
+    __syncwarp();
     for (u32 kk = lane; kk < nkc; kk += 32) {
-      const u64 s = my_sum[kk];
+      const u64 sm_ = my_sum[kk];
       const u128 q = ((u128)my_hi[kk] << 64) | my_lo[kk];
-      double term = 0.0;
-      if (I > 0) {
-        const double mean = u64_to_f64(s) / u64_to_f64(I);
-        const double sd = (I < 2) ? 0.0
-                                  : sqrt(u128_to_f64((u128)I * q - (u128)s * s) /
-                                         u64_to_f64((u64)I * (I - 1)));
-        term = (mean == 0.0) ? 0.0 : sd / mean;
-      }
-      cvw[(u64)ri * nk + k0 + kk] = term;
-      my_sum[kk] = 0;
-      my_lo[kk] = 0;
-      my_hi[kk] = 0;
+      const double mean = u64_to_f64(sm_) / u64_to_f64(I);
+      const double sd = (I < 2) ? 0.0
+                                : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
+                                       u64_to_f64((u64)I * (I - 1)));
+      cvw[(u64)ri * nk + k0 + kk] = (mean == 0.0) ? 0.0 : sd / mean;
+      my_sum[kk] = my_lo[kk] = my_hi[kk] = 0;
     }
     __syncwarp();
   }
-  __syncthreads();
-  if (cells_in_smem) {
-    for (u32 q = threadIdx.x; q < ncell; q += SP_NT) {
-      const u32 i = q / nkc, kk = q % nkc;
-      const u64 gq = (u64)i * nk + k0 + kk;
-      if (c_sum[q]) atomicAdd((unsigned long long*)&g_sum[gq], (unsigned long long)c_sum[q]);
-      if (c_max[q]) atomicMax((unsigned long long*)&g_max[gq], (unsigned long long)c_max[q]);
-      if (c_sqlo[q] | c_sqhi[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)c_sqhi[q] << 64) | c_sqlo[q]);
+}
+
+// (b) Cells (i, k) over ranks.  A work item is a tile of cells
+// [i0, i0 + di) x [k0, k0 + dk) (di * dk <= SP_CELLS) and a group of ranks;
+// the warp keeps the tile's partial sums private in shared memory.  It
+// processes one row at a time, so the lanes of an instruction touch distinct
+// cells (a row holds each context once) and plain updates suffice; the tile
+// is flushed to the global cells with one set of atomics per item.
+__global__ void __launch_bounds__(SP_NW * 32)
+    k_sp_cells(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
+               const u64* e_time, const u32* kmap, u32 nk, u32 I, u32 di, u32 dk, u32 n_itiles,
+               u32 n_ktiles, u32 rank_group, u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo,
+               u64* g_sqhi) {
+  __shared__ u64 c_sum[SP_NW][SP_CELLS], c_max[SP_NW][SP_CELLS], c_lo[SP_NW][SP_CELLS],
+      c_hi[SP_NW][SP_CELLS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  u64* cs = c_sum[warp];
+  u64* cm = c_max[warp];
+  u64* cl = c_lo[warp];
+  u64* ch = c_hi[warp];
+  const u64 gw = (u64)blockIdx.x * SP_NW + warp, nw = (u64)gridDim.x * SP_NW;
+  for (u64 item = gw; item < n_items; item += nw) {
+    const u64 tile = item % ((u64)n_itiles * n_ktiles);
+    const u64 grp = item / ((u64)n_itiles * n_ktiles);
+    const u32 i0 = (u32)(tile % n_itiles) * di, k0 = (u32)(tile / n_itiles) * dk;
+    const u32 ni = min(di, I - i0), nkk = min(dk, nk - k0);
+    for (u32 q = lane; q < SP_CELLS; q += 32) cs[q] = cm[q] = cl[q] = ch[q] = 0;
+    __syncwarp();
+    const u32 r_begin = (u32)(grp * rank_group);
+    const u32 r_end = min(n, r_begin + rank_group);
+    for (u32 rb = r_begin; rb < r_end; rb += 32) {
+      // 32 ranks' entry ranges for rows i0 .. i0 + ni, fetched in parallel
+      u64 my_row = 0;
+      if (rb + lane < r_end) my_row = row_off[rank_at(S, rb + lane)] + 1 + i0;
+      const u32 cnt = min(32u, r_end - rb);
+      for (u32 x = 0; x < cnt; ++x) {
+        const u64 row = __shfl_sync(FULL, my_row, x);
+        for (u32 ii = 0; ii < ni; ++ii) {
+          const u64 E0 = entry_off[row + ii], E1 = entry_off[row + ii + 1];
+          for (u64 j = E0 + lane; j < E1; j += 32) {
+            const u32 k = kmap[e_ctx[j]];
+            if (k == NONE32 || k < k0 || k >= k0 + nkk) continue;
+            const u32 q = ii * dk + (k - k0);
+            const u64 t = e_time[j];
+            const u128 t2 = (u128)t * t;
+            cs[q] += t;
+            if (t > cm[q]) cm[q] = t;
+            const u64 lo = cl[q] + (u64)t2;
+            ch[q] += (u64)(t2 >> 64) + (lo < cl[q] ? 1ull : 0ull);
+            cl[q] = lo;
+          }
+          __syncwarp();
+        }
+      }
     }
+    __syncwarp();
+    for (u32 q = lane; q < ni * dk; q += 32) {
+      const u32 ii = q / dk, kk = q % dk;
+      if (kk >= nkk) continue;
+      const u64 gq = (u64)(i0 + ii) * nk + k0 + kk;
+      if (cs[q]) atomicAdd((unsigned long long*)&g_sum[gq], (unsigned long long)cs[q]);
+      if (cm[q]) atomicMax((unsigned long long*)&g_max[gq], (unsigned long long)cm[q]);
+      if (cl[q] | ch[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)ch[q] << 64) | cl[q]);
+    }
+    __syncwarp();
   }
 }
 
@@ -873,19 +901,29 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
-  // chunk the context set so that a chunk's cells fit in shared memory
-  u32 nkc = std::min<u32>(std::min<u32>(nk, 256), I > 0 ? std::max<u32>(1, SP_SMEM_CELLS / I) : 256);
-  const bool smem_cells = (u64)I * nkc <= SP_SMEM_CELLS;
-  const int W = SP_NT / 32;
-  const size_t smem = ((size_t)W * 3 * nkc + (smem_cells ? (size_t)4 * I * nkc : 0)) * 8;
-  if (smem > 200 * 1024) return fail(TA_ERR_INVALID_ARG, "speedup: too many contexts per chunk");
-  cudaFuncSetAttribute(k_sp_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const int grid = std::max(1, std::min<int>(c->num_sms * 2, (int)((n + W - 1) / W)));
-  for (u32 k0 = 0; I > 0 && k0 < nk; k0 += nkc) {
-    const u32 cnk = std::min(nkc, nk - k0);
-    k_sp_rows<<<grid, SP_NT, smem, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
-                                               e->e_time, kmap, k0, cnk, nk, I, smem_cells, gs, gm,
-                                               gl, gh, cvw);
+  if (I > 0) {
+    const int grid = std::max(1, std::min<int>(c->num_sms * 8, (int)((n + SP_NW - 1) / SP_NW)));
+    for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
+      k_sp_within<<<grid, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
+                                                      e->e_time, kmap, k0, std::min(SP_KC, nk - k0),
+                                                      nk, I, cvw);
+      L.count();
+    }
+    const u32 dk = std::min<u32>(nk, SP_CELLS);
+    const u32 di = std::max<u32>(1, std::min<u32>(I, SP_CELLS / dk));
+    const u32 n_itiles = (I + di - 1) / di, n_ktiles = (nk + dk - 1) / dk;
+    // enough items to fill the GPU, each with a sizeable group of ranks
+    const u64 tiles = (u64)n_itiles * n_ktiles;
+    const u64 want_items = (u64)c->num_sms * 32;
+    u64 groups = std::max<u64>(1, want_items / tiles);
+    groups = std::min<u64>(groups, std::max<u64>(1, (n + 255) / 256));
+    const u32 rank_group = (u32)((n + groups - 1) / groups);
+    groups = (n + rank_group - 1) / rank_group;
+    const u64 n_items = tiles * groups;
+    const int grid2 = (int)std::min<u64>((u64)c->num_sms * 8, (n_items + SP_NW - 1) / SP_NW);
+    k_sp_cells<<<grid2, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
+                                                    e->e_time, kmap, nk, I, di, dk, n_itiles,
+                                                    n_ktiles, rank_group, n_items, gs, gm, gl, gh);
     L.count();
   }
   ta_speedup_ctx* dper;

@@ -241,6 +241,80 @@ __device__ __forceinline__ void lookback(UnitStatus* S, u32 t, u64 a, u64 b, u64
   *pre_b = sb;
 }
 
+// Warp-cooperative look-back: all 32 lanes call it.  Lane 0 publishes the
+// unit's aggregate; the warp then inspects 32 predecessors per memory round
+// trip (lane i looks at unit t-1-i), adds the aggregates up to the nearest
+// predecessor that has an inclusive prefix, and lane 0 publishes its own
+// inclusive prefix.  Waiting happens only while a predecessor in the window
+// has not published anything yet; every wait is bounded.
+__device__ __forceinline__ void lookback_warp(UnitStatus* S, u32 t, u64 a, u64 b, u64* pre_a,
+                                              u64* pre_b, u32* status) {
+  const int lane = threadIdx.x & 31;
+  if (t == 0) {
+    if (lane == 0) {
+      S[0].inc_a = a;
+      S[0].inc_b = b;
+      __threadfence();
+      st_release(&S[0].flag, 2);
+    }
+    *pre_a = 0;
+    *pre_b = 0;
+    __syncwarp();
+    return;
+  }
+  if (lane == 0) {
+    S[t].agg_a = a;
+    S[t].agg_b = b;
+    __threadfence();
+    st_release(&S[t].flag, 1);
+  }
+  u64 sa = 0, sb = 0;
+  long long base = (long long)t - 1;
+  u32 spins = 0;
+  for (;;) {
+    const long long idx = base - lane;
+    const u32 f = idx >= 0 ? ld_acquire(&S[idx].flag) : 2u;
+    const u32 m2 = __ballot_sync(FULL, f == 2);
+    const u32 m0 = __ballot_sync(FULL, f == 0);
+    const int first2 = m2 ? __ffs(m2) - 1 : 32;
+    const u32 below = first2 >= 32 ? FULL : ((1u << first2) - 1u);
+    if (m0 & below) {  // a nearer predecessor has not published yet
+      if (++spins > SPIN_LIMIT) {
+        if (lane == 0) flag(status, F_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+      continue;
+    }
+    u64 va = 0, vb = 0;
+    if (lane < first2) {
+      va = ld_relaxed(&S[idx].agg_a);
+      vb = ld_relaxed(&S[idx].agg_b);
+    } else if (lane == first2 && idx >= 0) {
+      va = ld_relaxed(&S[idx].inc_a);
+      vb = ld_relaxed(&S[idx].inc_b);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      va += __shfl_xor_sync(FULL, va, o);
+      vb += __shfl_xor_sync(FULL, vb, o);
+    }
+    sa += va;
+    sb += vb;
+    if (first2 < 32) break;
+    base -= 32;
+  }
+  if (lane == 0) {
+    S[t].inc_a = sa + a;
+    S[t].inc_b = sb + b;
+    __threadfence();
+    st_release(&S[t].flag, 2);
+  }
+  *pre_a = sa;
+  *pre_b = sb;
+  __syncwarp();
+}
+
 // ------------------------------------------- exact integer -> double ------
 // Correctly rounded (nearest, ties to even).  64-bit values use the CUDA
 // conversion; wider values are first narrowed to 64 bits keeping a sticky

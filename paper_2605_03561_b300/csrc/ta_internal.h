@@ -20,35 +20,42 @@ struct TensorArgs {
   const u64* rank_off;
   const u64* ts;
   const u32* ctx;
-  u32 R, C, m, n_tiles;
+  u32 R, C, m;
+  u64 n_tiles;
   u64 N;
   const u32* tfr;  // [n_tiles + 1] first rank starting at or after tile start
-  u32* unit_counter;
-  UnitStatus* ustat;  // [n_tiles]
+  // per-tile counts (count pass) and their exclusive prefix (scan)
+  u32* tile_rows;
+  u64* tile_ents;
+  u64* tile_row_off;
+  u64* tile_ent_off;
+  u64* totals;  // [2] rows, entries
+  u64* scan_scratch;  // 2 x scan_scratch_elems(n_tiles)
+  // outputs (write pass), exactly sized
   u64* row_off_of_rank;
   u64* entry_off;
   u32* e_ctx;
   u64* e_time;
   u32* e_cnt;
-  u64 rows_cap, nnz_cap;
-  u64* totals;  // [2] rows, nnz
-  u32* gbm;     // global bitmaps (per CTA x warp) when not in shared memory
+  u32* gbm;  // global bitmaps (per warp) when not in shared memory
   u32* gst_ctx;
   u64* gst_time;
   u32* gst_cnt;
-  u32 gst_cap;  // per CTA
+  u32 gst_cap;  // per warp: rows with more entries than shared staging holds
   u32 bm_in_smem;
   u32* status;
 };
 
 struct TensorPlan {
   int tile, threads, grid;
-  size_t smem;
+  size_t smem, smem_count;
   bool bm_in_smem;
   u32 gst_cap;
 };
 TensorPlan plan_tensor(u32 C, u64 N, int num_sms);
-void launch_tensor(const Launch& L, const TensorPlan& P, const TensorArgs& A);
+void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A);
+void launch_tile_scan(const Launch& L, const TensorArgs& A);
+void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A);
 
 void launch_rank_off(const Launch& L, const u64* rank_off, u32 R, u64 N, const u64* ts,
                      u64* span, u64* max_span, u32* status);
@@ -60,7 +67,7 @@ void launch_cct(const Launch& L, const u32* parent, u32 C, u32* depth, u32* max_
 void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_iter);
 
 // Per-rank CSR of distinct contexts (mode 0: exclusive from the tensor,
-// mode 1: inclusive from the exclusive CSR).
+// mode 1: inclusive from the exclusive CSR): count pass + scan, write pass.
 struct RankCsrArgs {
   u32 mode, R, C, max_depth;
   // mode 0 input: tensor
@@ -73,30 +80,37 @@ struct RankCsrArgs {
   const u32* in_cnt;
   const u32* parent;
   const u32* depth;
-  u32* unit_counter;
-  UnitStatus* ustat;
-  u64* out_off;
+  u32* out_cnt;  // [R] count pass
+  u64* out_off;  // [R+1] scan
   u32* out_ctx;
   u64* out_time;
-  u32* out_cnt;
-  u64 nnz_cap;
+  u32* out_cnt_e;
   u64* total;  // [1]
+  u64* scan_scratch;
   u32* gbm;
   u32* gst_ctx;
   u64* gst_time;
   u32* gst_cnt;
+  u32* gst_dep;
+  u32* gst_par;
   u32 gst_cap;
   u32 bm_in_smem;
   u32* status;
 };
 struct RankCsrPlan {
   int threads, grid;
-  size_t smem;
+  size_t smem, smem_count;
   bool bm_in_smem;
   u32 gst_cap;
   u32 n_units;
 };
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
-void launch_rank_csr(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+
+// Exclusive prefix sums (scan.cu); scratch holds scan_scratch_elems(n) u64.
+u64 scan_scratch_elems(u64 n);
+void scan_exclusive(const Launch& L, const u32* in, u64 n, u64* out, u64* total, u64* scratch);
+void scan_exclusive(const Launch& L, const u64* in, u64 n, u64* out, u64* total, u64* scratch);
 
 }  // namespace ta
