@@ -171,19 +171,65 @@ void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_it
 // boundaries) cost only their own work.
 namespace {
 
-constexpr u32 TW = 1024;   // samples per tile
+constexpr u32 TW = 4096;   // samples per tile
+constexpr u32 MASKW = TW / 32 + 4;  // rank-start mask words (positions 0 .. TW)
+constexpr int DEPTH = 3;   // steps prefetched ahead
 constexpr u32 STEP = 128;  // samples per warp step (4 per lane)
 constexpr u32 RS = 128;    // staged entries per warp in shared memory
 
+constexpr u32 TL = 128;    // touched bitmap words remembered per row
+
 struct WarpSmem {
-  static constexpr u32 mask_off = 0;               // u32[36] rank-start mask
-  static constexpr u32 time_off = 4 * 36 + 16;     // u64[RS] (8-byte aligned)
+  static constexpr u32 mask_off = 0;                  // u32[MASKW] rank-start mask
+  static constexpr u32 tl_off = 4 * MASKW;            // u32[TL + 4] touched words, count
+  static constexpr u32 time_off = tl_off + 4 * (TL + 4);  // u64[RS] (16-byte aligned)
   static constexpr u32 ctx_off = time_off + 8 * RS;
   static constexpr u32 cnt_off = ctx_off + 4 * RS;
-  static constexpr u32 bm_off = cnt_off + 4 * RS;  // bitmap words (16-byte aligned)
-  static constexpr u32 fixed_count = 4 * 36 + 16;  // count pass: mask only
+  static constexpr u32 bm_off = cnt_off + 4 * RS;     // bitmap words (16-byte aligned)
+  static constexpr u32 fixed_count = time_off;        // count pass: mask + touched list
   static constexpr u32 fixed_write = bm_off;
 };
+
+// Bitmap marking that also remembers which words became non-empty, so the
+// row's bitmap can be cleared by visiting only those words.  The count pass
+// keeps no summary level (with_l2 = false): it only needs the number of new
+// bits, and a row that touches more than TL words is cleared in full.
+struct Touched {
+  u32* list;  // [TL]
+  u32* cnt;   // [1]
+};
+
+template <bool WITH_L2>
+__device__ __forceinline__ u32 bm_mark(const Bm& b, const Touched& tw, u32 c) {
+  const u32 w = c >> 5, bit = 1u << (c & 31);
+  const u32 old = atomicOr(&b.L1[w], bit);
+  if (old == 0) {
+    if (WITH_L2) atomicOr(&b.L2[w >> 5], 1u << (w & 31));
+    const u32 i = atomicAdd(tw.cnt, 1u);
+    if (i < TL) tw.list[i] = w;
+  }
+  return (old & bit) ? 0u : 1u;
+}
+
+template <bool WITH_L2>
+__device__ __forceinline__ void bm_clear_touched(const Bm& b, const Touched& tw, int lane) {
+  __syncwarp();
+  const u32 n = *tw.cnt;
+  if (n <= TL) {
+    for (u32 i = lane; i < n; i += 32) {
+      const u32 w = tw.list[i];
+      b.L1[w] = 0;
+      if (WITH_L2) b.L2[w >> 5] = 0;
+    }
+  } else if (WITH_L2) {
+    bm_clear_warp(b, lane);
+  } else {
+    for (u32 i = lane; i < b.W1; i += 32) b.L1[i] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) *tw.cnt = 0;
+  __syncwarp();
+}
 
 struct Step {
   u32 c[4];
@@ -234,18 +280,11 @@ struct Stage {
   u32* cnt;
 };
 
-// Write pass: rank, accumulate and write the row [s, e) at entry eo.
-__device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Stage& sm,
-                                         const Stage& gl, u64 s, u64 e, bool e_rs, u64 eo,
-                                         int lane) {
-  __syncwarp();
-  const u32 nnz = bm_prefix_warp(bm, lane);
-  const Stage st = (nnz <= RS) ? sm : gl;
-  for (u32 k = lane; k < nnz; k += 32) {
-    st.time[k] = 0;
-    st.cnt[k] = 0;
-  }
-  __syncwarp();
+// Write pass, one row [s, e) whose ranks are in the bitmap: accumulate time
+// and count at each context's rank in the stage, then write the row at entry
+// eo.  The stage is shared memory or the warp's global region (compile time).
+__device__ __forceinline__ void accumulate_row(const TensorArgs& A, const Bm& bm, const Stage& st,
+                                               u64 s, u64 e, bool e_rs, int lane) {
   const u32 C = A.C;
   for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
     Step x;
@@ -286,33 +325,65 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
       st.ctx[k] = rc;
     }
   }
-  __syncwarp();
+}
+
+__device__ __forceinline__ void emit_row(const TensorArgs& A, const Stage& st, u32 nnz, u64 eo,
+                                         int lane) {
   for (u32 k = lane; k < nnz; k += 32) {
     const u64 g = eo + k;
-    A.e_ctx[g] = vld(&st.ctx[k]);
-    A.e_time[g] = vld(&st.time[k]);
-    A.e_cnt[g] = vld(&st.cnt[k]);
+    A.e_ctx[g] = st.ctx[k];
+    A.e_time[g] = st.time[k];
+    A.e_cnt[g] = st.cnt[k];
   }
-  bm_clear_warp(bm, lane);
+}
+
+__device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
+                                         const Stage& sm, const Stage& gl, u64 s, u64 e,
+                                         bool e_rs, u64 eo, int lane) {
   __syncwarp();
+  const u32 nnz = bm_prefix_warp(bm, lane);
+  if (nnz <= RS) {
+    for (u32 k = lane; k < nnz; k += 32) {
+      sm.time[k] = 0;
+      sm.cnt[k] = 0;
+    }
+    __syncwarp();
+    accumulate_row(A, bm, sm, s, e, e_rs, lane);
+    __syncwarp();
+    emit_row(A, sm, nnz, eo, lane);
+  } else {
+    for (u32 k = lane; k < nnz; k += 32) {
+      gl.time[k] = 0;
+      gl.cnt[k] = 0;
+    }
+    __syncwarp();
+    accumulate_row(A, bm, gl, s, e, e_rs, lane);
+    __syncwarp();
+    emit_row(A, gl, nnz, eo, lane);
+  }
+  bm_clear_touched<true>(bm, tw, lane);
   return nnz;
 }
 
 }  // namespace
 
-template <int NW, bool WRITE>
+template <int NW, bool WRITE, bool BMS>
 __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
   const u32 fixed = WRITE ? WarpSmem::fixed_write : WarpSmem::fixed_count;
-  const u32 wbytes = fixed + (A.bm_in_smem ? bmw * 4 : 0);
+  const u32 wbytes = fixed + (BMS ? bmw * 4 : 0);
   unsigned char* ws = sm + (size_t)warp * wbytes;
   const u64 gw = (u64)blockIdx.x * NW + warp;
   const u64 G = (u64)gridDim.x * NW;
   u32* mask = (u32*)(ws + WarpSmem::mask_off);
-  const Bm bm = bm_at(A.bm_in_smem ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
-  if (A.bm_in_smem)
+  Touched tw;
+  tw.list = (u32*)(ws + WarpSmem::tl_off);
+  tw.cnt = tw.list + TL;
+  if (lane == 0) *tw.cnt = 0;
+  const Bm bm = bm_at(BMS ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
+  if (BMS)
     for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
   Stage sst, gst;
   if (WRITE) {
@@ -339,7 +410,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       PR = A.tile_row_off[t];
       PE = A.tile_ent_off[t];
     }
-    for (u32 i = lane; i < 36; i += 32) mask[i] = 0;
+    for (u32 i = lane; i < MASKW; i += 32) mask[i] = 0;
     __syncwarp();
     for (u32 r = lo + lane; r < hi; r += 32) {
       const u32 p = (u32)(A.rank_off[r] - a);
@@ -348,41 +419,48 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     __syncwarp();
 
     u32 rank_ptr = lo, rows_local = 0, fl = 0;
+    u32 fresh = 0;  // count pass: contexts this lane saw first in the open row
     u64 cum = 0;
     bool row_open = false;
     u64 row_s = 0;
-    Step cur;
+    // ring of steps: ring[0] is processed while ring[1 .. DEPTH] are in flight
+    Step ring[DEPTH + 1];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      cur.c[j] = NONE32;
-      cur.t[j] = 0;
+    for (int d = 0; d <= DEPTH; ++d) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        ring[d].c[j] = NONE32;
+        ring[d].t[j] = 0;
+      }
     }
-    load_step(A, a, lane, WRITE && a < b, cur);
+#pragma unroll
+    for (int d = 0; d < DEPTH; ++d) {
+      const u64 qd = a + (u64)d * STEP;
+      if (qd < N) load_step(A, qd, lane, WRITE && qd < b, ring[d]);
+    }
     for (u64 q0 = a;; q0 += STEP) {
       const bool tile_step = q0 < b;
       if (!tile_step && !row_open) break;
       const u64 lim = tile_step ? b : qrank;
       if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, lim, true, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, lim, true, PE + cum, lane);
           else {
-            __syncwarp();
-            cum += bm_count_warp(bm, lane);
-            bm_clear_warp(bm, lane);
-            __syncwarp();
+            cum += __reduce_add_sync(FULL, fresh);
+            fresh = 0;
+            bm_clear_touched<false>(bm, tw, lane);
           }
         }
         row_open = false;
         break;
       }
-      Step nx;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        nx.c[j] = NONE32;
-        nx.t[j] = 0;
-      }
+      Step& cur = ring[0];
+      const Step& nx = ring[1];
       const u64 q1 = q0 + STEP;
-      if (q1 < N) load_step(A, q1, lane, WRITE && q1 < b, nx);
+      {
+        const u64 qd = q0 + (u64)DEPTH * STEP;
+        if (qd < N) load_step(A, qd, lane, WRITE && qd < b, ring[DEPTH]);
+      }
       const u64 q = q0 + 4 * (u64)lane;
       // samples of this step that exist (tile steps: below b; continuation:
       // below the next rank start)
@@ -445,22 +523,25 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         if (row_open) {
 #pragma unroll
           for (int j = 0; j < 4; ++j)
-            if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) bm_set(bm, cur.c[j] < C ? cur.c[j] : 0u);
+            if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) {
+              if (WRITE) bm_mark<true>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
+              else fresh += bm_mark<false>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
+            }
         }
         if (q1 >= b && b == N) {  // the last tile: rows end at N
           if (row_open) {
-            if (WRITE) cum += write_row(A, bm, sst, gst, row_s, N, true, PE + cum, lane);
+            if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, lane);
             else {
-              __syncwarp();
-              cum += bm_count_warp(bm, lane);
-              bm_clear_warp(bm, lane);
-              __syncwarp();
+              cum += __reduce_add_sync(FULL, fresh);
+              fresh = 0;
+              bm_clear_touched<false>(bm, tw, lane);
             }
           }
           row_open = false;
           break;
         }
-        cur = nx;
+#pragma unroll
+        for (int d = 0; d < DEPTH; ++d) ring[d] = ring[d + 1];
         continue;
       }
       u32 cc[4];
@@ -483,7 +564,10 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
           for (int j = 0; j < 4; ++j) {
             const u32 pos = pos0 + j;
             if (((valid4 >> j) & 1u) && pos >= seg_lo && pos < end)
-              if (q + j == row_s || pc[j] != cur.c[j]) bm_set(bm, cc[j]);
+              if (q + j == row_s || pc[j] != cur.c[j]) {
+                if (WRITE) bm_mark<true>(bm, tw, cc[j]);
+                else fresh += bm_mark<false>(bm, tw, cc[j]);
+              }
           }
         }
         if (nxt >= STEP) break;
@@ -492,12 +576,11 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         const bool p_rs = (__shfl_sync(FULL, rs4, src) >> bj) & 1u;
         const bool p_ms = (__shfl_sync(FULL, ms4, src) >> bj) & 1u;
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, p, p_rs, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, p, p_rs, PE + cum, lane);
           else {
-            __syncwarp();
-            cum += bm_count_warp(bm, lane);
-            bm_clear_warp(bm, lane);
-            __syncwarp();
+            cum += __reduce_add_sync(FULL, fresh);
+            fresh = 0;
+            bm_clear_touched<false>(bm, tw, lane);
           }
         }
         if (!tile_step) {  // the continuation found the end of the row
@@ -529,18 +612,18 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       if (stop) break;
       if (q1 >= b && b == N) {  // the last tile: rows end at N
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, sst, gst, row_s, N, true, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, lane);
           else {
-            __syncwarp();
-            cum += bm_count_warp(bm, lane);
-            bm_clear_warp(bm, lane);
-            __syncwarp();
+            cum += __reduce_add_sync(FULL, fresh);
+            fresh = 0;
+            bm_clear_touched<false>(bm, tw, lane);
           }
         }
         row_open = false;
         break;
       }
-      cur = nx;
+#pragma unroll
+      for (int d = 0; d < DEPTH; ++d) ring[d] = ring[d + 1];
     }
     fl = __reduce_or_sync(FULL, fl);
     if (lane == 0 && fl) flag(A.status, fl);
@@ -573,13 +656,15 @@ TensorPlan plan_tensor(u32 C, u64 N, int num_sms) {
   P.bm_in_smem = WarpSmem::fixed_write + bm <= 12 * 1024;
   P.smem_count = (WarpSmem::fixed_count + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
   P.smem = (WarpSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
-  set_smem((const void*)k_tensor_pass<TENSOR_NW, false>, P.smem_count);
-  set_smem((const void*)k_tensor_pass<TENSOR_NW, true>, P.smem);
+  const void* kc = P.bm_in_smem ? (const void*)k_tensor_pass<TENSOR_NW, false, true>
+                                 : (const void*)k_tensor_pass<TENSOR_NW, false, false>;
+  const void* kw = P.bm_in_smem ? (const void*)k_tensor_pass<TENSOR_NW, true, true>
+                                 : (const void*)k_tensor_pass<TENSOR_NW, true, false>;
+  set_smem(kc, P.smem_count);
+  set_smem(kw, P.smem);
   int o1 = 0, o2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_tensor_pass<TENSOR_NW, false>, P.threads,
-                                                P.smem_count);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_tensor_pass<TENSOR_NW, true>, P.threads,
-                                                P.smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, kc, P.threads, P.smem_count);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, kw, P.threads, P.smem);
   const int occ = std::max(1, std::min(o1, o2));
   const u64 n_tiles = std::max<u64>(1, (N + TW - 1) / TW);
   P.grid = (int)std::min<u64>((u64)num_sms * occ, (n_tiles + TENSOR_NW - 1) / TENSOR_NW);
@@ -588,7 +673,8 @@ TensorPlan plan_tensor(u32 C, u64 N, int num_sms) {
 }
 
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  k_tensor_pass<TENSOR_NW, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  if (P.bm_in_smem) k_tensor_pass<TENSOR_NW, false, true><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  else k_tensor_pass<TENSOR_NW, false, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
   L.count();
 }
 
@@ -599,7 +685,8 @@ void launch_tile_scan(const Launch& L, const TensorArgs& A) {
 }
 
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  k_tensor_pass<TENSOR_NW, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+  if (P.bm_in_smem) k_tensor_pass<TENSOR_NW, true, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+  else k_tensor_pass<TENSOR_NW, true, false><<<P.grid, P.threads, P.smem, L.stream>>>(A);
   L.count();
 }
 
@@ -615,7 +702,8 @@ void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs&
 // from the scan; rank, accumulate (and sweep) in shared memory; write.
 namespace {
 
-constexpr u32 RSR = 256;  // staged entries per warp in shared memory
+constexpr u32 RSR = 256;           // staged entries per warp in shared memory
+constexpr u32 DEPTH_BUCKETS = 64;  // depth range handled by the bucket sweep
 
 struct RankSmem {
   static constexpr u32 time_off = 0;                 // u64[RSR]
@@ -623,7 +711,8 @@ struct RankSmem {
   static constexpr u32 cnt_off = ctx_off + 4 * RSR;  // u32[RSR]
   static constexpr u32 dep_off = cnt_off + 4 * RSR;  // u32[RSR] (inclusive)
   static constexpr u32 par_off = dep_off + 4 * RSR;  // u32[RSR] (inclusive)
-  static constexpr u32 fixed_write = par_off + 4 * RSR;
+  static constexpr u32 bucket_off = par_off + 4 * RSR;  // u32[DEPTH_BUCKETS + 1 + RSR]
+  static constexpr u32 fixed_write = (bucket_off + 4 * (DEPTH_BUCKETS + 1 + RSR) + 15) & ~15u;
 };
 
 struct RStage {
@@ -636,26 +725,28 @@ struct RStage {
 
 }  // namespace
 
-template <int NW, int MODE, bool WRITE>
+template <int NW, int MODE, bool WRITE, bool BMS>
 __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
   const u32 fixed = WRITE ? RankSmem::fixed_write : 0u;
-  const u32 wbytes = fixed + (A.bm_in_smem ? bmw * 4 : 0);
+  const u32 wbytes = fixed + (BMS ? bmw * 4 : 0);
   unsigned char* ws = sm + (size_t)warp * wbytes;
   const u64 gw = (u64)blockIdx.x * NW + warp;
   const u64 G = (u64)gridDim.x * NW;
-  const Bm bm = bm_at(A.bm_in_smem ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
-  if (A.bm_in_smem)
+  const Bm bm = bm_at(BMS ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
+  if (BMS)
     for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
   RStage ss, gs;
+  u32* bucket_base = nullptr;
   if (WRITE) {
     ss.time = (u64*)(ws + RankSmem::time_off);
     ss.ctx = (u32*)(ws + RankSmem::ctx_off);
     ss.cnt = (u32*)(ws + RankSmem::cnt_off);
     ss.dep = (u32*)(ws + RankSmem::dep_off);
     ss.par = (u32*)(ws + RankSmem::par_off);
+    bucket_base = (u32*)(ws + RankSmem::bucket_off);
     const u64 gbase = gw * (u64)A.gst_cap;
     gs.time = A.gst_time + gbase;
     gs.ctx = A.gst_ctx + gbase;
@@ -669,9 +760,16 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
-      for (u64 j = E0 + lane; j < E1; j += 32) {
-        const u32 c = A.in_ctx[j];
-        if (!bm_has(bm, c)) bm_set(bm, c);
+      for (u64 j0 = E0; j0 < E1; j0 += 128) {
+        u32 c[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const u64 j = j0 + 32 * u + lane;
+          c[u] = j < E1 ? A.in_ctx[j] : NONE32;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (c[u] != NONE32 && !bm_has(bm, c[u])) bm_set(bm, c[u]);
       }
     } else {
       E0 = A.in_off[r];
@@ -693,19 +791,32 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       continue;
     }
     const u32 nnz = bm_prefix_warp(bm, lane);
-    const RStage st = nnz <= RSR ? ss : gs;
+    auto run = [&](const RStage& st) {
     for (u32 k = lane; k < nnz; k += 32) {
       st.time[k] = 0;
       st.cnt[k] = 0;
     }
     __syncwarp();
     if (MODE == 0) {
-      for (u64 j = E0 + lane; j < E1; j += 32) {
-        const u32 c = A.in_ctx[j];
-        const u32 k = bm_rank(bm, c);
-        atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)A.in_time[j]);
-        atomicAdd(&st.cnt[k], A.in_cnt[j]);
-        st.ctx[k] = c;
+      for (u64 j0 = E0; j0 < E1; j0 += 128) {
+        u32 c[4], n[4];
+        u64 t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const u64 j = j0 + 32 * u + lane;
+          const bool ok = j < E1;
+          c[u] = ok ? A.in_ctx[j] : NONE32;
+          t[u] = ok ? A.in_time[j] : 0ull;
+          n[u] = ok ? A.in_cnt[j] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (c[u] == NONE32) continue;
+          const u32 k = bm_rank(bm, c[u]);
+          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t[u]);
+          atomicAdd(&st.cnt[k], n[u]);
+          st.ctx[k] = c[u];
+        }
       }
     } else {
       bm_enumerate_warp(bm, st.ctx, lane);
@@ -725,15 +836,52 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         st.cnt[k] = A.in_cnt[j];
       }
       __syncwarp();
-      for (u32 d = maxd; d >= 1; --d) {
+      if (maxd < DEPTH_BUCKETS && nnz <= RSR) {
+        // order the entries by depth (counting sort in shared memory), then
+        // roll up one level at a time from the deepest: O(entries + depth)
+        u32* hist = bucket_base;
+        u32* order = bucket_base + DEPTH_BUCKETS + 1;
+        for (u32 d = lane; d <= DEPTH_BUCKETS; d += 32) hist[d] = 0;
+        __syncwarp();
+        for (u32 k = lane; k < nnz; k += 32) atomicAdd(&hist[st.dep[k]], 1u);
+        __syncwarp();
+        if (lane == 0) {
+          u32 run = 0;
+          for (u32 d = 0; d <= maxd; ++d) {
+            const u32 h = hist[d];
+            hist[d] = run;
+            run += h;
+          }
+          hist[maxd + 1] = run;
+        }
+        __syncwarp();
         for (u32 k = lane; k < nnz; k += 32) {
-          if (st.dep[k] == d) {
+          const u32 slot = atomicAdd(&hist[st.dep[k]], 1u);
+          order[slot] = k;
+        }
+        __syncwarp();
+        // after the scatter hist[d] is the end of bucket d = start of d + 1
+        for (u32 d = maxd; d >= 1; --d) {
+          const u32 b0 = hist[d - 1], b1 = hist[d];
+          for (u32 i = b0 + lane; i < b1; i += 32) {
+            const u32 k = order[i];
             const u32 kp = st.par[k];
             atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
             atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
           }
+          __syncwarp();
         }
-        __syncwarp();
+      } else {
+        for (u32 d = maxd; d >= 1; --d) {
+          for (u32 k = lane; k < nnz; k += 32) {
+            if (st.dep[k] == d) {
+              const u32 kp = st.par[k];
+              atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
+              atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
+            }
+          }
+          __syncwarp();
+        }
       }
     }
     __syncwarp();
@@ -743,6 +891,9 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       A.out_time[eo + k] = vld(&st.time[k]);
       A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
     }
+    };
+    if (nnz <= RSR) run(ss);
+    else run(gs);
     bm_clear_warp(bm, lane);
     __syncwarp();
   }
@@ -757,10 +908,18 @@ RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms) {
   P.bm_in_smem = RankSmem::fixed_write + bm <= 16 * 1024;
   P.smem_count = (P.bm_in_smem ? bm : 0) * RANK_NW;
   P.smem = (RankSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * RANK_NW;
-  const void* ks[4] = {(const void*)k_rank_pass<RANK_NW, 0, false>,
-                       (const void*)k_rank_pass<RANK_NW, 0, true>,
-                       (const void*)k_rank_pass<RANK_NW, 1, false>,
-                       (const void*)k_rank_pass<RANK_NW, 1, true>};
+  const void* ks[4];
+  if (P.bm_in_smem) {
+    ks[0] = (const void*)k_rank_pass<RANK_NW, 0, false, true>;
+    ks[1] = (const void*)k_rank_pass<RANK_NW, 0, true, true>;
+    ks[2] = (const void*)k_rank_pass<RANK_NW, 1, false, true>;
+    ks[3] = (const void*)k_rank_pass<RANK_NW, 1, true, true>;
+  } else {
+    ks[0] = (const void*)k_rank_pass<RANK_NW, 0, false, false>;
+    ks[1] = (const void*)k_rank_pass<RANK_NW, 0, true, false>;
+    ks[2] = (const void*)k_rank_pass<RANK_NW, 1, false, false>;
+    ks[3] = (const void*)k_rank_pass<RANK_NW, 1, true, false>;
+  }
   int occ = 1 << 20;
   for (int i = 0; i < 4; ++i) {
     const size_t s = (i & 1) ? P.smem : P.smem_count;
@@ -775,17 +934,24 @@ RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms) {
   return P;
 }
 
+template <int MODE, bool WRITE>
+static void rank_launch(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
+  const size_t smem = WRITE ? P.smem : P.smem_count;
+  if (P.bm_in_smem) k_rank_pass<RANK_NW, MODE, WRITE, true><<<P.grid, P.threads, smem, L.stream>>>(A);
+  else k_rank_pass<RANK_NW, MODE, WRITE, false><<<P.grid, P.threads, smem, L.stream>>>(A);
+}
+
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
-  if (A.mode == 0) k_rank_pass<RANK_NW, 0, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
-  else k_rank_pass<RANK_NW, 1, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  if (A.mode == 0) rank_launch<0, false>(L, P, A);
+  else rank_launch<1, false>(L, P, A);
   L.count();
   scan_exclusive(L, A.out_cnt, A.R, A.out_off, A.total, A.scan_scratch);
   cudaMemcpyAsync(A.out_off + A.R, A.total, 8, cudaMemcpyDeviceToDevice, L.stream);
 }
 
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
-  if (A.mode == 0) k_rank_pass<RANK_NW, 0, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
-  else k_rank_pass<RANK_NW, 1, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+  if (A.mode == 0) rank_launch<0, true>(L, P, A);
+  else rank_launch<1, true>(L, P, A);
   L.count();
 }
 

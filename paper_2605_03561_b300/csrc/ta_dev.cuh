@@ -118,6 +118,14 @@ __device__ __forceinline__ void bm_set(const Bm& b, u32 c) {
   if (old == 0) atomicOr(&b.L2[w >> 5], 1u << (w & 31));
 }
 
+// Sets c; returns 1 if this call set a new bit (first occurrence).
+__device__ __forceinline__ u32 bm_set_new(const Bm& b, u32 c) {
+  const u32 w = c >> 5, bit = 1u << (c & 31);
+  const u32 old = atomicOr(&b.L1[w], bit);
+  if (old == 0) atomicOr(&b.L2[w >> 5], 1u << (w & 31));
+  return (old & bit) ? 0u : 1u;
+}
+
 // Sets c; returns true if c was already set.
 __device__ __forceinline__ bool bm_test_set(const Bm& b, u32 c) {
   const u32 w = c >> 5, bit = 1u << (c & 31);
