@@ -375,6 +375,40 @@ typedef struct ta_speedup_out {
 } ta_speedup_out;
 ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_speedup_out* o);
 
+/* ------------------------------------------- allocation-free statistics ---- */
+
+/* ta_context_stats over every context, for callers that must not allocate
+ * device memory at call time -- for example code that runs while a CUDA
+ * graph is being captured, or inside a service whose device memory comes
+ * from a fixed budget that may not grow.  It uses no allocator: its
+ * temporaries live in one fixed device array inside this library (about 6 MB,
+ * held by every GPU that loads the library until the process exits).  The
+ * paper has no counterpart; this is an interface convenience.
+ *   cuda_stream     stream to run on; the current device must be its device.
+ *   off, ctx, time  a per-rank CSR on the device (e.g. ta_csr_get_view of an
+ *                   experiment): rank r owns [off[r], off[r+1]), contexts
+ *                   ascending, times in ns.
+ *   n_ranks, n_ctx  R and C; n_ctx must not exceed 65536.
+ *   ranks           sorted unique device rank ids, or NULL for all ranks.
+ *   tau_num/tau_den outlier threshold, as in ta_context_stats.
+ *   stats           device ta_ctx_stats[n_ctx] (context order).
+ *   outliers        device ta_outlier[outlier_cap], sorted by (ctx, rank);
+ *                   outlier_cap must not exceed 65536.
+ *   n_outliers      host: set to the number of outliers (TA_ERR_CAPACITY if
+ *                   above outlier_cap; then the outlier list is not written).
+ * Results equal ta_context_stats with ctxs = NULL.  Returns after the work is
+ * complete.  The first call on a device looks up the array's device address
+ * (make that first call before any stream capture).  Every call reuses the
+ * same array and resets what must start at zero; calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  Sizes above the limits return TA_ERR_INVALID_ARG. */
+ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off, const uint32_t* ctx,
+                                   const uint64_t* time, uint32_t n_ranks, uint32_t n_ctx,
+                                   const uint32_t* ranks, uint32_t n_ranks_subset,
+                                   uint32_t tau_num, uint32_t tau_den, ta_ctx_stats* stats,
+                                   ta_outlier* outliers, uint64_t outlier_cap,
+                                   uint64_t* n_outliers);
+
 #ifdef __cplusplus
 }
 #endif

@@ -154,6 +154,8 @@ _SIGS = {
     "ta_topology_rollup": (C.c_int, [P, C.POINTER(Topology), C.POINTER(TopoArgs),
                                      C.POINTER(TopoOut)]),
     "ta_potential_speedup": (C.c_int, [P, C.POINTER(SpeedupArgs), C.POINTER(SpeedupOut)]),
+    "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
+                                           C.POINTER(u64)]),
 }
 
 _lib = None

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -946,3 +947,151 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free statistics.  Callers that may not allocate device memory
+// (code running while a CUDA graph is being captured, or under a
+// fixed-budget allocator that forbids growth) get every temporary from one
+// file-scope device array instead of the allocator.  The array lives in every
+// GPU that loads this library until the process exits.
+namespace {
+
+constexpr u64 NA_MAX_CTX = 1u << 16;       // contexts
+constexpr u64 NA_MAX_OUTLIERS = 1u << 16;  // outlier capacity (power of two)
+// slot map u32[C] + ten per-context partial arrays (72 B per context) +
+// outlier keys and z (16 B each) + counters.
+constexpr u64 NA_BYTES = NA_MAX_CTX * 4 + NA_MAX_CTX * 72 + NA_MAX_OUTLIERS * 16 + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+constexpr int NA_MAX_DEVICES = 64;
+unsigned char* g_noalloc_ptr[NA_MAX_DEVICES];
+std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is not a device address).
+ta_status noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGetDevice");
+  if (dev < 0 || dev >= NA_MAX_DEVICES) return fail(TA_ERR_INVALID_ARG, "device %d", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return TA_OK;
+}
+
+}  // namespace
+
+extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off,
+                                              const uint32_t* ctx, const uint64_t* time,
+                                              uint32_t n_ranks, uint32_t n_ctx,
+                                              const uint32_t* ranks, uint32_t n_ranks_subset,
+                                              uint32_t tau_num, uint32_t tau_den,
+                                              ta_ctx_stats* stats, ta_outlier* outliers,
+                                              uint64_t outlier_cap, uint64_t* n_outliers) {
+  if (!off || !ctx || !time || !stats || !n_outliers || (outlier_cap && !outliers))
+    return fail(TA_ERR_INVALID_ARG, "ta_context_stats_noalloc: NULL argument");
+  if (n_ranks == 0 || n_ctx == 0) return fail(TA_ERR_INVALID_ARG, "n_ranks and n_ctx must be > 0");
+  if (n_ctx > NA_MAX_CTX)
+    return fail(TA_ERR_INVALID_ARG,
+                "ta_context_stats_noalloc: n_ctx = %u exceeds the fixed maximum %llu", n_ctx,
+                (unsigned long long)NA_MAX_CTX);
+  if (outlier_cap > NA_MAX_OUTLIERS)
+    return fail(TA_ERR_INVALID_ARG,
+                "ta_context_stats_noalloc: outlier_cap = %llu exceeds the fixed maximum %llu",
+                (unsigned long long)outlier_cap, (unsigned long long)NA_MAX_OUTLIERS);
+  if (tau_den == 0) return fail(TA_ERR_INVALID_ARG, "tau_den = 0");
+  if (ranks && n_ranks_subset == 0) return fail(TA_ERR_INVALID_ARG, "empty rank subset");
+  unsigned char* base;
+  TRY(noalloc_scratch(&base));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned long long launches = 0;
+  int num_sms = 1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  Launch L{st, num_sms, &launches};
+  const u64 C = n_ctx;
+  // carve the scratch array
+  u32* slot_of_ctx = (u32*)base;
+  unsigned char* q = base + NA_MAX_CTX * 4;
+  Partials P;
+  P.present = (u32*)q;
+  q += NA_MAX_CTX * 4;
+  P.argmax = (u32*)q;
+  q += NA_MAX_CTX * 4;
+  P.mn = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.mx = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.s1 = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.s2lo = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.s2hi = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.sd = (double*)q;
+  q += NA_MAX_CTX * 8;
+  P.Mlo = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  P.Mhi = (u64*)q;
+  q += NA_MAX_CTX * 8;
+  u64* keys = (u64*)q;
+  q += NA_MAX_OUTLIERS * 8;
+  double* zs = (double*)q;
+  q += NA_MAX_OUTLIERS * 8;
+  unsigned long long* n_out = (unsigned long long*)q;
+  u32* status = (u32*)(q + 8);
+  const u32 n = ranks ? n_ranks_subset : n_ranks;
+  // everything that accumulates starts from zero (the array keeps the last
+  // call's contents)
+  cudaMemsetAsync(q, 0, 16, st);
+  if (ranks) {  // the subset is checked before any kernel reads through it
+    k_check_sorted<<<blocks(n), 256, 0, st>>>(ranks, n, n_ranks, status);
+    L.count();
+    u32 hs = 0;
+    cudaError_t e2 = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "ta_context_stats_noalloc");
+    if (hs) return fail(TA_ERR_INVALID_ARG, "rank subset must be sorted, unique and < n_ranks");
+  }
+  cudaMemsetAsync(slot_of_ctx, 0xFF, C * 4, st);
+  k_slot_map<<<blocks(C), 256, 0, st>>>(nullptr, 0, n_ctx, slot_of_ctx);
+  cudaMemsetAsync(P.present, 0, C * 4, st);
+  cudaMemsetAsync(P.mn, 0xFF, C * 8, st);
+  cudaMemsetAsync(P.mx, 0, C * 8, st);
+  cudaMemsetAsync(P.s1, 0, C * 8, st);
+  cudaMemsetAsync(P.s2lo, 0, C * 8, st);
+  cudaMemsetAsync(P.s2hi, 0, C * 8, st);
+  const int grid = std::max(1, std::min<int>(num_sms * 4, (int)((n + 7) / 8)));
+  const u64 kcap = std::max<u64>(1, outlier_cap);
+  k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P);
+  k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats);
+  k_stats_z<<<grid, 256, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, tau_num, tau_den,
+                                  nullptr, keys, zs, kcap, n_out, nullptr);
+  k_stats_argmax<<<blocks(C), 256, 0, st>>>((u32)C, P.argmax, stats);
+  u64 h[2] = {0, 0};
+  cudaError_t err = cudaMemcpyAsync(h, n_out, 16, cudaMemcpyDeviceToHost, st);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaMemcpyAsync");
+  err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
+  *n_outliers = h[0];
+  if (h[0] > outlier_cap)
+    return fail(TA_ERR_CAPACITY, "%llu outliers, capacity %llu", (unsigned long long)h[0],
+                (unsigned long long)outlier_cap);
+  if (h[0] > 0) {
+    sort_pairs(L, keys, zs, h[0]);  // the key buffer holds NA_MAX_OUTLIERS (a power of two)
+    k_write_outliers<<<blocks(h[0]), 256, 0, st>>>(keys, zs, h[0], outliers);
+  }
+  err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
+  return TA_OK;
+}
