@@ -125,7 +125,8 @@ ta_status ta_get_profile(ta_ctx* ctx, ta_profile* out, int reset);
  *   mem_kind       where the four arrays live.
  *   flags          TA_LOAD_BORROW: device ts/ctx are used in place (no copy)
  *                  and must stay valid and unchanged until
- *                  ta_experiment_free(); TA_LOAD_NO_INCLUSIVE: skip the
+ *                  ta_experiment_free() (arrays not 16-byte aligned are
+ *                  copied instead); TA_LOAD_NO_INCLUSIVE: skip the
  *                  inclusive rollup.
  *   nnz_hint, rows_hint  optional first-try capacities of the tensor (0 =
  *                  library default); a too-small hint only costs a re-run.
@@ -408,6 +409,59 @@ ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off, const
                                    uint32_t tau_num, uint32_t tau_den, ta_ctx_stats* stats,
                                    ta_outlier* outliers, uint64_t outlier_cap,
                                    uint64_t* n_outliers);
+
+
+/* ----------------------------------------------------- batched form ---- */
+
+/* Many independent experiments (sets) analysed as one unit (the batched
+ * execution form).  ta_batch_plan copies every set into one device arena
+ * (ranks, samples and tree nodes concatenated; sample tiles never span two
+ * sets), validates all of them, runs the analysis once to size every product
+ * exactly, and captures the whole fixed launch sequence -- validation, the
+ * iteration tensor (Section V), exclusive and inclusive CSR, and the
+ * cross-rank statistics of the exclusive metric over all ranks of each set
+ * (Section VI-A/B) -- in one CUDA graph.  ta_batch_run replays that graph on
+ * the context's stream (the inputs of the plan, already on the device, are
+ * analysed again) and then sorts the outliers by set.
+ *   sets[s]   as for ta_load_traces; parent ids and samples' context ids are
+ *             local to their set; flags are ignored (every set is copied).
+ *   args      tau = tau_num / tau_den (NULL: 3/1); outlier_cap = capacity of
+ *             the outlier list over all sets (0: 2^20).
+ * Every product of set s is the product ta_load_traces + ta_context_stats
+ * (metric exclusive, all ranks, all contexts) would give for that set alone;
+ * ta_batch_get_set returns zero-copy device views with offsets relative to
+ * the set (valid until ta_batch_free).  Errors: as ta_load_traces for any
+ * set (the message names the set).  ta_batch_plan ends with one run; when
+ * the outliers exceed outlier_cap, ta_batch_run returns TA_ERR_CAPACITY, the
+ * info's n_outliers holds the full count, every set's outlier list is empty
+ * and the other products are valid. */
+typedef struct ta_batch ta_batch;
+typedef struct ta_batch_args {
+  uint32_t tau_num, tau_den;
+  uint64_t outlier_cap;
+} ta_batch_args;
+typedef struct ta_batch_info {
+  uint32_t n_sets, n_ranks;
+  uint64_t n_records, n_rows, tensor_nnz, excl_nnz, incl_nnz, n_outliers;
+  uint64_t graph_nodes;   /* kernels, memsets and copies in the graph */
+  uint64_t graph_kernels; /* kernel nodes among them                  */
+  uint64_t device_bytes; /* arena owned by the batch                 */
+} ta_batch_info;
+typedef struct ta_batch_set_view {
+  uint32_t n_ranks, n_ctx;
+  ta_tensor_view tensor;       /* offsets relative to the set       */
+  ta_csr_view exclusive;       /* off[n_ranks + 1] from 0           */
+  ta_csr_view inclusive;
+  const ta_ctx_stats* stats;   /* [n_ctx]                           */
+  const ta_outlier* outliers;  /* sorted by (ctx, rank); local ids  */
+  uint64_t n_outliers;
+} ta_batch_set_view;
+ta_status ta_batch_plan(ta_ctx* ctx, const ta_trace_desc* sets, uint32_t n_sets,
+                        const ta_batch_args* args, ta_batch** out);
+ta_status ta_batch_run(ta_batch* b);
+ta_status ta_batch_free(ta_batch* b);
+ta_status ta_batch_get_info(const ta_batch* b, ta_batch_info* info);
+ta_status ta_batch_get_set(const ta_batch* b, uint32_t set, ta_batch_set_view* v);
 
 #ifdef __cplusplus
 }

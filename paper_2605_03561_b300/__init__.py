@@ -126,6 +126,22 @@ class Profile(C.Structure):
                 ("tensor_rows", u64)]
 
 
+class BatchArgs(C.Structure):
+    _fields_ = [("tau_num", u32), ("tau_den", u32), ("outlier_cap", u64)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_sets", u32), ("n_ranks", u32), ("n_records", u64), ("n_rows", u64),
+                ("tensor_nnz", u64), ("excl_nnz", u64), ("incl_nnz", u64), ("n_outliers", u64),
+                ("graph_nodes", u64), ("graph_kernels", u64), ("device_bytes", u64)]
+
+
+class BatchSetView(C.Structure):
+    _fields_ = [("n_ranks", u32), ("n_ctx", u32), ("tensor", TensorView),
+                ("exclusive", CsrView), ("inclusive", CsrView), ("stats", P), ("outliers", P),
+                ("n_outliers", u64)]
+
+
 class SpeedupOut(C.Structure):
     _fields_ = [("per_ctx", P), ("total", P)]
 
@@ -156,6 +172,12 @@ _SIGS = {
     "ta_potential_speedup": (C.c_int, [P, C.POINTER(SpeedupArgs), C.POINTER(SpeedupOut)]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
+    "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
+                                C.POINTER(P)]),
+    "ta_batch_run": (C.c_int, [P]),
+    "ta_batch_free": (C.c_int, [P]),
+    "ta_batch_get_info": (C.c_int, [P, C.POINTER(BatchInfo)]),
+    "ta_batch_get_set": (C.c_int, [P, u32, C.POINTER(BatchSetView)]),
 }
 
 _lib = None
@@ -195,7 +217,7 @@ def device_array(ptr, n, dtype, device=0):
     """Zero-copy torch view of n elements of library-owned device memory
     (64-bit unsigned values are viewed as int64; reinterpret on the host)."""
     torch = _torch()
-    typestr = {np.uint64: "<i8", np.uint32: "<i4", np.float64: "<f8"}[dtype]
+    typestr = {np.uint64: "<i8", np.uint32: "<i4", np.float64: "<f8", np.uint8: "|u1"}[dtype]
     return torch.as_tensor(_CudaArray(int(ptr), int(n), typestr), device=f"cuda:{device}")
 
 
@@ -484,3 +506,102 @@ class Experiment:
         t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
         t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
         return d, t
+
+
+def _dev_to_np(ptr, n, dtype, device):
+    """Host copy of n elements of library-owned device memory."""
+    if n == 0 or not ptr:
+        return np.zeros(0, dtype)
+    return device_array(ptr, n, dtype, device).cpu().numpy().view(dtype)
+
+
+def _dev_structs(ptr, n, ctype, device):
+    """Host ctypes array copied from n device structs."""
+    arr = (ctype * max(n, 1))()
+    if n and ptr:
+        raw = _dev_to_np(ptr, n * C.sizeof(ctype), np.uint8, device)
+        C.memmove(arr, raw.ctypes.data, n * C.sizeof(ctype))
+    return arr
+
+
+class Batch:
+    """Many independent trace sets analysed as one unit (ta_batch_plan): the
+    whole analysis is one captured CUDA graph, replayed by run()."""
+
+    def __init__(self, ctx: Context, sets, tau=(3, 1), outlier_cap=1 << 20):
+        """sets: sequence of (rank_off, ts, ctx, parent, marker) host arrays."""
+        self.ctx = ctx
+        keep, descs = [], (TraceDesc * len(sets))()
+        for d, (rank_off, ts, cx, parent, marker) in zip(descs, sets):
+            rank_off, ts, cx = _np(rank_off, np.uint64), _np(ts, np.uint64), _np(cx, np.uint32)
+            parent = _np(parent, np.uint32)
+            keep.append((rank_off, ts, cx, parent))
+            d.n_ranks = rank_off.shape[0] - 1
+            d.n_ctx = parent.shape[0]
+            d.marker_ctx = int(marker)
+            d.mem_kind = MEM_HOST
+            d.n_records = ts.shape[0]
+            d.rank_off, d.ts, d.ctx, d.parent = _ptr(rank_off), _ptr(ts), _ptr(cx), _ptr(parent)
+        a = BatchArgs()
+        a.tau_num, a.tau_den = tau
+        a.outlier_cap = outlier_cap
+        h = P()
+        _check(lib().ta_batch_plan(ctx.h, descs, len(sets), C.byref(a), C.byref(h)))
+        self.h = h
+        self.S = len(sets)
+
+    def run(self):
+        _check(lib().ta_batch_run(self.h))
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().ta_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(lib().ta_batch_get_info(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in BatchInfo._fields_}
+
+    def view(self, s: int) -> BatchSetView:
+        v = BatchSetView()
+        _check(lib().ta_batch_get_set(self.h, s, C.byref(v)))
+        return v
+
+    def products(self, s: int) -> dict:
+        """Host copies of every product of set s (offsets relative to the set)."""
+        v = self.view(s)
+        dev = self.ctx.device
+        R, Cn = int(v.n_ranks), int(v.n_ctx)
+        t = v.tensor
+        rows, nnz = int(t.rows), int(t.nnz)
+        out = dict(R=R, C=Cn)
+        out["tensor"] = dict(n_iter=_dev_to_np(t.n_iter, R, np.uint32, dev),
+                             row_off_of_rank=_dev_to_np(t.row_off_of_rank, R + 1, np.uint64, dev),
+                             entry_off=_dev_to_np(t.entry_off, rows + 1, np.uint64, dev),
+                             e_ctx=_dev_to_np(t.e_ctx, nnz, np.uint32, dev),
+                             e_time=_dev_to_np(t.e_time, nnz, np.uint64, dev),
+                             e_cnt=_dev_to_np(t.e_cnt, nnz, np.uint32, dev),
+                             span=_dev_to_np(t.span, R, np.uint64, dev))
+        for name in ("exclusive", "inclusive"):
+            c = getattr(v, name)
+            n = int(c.nnz)
+            out[name] = dict(off=_dev_to_np(c.off, R + 1, np.uint64, dev),
+                             ctx=_dev_to_np(c.ctx, n, np.uint32, dev),
+                             time=_dev_to_np(c.time, n, np.uint64, dev),
+                             cnt=_dev_to_np(c.cnt, n, np.uint32, dev))
+        st = _dev_structs(v.stats, Cn, CtxStats, dev)
+        out["stats"] = {f: np.array([getattr(x, f) for x in st[:Cn]]) for f, _ in CtxStats._fields_
+                        if f != "reserved"}
+        m = int(v.n_outliers)
+        ol = _dev_structs(v.outliers, m, Outlier, dev)
+        out["outliers"] = dict(ctx=np.array([x.ctx for x in ol[:m]], np.uint32),
+                               rank=np.array([x.rank for x in ol[:m]], np.uint32),
+                               z=np.array([x.z for x in ol[:m]], np.float64))
+        return out

@@ -214,7 +214,7 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   TensorArgs A;
   std::memset(&A, 0, sizeof A);
   TRY(tmp.get_n(n_tiles + 1, (u32**)&A.tfr, "tile map"));
-  launch_tile_first_rank(L, e->rank_off, R, P.tile, (u32)n_tiles, (u32*)A.tfr);
+  launch_tile_first_rank(L, e->rank_off, R, P.tile, (u32)n_tiles, (u32*)A.tfr, SetMap{});
   TRY(tmp.get_n(n_tiles, &A.tile_rows, "tile rows"));
   TRY(tmp.get_n(n_tiles, &A.tile_ents, "tile entries"));
   TRY(tmp.get_n(n_tiles, &A.tile_row_off, "tile row offsets"));
@@ -375,7 +375,9 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   TRY(copy(c, e->rank_off, d->rank_off, ((u64)R + 1) * 8));
   TRY(e->own((u64)C * 4, (void**)&e->parent, "parent"));
   TRY(copy(c, e->parent, d->parent, (u64)C * 4));
-  if (dev && (d->flags & TA_LOAD_BORROW)) {
+  // the sample passes read ts and ctx in 16-byte vectors: borrow only aligned arrays
+  const bool aligned = ((uintptr_t)d->ts % 16 == 0) && ((uintptr_t)d->ctx % 16 == 0);
+  if (dev && (d->flags & TA_LOAD_BORROW) && aligned) {
     e->ts = d->ts;
     e->ctxv = d->ctx;
   } else {
@@ -399,8 +401,9 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   cudaMemsetAsync(meta, 0, 64, c->stream);
   u32* status = (u32*)meta;
   PhaseTimer timer(c, &c->prof.validate_ms);
-  launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status);
-  launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status);
+  launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status, SetMap{});
+  launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status,
+             SetMap{});
   timer.stop_and_sync();
   u64 h[3];
   TRY(copy(c, h, meta, sizeof h));

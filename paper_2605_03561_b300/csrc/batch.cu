@@ -1,0 +1,648 @@
+// batch.cu -- many independent trace sets analysed as one unit.
+//
+// All sets are copied into one device arena (ranks, samples and tree nodes
+// concatenated, tiles never spanning two sets) and every kernel works on all
+// sets at once, looking up each tile's or rank's set.  The launch sequence of
+// the whole analysis is therefore fixed by the batch's shape: it is run once
+// eagerly to size every product exactly, captured in a CUDA graph, and each
+// ta_batch_run replays the graph (then sorts the outliers, whose number is
+// only known afterwards, and splits them by set).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ta.h"
+#include "ta_api_internal.h"
+
+using namespace ta;
+
+#define TRY(x)                  \
+  do {                          \
+    ta_status _s = (x);         \
+    if (_s != TA_OK) return _s; \
+  } while (0)
+
+namespace {
+
+__global__ void k_put_u64(u64* p, u64 v) { *p = v; }
+
+// out[g] for g in [0, seg0[S] + S): element k of segment s (g = seg0[s] + s + k,
+// k <= len_s) is in[seg0[s] + k] - in[seg0[s]]: per-set offsets starting at 0,
+// each set with its own closing element.
+__global__ void k_rel_offsets(const u64* in, u64* out, const u64* seg0, u32 S) {
+  const u64 g = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= seg0[S] + S) return;
+  u32 lo = 0, hi = S;  // last s with seg0[s] + s <= g
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) / 2;
+    if (seg0[mid] + mid <= g) lo = mid;
+    else hi = mid;
+  }
+  const u64 k = g - seg0[lo] - lo;
+  out[g] = in[seg0[lo] + k] - in[seg0[lo]];
+}
+
+constexpr u64 SET_ALIGN = 32;
+
+inline unsigned nblocks(u64 n) { return (unsigned)std::max<u64>(1, (n + 255) / 256); }
+
+}  // namespace
+
+struct ta_batch {
+  ta_ctx* ctx = nullptr;
+  u32 S = 0, R = 0, Ctot = 0, Cmax = 0, max_depth = 0;
+  u64 N = 0, n_tiles = 0;
+  u32 tau_num = 3, tau_den = 1;
+  u64 outlier_cap = 0;
+  // host copies of the set layout
+  std::vector<u64> h_rec0, h_rec_end, h_tile0;
+  u64 n_samples = 0;  // without alignment padding
+  std::vector<u32> h_rank0, h_ctx0, h_C, h_m;
+  std::vector<u64> h_row0, h_ent0, h_x0, h_i0, h_out0;
+  // device arena
+  u64* rank_off = nullptr;
+  u64* ts = nullptr;
+  u32* cx = nullptr;
+  u32* parent = nullptr;
+  u32* depth = nullptr;
+  u64* span = nullptr;
+  u32* n_iter = nullptr;
+  u64* row_off = nullptr;
+  u64* entry_off = nullptr;
+  u32* e_ctx = nullptr;
+  u64* e_time = nullptr;
+  u32* e_cnt = nullptr;
+  Csr x, in;
+  ta_ctx_stats* stats = nullptr;
+  u64* keys = nullptr;
+  double* zs = nullptr;
+  ta_outlier* outl = nullptr;
+  u64* set_out0 = nullptr;
+  // per-set relative offsets
+  u64* rel_row_off = nullptr;
+  u64* rel_entry_off = nullptr;
+  u64* rel_x_off = nullptr;
+  u64* rel_i_off = nullptr;
+  u64* d_row0 = nullptr;
+  u64* d_rank0_64 = nullptr;
+  // set map
+  SetMap sets{};
+  // kernel scratch
+  TensorArgs T{};
+  TensorPlan TP{};
+  RankCsrArgs X[2]{};
+  RankCsrPlan XP{};
+  u64* meta = nullptr;   // [0] status, [1..2] tensor totals, [3] excl total, [4] incl total,
+                         // [5] max span, [6] max depth | pad, [7] n_out
+  u32* roots = nullptr;  // [S]
+  u32* cct_scratch = nullptr;
+  unsigned char* stats_scratch = nullptr;
+  u64 rows = 0, nnz = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  u64 graph_nodes = 0, graph_kernels = 0;
+  u64 n_out = 0;
+  u64 device_bytes = 0;
+  std::vector<Block> owned;
+
+  ta_status own(size_t bytes, void** p, const char* what) {
+    void* q = dalloc(ctx, bytes);
+    if (!q) return fail(TA_ERR_OOM, "batch: allocation of %zu bytes for %s failed", bytes, what);
+    owned.push_back({q, bytes});
+    device_bytes += bytes;
+    *p = q;
+    return TA_OK;
+  }
+  template <class T_>
+  ta_status own_n(u64 n, T_** p, const char* what) {
+    return own(std::max<u64>(n, 1) * sizeof(T_), (void**)p, what);
+  }
+  void drop() {
+    for (auto& b : owned) dfree(ctx, b.p, b.n);
+    owned.clear();
+  }
+};
+
+namespace {
+
+Launch launch_of(ta_batch* b) { return Launch{b->ctx->stream, b->ctx->num_sms, &b->ctx->launches}; }
+
+// Validation and tree depth for all sets (status bits in meta[0]).
+void enqueue_validate(ta_batch* b) {
+  const Launch L = launch_of(b);
+  u32* status = (u32*)b->meta;
+  cudaMemsetAsync(b->meta, 0, 64, L.stream);
+  cudaMemsetAsync(b->roots, 0, (size_t)b->S * 4, L.stream);
+  launch_rank_off(L, b->rank_off, b->R, b->N, b->ts, b->span, b->meta + 5, status, b->sets);
+  launch_cct(L, b->parent, b->Ctot, b->depth, (u32*)(b->meta + 6), b->roots, b->cct_scratch, status,
+             b->sets);
+}
+
+void enqueue_tensor_count(ta_batch* b) {
+  const Launch L = launch_of(b);
+  launch_tile_first_rank(L, b->rank_off, b->R, b->TP.tile, (u32)b->n_tiles, (u32*)b->T.tfr,
+                         b->sets);
+  launch_tensor_count(L, b->TP, b->T);
+  launch_tile_scan(L, b->T);
+}
+
+void enqueue_tensor_write(ta_batch* b) {
+  const Launch L = launch_of(b);
+  k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
+  k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->nnz);
+  L.count(2);
+  launch_tensor_write(L, b->TP, b->T);
+  launch_n_iter(L, b->row_off, b->R, b->n_iter);
+}
+
+void enqueue_stats(ta_batch* b) {
+  const Launch L = launch_of(b);
+  launch_batch_stats(L, b->R, b->Ctot, b->x.off, b->x.ctx, b->x.time, b->sets, b->tau_num,
+                     b->tau_den, b->stats_scratch, b->stats, b->keys, b->zs, b->outlier_cap,
+                     (unsigned long long*)(b->meta + 7));
+}
+
+void enqueue_views(ta_batch* b) {
+  const Launch L = launch_of(b);
+  k_rel_offsets<<<nblocks((u64)b->R + b->S), 256, 0, L.stream>>>(b->row_off, b->rel_row_off,
+                                                                   b->d_rank0_64, b->S);
+  k_rel_offsets<<<nblocks(b->rows + b->S), 256, 0, L.stream>>>(b->entry_off, b->rel_entry_off,
+                                                                b->d_row0, b->S);
+  k_rel_offsets<<<nblocks((u64)b->R + b->S), 256, 0, L.stream>>>(b->x.off, b->rel_x_off,
+                                                                   b->d_rank0_64, b->S);
+  k_rel_offsets<<<nblocks((u64)b->R + b->S), 256, 0, L.stream>>>(b->in.off, b->rel_i_off,
+                                                                   b->d_rank0_64, b->S);
+  L.count(4);
+}
+
+// Everything that runs every time, in order (sizes fixed by the plan).
+void enqueue_all(ta_batch* b) {
+  const Launch L = launch_of(b);
+  enqueue_validate(b);
+  enqueue_tensor_count(b);
+  enqueue_tensor_write(b);
+  for (int mode = 0; mode < 2; ++mode) {
+    launch_rank_count(L, b->XP, b->X[mode]);
+    launch_rank_write(L, b->XP, b->X[mode]);
+  }
+  enqueue_stats(b);
+  enqueue_views(b);
+}
+
+ta_status check_flags(ta_batch* b, const char* where) {
+  u64 h[8];
+  TRY(copy(b->ctx, h, b->meta, sizeof h));
+  TRY(sync_check(b->ctx, where));
+  const u32 f = (u32)h[0];
+  if (f & F_INVALID)
+    return fail(TA_ERR_INVALID_ARG, "%s: rank offsets of a set are not a valid CSR", where);
+  std::vector<u32> roots(b->S);
+  TRY(copy(b->ctx, roots.data(), b->roots, (size_t)b->S * 4));
+  TRY(sync_check(b->ctx, where));
+  for (u32 s = 0; s < b->S; ++s)
+    if (roots[s] != 1) return fail(TA_ERR_BAD_CCT, "%s: set %u has %u tree roots", where, s, roots[s]);
+  if (f & F_BAD_CCT) return fail(TA_ERR_BAD_CCT, "%s: a set's parent array is invalid", where);
+  if ((unsigned __int128)h[5] * b->R >= ((unsigned __int128)1 << 63))
+    return fail(TA_ERR_INVALID_ARG, "%s: R * longest span >= 2^63", where);
+  TRY(status_from_flags(f, where));
+  b->max_depth = (u32)h[6];
+  b->n_out = h[7];
+  return TA_OK;
+}
+
+ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
+  ta_ctx* c = b->ctx;
+  const Launch L = launch_of(b);
+  // ---- layout --------------------------------------------------------------
+  b->S = S;
+  b->h_rec0.assign(S + 1, 0);
+  b->h_rec_end.assign(S, 0);
+  b->h_tile0.assign(S + 1, 0);
+  b->h_rank0.assign(S + 1, 0);
+  b->h_ctx0.assign(S + 1, 0);
+  b->h_C.resize(S);
+  b->h_m.resize(S);
+  b->TP = plan_tensor(1, 1, c->num_sms);  // for the tile size
+  const u64 TWt = (u64)b->TP.tile;
+  for (u32 s = 0; s < S; ++s) {
+    const ta_trace_desc& d = sets[s];
+    if (d.n_ranks == 0 || d.n_ctx == 0 || d.marker_ctx >= d.n_ctx || !d.rank_off || !d.parent ||
+        (d.n_records && (!d.ts || !d.ctx)) || d.mem_kind > 1)
+      return fail(TA_ERR_INVALID_ARG, "batch: set %u: invalid description", s);
+    if (d.n_ctx > 0x7FFFFFFFu) return fail(TA_ERR_INVALID_ARG, "batch: set %u: n_ctx", s);
+    // every set starts on a 32-sample boundary: the sample passes read
+    // 4-sample vectors at tile-relative offsets
+    b->h_rec_end[s] = b->h_rec0[s] + d.n_records;
+    b->h_rec0[s + 1] = (b->h_rec_end[s] + SET_ALIGN - 1) / SET_ALIGN * SET_ALIGN;
+    b->n_samples += d.n_records;
+    b->h_tile0[s + 1] = b->h_tile0[s] + std::max<u64>(1, (d.n_records + TWt - 1) / TWt);
+    if ((u64)b->h_rank0[s] + d.n_ranks >= 0xFFFFFFFFull)
+      return fail(TA_ERR_INVALID_ARG, "batch: too many ranks");
+    b->h_rank0[s + 1] = b->h_rank0[s] + d.n_ranks;
+    if ((u64)b->h_ctx0[s] + d.n_ctx >= 0x7FFFFFFFull)
+      return fail(TA_ERR_INVALID_ARG, "batch: too many contexts");
+    b->h_ctx0[s + 1] = b->h_ctx0[s] + d.n_ctx;
+    b->h_C[s] = d.n_ctx;
+    b->h_m[s] = d.marker_ctx;
+    b->Cmax = std::max(b->Cmax, d.n_ctx);
+  }
+  b->N = b->h_rec0[S];
+  b->R = b->h_rank0[S];
+  b->Ctot = b->h_ctx0[S];
+  b->n_tiles = b->h_tile0[S];
+  // ---- inputs ---------------------------------------------------------------
+  TRY(b->own_n((u64)b->R + 1, &b->rank_off, "rank_off"));
+  TRY(b->own_n(b->N, &b->ts, "ts"));
+  TRY(b->own_n(b->N, &b->cx, "ctx"));
+  TRY(b->own_n(b->Ctot, &b->parent, "parent"));
+  std::vector<u64> ro((u64)b->R + 1);
+  for (u32 s = 0; s < S; ++s) {
+    const ta_trace_desc& d = sets[s];
+    std::vector<u64> local((u64)d.n_ranks + 1);
+    TRY(copy(c, local.data(), d.rank_off, local.size() * 8));
+    TRY(sync_check(c, "batch: rank offsets"));
+    if (local[0] != 0 || local[d.n_ranks] != d.n_records)
+      return fail(TA_ERR_INVALID_ARG, "batch: set %u: rank_off must start at 0 and end at n_records",
+                  s);
+    for (u32 r = 0; r <= d.n_ranks; ++r) ro[b->h_rank0[s] + r] = b->h_rec0[s] + local[r];
+    TRY(copy(c, b->ts + b->h_rec0[s], d.ts, d.n_records * 8));
+    TRY(copy(c, b->cx + b->h_rec0[s], d.ctx, d.n_records * 4));
+    TRY(copy(c, b->parent + b->h_ctx0[s], d.parent, (u64)d.n_ctx * 4));
+    const u64 pad = b->h_rec0[s + 1] - b->h_rec_end[s];
+    if (pad) {  // padding samples belong to no rank; keep them defined
+      cudaMemsetAsync(b->ts + b->h_rec_end[s], 0, pad * 8, c->stream);
+      cudaMemsetAsync(b->cx + b->h_rec_end[s], 0, pad * 4, c->stream);
+    }
+  }
+  ro[b->R] = b->N;
+  TRY(copy(c, b->rank_off, ro.data(), ro.size() * 8));
+  // ---- set map on the device ------------------------------------------------
+  std::vector<u32> tile_set(b->n_tiles), rank_set(b->R);
+  for (u32 s = 0; s < S; ++s) {
+    for (u64 t = b->h_tile0[s]; t < b->h_tile0[s + 1]; ++t) tile_set[t] = s;
+    for (u32 r = b->h_rank0[s]; r < b->h_rank0[s + 1]; ++r) rank_set[r] = s;
+  }
+  u32 *d_tile_set, *d_rank_set, *d_rank0, *d_ctx0, *d_C, *d_m;
+  u64 *d_tile0, *d_rec0, *d_rec_end;
+  TRY(b->own_n(b->n_tiles, &d_tile_set, "set map"));
+  TRY(b->own_n(b->R, &d_rank_set, "set map"));
+  TRY(b->own_n(S + 1, &d_rank0, "set map"));
+  TRY(b->own_n(S + 1, &d_ctx0, "set map"));
+  TRY(b->own_n(S, &d_C, "set map"));
+  TRY(b->own_n(S, &d_m, "set map"));
+  TRY(b->own_n(S + 1, &d_tile0, "set map"));
+  TRY(b->own_n(S + 1, &d_rec0, "set map"));
+  TRY(b->own_n(S, &d_rec_end, "set map"));
+  TRY(b->own_n(S + 1, &b->d_rank0_64, "set map"));
+  TRY(copy(c, d_tile_set, tile_set.data(), tile_set.size() * 4));
+  TRY(copy(c, d_rank_set, rank_set.data(), rank_set.size() * 4));
+  TRY(copy(c, d_rank0, b->h_rank0.data(), (S + 1) * 4));
+  TRY(copy(c, d_ctx0, b->h_ctx0.data(), (S + 1) * 4));
+  TRY(copy(c, d_C, b->h_C.data(), S * 4));
+  TRY(copy(c, d_m, b->h_m.data(), S * 4));
+  TRY(copy(c, d_tile0, b->h_tile0.data(), (S + 1) * 8));
+  TRY(copy(c, d_rec0, b->h_rec0.data(), (S + 1) * 8));
+  TRY(copy(c, d_rec_end, b->h_rec_end.data(), S * 8));
+  std::vector<u64> rank0_64(b->h_rank0.begin(), b->h_rank0.end());
+  TRY(copy(c, b->d_rank0_64, rank0_64.data(), (S + 1) * 8));
+  TRY(sync_check(c, "batch: upload"));
+  b->sets.S = S;
+  b->sets.tile_set = d_tile_set;
+  b->sets.set_tile0 = d_tile0;
+  b->sets.set_rec0 = d_rec0;
+  b->sets.set_rec_end = d_rec_end;
+  b->sets.set_rank0 = d_rank0;
+  b->sets.set_ctx0 = d_ctx0;
+  b->sets.set_C = d_C;
+  b->sets.set_m = d_m;
+  b->sets.rank_set = d_rank_set;
+  // ---- products and scratch whose size is known now --------------------------
+  TRY(b->own(64, (void**)&b->meta, "meta"));
+  TRY(b->own_n(S, &b->roots, "roots"));
+  TRY(b->own_n(4 * (u64)b->Ctot, &b->cct_scratch, "tree scratch"));
+  TRY(b->own_n(b->Ctot, &b->depth, "depth"));
+  TRY(b->own_n(b->R, &b->span, "span"));
+  TRY(b->own_n((u64)b->R + 1, &b->n_iter, "n_iter"));
+  TRY(b->own_n((u64)b->R + 1, &b->row_off, "row_off_of_rank"));
+  enqueue_validate(b);
+  TRY(check_flags(b, "ta_batch_plan"));
+  // tensor: count, size, write
+  b->TP = plan_tensor(b->Cmax, b->N, c->num_sms);
+  TensorArgs& A = b->T;
+  std::memset(&A, 0, sizeof A);
+  const u64 nt = b->n_tiles;
+  TRY(b->own_n(nt + 1, (u32**)&A.tfr, "tile map"));
+  TRY(b->own_n(nt, &A.tile_rows, "tile rows"));
+  TRY(b->own_n(nt, &A.tile_ents, "tile entries"));
+  TRY(b->own_n(nt, &A.tile_row_off, "tile row offsets"));
+  TRY(b->own_n(nt, &A.tile_ent_off, "tile entry offsets"));
+  TRY(b->own_n(2 * scan_scratch_elems(nt), &A.scan_scratch, "tile scan"));
+  const u32 W = b->TP.threads / 32;
+  if (!b->TP.bm_in_smem) {
+    const u64 words = (u64)b->TP.grid * W * bm_words(b->Cmax);
+    TRY(b->own_n(words, &A.gbm, "tensor bitmaps"));
+    cudaMemsetAsync(A.gbm, 0, words * 4, c->stream);
+  }
+  const u64 gn = (u64)b->TP.grid * W * b->TP.gst_cap;
+  TRY(b->own_n(gn, &A.gst_ctx, "tensor stage"));
+  TRY(b->own_n(gn, &A.gst_cnt, "tensor stage"));
+  TRY(b->own_n(gn, &A.gst_time, "tensor stage"));
+  A.rank_off = b->rank_off;
+  A.ts = b->ts;
+  A.ctx = b->cx;
+  A.R = b->R;
+  A.C = b->Cmax;
+  A.m = 0;
+  A.n_tiles = nt;
+  A.N = b->N;
+  A.status = (u32*)b->meta;
+  A.totals = b->meta + 1;
+  A.gst_cap = b->TP.gst_cap;
+  A.bm_in_smem = b->TP.bm_in_smem ? 1u : 0u;
+  A.sets = b->sets;
+  enqueue_tensor_count(b);
+  u64 h[3];
+  TRY(copy(c, h, b->meta, sizeof h));
+  TRY(sync_check(c, "batch: tensor count"));
+  TRY(status_from_flags((u32)h[0], "ta_batch_plan"));
+  b->rows = h[1];
+  b->nnz = h[2];
+  TRY(b->own_n(b->rows + 1, &b->entry_off, "entry_off"));
+  TRY(b->own_n(b->nnz, &b->e_ctx, "e_ctx"));
+  TRY(b->own_n(b->nnz, &b->e_time, "e_time"));
+  TRY(b->own_n(b->nnz, &b->e_cnt, "e_cnt"));
+  A.row_off_of_rank = b->row_off;
+  A.entry_off = b->entry_off;
+  A.e_ctx = b->e_ctx;
+  A.e_time = b->e_time;
+  A.e_cnt = b->e_cnt;
+  enqueue_tensor_write(b);
+  TRY(check_flags(b, "ta_batch_plan"));
+  // exclusive and inclusive CSR
+  b->XP = plan_rank_csr(b->R, b->Cmax, c->num_sms);
+  const u64 rg = (u64)b->XP.grid * (b->XP.threads / 32) * b->XP.gst_cap;
+  u32 *xg_ctx, *xg_cnt, *xg_dep, *xg_par, *x_cnt_r, *xgbm = nullptr;
+  u64 *xg_time, *x_scan;
+  TRY(b->own_n(rg, &xg_ctx, "csr stage"));
+  TRY(b->own_n(rg, &xg_cnt, "csr stage"));
+  TRY(b->own_n(rg, &xg_time, "csr stage"));
+  TRY(b->own_n(rg, &xg_dep, "csr stage"));
+  TRY(b->own_n(rg, &xg_par, "csr stage"));
+  TRY(b->own_n(b->R, &x_cnt_r, "csr counts"));
+  TRY(b->own_n(scan_scratch_elems(b->R), &x_scan, "csr scan"));
+  if (!b->XP.bm_in_smem) {
+    const u64 words = (u64)b->XP.grid * (b->XP.threads / 32) * bm_words(b->Cmax);
+    TRY(b->own_n(words, &xgbm, "csr bitmaps"));
+    cudaMemsetAsync(xgbm, 0, words * 4, c->stream);
+  }
+  for (int mode = 0; mode < 2; ++mode) {
+    RankCsrArgs& X = b->X[mode];
+    std::memset(&X, 0, sizeof X);
+    Csr& out = mode == 0 ? b->x : b->in;
+    TRY(b->own_n((u64)b->R + 1, &out.off, "csr off"));
+    X.mode = (u32)mode;
+    X.R = b->R;
+    X.C = b->Cmax;
+    X.max_depth = b->max_depth;
+    X.row_off_of_rank = b->row_off;
+    X.entry_off = b->entry_off;
+    if (mode == 0) {
+      X.in_ctx = b->e_ctx;
+      X.in_time = b->e_time;
+      X.in_cnt = b->e_cnt;
+    } else {
+      X.in_off = b->x.off;
+      X.in_ctx = b->x.ctx;
+      X.in_time = b->x.time;
+      X.in_cnt = b->x.cnt;
+    }
+    X.parent = b->parent;
+    X.depth = b->depth;
+    X.out_off = out.off;
+    X.out_cnt = x_cnt_r;
+    X.total = b->meta + 3 + mode;
+    X.scan_scratch = x_scan;
+    X.status = (u32*)b->meta;
+    X.gbm = xgbm;
+    X.gst_ctx = xg_ctx;
+    X.gst_cnt = xg_cnt;
+    X.gst_time = xg_time;
+    X.gst_dep = xg_dep;
+    X.gst_par = xg_par;
+    X.gst_cap = b->XP.gst_cap;
+    X.bm_in_smem = b->XP.bm_in_smem ? 1u : 0u;
+    X.sets = b->sets;
+    launch_rank_count(L, b->XP, X);
+    u64 t = 0;
+    TRY(copy(c, &t, b->meta + 3 + mode, 8));
+    TRY(sync_check(c, "batch: csr count"));
+    out.nnz = t;
+    TRY(b->own_n(t, &out.ctx, "csr ctx"));
+    TRY(b->own_n(t, &out.time, "csr time"));
+    TRY(b->own_n(t, &out.cnt, "csr cnt"));
+    X.out_ctx = out.ctx;
+    X.out_time = out.time;
+    X.out_cnt_e = out.cnt;
+    launch_rank_write(L, b->XP, X);
+    TRY(check_flags(b, "ta_batch_plan"));
+  }
+  // statistics
+  TRY(b->own(batch_stats_scratch_bytes(b->Ctot), (void**)&b->stats_scratch, "stats scratch"));
+  TRY(b->own_n(b->Ctot, &b->stats, "stats"));
+  u64 P2 = 1;
+  while (P2 < std::max<u64>(b->outlier_cap, 1)) P2 <<= 1;
+  TRY(b->own_n(P2, &b->keys, "outlier keys"));
+  TRY(b->own_n(P2, &b->zs, "outlier z"));
+  TRY(b->own_n(std::max<u64>(b->outlier_cap, 1), &b->outl, "outliers"));
+  TRY(b->own_n(S + 1, &b->set_out0, "outlier offsets"));
+  // per-set relative offsets
+  std::vector<u64> h_ro((u64)b->R + 1), h_xo((u64)b->R + 1), h_io((u64)b->R + 1);
+  TRY(copy(c, h_ro.data(), b->row_off, h_ro.size() * 8));
+  TRY(copy(c, h_xo.data(), b->x.off, h_xo.size() * 8));
+  TRY(copy(c, h_io.data(), b->in.off, h_io.size() * 8));
+  TRY(sync_check(c, "batch: offsets"));
+  b->h_row0.resize(S + 1);
+  b->h_x0.resize(S + 1);
+  b->h_i0.resize(S + 1);
+  b->h_ent0.resize(S + 1);
+  std::vector<u64> h_ent0(S + 1);
+  for (u32 s = 0; s <= S; ++s) {
+    b->h_row0[s] = h_ro[b->h_rank0[s]];
+    b->h_x0[s] = h_xo[b->h_rank0[s]];
+    b->h_i0[s] = h_io[b->h_rank0[s]];
+  }
+  std::vector<u64> row0_dev(b->h_row0);
+  for (u32 s = 0; s <= S; ++s) {
+    u64 v = 0;
+    TRY(copy(c, &v, b->entry_off + b->h_row0[s], 8));
+    TRY(sync_check(c, "batch: offsets"));
+    b->h_ent0[s] = v;
+  }
+  TRY(b->own_n(S + 1, &b->d_row0, "row starts"));
+  TRY(copy(c, b->d_row0, row0_dev.data(), (S + 1) * 8));
+  TRY(b->own_n((u64)b->R + S, &b->rel_row_off, "relative offsets"));
+  TRY(b->own_n(b->rows + S, &b->rel_entry_off, "relative offsets"));
+  TRY(b->own_n((u64)b->R + S, &b->rel_x_off, "relative offsets"));
+  TRY(b->own_n((u64)b->R + S, &b->rel_i_off, "relative offsets"));
+  // ---- capture the whole sequence once, then run it -------------------------
+  cudaStream_t st = c->stream;
+  bool own_stream = false;
+  if (st == nullptr) {  // the legacy default stream cannot be captured
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(TA_ERR_CUDA, "batch: stream");
+    own_stream = true;
+  }
+  cudaStream_t saved = c->stream;
+  const unsigned long long launches = c->launches;  // capture launches nothing
+  c->stream = st;
+  cudaError_t err = cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed);
+  if (err != cudaSuccess) {
+    c->stream = saved;
+    return cuda_fail(err, "cudaStreamBeginCapture");
+  }
+  enqueue_all(b);
+  err = cudaStreamEndCapture(st, &b->graph);
+  c->stream = saved;
+  c->launches = launches;
+  if (own_stream) cudaStreamDestroy(st);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaStreamEndCapture");
+  size_t nodes = 0;
+  cudaGraphGetNodes(b->graph, nullptr, &nodes);
+  b->graph_nodes = nodes;
+  std::vector<cudaGraphNode_t> list(nodes);
+  if (nodes) cudaGraphGetNodes(b->graph, list.data(), &nodes);
+  for (auto n : list) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(n, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+      ++b->graph_kernels;
+  }
+  err = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGraphInstantiate");
+  const ta_status s = ta_batch_run(b);  // too many outliers is reported by each run
+  return s == TA_ERR_CAPACITY ? TA_OK : s;
+}
+
+}  // namespace
+
+extern "C" {
+
+ta_status ta_batch_plan(ta_ctx* c, const ta_trace_desc* sets, uint32_t n_sets,
+                          const ta_batch_args* args, ta_batch** out) {
+  if (!c || !sets || !out || n_sets == 0) return fail(TA_ERR_INVALID_ARG, "ta_batch_plan: arguments");
+  *out = nullptr;
+  cudaSetDevice(c->device);
+  ta_batch* b = new ta_batch();
+  b->ctx = c;
+  if (args) {
+    b->tau_num = args->tau_num;
+    b->tau_den = args->tau_den;
+    b->outlier_cap = args->outlier_cap;
+  }
+  if (b->tau_den == 0) {
+    delete b;
+    return fail(TA_ERR_INVALID_ARG, "ta_batch_plan: tau_den = 0");
+  }
+  if (b->outlier_cap == 0) b->outlier_cap = 1u << 20;
+  ta_status s = create_impl(b, sets, n_sets);
+  if (s != TA_OK) {
+    std::string keep = ta_last_error_message();
+    cudaStreamSynchronize(c->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->drop();
+    cudaStreamSynchronize(c->stream);
+    delete b;
+    fail(s, "%s", keep.c_str());
+    return s;
+  }
+  *out = b;
+  return TA_OK;
+}
+
+ta_status ta_batch_run(ta_batch* b) {
+  if (!b || !b->exec) return fail(TA_ERR_STATE, "ta_batch_run: batch not ready");
+  ta_ctx* c = b->ctx;
+  cudaSetDevice(c->device);
+  cudaError_t err = cudaGraphLaunch(b->exec, c->stream);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGraphLaunch");
+  c->launches += b->graph_kernels;
+  TRY(check_flags(b, "ta_batch_run"));
+  const u64 n = std::min(b->n_out, b->outlier_cap);
+  const Launch L = launch_of(b);
+  launch_batch_outliers(L, b->keys, b->zs, b->n_out <= b->outlier_cap ? n : 0, b->sets, b->outl,
+                        b->set_out0);
+  b->h_out0.resize(b->S + 1);
+  TRY(copy(c, b->h_out0.data(), b->set_out0, (b->S + 1) * 8));
+  TRY(sync_check(c, "ta_batch_run"));
+  if (b->n_out > b->outlier_cap)
+    return fail(TA_ERR_CAPACITY, "batch: %llu outliers, capacity %llu",
+                (unsigned long long)b->n_out, (unsigned long long)b->outlier_cap);
+  return TA_OK;
+}
+
+ta_status ta_batch_free(ta_batch* b) {
+  if (!b) return TA_OK;
+  cudaStreamSynchronize(b->ctx->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->drop();
+  cudaStreamSynchronize(b->ctx->stream);
+  delete b;
+  return TA_OK;
+}
+
+ta_status ta_batch_get_info(const ta_batch* b, ta_batch_info* i) {
+  if (!b || !i) return fail(TA_ERR_INVALID_ARG, "ta_batch_get_info: NULL argument");
+  i->n_sets = b->S;
+  i->n_ranks = b->R;
+  i->n_records = b->n_samples;
+  i->n_rows = b->rows;
+  i->tensor_nnz = b->nnz;
+  i->excl_nnz = b->x.nnz;
+  i->incl_nnz = b->in.nnz;
+  i->n_outliers = b->n_out;
+  i->graph_nodes = b->graph_nodes;
+  i->graph_kernels = b->graph_kernels;
+  i->device_bytes = b->device_bytes;
+  return TA_OK;
+}
+
+ta_status ta_batch_get_set(const ta_batch* b, uint32_t s, ta_batch_set_view* v) {
+  if (!b || !v || s >= b->S) return fail(TA_ERR_INVALID_ARG, "ta_batch_get_set: arguments");
+  const u32 r0 = b->h_rank0[s];
+  v->n_ranks = b->h_rank0[s + 1] - r0;
+  v->n_ctx = b->h_C[s];
+  v->tensor.n_iter = b->n_iter + r0;
+  v->tensor.row_off_of_rank = b->rel_row_off + r0 + s;
+  v->tensor.entry_off = b->rel_entry_off + b->h_row0[s] + s;
+  v->tensor.e_ctx = b->e_ctx + b->h_ent0[s];
+  v->tensor.e_time = b->e_time + b->h_ent0[s];
+  v->tensor.e_cnt = b->e_cnt + b->h_ent0[s];
+  v->tensor.span = b->span + r0;
+  v->tensor.rows = b->h_row0[s + 1] - b->h_row0[s];
+  v->tensor.nnz = b->h_ent0[s + 1] - b->h_ent0[s];
+  v->exclusive.off = b->rel_x_off + r0 + s;
+  v->exclusive.ctx = b->x.ctx + b->h_x0[s];
+  v->exclusive.time = b->x.time + b->h_x0[s];
+  v->exclusive.cnt = b->x.cnt + b->h_x0[s];
+  v->exclusive.nnz = b->h_x0[s + 1] - b->h_x0[s];
+  v->inclusive.off = b->rel_i_off + r0 + s;
+  v->inclusive.ctx = b->in.ctx + b->h_i0[s];
+  v->inclusive.time = b->in.time + b->h_i0[s];
+  v->inclusive.cnt = b->in.cnt + b->h_i0[s];
+  v->inclusive.nnz = b->h_i0[s + 1] - b->h_i0[s];
+  v->stats = b->stats + b->h_ctx0[s];
+  if (b->h_out0.size() == b->S + 1) {
+    v->outliers = b->outl + b->h_out0[s];
+    v->n_outliers = b->h_out0[s + 1] - b->h_out0[s];
+  } else {
+    v->outliers = nullptr;
+    v->n_outliers = 0;
+  }
+  return TA_OK;
+}
+
+}  // extern "C"

@@ -14,7 +14,7 @@ namespace ta {
 // shorter than 2^32 samples; per-rank span ts_last - ts_first.
 __global__ void k_rank_off(const u64* __restrict__ rank_off, u32 R, u64 N,
                            const u64* __restrict__ ts, u64* span, unsigned long long* max_span,
-                           u32* status) {
+                           u32* status, SetMap sets) {
   const u64 r = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (r > R) return;
   if (r == 0 && rank_off[0] != 0) flag(status, F_INVALID);
@@ -22,7 +22,12 @@ __global__ void k_rank_off(const u64* __restrict__ rank_off, u32 R, u64 N,
     if (rank_off[R] != N) flag(status, F_INVALID);
     return;
   }
-  const u64 b = rank_off[r], e = rank_off[r + 1];
+  const u64 b = rank_off[r];
+  u64 e = rank_off[r + 1];
+  if (sets.S) {
+    const u32 s = sets.rank_set[r];
+    if (r + 1 == sets.set_rank0[s + 1]) e = sets.set_rec_end[s];
+  }
   if (e < b || e > N || b > N) {
     flag(status, F_INVALID);
     span[r] = 0;
@@ -39,26 +44,32 @@ __global__ void k_rank_off(const u64* __restrict__ rank_off, u32 R, u64 N,
 }
 
 void launch_rank_off(const Launch& L, const u64* rank_off, u32 R, u64 N, const u64* ts,
-                     u64* span, u64* max_span, u32* status) {
+                     u64* span, u64* max_span, u32* status, const SetMap& sets) {
   const u64 n = (u64)R + 1;
   k_rank_off<<<(unsigned)((n + 255) / 256), 256, 0, L.stream>>>(
-      rank_off, R, N, ts, span, (unsigned long long*)max_span, status);
+      rank_off, R, N, ts, span, (unsigned long long*)max_span, status, sets);
   L.count();
 }
 
 // First rank whose samples start at or after each tile start (tile = fixed
-// number of samples); tfr[n_tiles] = R so the last tile also owns the ranks
-// that start at N (empty trailing ranks).
+// number of samples, tiles never span sets); tfr[n_tiles] = R so the last tile
+// also owns the ranks that start at N (empty trailing ranks).
 __global__ void k_tile_first_rank(const u64* __restrict__ rank_off, u32 R, u32 tile,
-                                  u32 n_tiles, u32* tfr) {
+                                  u32 n_tiles, u32* tfr, SetMap sets) {
   const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t > n_tiles) return;
   if (t == n_tiles) {
     tfr[t] = R;
     return;
   }
-  const u64 x = (u64)t * tile;
+  u64 x = (u64)t * tile;
   u32 lo = 0, hi = R;
+  if (sets.S) {
+    const u32 s = sets.tile_set[t];
+    x = sets.set_rec0[s] + (u64)(t - sets.set_tile0[s]) * tile;
+    lo = sets.set_rank0[s];
+    hi = sets.set_rank0[s + 1];
+  }
   while (lo < hi) {
     const u32 mid = lo + (hi - lo) / 2;
     if (rank_off[mid] < x) lo = mid + 1;
@@ -68,9 +79,9 @@ __global__ void k_tile_first_rank(const u64* __restrict__ rank_off, u32 R, u32 t
 }
 
 void launch_tile_first_rank(const Launch& L, const u64* rank_off, u32 R, u32 tile, u32 n_tiles,
-                            u32* tfr) {
+                            u32* tfr, const SetMap& sets) {
   const u32 n = n_tiles + 1;
-  k_tile_first_rank<<<(n + 255) / 256, 256, 0, L.stream>>>(rank_off, R, tile, n_tiles, tfr);
+  k_tile_first_rank<<<(n + 255) / 256, 256, 0, L.stream>>>(rank_off, R, tile, n_tiles, tfr, sets);
   L.count();
 }
 
@@ -79,20 +90,26 @@ void launch_tile_first_rank(const Launch& L, const u64* rank_off, u32 R, u32 til
 // node by pointer jumping (log2 C rounds); a node that has not reached the
 // root after 2^rounds >= C jumps lies on a cycle.
 __global__ void k_cct_init(const u32* __restrict__ parent, u32 C, u32* anc, u32* dep, u32* roots,
-                           u32* status) {
+                           u32* status, SetMap sets) {
   const u32 v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= C) return;
   const u32 p = parent[v];
+  u32 s = 0, base = 0, Cs = C;
+  if (sets.S) {
+    s = set_of_ctx(sets, v);
+    base = sets.set_ctx0[s];
+    Cs = sets.set_C[s];
+  }
   if (p == NONE32) {
-    atomicAdd(roots, 1u);
+    atomicAdd(&roots[s], 1u);
     anc[v] = NONE32;
     dep[v] = 0;
-  } else if (p >= C) {
+  } else if (p >= Cs) {
     flag(status, F_BAD_CCT);
     anc[v] = NONE32;
     dep[v] = 0;
   } else {
-    anc[v] = p;
+    anc[v] = base + p;
     dep[v] = 1;
   }
 }
@@ -121,13 +138,13 @@ __global__ void k_cct_final(const u32* __restrict__ anc, const u32* __restrict__
 }
 
 void launch_cct(const Launch& L, const u32* parent, u32 C, u32* depth, u32* max_depth,
-                u32* roots, u32* scratch, u32* status) {
+                u32* roots, u32* scratch, u32* status, const SetMap& sets) {
   u32* anc0 = scratch;
   u32* dep0 = scratch + C;
   u32* anc1 = scratch + 2 * (u64)C;
   u32* dep1 = scratch + 3 * (u64)C;
   const unsigned g = (C + 255) / 256;
-  k_cct_init<<<g, 256, 0, L.stream>>>(parent, C, anc0, dep0, roots, status);
+  k_cct_init<<<g, 256, 0, L.stream>>>(parent, C, anc0, dep0, roots, status, sets);
   int rounds = 1;
   while (rounds < 40 && (1ull << rounds) < (u64)C) ++rounds;
   for (int i = 0; i < rounds; ++i) {
@@ -284,8 +301,7 @@ struct Stage {
 // and count at each context's rank in the stage, then write the row at entry
 // eo.  The stage is shared memory or the warp's global region (compile time).
 __device__ __forceinline__ void accumulate_row(const TensorArgs& A, const Bm& bm, const Stage& st,
-                                               u64 s, u64 e, bool e_rs, int lane) {
-  const u32 C = A.C;
+                                               u64 s, u64 e, bool e_rs, u32 C, int lane) {
   for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
     Step x;
     load_step(A, g0, lane, true, x);
@@ -339,7 +355,7 @@ __device__ __forceinline__ void emit_row(const TensorArgs& A, const Stage& st, u
 
 __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
                                          const Stage& sm, const Stage& gl, u64 s, u64 e,
-                                         bool e_rs, u64 eo, int lane) {
+                                         bool e_rs, u64 eo, u32 C, int lane) {
   __syncwarp();
   const u32 nnz = bm_prefix_warp(bm, lane);
   if (nnz <= RS) {
@@ -348,7 +364,7 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
       sm.cnt[k] = 0;
     }
     __syncwarp();
-    accumulate_row(A, bm, sm, s, e, e_rs, lane);
+    accumulate_row(A, bm, sm, s, e, e_rs, C, lane);
     __syncwarp();
     emit_row(A, sm, nnz, eo, lane);
   } else {
@@ -357,7 +373,7 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
       gl.cnt[k] = 0;
     }
     __syncwarp();
-    accumulate_row(A, bm, gl, s, e, e_rs, lane);
+    accumulate_row(A, bm, gl, s, e, e_rs, C, lane);
     __syncwarp();
     emit_row(A, gl, nnz, eo, lane);
   }
@@ -395,16 +411,27 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     gst.cnt = A.gst_cnt + gw * A.gst_cap;
   }
   __syncwarp();
-  const u32 m = A.m, C = A.C;
-  const u64 N = A.N;
-
   for (u64 t = gw; t < A.n_tiles; t += G) {
-    const u64 a = t * TW;
+    // the tile's trace set (a single experiment is one set)
+    u64 sbase = 0, N = A.N, t0 = 0, t1 = A.n_tiles;
+    u32 rlo = 0, rhi = A.R, C = A.C, m = A.m;
+    if (A.sets.S) {
+      const u32 s = A.sets.tile_set[t];
+      sbase = A.sets.set_rec0[s];
+      N = A.sets.set_rec_end[s];
+      t0 = A.sets.set_tile0[s];
+      t1 = A.sets.set_tile0[s + 1];
+      rlo = A.sets.set_rank0[s];
+      rhi = A.sets.set_rank0[s + 1];
+      C = A.sets.set_C[s];
+      m = A.sets.set_m[s];
+    }
+    const u64 a = sbase + (t - t0) * TW;
     const u64 b = min(a + (u64)TW, N);
-    const bool last = (t == A.n_tiles - 1);
-    const u32 lo = A.tfr[t], hi = A.tfr[t + 1];
-    const u64 qrank = (hi < A.R) ? A.rank_off[hi] : N;  // first rank start >= b (or N)
-    u32 carry = (a > 0) ? A.ctx[a - 1] : NONE32;
+    const bool last = (t + 1 == t1);
+    const u32 lo = A.tfr[t], hi = last ? rhi : A.tfr[t + 1];
+    const u64 qrank = (hi < rhi) ? A.rank_off[hi] : N;  // first rank start >= b (or N)
+    u32 carry = (a > sbase) ? A.ctx[a - 1] : NONE32;
     u64 PR = 0, PE = 0;
     if (WRITE) {
       PR = A.tile_row_off[t];
@@ -436,7 +463,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) {
       const u64 qd = a + (u64)d * STEP;
-      if (qd < N) load_step(A, qd, lane, WRITE && qd < b, ring[d]);
+      if (qd < A.N) load_step(A, qd, lane, WRITE && qd < b, ring[d]);
     }
     for (u64 q0 = a;; q0 += STEP) {
       const bool tile_step = q0 < b;
@@ -444,7 +471,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       const u64 lim = tile_step ? b : qrank;
       if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, lim, true, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, lim, true, PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
@@ -459,7 +486,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       const u64 q1 = q0 + STEP;
       {
         const u64 qd = q0 + (u64)DEPTH * STEP;
-        if (qd < N) load_step(A, qd, lane, WRITE && qd < b, ring[DEPTH]);
+        if (qd < A.N) load_step(A, qd, lane, WRITE && qd < b, ring[DEPTH]);
       }
       const u64 q = q0 + 4 * (u64)lane;
       // samples of this step that exist (tile steps: below b; continuation:
@@ -530,7 +557,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         }
         if (q1 >= b && b == N) {  // the last tile: rows end at N
           if (row_open) {
-            if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, lane);
+            if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, C, lane);
             else {
               cum += __reduce_add_sync(FULL, fresh);
               fresh = 0;
@@ -576,7 +603,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         const bool p_rs = (__shfl_sync(FULL, rs4, src) >> bj) & 1u;
         const bool p_ms = (__shfl_sync(FULL, ms4, src) >> bj) & 1u;
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, p, p_rs, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, p, p_rs, PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
@@ -612,7 +639,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       if (stop) break;
       if (q1 >= b && b == N) {  // the last tile: rows end at N
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, lane);
+          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
@@ -632,7 +659,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       const u64 row0 = PR + rows_local;
       for (u32 k = lane; k < n_end; k += 32) {
         A.entry_off[row0 + k] = PE + cum;
-        A.row_off_of_rank[A.R - n_end + k] = row0 + k;
+        A.row_off_of_rank[rhi - n_end + k] = row0 + k;
       }
     } else if (lane == 0) {
       A.tile_rows[t] = rows_local + n_end;
@@ -704,6 +731,7 @@ namespace {
 
 constexpr u32 RSR = 256;           // staged entries per warp in shared memory
 constexpr u32 DEPTH_BUCKETS = 64;  // depth range handled by the bucket sweep
+constexpr u32 BUCKET_MAX = 1024;   // closure size handled by the bucket sweep
 
 struct RankSmem {
   static constexpr u32 time_off = 0;                 // u64[RSR]
@@ -711,8 +739,9 @@ struct RankSmem {
   static constexpr u32 cnt_off = ctx_off + 4 * RSR;  // u32[RSR]
   static constexpr u32 dep_off = cnt_off + 4 * RSR;  // u32[RSR] (inclusive)
   static constexpr u32 par_off = dep_off + 4 * RSR;  // u32[RSR] (inclusive)
-  static constexpr u32 bucket_off = par_off + 4 * RSR;  // u32[DEPTH_BUCKETS + 1 + RSR]
-  static constexpr u32 fixed_write = (bucket_off + 4 * (DEPTH_BUCKETS + 1 + RSR) + 15) & ~15u;
+  static constexpr u32 bucket_off = par_off + 4 * RSR;  // u32[DEPTH_BUCKETS + 1], u16[BUCKET_MAX]
+  static constexpr u32 fixed_write =
+      (bucket_off + 4 * (DEPTH_BUCKETS + 1) + 2 * BUCKET_MAX + 15) & ~15u;
 };
 
 struct RStage {
@@ -756,6 +785,8 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   }
   __syncwarp();
   for (u64 r = gw; r < A.R; r += G) {
+    // context ids are local to the rank's set; tree arrays are concatenated
+    const u32 cbase = A.sets.S ? A.sets.set_ctx0[A.sets.rank_set[r]] : 0u;
     u64 E0, E1;
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
@@ -778,7 +809,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         u32 c = A.in_ctx[j];
         for (u32 step = 0; c != NONE32 && step <= A.max_depth; ++step) {
           if (bm_test_set(bm, c)) break;
-          c = A.parent[c];
+          c = A.parent[cbase + c];
         }
       }
     }
@@ -824,9 +855,9 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       u32 maxd = 0;
       for (u32 k = lane; k < nnz; k += 32) {
         const u32 c = st.ctx[k];
-        const u32 d = A.depth[c];
+        const u32 d = A.depth[cbase + c];
         st.dep[k] = d;
-        st.par[k] = d > 0 ? bm_rank(bm, A.parent[c]) : NONE32;
+        st.par[k] = d > 0 ? bm_rank(bm, A.parent[cbase + c]) : NONE32;
         maxd = max(maxd, d);
       }
       maxd = __reduce_max_sync(FULL, maxd);
@@ -836,11 +867,11 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         st.cnt[k] = A.in_cnt[j];
       }
       __syncwarp();
-      if (maxd < DEPTH_BUCKETS && nnz <= RSR) {
+      if (maxd < DEPTH_BUCKETS && nnz <= BUCKET_MAX) {
         // order the entries by depth (counting sort in shared memory), then
         // roll up one level at a time from the deepest: O(entries + depth)
         u32* hist = bucket_base;
-        u32* order = bucket_base + DEPTH_BUCKETS + 1;
+        uint16_t* order = (uint16_t*)(bucket_base + DEPTH_BUCKETS + 1);
         for (u32 d = lane; d <= DEPTH_BUCKETS; d += 32) hist[d] = 0;
         __syncwarp();
         for (u32 k = lane; k < nnz; k += 32) atomicAdd(&hist[st.dep[k]], 1u);
@@ -857,7 +888,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         __syncwarp();
         for (u32 k = lane; k < nnz; k += 32) {
           const u32 slot = atomicAdd(&hist[st.dep[k]], 1u);
-          order[slot] = k;
+          order[slot] = (uint16_t)k;
         }
         __syncwarp();
         // after the scatter hist[d] is the end of bucket d = start of d + 1

@@ -70,7 +70,7 @@ constexpr int STATS_NT = 256;
 __global__ void __launch_bounds__(STATS_NT)
     k_stats_partial(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
                     const u32* __restrict__ ctx, const u64* __restrict__ time,
-                    const u32* __restrict__ slot_of_ctx, Partials P) {
+                    const u32* __restrict__ slot_of_ctx, Partials P, SetMap sets) {
   __shared__ u32 hkey[HCAP];
   __shared__ u32 hpres[HCAP];
   __shared__ unsigned long long hmn[HCAP], hmx[HCAP], hs1[HCAP], hs2lo[HCAP], hs2hi[HCAP];
@@ -89,9 +89,10 @@ __global__ void __launch_bounds__(STATS_NT)
   const u32 nw = (gridDim.x * STATS_NT) >> 5;
   for (u32 i = gw; i < n; i += nw) {
     const u32 r = rank_at(S, i);
+    const u32 cbase = sets.S ? sets.set_ctx0[sets.rank_set[r]] : 0u;
     const u64 E0 = off[r], E1 = off[r + 1];
     for (u64 j = E0 + lane; j < E1; j += 32) {
-      const u32 slot = slot_of_ctx[ctx[j]];
+      const u32 slot = sets.S ? cbase + ctx[j] : slot_of_ctx[ctx[j]];
       if (slot == NONE32) continue;
       const u64 x = time[j];
       const u128 x2 = (u128)x * x;
@@ -140,10 +141,19 @@ __global__ void __launch_bounds__(STATS_NT)
 }
 
 // Per slot: mean, std (ddof 1), cv, balance from the exact partials.
-__global__ void k_stats_finalize(u32 n_slots, u64 n, const u32* S, Partials P,
-                                 ta_ctx_stats* out) {
+__global__ void k_stats_finalize(u32 n_slots, u64 n_all, const u32* S, Partials P,
+                                 ta_ctx_stats* out, SetMap sets) {
   const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots) return;
+  u64 n = n_all;
+  u32 first_rank = 0;
+  if (sets.S) {  // every context of a set is taken over that set's ranks
+    const u32 set = set_of_ctx(sets, s);
+    first_rank = sets.set_rank0[set];
+    n = sets.set_rank0[set + 1] - first_rank;
+  } else {
+    first_rank = rank_at(S, 0);
+  }
   const u32 present = P.present[s];
   const u64 mx = P.mx[s], s1 = P.s1[s];
   const u128 S2 = ((u128)P.s2hi[s] << 64) | P.s2lo[s];
@@ -168,24 +178,31 @@ __global__ void k_stats_finalize(u32 n_slots, u64 n, const u32* S, Partials P,
   P.sd[s] = sd;
   P.Mlo[s] = (u64)M;
   P.Mhi[s] = (u64)(M >> 64);
-  P.argmax[s] = (mx == 0) ? rank_at(S, 0) : NONE32;
+  P.argmax[s] = (mx == 0) ? first_rank : NONE32;
 }
 
 // Argmax (lowest rank attaining max), z-scores and the exact outlier rule.
-__global__ void k_stats_z(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
+__global__ void k_stats_z(const u32* __restrict__ S, u32 n_all, const u64* __restrict__ off,
                           const u32* __restrict__ ctx, const u64* __restrict__ time,
                           const u32* __restrict__ slot_of_ctx, Partials P, u32 tn, u32 td,
                           double* z_out, u64* keys, double* zs, u64 cap,
-                          unsigned long long* n_out, uint8_t* rank_flag) {
+                          unsigned long long* n_out, uint8_t* rank_flag, SetMap sets) {
   const int lane = threadIdx.x & 31;
   const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
-  for (u32 i = gw; i < n; i += nw) {
+  for (u32 i = gw; i < n_all; i += nw) {
     const u32 r = rank_at(S, i);
+    u64 n = n_all;
+    u32 cbase = 0;
+    if (sets.S) {
+      const u32 set = sets.rank_set[r];
+      cbase = sets.set_ctx0[set];
+      n = sets.set_rank0[set + 1] - sets.set_rank0[set];
+    }
     const u64 E0 = off[r], E1 = off[r + 1];
     for (u64 j = E0 + lane; j < E1; j += 32) {
       const u32 c = ctx[j];
-      const u32 slot = slot_of_ctx[c];
+      const u32 slot = sets.S ? cbase + c : slot_of_ctx[c];
       if (slot == NONE32) continue;
       const u64 x = time[j];
       const u64 mx = P.mx[slot];
@@ -198,7 +215,7 @@ __global__ void k_stats_z(const u32* __restrict__ S, u32 n, const u64* __restric
       if (is_outlier(D, n, M, tn, td)) {
         const unsigned long long q = atomicAdd(n_out, 1ull);
         if (q < cap) {
-          keys[q] = ((u64)c << 32) | r;
+          keys[q] = ((u64)slot << 32) | r;
           zs[q] = z;
         }
         if (rank_flag) rank_flag[r] = 1;
@@ -207,9 +224,12 @@ __global__ void k_stats_z(const u32* __restrict__ S, u32 n, const u64* __restric
   }
 }
 
-__global__ void k_stats_argmax(u32 n_slots, const u32* argmax, ta_ctx_stats* out) {
+// Argmax into the output; with sets, as a rank id local to the slot's set.
+__global__ void k_stats_argmax(u32 n_slots, const u32* argmax, ta_ctx_stats* out,
+                               SetMap sets = SetMap{}) {
   const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s < n_slots) out[s].argmax = argmax[s];
+  if (s >= n_slots) return;
+  out[s].argmax = argmax[s] - (sets.S ? sets.set_rank0[set_of_ctx(sets, s)] : 0u);
 }
 
 // ---- sort of (key, z) pairs by key: bitonic, in shared memory when small --
@@ -267,11 +287,15 @@ __global__ void k_sort_step(u64* keys, double* vals, u64 P, u64 j, u64 k) {
   }
 }
 
-__global__ void k_write_outliers(const u64* keys, const double* zs, u64 n, ta_outlier* out) {
+// Keys are (slot << 32 | rank); slot_ctx maps a slot back to its context
+// (null: the slot is the context).
+__global__ void k_write_outliers(const u64* keys, const double* zs, u64 n, ta_outlier* out,
+                                 const u32* slot_ctx) {
   const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ta_outlier o;
-  o.ctx = (u32)(keys[i] >> 32);
+  const u32 slot = (u32)(keys[i] >> 32);
+  o.ctx = slot_ctx ? slot_ctx[slot] : slot;
   o.rank = (u32)keys[i];
   o.z = zs[i];
   out[i] = o;
@@ -391,10 +415,11 @@ ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 
   cudaMemsetAsync(n_out, 0, 8, c->stream);
   if (z_out) cudaMemsetAsync(z_out, 0, m->nnz * 8, c->stream);
   const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + 7) / 8)));
-  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P);
-  k_stats_finalize<<<blocks(ns), 256, 0, L.stream>>>(ns, n, dS, P, R.stats);
+  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P,
+                                                   SetMap{});
+  k_stats_finalize<<<blocks(ns), 256, 0, L.stream>>>(ns, n, dS, P, R.stats, SetMap{});
   k_stats_z<<<grid, 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P, tn, td,
-                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag);
+                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag, SetMap{});
   k_stats_argmax<<<blocks(ns), 256, 0, L.stream>>>(ns, P.argmax, R.stats);
   L.count(4);
   u64 h = 0;
@@ -720,7 +745,7 @@ ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_ou
   if (fits && R.kept > 0 && o->outliers) {
     if (a->mem_kind == TA_MEM_DEVICE) dout = o->outliers;
     else TRY(tmp.get_n(R.kept, &dout, "outliers"));
-    k_write_outliers<<<blocks(R.kept), 256, 0, L.stream>>>(R.keys, R.zs, R.kept, dout);
+    k_write_outliers<<<blocks(R.kept), 256, 0, L.stream>>>(R.keys, R.zs, R.kept, dout, dK);
     L.count();
     if (a->mem_kind == TA_MEM_HOST) TRY(copy(c, o->outliers, dout, R.kept * sizeof(ta_outlier)));
   }
@@ -1071,10 +1096,10 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   cudaMemsetAsync(P.s2hi, 0, C * 8, st);
   const int grid = std::max(1, std::min<int>(num_sms * 4, (int)((n + 7) / 8)));
   const u64 kcap = std::max<u64>(1, outlier_cap);
-  k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P);
-  k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats);
+  k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, SetMap{});
+  k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats, SetMap{});
   k_stats_z<<<grid, 256, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, tau_num, tau_den,
-                                  nullptr, keys, zs, kcap, n_out, nullptr);
+                                  nullptr, keys, zs, kcap, n_out, nullptr, SetMap{});
   k_stats_argmax<<<blocks(C), 256, 0, st>>>((u32)C, P.argmax, stats);
   u64 h[2] = {0, 0};
   cudaError_t err = cudaMemcpyAsync(h, n_out, 16, cudaMemcpyDeviceToHost, st);
@@ -1087,7 +1112,7 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
                 (unsigned long long)outlier_cap);
   if (h[0] > 0) {
     sort_pairs(L, keys, zs, h[0]);  // the key buffer holds NA_MAX_OUTLIERS (a power of two)
-    k_write_outliers<<<blocks(h[0]), 256, 0, st>>>(keys, zs, h[0], outliers);
+    k_write_outliers<<<blocks(h[0]), 256, 0, st>>>(keys, zs, h[0], outliers, nullptr);
   }
   err = cudaStreamSynchronize(st);
   if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
@@ -1095,3 +1120,94 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
   return TA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Statistics of every context of every set of a batch (set-aware kernels).
+namespace {
+
+// Per set: index of the first outlier key whose slot is in the set.
+__global__ void k_outlier_set_bounds(const u64* keys, u64 n, SetMap sets, u64* set_off) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s > sets.S) return;
+  const u64 key = (u64)sets.set_ctx0[s] << 32;
+  u64 lo = 0, hi = n;
+  while (lo < hi) {
+    const u64 mid = (lo + hi) / 2;
+    if (keys[mid] < key) lo = mid + 1;
+    else hi = mid;
+  }
+  set_off[s] = lo;
+}
+
+// Outliers of a batch with set-local contexts and ranks.
+__global__ void k_write_batch_outliers(const u64* keys, const double* zs, u64 n, SetMap sets,
+                                       ta_outlier* out) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const u32 slot = (u32)(keys[i] >> 32), r = (u32)keys[i];
+  const u32 s = set_of_ctx(sets, slot);
+  ta_outlier o;
+  o.ctx = slot - sets.set_ctx0[s];
+  o.rank = r - sets.set_rank0[s];
+  o.z = zs[i];
+  out[i] = o;
+}
+
+}  // namespace
+
+namespace ta {
+
+u64 batch_stats_scratch_bytes(u32 Ctot) { return (u64)Ctot * 72 + 64; }
+
+// All ranks, all contexts of every set, threshold tau; outlier keys
+// (global slot << 32 | global rank) and z go to keys/zs (capacity cap);
+// *n_out receives the full count.  scratch: batch_stats_scratch_bytes.
+void launch_batch_stats(const Launch& L, u32 R, u32 Ctot, const u64* off, const u32* ctx,
+                        const u64* time, const SetMap& sets, u32 tau_num, u32 tau_den,
+                        unsigned char* scratch, ta_ctx_stats* stats, u64* keys, double* zs,
+                        u64 cap, unsigned long long* n_out) {
+  Partials P;
+  unsigned char* q = scratch;
+  P.present = (u32*)q;
+  q += (u64)Ctot * 4;
+  P.argmax = (u32*)q;
+  q += (u64)Ctot * 4;
+  P.mn = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.mx = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.s1 = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.s2lo = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.s2hi = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.sd = (double*)q;
+  q += (u64)Ctot * 8;
+  P.Mlo = (u64*)q;
+  q += (u64)Ctot * 8;
+  P.Mhi = (u64*)q;
+  cudaMemsetAsync(P.present, 0, (u64)Ctot * 4, L.stream);
+  cudaMemsetAsync(P.mn, 0xFF, (u64)Ctot * 8, L.stream);
+  cudaMemsetAsync(P.mx, 0, (u64)Ctot * 8 * 4, L.stream);  // mx, s1, s2lo, s2hi
+  cudaMemsetAsync(n_out, 0, 8, L.stream);
+  const int grid = std::max(1, std::min<int>(L.num_sms * 4, (int)((R + 7) / 8)));
+  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(nullptr, R, off, ctx, time, nullptr, P, sets);
+  k_stats_finalize<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, R, nullptr, P, stats, sets);
+  k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, R, off, ctx, time, nullptr, P, tau_num, tau_den,
+                                        nullptr, keys, zs, std::max<u64>(cap, 1), n_out, nullptr,
+                                        sets);
+  k_stats_argmax<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, P.argmax, stats, sets);
+  L.count(4);
+}
+
+// Sort n (<= capacity, buffers of next_pow2(capacity)) keys and split them by set.
+void launch_batch_outliers(const Launch& L, u64* keys, double* zs, u64 n, const SetMap& sets,
+                           ta_outlier* out, u64* set_off) {
+  sort_pairs(L, keys, zs, n);
+  k_outlier_set_bounds<<<blocks(sets.S + 1), 256, 0, L.stream>>>(keys, n, sets, set_off);
+  if (n) k_write_batch_outliers<<<blocks(n), 256, 0, L.stream>>>(keys, zs, n, sets, out);
+  L.count(2);
+}
+
+}  // namespace ta

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "ta.h"
 #include "ta_dev.cuh"
 
 namespace ta {
@@ -14,6 +15,33 @@ struct Launch {
   unsigned long long* launches;  // counter of kernel launches
   void count(int k = 1) const { *launches += (unsigned long long)k; }
 };
+
+// Several independent trace sets analysed together: sets are concatenated
+// (ranks, samples, contexts) and every kernel looks up its set.  All arrays
+// are null for a single experiment.
+struct SetMap {
+  u32 S;                  // number of sets (0 = single experiment)
+  const u32* tile_set;    // [n_tiles] set of each tile
+  const u64* set_tile0;   // [S+1] first tile of each set
+  const u64* set_rec0;    // [S+1] first sample of each set (aligned; [S] = arena end)
+  const u64* set_rec_end; // [S] one past the last sample of each set (<= set_rec0[s+1])
+  const u32* set_rank0;   // [S+1] first rank of each set
+  const u32* set_ctx0;    // [S+1] first context of each set (tree arrays)
+  const u32* set_C;       // [S] contexts of each set
+  const u32* set_m;       // [S] marker of each set
+  const u32* rank_set;    // [R] set of each rank
+};
+
+// Set of a (global) context id: the last set whose first context is <= v.
+__device__ __forceinline__ u32 set_of_ctx(const SetMap& sets, u32 v) {
+  u32 lo = 0, hi = sets.S;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) / 2;
+    if (sets.set_ctx0[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
 
 // ------------------------------------------------------------- ingest ----
 struct TensorArgs {
@@ -44,6 +72,7 @@ struct TensorArgs {
   u32 gst_cap;  // per warp: rows with more entries than shared staging holds
   u32 bm_in_smem;
   u32* status;
+  SetMap sets;
 };
 
 struct TensorPlan {
@@ -57,13 +86,17 @@ void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs&
 void launch_tile_scan(const Launch& L, const TensorArgs& A);
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A);
 
+// With sets, the last rank of set s ends at set_rec_end[s] (samples between
+// set_rec_end[s] and set_rec0[s+1] are alignment padding of no rank).
 void launch_rank_off(const Launch& L, const u64* rank_off, u32 R, u64 N, const u64* ts,
-                     u64* span, u64* max_span, u32* status);
+                     u64* span, u64* max_span, u32* status, const SetMap& sets);
 void launch_tile_first_rank(const Launch& L, const u64* rank_off, u32 R, u32 tile, u32 n_tiles,
-                            u32* tfr);
+                            u32* tfr, const SetMap& sets);
 // parent[C] -> depth[C], *max_depth; scratch: 4*C u32.
+// With sets, parent ids are local to each set's tree and roots[s] counts the
+// roots of set s (roots has S entries); depth is per tree.
 void launch_cct(const Launch& L, const u32* parent, u32 C, u32* depth, u32* max_depth,
-                u32* roots, u32* scratch, u32* status);
+                u32* roots, u32* scratch, u32* status, const SetMap& sets);
 void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_iter);
 
 // Per-rank CSR of distinct contexts (mode 0: exclusive from the tensor,
@@ -96,6 +129,7 @@ struct RankCsrArgs {
   u32 gst_cap;
   u32 bm_in_smem;
   u32* status;
+  SetMap sets;
 };
 struct RankCsrPlan {
   int threads, grid;
@@ -107,6 +141,15 @@ struct RankCsrPlan {
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+
+// Batch statistics (stats.cu).
+u64 batch_stats_scratch_bytes(u32 Ctot);
+void launch_batch_stats(const Launch& L, u32 R, u32 Ctot, const u64* off, const u32* ctx,
+                        const u64* time, const SetMap& sets, u32 tau_num, u32 tau_den,
+                        unsigned char* scratch, ta_ctx_stats* stats, u64* keys, double* zs,
+                        u64 cap, unsigned long long* n_out);
+void launch_batch_outliers(const Launch& L, u64* keys, double* zs, u64 n, const SetMap& sets,
+                           ta_outlier* out, u64* set_off);
 
 // Exclusive prefix sums (scan.cu); scratch holds scan_scratch_elems(n) u64.
 u64 scan_scratch_elems(u64 n);

@@ -18,7 +18,8 @@ STRUCTS = {"ta_trace_desc": ta.TraceDesc, "ta_experiment_info": ta.ExperimentInf
            "ta_topo_args": ta.TopoArgs, "ta_topo_out": ta.TopoOut,
            "ta_speedup_args": ta.SpeedupArgs, "ta_speedup_ctx": ta.SpeedupCtx,
            "ta_speedup_total": ta.SpeedupTotal, "ta_speedup_out": ta.SpeedupOut,
-           "ta_profile": ta.Profile}
+           "ta_profile": ta.Profile, "ta_batch_args": ta.BatchArgs,
+           "ta_batch_info": ta.BatchInfo, "ta_batch_set_view": ta.BatchSetView}
 
 
 def test_library_builds_and_exports_every_declared_symbol():

@@ -1,0 +1,142 @@
+"""Parity of the batched form (ta_batch_plan / ta_batch_run) with the oracle.
+
+Every set of a batch must give, through its set-relative views, exactly the
+products the oracle gives for that set alone: the iteration tensor, the
+exclusive and inclusive CSR, spans, and the cross-rank statistics of the
+exclusive metric over all ranks with their outliers.  Sets differ in rank
+count, context count, marker and length, include empty and degenerate sets,
+and share 4096-sample tiles with nobody."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_03561_b300 as ta
+from paper_2605_03561_b300 import synth
+from paper_2605_03561_b300.synth import edge
+from gpu_helpers import FP_FIELDS, INT_FIELDS, close, context
+
+pytestmark = pytest.mark.gpu
+
+
+def _sets_mixed(seed):
+    sets = [edge.case(n, seed) for n in edge.EDGE_CASES]
+    sets += [edge.case("random_small", seed * 10 + k) for k in range(6)]
+    sets += [edge.case("random_medium", seed * 10 + k) for k in range(3)]
+    sets.append(synth.generate(synth.preset(1, seed=seed + 3, n_ranks=24)))
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(len(sets))
+    return [sets[i] for i in order]
+
+
+def _tuple(d):
+    return (d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+
+
+def _check_set(got, d, tau):
+    tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+    a = oracle.Analysis(tr, 0, None, rows=True, incl=True)
+    assert got["R"] == tr.R and got["C"] == tr.C
+    gt, ot = got["tensor"], a.tensor()
+    for k in ("n_iter", "row_off_of_rank", "entry_off", "e_ctx", "e_time", "e_cnt"):
+        assert np.array_equal(gt[k], ot[k]), k
+    assert np.array_equal(gt["span"], a.span())
+    for name, metric in (("exclusive", ta.EXCLUSIVE), ("inclusive", ta.INCLUSIVE)):
+        g, o = got[name], a.csr(metric)
+        for k in ("off", "ctx", "time", "cnt"):
+            assert np.array_equal(g[k], o[k]), (name, k)
+    os_, oo, on, _ = a.stats(ta.EXCLUSIVE, tau=tau, want_z=False)
+    gs, go = got["stats"], got["outliers"]
+    for k in INT_FIELDS:
+        assert np.array_equal(gs[k], os_[k]), k
+    for k in FP_FIELDS:
+        close(gs[k], os_[k], k)
+    assert len(go["ctx"]) == on
+    assert np.array_equal(go["ctx"], oo["ctx"]) and np.array_equal(go["rank"], oo["rank"])
+    close(go["z"], oo["z"], "outlier z")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_batch_mixed_sets(seed):
+    sets = _sets_mixed(seed)
+    tau = (1, 1)
+    b = ta.Batch(context(), [_tuple(d) for d in sets], tau=tau)
+    info = b.info()
+    assert info["n_sets"] == len(sets)
+    assert info["graph_kernels"] > 0
+    for s, d in enumerate(sets):
+        _check_set(b.products(s), d, tau)
+    b.free()
+
+
+def test_batch_rerun_is_identical_and_counts_launches():
+    sets = _sets_mixed(7)
+    b = ta.Batch(context(), [_tuple(d) for d in sets], tau=(2, 1))
+    first = [b.products(s) for s in range(len(sets))]
+    n0 = context().launches()
+    b.run()
+    b.run()
+    kern = b.info()["graph_kernels"]
+    assert context().launches() - n0 >= 2 * kern
+    for s in range(len(sets)):
+        again = b.products(s)
+        for part in ("tensor", "exclusive", "inclusive", "stats", "outliers"):
+            for k, v in first[s][part].items():
+                assert np.array_equal(v, again[part][k]), (s, part, k)
+    _check_set(b.products(len(sets) - 1), sets[-1], (2, 1))
+
+
+def test_batch_many_generated_sets():
+    # Uneven generated sets (ranks, contexts, lengths) as the batched workload draws them.
+    rng = np.random.default_rng(11)
+    sets = []
+    for k in range(40):
+        R = int(rng.integers(4, 60))
+        Cn = int(np.exp(rng.uniform(np.log(100), np.log(3000))))
+        cfg = synth.preset(1, seed=100 + k, n_ranks=R, n_ctx=Cn,
+                           len_mean=float(rng.integers(2000, 12000)))
+        sets.append(synth.generate(cfg))
+    b = ta.Batch(context(), [_tuple(d) for d in sets])
+    for s in (0, 7, 19, 39):
+        _check_set(b.products(s), sets[s], (3, 1))
+
+
+def test_batch_capacity_then_views_empty():
+    sets = _sets_mixed(1)
+    b = ta.Batch(context(), [_tuple(d) for d in sets], tau=(1, 2), outlier_cap=2)
+    with pytest.raises(ta.TaError) as ei:
+        b.run()
+    assert ei.value.status == ta.CAPACITY
+    assert b.info()["n_outliers"] > 2
+    assert b.view(0).n_outliers == 0
+    # the other products stay valid
+    got = b.products(3)
+    tr = oracle.Traces(*_tuple(sets[3]))
+    a = oracle.Analysis(tr, 0, None, rows=True, incl=True)
+    assert np.array_equal(got["tensor"]["e_time"], a.tensor()["e_time"])
+
+
+def test_batch_rejects_invalid_sets():
+    good = edge.case("random_small", 1)
+    bad_ctx = dict(good)
+    bad_ctx["ctx"] = good["ctx"].copy()
+    if len(bad_ctx["ctx"]):
+        bad_ctx["ctx"][0] = len(good["parent"])
+        with pytest.raises(ta.TaError) as ei:
+            ta.Batch(context(), [_tuple(good), _tuple(bad_ctx)])
+        assert ei.value.status == ta.BAD_CTX
+    two_roots = dict(good)
+    p = np.full(3, 0xFFFFFFFF, np.uint32)
+    two_roots.update(parent=p, ctx=np.zeros_like(good["ctx"]), marker=0)
+    with pytest.raises(ta.TaError) as ei:
+        ta.Batch(context(), [_tuple(good), _tuple(two_roots)])
+    assert ei.value.status == ta.BAD_CCT and "set 1" in str(ei.value)
+    unsorted = dict(good)
+    ts = good["ts"].copy()
+    ro = good["rank_off"]
+    r = int(np.argmax(np.diff(ro.astype(np.int64)) >= 2))
+    b0 = int(ro[r])
+    ts[b0], ts[b0 + 1] = ts[b0] + 5, ts[b0]
+    unsorted["ts"] = ts
+    with pytest.raises(ta.TaError) as ei:
+        ta.Batch(context(), [_tuple(unsorted), _tuple(good)])
+    assert ei.value.status == ta.NOT_SORTED

@@ -101,6 +101,26 @@ def test_borrowed_device_input():
     check_stats(a, e, ta.EXCLUSIVE)
 
 
+def test_borrowed_unaligned_device_input_is_copied():
+    # Views starting one element into their storage are not 16-byte aligned;
+    # the library copies them instead of reading them in place.
+    import torch
+    d = edge.case("random_medium", 5)
+    tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+    a = oracle.Analysis(tr)
+    n = len(d["ts"])
+    ts = torch.zeros(n + 1, dtype=torch.int64, device="cuda")
+    cx = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
+    ts[1:] = torch.from_numpy(d["ts"].view(np.int64)).cuda()
+    cx[1:] = torch.from_numpy(d["ctx"].view(np.int32)).cuda()
+    ts, cx = ts.view(torch.uint64)[1:], cx.view(torch.uint32)[1:]
+    assert ts.data_ptr() % 16 and cx.data_ptr() % 16
+    from gpu_helpers import context
+    e = context().load(torch.from_numpy(d["rank_off"]).cuda(), ts, cx,
+                       torch.from_numpy(d["parent"]).cuda(), d["marker"], borrow=True)
+    check_products(tr, a, e)
+
+
 @pytest.mark.parametrize("preset,R", [(0, 8), (1, 64), (2, 96), (3, 1500)])
 def test_generated_configs(preset, R):
     """The structured generator at reduced rank counts (full trace lengths)."""
