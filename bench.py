@@ -64,6 +64,56 @@ def make_workload(preset: int, seed: int = 1, pinned: bool = True, ranks: int = 
                 marker=cfg.marker_ctx, truth=truth, topo=topo)
 
 
+BATCHED = ("batched: 256 independent trace sets, ranks per set lognormal (median 362, sigma "
+           "1.04) in 16..8192, C log-uniform in 100..10,000, trace lengths lognormal (mean 30k, "
+           "sigma 1.0), I=50, jitter 5%, 1% of ranks 1.2-2x on random iterations")
+SET_ALIGN = 32  # samples; every set of the input arena starts 16-byte aligned
+
+
+def batch_shapes(n_sets: int, seed: int):
+    """Per-set rank and context counts of the batched workload."""
+    rng = np.random.default_rng(seed)
+    R = np.clip(np.rint(np.exp(np.log(362.0) + 1.04 * rng.standard_normal(n_sets))), 16, 8192)
+    Cn = np.rint(np.exp(rng.uniform(np.log(100.0), np.log(10000.0), n_sets)))
+    return R.astype(np.int64), Cn.astype(np.int64)
+
+
+def make_batch_workload(n_sets: int, seed: int, device: str, scale: float = 1.0):
+    """Generate every set into one device arena (aligned per set) through a
+    pinned staging buffer; returns per-set host metadata and device views."""
+    import torch
+    from paper_2605_03561_b300 import synth
+    R, Cn = batch_shapes(n_sets, seed)
+    sets, starts, total = [], [], 0
+    for k in range(n_sets):
+        cfg = synth.preset(2, seed=seed * 1000 + k, n_ranks=int(max(16, R[k] * scale)),
+                           n_ctx=int(Cn[k]), len_mean=30000.0, len_sigma=1.0,
+                           n_segments=int(min(64, Cn[k] - 2)))
+        rank_off, parent, info = synth.plan(cfg)
+        sets.append(dict(cfg=cfg, rank_off=rank_off, parent=parent, marker=cfg.marker_ctx,
+                         N=int(rank_off[-1])))
+        starts.append(total)
+        total += (int(rank_off[-1]) + SET_ALIGN - 1) // SET_ALIGN * SET_ALIGN
+    t0 = time.time()
+    d_ts = torch.empty(max(total, 1), dtype=torch.uint64, device=device)
+    d_cx = torch.empty(max(total, 1), dtype=torch.uint32, device=device)
+    big = max(x["N"] for x in sets)
+    h_ts = torch.empty(max(big, 1), dtype=torch.uint64, pin_memory=True)
+    h_cx = torch.empty(max(big, 1), dtype=torch.uint32, pin_memory=True)
+    for x, a in zip(sets, starts):
+        n = x["N"]
+        synth.fill(x["cfg"], x["rank_off"], 0, x["cfg"].n_ranks, h_ts.data_ptr(), h_cx.data_ptr(), 0)
+        d_ts[a:a + n].copy_(h_ts[:n])
+        d_cx[a:a + n].copy_(h_cx[:n])
+        torch.cuda.synchronize()
+        x["ts"], x["ctx"] = d_ts[a:a + n], d_cx[a:a + n]
+        x["d_rank_off"] = torch.from_numpy(x["rank_off"]).to(device)
+        x["d_parent"] = torch.from_numpy(x["parent"]).to(device)
+    log(f"generated {len(sets)} sets, {sum(x['N'] for x in sets)} records in "
+        f"{time.time() - t0:.1f} s")
+    return sets, (d_ts, d_cx)
+
+
 def analysis_args(w):
     segs = np.unique(w["truth"]["segment_ctx"]).astype(np.uint32)
     comm = w["truth"]["segment_ctx"][w["truth"]["comm_segment"].astype(bool)]
@@ -151,13 +201,13 @@ class ClockSampler:
     def __init__(self, device=0):
         self.device = device
         self.proc = None
-        self.lines = []
+        self.lines = []  # (arrival time, csv line)
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
                 stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
@@ -166,9 +216,19 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self):
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has produced its first sample."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.02)
+
+    def mark(self):
+        return time.perf_counter()
+
+    def stop(self, t0=None, t1=None):
+        """Summary of the samples taken between t0 and t1 (perf_counter)."""
         if self.proc:
             self.proc.terminate()
             try:
@@ -177,7 +237,9 @@ class ClockSampler:
                 self.proc.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for ts, line in self.lines:
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1 + 0.25):
+                continue
             p = [x.strip() for x in line.split(",")]
             if len(p) < 9:
                 continue
@@ -246,6 +308,83 @@ def committed_traffic(preset):
     return d.get("per_record_bytes")
 
 
+# ------------------------------------------------------ batched vs plain --
+def run_batched(args, ctx, local):
+    """The batched form (one graph replay over every set) against plain
+    per-experiment calls on the same device-resident sets, same products:
+    tensor, exclusive, inclusive, statistics of the exclusive metric over all
+    ranks and contexts (tau = 3) with outliers."""
+    import torch
+    import paper_2605_03561_b300 as ta
+    dev = f"cuda:{local}"
+    sets, arena = make_batch_workload(args.batch_sets, 7, dev, args.batch_scale)
+    N = sum(x["N"] for x in sets)
+    R = sum(len(x["rank_off"]) - 1 for x in sets)
+    stream = ctx.stream
+    cmax = max(len(x["parent"]) for x in sets)
+    st = torch.empty(cmax * C.sizeof(ta.CtxStats), dtype=torch.uint8, device=dev)
+    cap = 1 << 20
+    ol = torch.empty(cap * C.sizeof(ta.Outlier), dtype=torch.uint8, device=dev)
+
+    def plain_step():
+        launches = 0
+        for x in sets:
+            e = ctx.load(x["d_rank_off"], x["ts"], x["ctx"], x["d_parent"], x["marker"],
+                         borrow=True)
+            a = ta.StatsArgs()
+            a.metric, a.mem_kind, a.tau_num, a.tau_den = ta.EXCLUSIVE, ta.MEM_DEVICE, 3, 1
+            o = ta.StatsOut()
+            o.stats, o.outliers, o.outlier_cap = st.data_ptr(), ol.data_ptr(), cap
+            ta._check(ta.lib().ta_context_stats(e.h, C.byref(a), C.byref(o)))
+            e.free()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        clocks = ClockSampler(local)
+        clocks.start()
+        clocks.wait_first()
+        torch.cuda.synchronize()
+        l0 = ctx.launches()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tc0 = clocks.mark()
+        ev0.record(stream)
+        for _ in range(steps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        tc1 = clocks.mark()
+        return (ev0.elapsed_time(ev1) / steps, (ctx.launches() - l0) / steps,
+                clocks.stop(tc0, tc1))
+
+    steps = max(1, min(args.steps, 3))
+    plain_ms, plain_l, plain_clk = timed(plain_step, steps, 1)
+    t0 = time.perf_counter()
+    b = ta.Batch(ctx, [(x["d_rank_off"], x["ts"], x["ctx"], x["d_parent"], x["marker"])
+                       for x in sets], tau=(3, 1), outlier_cap=cap)
+    plan_s = time.perf_counter() - t0
+    info = b.info()
+    batch_ms, batch_l, batch_clk = timed(b.run, args.steps, max(3, args.warmup))
+    alg = 12 * N + 16 * info["tensor_nnz"] + 8 * info["n_rows"] + 8 * (R + len(sets))
+    out = {"workload": BATCHED + (f" (rank scale {args.batch_scale})" if args.batch_scale != 1 else ""),
+           "sets": len(sets), "records": N, "ranks": R, "tensor_entries": info["tensor_nnz"],
+           "outliers": info["n_outliers"],
+           "plain": {"value": N / (plain_ms / 1e3), "unit": "records/s", "ms_per_step": plain_ms,
+                     "gpu_launches_per_step": plain_l, "steps": steps, "clocks": plain_clk,
+                     "hbm_gbs_tensor_floor": alg / (plain_ms / 1e3) / 1e9},
+           "batched": {"value": N / (batch_ms / 1e3), "unit": "records/s",
+                       "ms_per_step": batch_ms, "gpu_launches_per_step": batch_l,
+                       "graph_kernels": info["graph_kernels"], "steps": args.steps,
+                       "clocks": batch_clk,
+                       "plan_s": plan_s, "hbm_gbs_tensor_floor": alg / (batch_ms / 1e3) / 1e9},
+           "speedup_batched_over_plain": plain_ms / batch_ms,
+           "device_bytes_batch": info["device_bytes"]}
+    b.free()
+    del arena, sets
+    torch.cuda.empty_cache()
+    return out
+
+
 # --------------------------------------------------------------------- arms --
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -312,21 +451,24 @@ def run_gpu(args):
     launches0 = ctx.launches()
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.wait_first()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tc0 = clocks.mark()
     ev0.record(stream)
     for _ in range(args.steps):
         info, n_out = step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    tc1 = clocks.mark()
     ms = ev0.elapsed_time(ev1)
     if world > 1:
         t = torch.tensor([ms], dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t[0])
-    clk = clocks.stop()
+    clk = clocks.stop(tc0, tc1)
     prof = ctx.profile(reset=True)
     launches = ctx.launches() - launches0
     ms_step = ms / args.steps
@@ -381,6 +523,14 @@ def run_gpu(args):
                "sample": f"ranks [0, {k}) = {n} records of the same workload, whole path "
                          f"(analysis, stats over all contexts, rack rollup, speedup); {s:.1f} s"}
 
+    batched = None
+    if not args.no_batched:
+        for k in ("ts", "ctx"):
+            w[k] = None
+        d_ro = d_par = d_ts = d_cx = calls = None
+        torch.cuda.empty_cache()
+        batched = run_batched(args, ctx, local)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -401,6 +551,7 @@ def run_gpu(args):
                                       ("validate_ms", "tensor_count_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "batched_vs_plain": batched,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -410,7 +561,7 @@ def run_gpu(args):
 def main():
     p = argparse.ArgumentParser(description=__doc__)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--config", type=int, default=3, choices=[1, 2, 3])
@@ -420,6 +571,10 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-records", type=float, default=1.5e8)
     p.add_argument("--ref-records", type=float, default=5e6)
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--batch-sets", type=int, default=256)
+    p.add_argument("--batch-scale", type=float, default=1.0,
+                   help="scale the rank count of every batched set (smaller runs)")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)

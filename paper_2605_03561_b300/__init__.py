@@ -529,17 +529,26 @@ class Batch:
     whole analysis is one captured CUDA graph, replayed by run()."""
 
     def __init__(self, ctx: Context, sets, tau=(3, 1), outlier_cap=1 << 20):
-        """sets: sequence of (rank_off, ts, ctx, parent, marker) host arrays."""
+        """sets: sequence of (rank_off, ts, ctx, parent, marker), either all
+        numpy arrays (host) or all torch CUDA tensors (device)."""
         self.ctx = ctx
         keep, descs = [], (TraceDesc * len(sets))()
         for d, (rank_off, ts, cx, parent, marker) in zip(descs, sets):
-            rank_off, ts, cx = _np(rank_off, np.uint64), _np(ts, np.uint64), _np(cx, np.uint32)
-            parent = _np(parent, np.uint32)
+            dev = _is_dev(ts) or _is_dev(rank_off)
+            if dev:
+                torch = _torch()
+                rank_off, ts = rank_off.contiguous(), ts.contiguous()
+                cx, parent = cx.contiguous(), parent.contiguous()
+                assert rank_off.dtype == torch.uint64 and ts.dtype == torch.uint64
+                assert cx.dtype == torch.uint32 and parent.dtype == torch.uint32
+            else:
+                rank_off, ts = _np(rank_off, np.uint64), _np(ts, np.uint64)
+                cx, parent = _np(cx, np.uint32), _np(parent, np.uint32)
             keep.append((rank_off, ts, cx, parent))
             d.n_ranks = rank_off.shape[0] - 1
             d.n_ctx = parent.shape[0]
             d.marker_ctx = int(marker)
-            d.mem_kind = MEM_HOST
+            d.mem_kind = MEM_DEVICE if dev else MEM_HOST
             d.n_records = ts.shape[0]
             d.rank_off, d.ts, d.ctx, d.parent = _ptr(rank_off), _ptr(ts), _ptr(cx), _ptr(parent)
         a = BatchArgs()
