@@ -103,6 +103,11 @@ def lib():
         L.or_speedup.restype = C.c_int
         L.or_speedup.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_void_p, C.c_uint32,
                                  C.c_uint64, C.c_void_p, C.POINTER(SpeedupTotal)]
+        L.or_slice.restype = C.c_int
+        L.or_slice.argtypes = [C.c_void_p] + [C.c_uint32] * 5 + [C.c_void_p]
+        L.or_topk.restype = C.c_int
+        L.or_topk.argtypes = [C.c_void_p, C.c_int, C.c_uint32, C.c_uint32, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32)]
         L.or_savings_from_averages.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32,
                                                C.c_double, C.c_void_p, C.c_void_p,
                                                C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -241,6 +246,26 @@ class Analysis:
             raise OracleError(s)
         o["flagged_racks"] = o["flagged_racks"][: int(nf[0])]
         return o
+
+    def slice(self, ctx, r0, r1, i0, i1):
+        """Dense [r1 - r0, i1 - i0] time of ctx per (rank, iteration)."""
+        out = np.zeros((r1 - r0) * (i1 - i0), np.uint64)
+        s = lib().or_slice(self.h, ctx, r0, r1, i0, i1, _p(out))
+        if s != OK:
+            raise OracleError(s)
+        return out.reshape(r1 - r0, i1 - i0)
+
+    def topk(self, ctx, k, metric=EXCL):
+        """(ranks, x, z) of the k largest values of ctx, ties to lower rank."""
+        n = self.r1 - self.r0
+        rk = np.zeros(max(min(k, n), 1), np.uint32)
+        x = np.zeros(max(min(k, n), 1), np.uint64)
+        z = np.zeros(max(min(k, n), 1), np.float64)
+        m = C.c_uint32(0)
+        s = lib().or_topk(self.h, metric, ctx, k, _p(rk), _p(x), _p(z), C.byref(m))
+        if s != OK:
+            raise OracleError(s)
+        return rk[: m.value], x[: m.value], z[: m.value]
 
     def speedup(self, ctxs, ranks=None, app_time_ns=0):
         ctxs, ranks = _u32(ctxs), _u32(ranks)

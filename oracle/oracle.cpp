@@ -698,6 +698,61 @@ int or_speedup(void* hp, const uint32_t* ctxs, uint32_t n_ctxs, const uint32_t* 
   return OR_OK;
 }
 
+// Q2, a slice of the tri-dimensional model (Section V; slicing by fixing a
+// context, Section VI): out[(r - r0) * (i1 - i0) + (i - i0)] is the time of
+// context c in iteration i of rank r (iteration rows only, the prologue is
+// not an iteration), 0 where the context is absent or the rank has fewer
+// iterations.  Ranks [r0, r1) must lie in the handle.
+int or_slice(void* hp, uint32_t c, uint32_t r0, uint32_t r1, uint32_t i0, uint32_t i1,
+             uint64_t* out) {
+  Handle* h = (Handle*)hp;
+  if (c >= h->in.C || r0 > r1 || i0 > i1 || r0 < h->r0 || r1 > h->r1) return OR_INVALID;
+  const uint64_t w = i1 - i0;
+  for (uint32_t r = r0; r < r1; ++r)
+    for (uint32_t i = i0; i < i1; ++i)
+      out[(uint64_t)(r - r0) * w + (i - i0)] = row_time(h->ranks[r - h->r0], (size_t)i + 1, c);
+  return OR_OK;
+}
+
+// Q3, the k slowest ranks of context c over every rank of the handle (the
+// ranks a per-context view ranks first, Section VI-B): ranks ordered by the
+// metric's value x descending, equal values by rank ascending; the first
+// min(k, n) are written with x and their z-score (n x - S1) / (n std) over all
+// n ranks (0 when n < 2 or every value is equal), std with ddof 1 as in the
+// statistics above.  Absent ranks take part with x = 0.
+int or_topk(void* hp, int metric, uint32_t c, uint32_t k, uint32_t* out_rank, uint64_t* out_x,
+            double* out_z, uint32_t* n_out) {
+  Handle* h = (Handle*)hp;
+  if (c >= h->in.C) return OR_INVALID;
+  const uint64_t n = h->r1 - h->r0;
+  std::vector<std::pair<uint64_t, uint32_t>> xs;
+  uint64_t S1 = 0;
+  u128 S2 = 0;
+  for (uint32_t r = h->r0; r < h->r1; ++r) {
+    uint64_t x, cnt;
+    lookup(metric_of(h->ranks[r - h->r0], metric), c, x, cnt);
+    xs.push_back({x, r});
+    S1 += x;
+    S2 += (u128)x * x;
+  }
+  const u128 M = (u128)n * S2 - (u128)S1 * S1;
+  const double sd =
+      (n < 2) ? 0.0 : std::sqrt(u128_to_double(M) / u128_to_double((u128)n * (n - 1)));
+  std::sort(xs.begin(), xs.end(), [](const std::pair<uint64_t, uint32_t>& a,
+                                     const std::pair<uint64_t, uint32_t>& b) {
+    return a.first != b.first ? a.first > b.first : a.second < b.second;
+  });
+  const uint32_t m = (uint32_t)std::min<uint64_t>(k, n);
+  for (uint32_t j = 0; j < m; ++j) {
+    const i128 D = (i128)((u128)n * xs[j].first) - (i128)S1;
+    out_rank[j] = xs[j].second;
+    out_x[j] = xs[j].first;
+    out_z[j] = (n < 2 || M == 0) ? 0.0 : i128_to_double(D) / (u128_to_double(n) * sd);
+  }
+  *n_out = m;
+  return OR_OK;
+}
+
 // Finalize-only entry for the Table V pin: the paper prints per-kernel
 // average mean and average max over ranks; savings per iteration is their
 // difference, the kernel's total is that times the iteration count, and the
