@@ -463,6 +463,112 @@ ta_status ta_batch_free(ta_batch* b);
 ta_status ta_batch_get_info(const ta_batch* b, ta_batch_info* info);
 ta_status ta_batch_get_set(const ta_batch* b, uint32_t set, ta_batch_set_view* v);
 
+/* ------------------------------------------------------ serving form ---- */
+
+/* An interactive query server over resident experiments (the serving form).
+ * Experiments loaded with ta_load_traces are registered with the server and
+ * stay on the device (their derived products only).  Queries are submitted
+ * from any host thread and answered asynchronously.  A worker thread admits
+ * pending queries in arrival order as long as an in-flight slot and room in
+ * the result, scratch and input-staging arenas are free (continuous
+ * batching: queries that arrive while earlier batches run are packed into the
+ * next batch); each batch is one descriptor upload, three kernel launches
+ * over all of its queries (cut into per-chunk work items), and one download
+ * of its results, and up to n_streams batches overlap on the device.
+ * max_batch = 1 with n_streams = 1 runs one query per launch, one at a time
+ * (the plain form the batching is measured against).
+ *
+ * Query kinds (slices and per-context views of the tri-dimensional model,
+ * Sections V and VI; statistics as ta_context_stats, rollup as
+ * ta_topology_rollup):
+ *   TA_Q_STATS   statistics of context ctx over a rank subset (sorted, unique,
+ *                host array, copied at submit), threshold tau:
+ *                payload ta_q_stats = the ta_ctx_stats ta_context_stats gives
+ *                for (ranks, ctxs = {ctx}) and the number of its outliers.
+ *   TA_Q_SLICE   time of ctx in every (rank, iteration) cell of
+ *                [r0, r1) x [i0, i1) (iteration rows only; 0 where absent or
+ *                past the rank's last iteration): payload uint64 cells,
+ *                row-major by rank.
+ *   TA_Q_TOPK    the k ranks (1 <= k <= 1024) with the largest value of ctx
+ *                over all ranks, equal values by lower rank, with x and the
+ *                z-score over all ranks: payload uint64 count then
+ *                ta_q_topk_entry[count].
+ *   TA_Q_RACKS   rack rollup of ctx over all ranks (outlier rule tau,
+ *                min_ranks) on the experiment's registered topology: payload
+ *                ta_q_racks header, uint64 rack_sum[n_racks],
+ *                uint32 rack_flagged[n_racks], uint32 rack_nodes[n_racks],
+ *                uint32 flagged_racks[n_flagged_racks].
+ * metric selects the exclusive or inclusive value (the inclusive rollup must
+ * have been built).  Invalid queries are refused by ta_serve_submit
+ * (TA_ERR_INVALID_ARG); a query larger than an arena returns
+ * TA_ERR_CAPACITY. */
+typedef struct ta_server ta_server;
+#define TA_Q_STATS 1u
+#define TA_Q_SLICE 2u
+#define TA_Q_TOPK 3u
+#define TA_Q_RACKS 4u
+typedef struct ta_serve_config {
+  uint32_t max_batch;     /* queries per batch (0: 1024)                    */
+  uint32_t n_streams;     /* batches in flight (0: 3)                       */
+  uint32_t max_inflight;  /* admitted, unreleased queries (0: 8192)         */
+  uint32_t reserved;
+  uint64_t result_bytes;  /* device result arena + pinned mirror (0: 1 GiB) */
+  uint64_t scratch_bytes; /* device scratch arena (0: 256 MiB)              */
+  uint64_t staging_bytes; /* per-stream input staging (0: 32 MiB)           */
+  uint64_t device_budget; /* resident experiment bytes (0: no limit)        */
+} ta_serve_config;
+typedef struct ta_query {
+  uint32_t kind, experiment, metric, ctx;
+  uint32_t tau_num, tau_den; /* STATS, RACKS        */
+  uint32_t k;                /* TOPK               */
+  uint32_t min_ranks;        /* RACKS              */
+  uint32_t r0, r1, i0, i1;   /* SLICE              */
+  const uint32_t* ranks;     /* STATS (host)        */
+  uint32_t n_ranks;          /* STATS              */
+  uint32_t reserved;
+} ta_query;
+typedef struct ta_q_stats {
+  ta_ctx_stats stats;
+  uint64_t n_outliers;
+} ta_q_stats;
+typedef struct ta_q_topk_entry {
+  uint32_t rank, reserved;
+  uint64_t x;
+  double z;
+} ta_q_topk_entry;
+typedef struct ta_q_racks {
+  uint32_t n_racks, n_flagged_racks;
+} ta_q_racks;
+typedef struct ta_query_result {
+  uint32_t status; /* ta_status of the query                            */
+  uint32_t kind;
+  uint64_t t_submit_ns, t_admit_ns, t_launch_ns, t_done_ns; /* steady clock */
+  uint64_t bytes;   /* payload size                                      */
+  const void* data; /* payload in the server's pinned host mirror, valid
+                       until ta_serve_release of the ticket               */
+} ta_query_result;
+ta_status ta_serve_open(ta_ctx* ctx, const ta_serve_config* cfg, ta_server** out);
+/* Waits for the batches on the device; pending queries are dropped. */
+ta_status ta_serve_close(ta_server* s);
+/* Registers a loaded experiment (which must outlive the server).  Admission
+ * by memory: TA_ERR_OOM if its device bytes exceed what is left of
+ * device_budget.  topo (host arrays, copied; may be NULL) enables rack
+ * queries. */
+ta_status ta_serve_add_experiment(ta_server* s, ta_experiment* e, const ta_topology* topo,
+                                  uint32_t* experiment_id);
+ta_status ta_serve_submit(ta_server* s, const ta_query* q, uint64_t* ticket);
+/* Fills r when the query is done (waiting up to wait_ns; < 0 = forever);
+ * TA_ERR_STATE while it is not. */
+ta_status ta_serve_poll(ta_server* s, uint64_t ticket, int64_t wait_ns, ta_query_result* r);
+/* Frees a finished query's result space and slot. */
+ta_status ta_serve_release(ta_server* s, uint64_t ticket);
+/* Open-loop replay: submits qs[i] at arrival_ns[i] after the start (host
+ * steady clock) while a second thread collects results in order, writes
+ * latency_ns[i] = done - arrival (queueing included) and releases them;
+ * *wall_ns = start to last completion.  Returns the first failing status. */
+ta_status ta_serve_replay(ta_server* s, const ta_query* qs, const uint64_t* arrival_ns,
+                          uint64_t n, uint64_t* latency_ns, uint64_t* wall_ns);
+
 #ifdef __cplusplus
 }
 #endif

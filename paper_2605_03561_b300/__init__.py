@@ -142,12 +142,44 @@ class BatchSetView(C.Structure):
                 ("n_outliers", u64)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("max_batch", u32), ("n_streams", u32), ("max_inflight", u32), ("reserved", u32),
+                ("result_bytes", u64), ("scratch_bytes", u64), ("staging_bytes", u64),
+                ("device_budget", u64)]
+
+
+class Query(C.Structure):
+    _fields_ = [("kind", u32), ("experiment", u32), ("metric", u32), ("ctx", u32),
+                ("tau_num", u32), ("tau_den", u32), ("k", u32), ("min_ranks", u32), ("r0", u32),
+                ("r1", u32), ("i0", u32), ("i1", u32), ("ranks", P), ("n_ranks", u32),
+                ("reserved", u32)]
+
+
+class QueryResult(C.Structure):
+    _fields_ = [("status", u32), ("kind", u32), ("t_submit_ns", u64), ("t_admit_ns", u64),
+                ("t_launch_ns", u64), ("t_done_ns", u64), ("bytes", u64), ("data", P)]
+
+
 class SpeedupOut(C.Structure):
     _fields_ = [("per_ctx", P), ("total", P)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+class QStats(C.Structure):
+    _fields_ = [("stats", CtxStats), ("n_outliers", u64)]
+
+
+class QTopkEntry(C.Structure):
+    _fields_ = [("rank", u32), ("reserved", u32), ("x", u64), ("z", C.c_double)]
+
+
+class QRacks(C.Structure):
+    _fields_ = [("n_racks", u32), ("n_flagged_racks", u32)]
+
+
+Q_STATS, Q_SLICE, Q_TOPK, Q_RACKS = 1, 2, 3, 4
 
 _SIGS = {
     "ta_create": (C.c_int, [C.c_int, P, C.POINTER(P)]),
@@ -178,6 +210,13 @@ _SIGS = {
     "ta_batch_free": (C.c_int, [P]),
     "ta_batch_get_info": (C.c_int, [P, C.POINTER(BatchInfo)]),
     "ta_batch_get_set": (C.c_int, [P, u32, C.POINTER(BatchSetView)]),
+    "ta_serve_open": (C.c_int, [P, C.POINTER(ServeConfig), C.POINTER(P)]),
+    "ta_serve_close": (C.c_int, [P]),
+    "ta_serve_add_experiment": (C.c_int, [P, P, C.POINTER(Topology), C.POINTER(u32)]),
+    "ta_serve_submit": (C.c_int, [P, C.POINTER(Query), C.POINTER(u64)]),
+    "ta_serve_poll": (C.c_int, [P, u64, C.c_int64, C.POINTER(QueryResult)]),
+    "ta_serve_release": (C.c_int, [P, u64]),
+    "ta_serve_replay": (C.c_int, [P, P, P, u64, P, C.POINTER(u64)]),
 }
 
 _lib = None
@@ -614,3 +653,128 @@ class Batch:
                                rank=np.array([x.rank for x in ol[:m]], np.uint32),
                                z=np.array([x.z for x in ol[:m]], np.float64))
         return out
+
+
+def make_query(kind, experiment=0, ctx=0, metric=EXCLUSIVE, ranks=None, tau=(3, 1), k=10,
+               min_ranks=1, r0=0, r1=0, i0=0, i1=0):
+    """A ta_query; keeps the rank subset alive on the returned object."""
+    q = Query()
+    q.kind, q.experiment, q.metric, q.ctx = kind, experiment, metric, ctx
+    q.tau_num, q.tau_den, q.k, q.min_ranks = tau[0], tau[1], k, min_ranks
+    q.r0, q.r1, q.i0, q.i1 = r0, r1, i0, i1
+    if ranks is not None:
+        arr = _np(ranks, np.uint32)
+        q._ranks = arr
+        q.ranks, q.n_ranks = arr.ctypes.data, len(arr)
+    return q
+
+
+def parse_payload(kind, data, nbytes):
+    """Decode a query payload (bytes) into numpy / dict form."""
+    if kind == Q_STATS:
+        r = QStats.from_buffer_copy(data[: C.sizeof(QStats)])
+        d = {f: getattr(r.stats, f) for f, _ in CtxStats._fields_ if f != "reserved"}
+        d["n_outliers"] = r.n_outliers
+        return d
+    if kind == Q_SLICE:
+        return np.frombuffer(data, np.uint64).copy()
+    if kind == Q_TOPK:
+        n = int(np.frombuffer(data[:8], np.uint64)[0])
+        ent = (QTopkEntry * max(n, 1)).from_buffer_copy(data[8: 8 + max(n, 1) * C.sizeof(QTopkEntry)]
+                                                       if n else bytes(C.sizeof(QTopkEntry)))
+        return dict(rank=np.array([e.rank for e in ent[:n]], np.uint32),
+                    x=np.array([e.x for e in ent[:n]], np.uint64),
+                    z=np.array([e.z for e in ent[:n]], np.float64))
+    h = QRacks.from_buffer_copy(data[:8])
+    nr, nf = h.n_racks, h.n_flagged_racks
+    o = 8
+    rack_sum = np.frombuffer(data[o: o + 8 * nr], np.uint64).copy()
+    o += 8 * nr
+    rack_flagged = np.frombuffer(data[o: o + 4 * nr], np.uint32).copy()
+    o += 4 * nr
+    rack_nodes = np.frombuffer(data[o: o + 4 * nr], np.uint32).copy()
+    o += 4 * nr
+    flagged = np.frombuffer(data[o: o + 4 * nf], np.uint32).copy()
+    return dict(rack_sum=rack_sum, rack_flagged=rack_flagged, rack_nodes=rack_nodes,
+                flagged_racks=flagged)
+
+
+class Server:
+    """Query server over resident experiments (ta_serve_*)."""
+
+    def __init__(self, ctx: Context, max_batch=0, n_streams=0, max_inflight=0, result_bytes=0,
+                 scratch_bytes=0, staging_bytes=0, device_budget=0):
+        self.ctx = ctx
+        c = ServeConfig()
+        c.max_batch, c.n_streams, c.max_inflight = max_batch, n_streams, max_inflight
+        c.result_bytes, c.scratch_bytes, c.staging_bytes = result_bytes, scratch_bytes, staging_bytes
+        c.device_budget = device_budget
+        h = P()
+        _check(lib().ta_serve_open(ctx.h, C.byref(c), C.byref(h)))
+        self.h = h
+        self._exps = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ta_serve_close(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, e: "Experiment", topo=None) -> int:
+        t = None
+        if topo is not None:
+            t = Topology()
+            keep = [_np(topo["node_of_rank"], np.uint32), _np(topo["rack_of_node"], np.uint32),
+                    _np(topo["chassis_of_node"], np.uint32)]
+            t.n_nodes, t.n_chassis, t.n_racks = len(keep[1]), int(topo["n_chassis"]), int(topo["n_racks"])
+            t.mem_kind = MEM_HOST
+            t.node_of_rank, t.rack_of_node, t.chassis_of_node = (a.ctypes.data for a in keep)
+        i = u32(0)
+        _check(lib().ta_serve_add_experiment(self.h, e.h, C.byref(t) if t is not None else None,
+                                             C.byref(i)))
+        self._exps.append(e)
+        return int(i.value)
+
+    def submit(self, q: Query) -> int:
+        t = u64(0)
+        _check(lib().ta_serve_submit(self.h, C.byref(q), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ns: int = -1):
+        """(payload, timings) when done, None while pending."""
+        r = QueryResult()
+        s = lib().ta_serve_poll(self.h, ticket, wait_ns, C.byref(r))
+        if s == STATE:
+            return None
+        _check(s)
+        if r.status != OK:
+            raise TaError(r.status, "query failed on the device")
+        data = C.string_at(r.data, r.bytes)
+        times = dict(submit=r.t_submit_ns, admit=r.t_admit_ns, launch=r.t_launch_ns,
+                     done=r.t_done_ns)
+        return parse_payload(r.kind, data, r.bytes), times
+
+    def release(self, ticket: int):
+        _check(lib().ta_serve_release(self.h, ticket))
+
+    def query(self, q: Query):
+        t = self.submit(q)
+        out, _ = self.poll(t, -1)
+        self.release(t)
+        return out
+
+    def replay(self, queries, arrival_ns):
+        """Open-loop replay; returns (latency_ns array, wall_ns)."""
+        n = len(queries)
+        arr = (Query * max(n, 1))(*queries)
+        arrival = _np(arrival_ns, np.uint64)
+        lat = np.zeros(max(n, 1), np.uint64)
+        wall = u64(0)
+        _check(lib().ta_serve_replay(self.h, C.cast(arr, P), arrival.ctypes.data, n,
+                                     lat.ctypes.data, C.byref(wall)))
+        return lat[:n], int(wall.value)

@@ -13,7 +13,9 @@ struct Launch {
   cudaStream_t stream;
   int num_sms;
   unsigned long long* launches;  // counter of kernel launches
-  void count(int k = 1) const { *launches += (unsigned long long)k; }
+  void count(int k = 1) const {
+    __atomic_fetch_add(launches, (unsigned long long)k, __ATOMIC_RELAXED);
+  }
 };
 
 // Several independent trace sets analysed together: sets are concatenated
