@@ -385,6 +385,136 @@ def run_batched(args, ctx, local):
     return out
 
 
+# ------------------------------------------------------------------ serving --
+SERVING = ("serving: 8 resident experiments, R uniform in 1k..50k, C=5000 (depth<=24), I=50, "
+           "jitter 5%, 1% of ranks 1.2-2x (trace lengths mean 20k, sigma 0.5: the resident "
+           "products, R x 51 rows x ~64 contexts, do not depend on trace length), Poisson stream "
+           "of queries: 40% context stats over a rank subset (size log-uniform 16..R), 30% "
+           "rank x iteration slices (area log-uniform up to 1e6 cells), 20% top-k (k in 1, 10, "
+           "100), 10% rack rollups")
+
+
+def make_serving(args, ctx, device):
+    """Load the serving experiments one by one (raw traces generated into
+    device memory in chunks, ingested, then dropped: only products stay)."""
+    import torch
+    from paper_2605_03561_b300 import synth
+    rng = np.random.default_rng(17)
+    exps = []
+    t0 = time.time()
+    for k in range(args.serve_exps):
+        R = int(rng.integers(1000, 50001) * args.serve_scale)
+        cfg = synth.preset(2, seed=500 + k, n_ranks=max(R, 16), len_mean=20000.0)
+        rank_off, parent, info = synth.plan(cfg)
+        N = int(rank_off[-1])
+        d_ts = torch.empty(N, dtype=torch.uint64, device=device)
+        d_cx = torch.empty(N, dtype=torch.uint32, device=device)
+        step = max(1, cfg.n_ranks // 16)
+        big = int(max(rank_off[min(r + step, cfg.n_ranks)] - rank_off[r]
+                      for r in range(0, cfg.n_ranks, step)))
+        h_ts = torch.empty(big, dtype=torch.uint64, pin_memory=True)
+        h_cx = torch.empty(big, dtype=torch.uint32, pin_memory=True)
+        for r0 in range(0, cfg.n_ranks, step):
+            r1 = min(r0 + step, cfg.n_ranks)
+            a, b = int(rank_off[r0]), int(rank_off[r1])
+            sub = (rank_off[r0: r1 + 1] - rank_off[r0]).astype(np.uint64)
+            synth.fill(cfg, rank_off, r0, r1, h_ts.data_ptr(), h_cx.data_ptr(), 0)
+            d_ts[a:b].copy_(h_ts[: b - a])
+            d_cx[a:b].copy_(h_cx[: b - a])
+            torch.cuda.synchronize()
+        e = ctx.load(torch.from_numpy(rank_off).to(device), d_ts, d_cx,
+                     torch.from_numpy(parent).to(device), cfg.marker_ctx)
+        del d_ts, d_cx
+        torch.cuda.empty_cache()
+        topo = synth.topology(cfg, info)
+        truth = synth.truth(cfg, info)
+        exps.append(dict(e=e, R=cfg.n_ranks, C=cfg.n_ctx, N=N, topo=topo,
+                         ctxs=np.unique(truth["segment_ctx"]).astype(np.uint32),
+                         iters=cfg.n_iter))
+    log(f"serving: {len(exps)} experiments, {sum(x['R'] for x in exps)} ranks, "
+        f"{sum(x['N'] for x in exps)} records ingested in {time.time() - t0:.1f} s")
+    return exps
+
+
+def serving_queries(ta, exps, n, seed):
+    rng = np.random.default_rng(seed)
+    qs = []
+    kinds = rng.choice([1, 2, 3, 4], size=n, p=[0.4, 0.3, 0.2, 0.1])
+    for kind in kinds:
+        x = int(rng.integers(0, len(exps)))
+        E = exps[x]
+        R = E["R"]
+        c = int(rng.choice(E["ctxs"]))
+        if kind == 1:
+            m = int(np.exp(rng.uniform(np.log(16), np.log(R))))
+            ranks = np.unique(rng.integers(0, R, size=m)).astype(np.uint32)  # ~m distinct
+            qs.append(ta.make_query(1, x, c, ranks=ranks))
+        elif kind == 2:
+            area = int(np.exp(rng.uniform(0, np.log(1e6))))
+            w = int(rng.integers(1, E["iters"] + 1))
+            h = max(1, min(R, area // w))
+            r0 = int(rng.integers(0, R - h + 1))
+            i0 = int(rng.integers(0, E["iters"] - w + 1))
+            qs.append(ta.make_query(2, x, c, r0=r0, r1=r0 + h, i0=i0, i1=i0 + w))
+        elif kind == 3:
+            qs.append(ta.make_query(3, x, c, k=int(rng.choice([1, 10, 100]))))
+        else:
+            qs.append(ta.make_query(4, x, c, tau=(2, 1), min_ranks=1))
+    return qs
+
+
+def run_serving(args, ctx, local):
+    """Plain (one query per launch, one at a time) against continuous
+    batching on the same open-loop Poisson stream, at the arrival rate where
+    the plain path is 50% busy."""
+    import paper_2605_03561_b300 as ta
+    dev = f"cuda:{local}"
+    exps = make_serving(args, ctx, dev)
+    queries = serving_queries(ta, exps, args.serve_queries, 23)
+
+    def server(plain):
+        s = ta.Server(ctx, max_batch=1 if plain else 256, n_streams=1 if plain else 3,
+                      result_bytes=2 << 30, scratch_bytes=1 << 30)
+        for E in exps:
+            s.add(E["e"], E["topo"])
+        return s
+
+    # plain service time: back-to-back stream (every query queued at t = 0)
+    probe = queries[: min(len(queries), 3000)]
+    sp = server(True)
+    sp.replay(probe[:200], np.zeros(200, np.uint64))  # warm-up
+    _, wall = sp.replay(probe, np.zeros(len(probe), np.uint64))
+    service = wall / len(probe)
+    rate = 0.5 / (service * 1e-9)  # queries/s at 50% utilisation of the plain path
+    rng = np.random.default_rng(29)
+    arrival = np.cumsum(rng.exponential(1e9 / rate, size=len(queries))).astype(np.uint64)
+    out = {"workload": SERVING + (f" (rank scale {args.serve_scale})" if args.serve_scale != 1 else ""),
+           "experiments": len(exps), "ranks": sum(E["R"] for E in exps),
+           "queries": len(queries), "plain_service_us": service / 1e3,
+           "arrival_rate_qps": rate}
+    for name, plain in (("plain", True), ("serving", False)):
+        s = sp if plain else server(False)
+        if not plain:
+            s.replay(probe[:200], np.zeros(200, np.uint64))
+        l0 = ctx.launches()
+        lat, wall = s.replay(queries, arrival)
+        launches = ctx.launches() - l0
+        lat = lat.astype(np.float64) / 1e3
+        out[name] = {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                     "mean_us": float(lat.mean()), "qps": len(queries) / (wall * 1e-9),
+                     "gpu_launches": launches}
+        # saturated throughput: the whole stream queued at once
+        _, wall_sat = s.replay(queries, np.zeros(len(queries), np.uint64))
+        out[name]["saturated_qps"] = len(queries) / (wall_sat * 1e-9)
+        s.close()
+    out["p99_plain_over_serving"] = out["plain"]["p99_us"] / out["serving"]["p99_us"]
+    out["saturated_serving_over_plain"] = (out["serving"]["saturated_qps"]
+                                           / out["plain"]["saturated_qps"])
+    for E in exps:
+        E["e"].free()
+    return out
+
+
 # --------------------------------------------------------------------- arms --
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -530,6 +660,9 @@ def run_gpu(args):
         d_ro = d_par = d_ts = d_cx = calls = None
         torch.cuda.empty_cache()
         batched = run_batched(args, ctx, local)
+    serving = None
+    if not args.no_serving:
+        serving = run_serving(args, ctx, local)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world,
@@ -551,7 +684,7 @@ def run_gpu(args):
                                       ("validate_ms", "tensor_count_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "batched_vs_plain": batched,
+                "batched_vs_plain": batched, "serving": serving,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -572,6 +705,11 @@ def main():
     p.add_argument("--cpu-records", type=float, default=1.5e8)
     p.add_argument("--ref-records", type=float, default=5e6)
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-exps", type=int, default=8)
+    p.add_argument("--serve-queries", type=int, default=100000)
+    p.add_argument("--serve-scale", type=float, default=1.0,
+                   help="scale the rank count of every served experiment")
     p.add_argument("--batch-sets", type=int, default=256)
     p.add_argument("--batch-scale", type=float, default=1.0,
                    help="scale the rank count of every batched set (smaller runs)")
