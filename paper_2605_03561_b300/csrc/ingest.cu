@@ -195,6 +195,7 @@ constexpr u32 STEP = 128;  // samples per warp step (4 per lane)
 constexpr u32 RS = 128;    // staged entries per warp in shared memory
 
 constexpr u32 TL = 128;    // touched bitmap words remembered per row
+constexpr u32 RL = 128;    // run heads remembered per row (write pass)
 
 struct WarpSmem {
   static constexpr u32 mask_off = 0;                  // u32[MASKW] rank-start mask
@@ -202,7 +203,10 @@ struct WarpSmem {
   static constexpr u32 time_off = tl_off + 4 * (TL + 4);  // u64[RS] (16-byte aligned)
   static constexpr u32 ctx_off = time_off + 8 * RS;
   static constexpr u32 cnt_off = ctx_off + 4 * RS;
-  static constexpr u32 bm_off = cnt_off + 4 * RS;     // bitmap words (16-byte aligned)
+  static constexpr u32 run_ts_off = cnt_off + 4 * RS;     // u64[RL] run-head timestamps
+  static constexpr u32 run_ctx_off = run_ts_off + 8 * RL;  // u32[RL] run contexts
+  static constexpr u32 run_pos_off = run_ctx_off + 4 * RL;  // u32[RL] offsets in the row
+  static constexpr u32 bm_off = run_pos_off + 4 * RL;     // bitmap words (16-byte aligned)
   static constexpr u32 fixed_count = time_off;        // count pass: mask + touched list
   static constexpr u32 fixed_write = bm_off;
 };
@@ -246,6 +250,12 @@ __device__ __forceinline__ void bm_clear_touched(const Bm& b, const Touched& tw,
   __syncwarp();
   if (lane == 0) *tw.cnt = 0;
   __syncwarp();
+}
+
+// Element j (warp-uniform or per-lane) of a 4-element register array without
+// dynamic register indexing.
+__device__ __forceinline__ u64 sel4(const u64* v, u32 j) {
+  return j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
 }
 
 struct Step {
@@ -296,6 +306,54 @@ struct Stage {
   u64* time;
   u32* cnt;
 };
+
+// The write pass remembers the run heads of the open row (a run = samples of
+// one context in a row, in order): its context, first timestamp and offset in
+// the row.  A run lasts until the next run head, the last one until the row
+// end, so its time is a difference of two head timestamps (the per-sample
+// durations telescope) and its samples a difference of two offsets.
+struct RunList {
+  u64* ts;
+  u32* ctx;
+  u32* pos;
+};
+
+// Appends this lane's run heads (bits j of h4 among its 4 samples at q..q+3)
+// to the list after the nrun already there; returns the warp's head count.
+__device__ __forceinline__ u32 capture_runs(const RunList& rl, u32 nrun, u32 h4, const u32* c,
+                                            const u64* t, u64 q, u64 row_s, u32 C, int lane) {
+  const u32 cnt = __popc(h4);
+  const u32 incl = warp_incl_scan(cnt, lane);
+  u32 slot = nrun + incl - cnt;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if ((h4 >> j) & 1u) {
+      if (slot < RL) {
+        rl.ctx[slot] = c[j] < C ? c[j] : 0u;
+        rl.ts[slot] = t[j];
+        rl.pos[slot] = (u32)(q + j - row_s);
+      }
+      ++slot;
+    }
+  return __shfl_sync(FULL, incl, 31);
+}
+
+// Accumulates the row's runs (nrun <= RL) at their contexts' ranks.
+__device__ __forceinline__ void accumulate_runs(const Bm& bm, const Stage& st, const RunList& rl,
+                                                u32 nrun, u64 ts_end, u32 len, int lane) {
+  for (u32 k = lane; k < nrun; k += 32) {
+    const u64 t0 = rl.ts[k];
+    const u32 p0 = rl.pos[k];
+    const bool more = k + 1 < nrun;
+    const u64 t1 = more ? rl.ts[k + 1] : ts_end;
+    const u32 p1 = more ? rl.pos[k + 1] : len;
+    const u32 c = rl.ctx[k];
+    const u32 r = bm_rank(bm, c);
+    atomicAdd((unsigned long long*)&st.time[r], (unsigned long long)(t1 >= t0 ? t1 - t0 : 0ull));
+    atomicAdd(&st.cnt[r], p1 - p0);
+    st.ctx[r] = c;
+  }
+}
 
 // Write pass, one row [s, e) whose ranks are in the bitmap: accumulate time
 // and count at each context's rank in the stage, then write the row at entry
@@ -353,30 +411,25 @@ __device__ __forceinline__ void emit_row(const TensorArgs& A, const Stage& st, u
   }
 }
 
+// Writes the open row [s, e): from its remembered runs when they all fit the
+// run list, else by re-reading its samples.  ts_end is the timestamp the last
+// run lasts until: the sample at e, or the last sample when e ends the rank.
 __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
-                                         const Stage& sm, const Stage& gl, u64 s, u64 e,
-                                         bool e_rs, u64 eo, u32 C, int lane) {
+                                         const Stage& sm, const Stage& gl, const RunList& rl,
+                                         u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs, u64 eo,
+                                         u32 C, int lane) {
   __syncwarp();
   const u32 nnz = bm_prefix_warp(bm, lane);
-  if (nnz <= RS) {
-    for (u32 k = lane; k < nnz; k += 32) {
-      sm.time[k] = 0;
-      sm.cnt[k] = 0;
-    }
-    __syncwarp();
-    accumulate_row(A, bm, sm, s, e, e_rs, C, lane);
-    __syncwarp();
-    emit_row(A, sm, nnz, eo, lane);
-  } else {
-    for (u32 k = lane; k < nnz; k += 32) {
-      gl.time[k] = 0;
-      gl.cnt[k] = 0;
-    }
-    __syncwarp();
-    accumulate_row(A, bm, gl, s, e, e_rs, C, lane);
-    __syncwarp();
-    emit_row(A, gl, nnz, eo, lane);
+  const Stage& st = (nnz <= RS) ? sm : gl;
+  for (u32 k = lane; k < nnz; k += 32) {
+    st.time[k] = 0;
+    st.cnt[k] = 0;
   }
+  __syncwarp();
+  if (nrun <= RL) accumulate_runs(bm, st, rl, nrun, ts_end, (u32)(e - s), lane);
+  else accumulate_row(A, bm, st, s, e, e_rs, C, lane);
+  __syncwarp();
+  emit_row(A, st, nnz, eo, lane);
   bm_clear_touched<true>(bm, tw, lane);
   return nnz;
 }
@@ -402,7 +455,11 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
   if (BMS)
     for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
   Stage sst, gst;
+  RunList rl;
   if (WRITE) {
+    rl.ts = (u64*)(ws + WarpSmem::run_ts_off);
+    rl.ctx = (u32*)(ws + WarpSmem::run_ctx_off);
+    rl.pos = (u32*)(ws + WarpSmem::run_pos_off);
     sst.time = (u64*)(ws + WarpSmem::time_off);
     sst.ctx = (u32*)(ws + WarpSmem::ctx_off);
     sst.cnt = (u32*)(ws + WarpSmem::cnt_off);
@@ -432,6 +489,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     const u32 lo = A.tfr[t], hi = last ? rhi : A.tfr[t + 1];
     const u64 qrank = (hi < rhi) ? A.rank_off[hi] : N;  // first rank start >= b (or N)
     u32 carry = (a > sbase) ? A.ctx[a - 1] : NONE32;
+    u64 tcarry = (WRITE && a > sbase) ? A.ts[a - 1] : 0ull;  // timestamp before the step
     u64 PR = 0, PE = 0;
     if (WRITE) {
       PR = A.tile_row_off[t];
@@ -447,6 +505,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
 
     u32 rank_ptr = lo, rows_local = 0, fl = 0;
     u32 fresh = 0;  // count pass: contexts this lane saw first in the open row
+    u32 nrun = 0;   // write pass: run heads of the open row so far
     u64 cum = 0;
     bool row_open = false;
     u64 row_s = 0;
@@ -463,7 +522,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
 #pragma unroll
     for (int d = 0; d < DEPTH; ++d) {
       const u64 qd = a + (u64)d * STEP;
-      if (qd < A.N) load_step(A, qd, lane, WRITE && qd < b, ring[d]);
+      if (qd < A.N) load_step(A, qd, lane, WRITE, ring[d]);
     }
     for (u64 q0 = a;; q0 += STEP) {
       const bool tile_step = q0 < b;
@@ -471,7 +530,9 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       const u64 lim = tile_step ? b : qrank;
       if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, lim, true, PE + cum, C, lane);
+          if (WRITE)
+            cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[lim - 1], row_s, lim, true,
+                             PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
@@ -486,7 +547,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       const u64 q1 = q0 + STEP;
       {
         const u64 qd = q0 + (u64)DEPTH * STEP;
-        if (qd < A.N) load_step(A, qd, lane, WRITE && qd < b, ring[DEPTH]);
+        if (qd < A.N) load_step(A, qd, lane, WRITE, ring[DEPTH]);
       }
       const u64 q = q0 + 4 * (u64)lane;
       // samples of this step that exist (tile steps: below b; continuation:
@@ -500,6 +561,8 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       pc[2] = cur.c[1];
       pc[3] = cur.c[2];
       carry = __shfl_sync(FULL, cur.c[3], 31);
+      const u64 tprev = tcarry;  // timestamp of sample q0 - 1
+      if (WRITE) tcarry = __shfl_sync(FULL, cur.t[3], 31);
       const u32 rel = (u32)(q - a);
       // rank-start bits of this lane's 4 samples (positions rel .. rel + 3)
       const u32 rs4 = tile_step ? ((mask[rel >> 5] >> (rel & 31)) & 0xFu) : 0u;
@@ -548,16 +611,21 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         // fast path: no row starts in this step; mark the run heads of the
         // open row
         if (row_open) {
+          u32 h4 = 0;
 #pragma unroll
           for (int j = 0; j < 4; ++j)
             if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) {
+              h4 |= 1u << j;
               if (WRITE) bm_mark<true>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
               else fresh += bm_mark<false>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
             }
+          if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
         }
         if (q1 >= b && b == N) {  // the last tile: rows end at N
           if (row_open) {
-            if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, C, lane);
+            if (WRITE)
+              cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[N - 1], row_s, N, true,
+                               PE + cum, C, lane);
             else {
               cum += __reduce_add_sync(FULL, fresh);
               fresh = 0;
@@ -587,15 +655,18 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         const u32 nxt = __reduce_min_sync(FULL, mypos);
         const u32 end = nxt < STEP ? nxt : STEP;
         if (row_open) {
+          u32 h4 = 0;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const u32 pos = pos0 + j;
             if (((valid4 >> j) & 1u) && pos >= seg_lo && pos < end)
               if (q + j == row_s || pc[j] != cur.c[j]) {
+                h4 |= 1u << j;
                 if (WRITE) bm_mark<true>(bm, tw, cc[j]);
                 else fresh += bm_mark<false>(bm, tw, cc[j]);
               }
           }
+          if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
         }
         if (nxt >= STEP) break;
         const u64 p = q0 + nxt;
@@ -603,7 +674,15 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         const bool p_rs = (__shfl_sync(FULL, rs4, src) >> bj) & 1u;
         const bool p_ms = (__shfl_sync(FULL, ms4, src) >> bj) & 1u;
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, p, p_rs, PE + cum, C, lane);
+          if (WRITE) {
+            // timestamp the last run lasts until: sample p, or p - 1 at a rank start
+            const u32 n1 = nxt - 1;
+            const u64 tp = __shfl_sync(FULL, sel4(cur.t, bj), src);
+            const u64 tm = __shfl_sync(FULL, sel4(cur.t, n1 & 3), (n1 >> 2) & 31);
+            const u64 ts_end = p_rs ? (nxt ? tm : tprev) : tp;
+            cum += write_row(A, bm, tw, sst, gst, rl, nrun, ts_end, row_s, p, p_rs, PE + cum, C,
+                             lane);
+          }
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
@@ -633,13 +712,16 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         rows_local += nrow;
         row_open = true;
         row_s = p;
+        nrun = 0;
         seg_lo = nxt;
         from = nxt + 1;
       }
       if (stop) break;
       if (q1 >= b && b == N) {  // the last tile: rows end at N
         if (row_open) {
-          if (WRITE) cum += write_row(A, bm, tw, sst, gst, row_s, N, true, PE + cum, C, lane);
+          if (WRITE)
+            cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[N - 1], row_s, N, true,
+                             PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
             fresh = 0;
