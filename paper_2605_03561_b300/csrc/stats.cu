@@ -558,7 +558,7 @@ __global__ void __launch_bounds__(SP_NW * 32)
       const double sd = (I < 2) ? 0.0
                                 : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
                                        u64_to_f64((u64)I * (I - 1)));
-      cvw[(u64)ri * nk + k0 + kk] = (mean == 0.0) ? 0.0 : sd / mean;
+      cvw[(u64)(k0 + kk) * n + ri] = (mean == 0.0) ? 0.0 : sd / mean;
       my_sum[kk] = my_lo[kk] = my_hi[kk] = 0;
     }
     __syncwarp();
@@ -631,29 +631,153 @@ __global__ void __launch_bounds__(SP_NW * 32)
   }
 }
 
-// One thread per context: sums in ascending iteration / rank order.
+// (a) + (b) in one pass over the tensor, used when the cells of all I*
+// iterations for a chunk of kc contexts fit in shared memory.  Each CTA keeps
+// the cells (i, k) of the chunk (sum, max, 128-bit sum of squares) for the
+// ranks its warps visit and flushes them with one set of atomics at the end;
+// each warp keeps the within-rank sums of its current rank and writes that
+// rank's CV terms when it moves on.  A lane handles 16 entries per round (all
+// loads issued before any update) and follows the row of its entries with a
+// forward cursor over the rank's row offsets.
+constexpr int SPF_NW = 8;
+constexpr u32 SPF_U = 16;
+constexpr u32 SPF_SMEM_MAX = 227 * 1024;
+
+__host__ __device__ inline u64 spf_warp_bytes(u32 kc, u32 I) { return 24ull * kc + 8ull * (I + 1); }
+__host__ __device__ inline u64 spf_smem(u32 kc, u32 I) {
+  return 32ull * I * kc + SPF_NW * spf_warp_bytes(kc, I);
+}
+
+__global__ void __launch_bounds__(SPF_NW * 32, 1)
+    k_sp_fused(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
+               const u64* __restrict__ entry_off, const u32* __restrict__ e_ctx,
+               const u64* __restrict__ e_time, const u32* __restrict__ kmap, u32 k0, u32 kc,
+               u32 nk, u32 I, double* cvw, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi) {
+  extern __shared__ __align__(16) unsigned char spf_sm[];
+  const u32 ncell = I * kc;
+  unsigned long long* cs = (unsigned long long*)spf_sm;
+  unsigned long long* cm = cs + ncell;
+  u64* cl = (u64*)(cm + ncell);
+  u64* ch = cl + ncell;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wb = (unsigned char*)(ch + ncell) + (u64)warp * spf_warp_bytes(kc, I);
+  unsigned long long* ws = (unsigned long long*)wb;
+  u64* wl = (u64*)(ws + kc);
+  u64* wh = wl + kc;
+  u64* rowo = wh + kc;  // [I + 1] entry offsets of the rank's iteration rows
+  for (u32 q = threadIdx.x; q < ncell; q += blockDim.x) cs[q] = cm[q] = cl[q] = ch[q] = 0;
+  for (u32 q = lane; q < kc; q += 32) ws[q] = wl[q] = wh[q] = 0;
+  __syncthreads();
+  const u32 gw = blockIdx.x * SPF_NW + warp, nw = gridDim.x * SPF_NW;
+  for (u32 ri = gw; ri < n; ri += nw) {
+    const u32 r = rank_at(S, ri);
+    const u64 row0 = row_off[r] + 1;  // skip the prologue row
+    for (u32 i = lane; i <= I; i += 32) rowo[i] = entry_off[row0 + i];
+    __syncwarp();
+    const u64 E0 = rowo[0], E1 = rowo[I];
+    u32 cur = 0;
+    for (u64 jb = E0; jb < E1; jb += 32 * SPF_U) {
+      u32 c[SPF_U], k[SPF_U];
+      u64 t[SPF_U];
+#pragma unroll
+      for (u32 u = 0; u < SPF_U; ++u) {
+        const u64 j = jb + u * 32 + lane;
+        c[u] = j < E1 ? e_ctx[j] : NONE32;
+        t[u] = j < E1 ? e_time[j] : 0ull;
+      }
+#pragma unroll
+      for (u32 u = 0; u < SPF_U; ++u) k[u] = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
+#pragma unroll
+      for (u32 u = 0; u < SPF_U; ++u) {
+        const u64 j = jb + u * 32 + lane;
+        if (j >= E1) break;
+        while (rowo[cur + 1] <= j) ++cur;
+        if (k[u] == NONE32 || k[u] < k0 || k[u] >= k0 + kc) continue;
+        const u32 kk = k[u] - k0;
+        const u64 tv = t[u];
+        const u128 t2 = (u128)tv * tv;
+        const u32 q = cur * kc + kk;
+        atomicAdd(&cs[q], (unsigned long long)tv);
+        atomicMax(&cm[q], (unsigned long long)tv);
+        atomic_add_u128(&cl[q], &ch[q], t2);
+        atomicAdd(&ws[kk], (unsigned long long)tv);
+        atomic_add_u128(&wl[kk], &wh[kk], t2);
+      }
+    }
+    __syncwarp();
+    for (u32 kk = lane; kk < kc; kk += 32) {
+      const u64 sm_ = ws[kk];
+      const u128 q = ((u128)wh[kk] << 64) | wl[kk];
+      const double mean = u64_to_f64(sm_) / u64_to_f64(I);
+      const double sd = (I < 2) ? 0.0
+                                : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
+                                       u64_to_f64((u64)I * (I - 1)));
+      cvw[(u64)(k0 + kk) * n + ri] = (mean == 0.0) ? 0.0 : sd / mean;
+      ws[kk] = wl[kk] = wh[kk] = 0;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (u32 q = threadIdx.x; q < ncell; q += blockDim.x) {
+    const u32 i = q / kc, kk = q % kc;
+    const u64 gq = (u64)i * nk + k0 + kk;
+    if (cs[q]) atomicAdd((unsigned long long*)&g_sum[gq], cs[q]);
+    if (cm[q]) atomicMax((unsigned long long*)&g_max[gq], cm[q]);
+    if (cl[q] | ch[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)ch[q] << 64) | cl[q]);
+  }
+}
+
+// One warp per context: sums in ascending iteration / rank order (the
+// oracle's rounding).  The lanes fetch 32 consecutive terms at a time and
+// every lane adds them in order from shuffles, so the loads overlap while
+// the additions stay sequential.
 __global__ void k_sp_final_k(u32 nk, u32 n, u32 I, const u64* g_sum, const u64* g_max,
                              const u64* g_sqlo, const u64* g_sqhi, const double* cvw,
                              ta_speedup_ctx* per) {
-  const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const u32 k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (k >= nk) return;
   u64 A = 0, B = 0;
   double across = 0.0;
-  for (u32 i = 0; i < I; ++i) {
-    const u64 q = (u64)i * nk + k;
-    const u64 sum = g_sum[q], mx = g_max[q];
-    const u128 sq = ((u128)g_sqhi[q] << 64) | g_sqlo[q];
-    A += mx;
-    B += sum;
-    const double mean = u64_to_f64(sum) / u64_to_f64(n);
-    const double sd = (n < 2) ? 0.0
-                              : sqrt(u128_to_f64((u128)n * sq - (u128)sum * sum) /
-                                     u64_to_f64((u64)n * (n - 1)));
-    across += (mean == 0.0) ? 0.0 : sd / mean;
+  for (u32 i0 = 0; i0 < I; i0 += 32) {
+    const u32 i = i0 + lane;
+    u64 sum = 0, mx = 0;
+    double term = 0.0;
+    if (i < I) {
+      const u64 q = (u64)i * nk + k;
+      sum = g_sum[q];
+      mx = g_max[q];
+      const u128 sq = ((u128)g_sqhi[q] << 64) | g_sqlo[q];
+      const double mean = u64_to_f64(sum) / u64_to_f64(n);
+      const double sd = (n < 2) ? 0.0
+                                : sqrt(u128_to_f64((u128)n * sq - (u128)sum * sum) /
+                                       u64_to_f64((u64)n * (n - 1)));
+      term = (mean == 0.0) ? 0.0 : sd / mean;
+    }
+    const u32 m = min(32u, I - i0);
+    for (u32 x = 0; x < m; ++x) {
+      A += __shfl_sync(FULL, mx, x);
+      B += __shfl_sync(FULL, sum, x);
+      across += __shfl_sync(FULL, term, x);
+    }
   }
   double within = 0.0;
-  if (I > 0)
-    for (u32 ri = 0; ri < n; ++ri) within += cvw[(u64)ri * nk + k];
+  if (I > 0) {
+    const double* col = cvw + (u64)k * n;
+    double v = (lane < n) ? col[lane] : 0.0;
+    for (u32 r0 = 0; r0 < n; r0 += 32) {
+      const double nv = (r0 + 32 + lane < n) ? col[r0 + 32 + lane] : 0.0;  // next chunk
+      const u32 m = min(32u, n - r0);
+      double w[32];
+#pragma unroll
+      for (u32 x = 0; x < 32; ++x) w[x] = __shfl_sync(FULL, v, x);  // all issued first
+#pragma unroll
+      for (u32 x = 0; x < 32; ++x)
+        if (x < m) within += w[x];
+      v = nv;
+    }
+  }
+  if (lane != 0) return;
   const u128 G = (u128)n * A - B;
   ta_speedup_ctx p;
   p.A = A;
@@ -927,7 +1051,26 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
+  // contexts per fused pass: the cells of all I* iterations must fit
+  u32 kcf = 0;
   if (I > 0) {
+    const u64 per = 32ull * I + 24ull * SPF_NW, fixed = 8ull * SPF_NW * (I + 1);
+    if (fixed < SPF_SMEM_MAX) kcf = (u32)std::min<u64>(nk, (SPF_SMEM_MAX - fixed) / per);
+  }
+  if (I > 0 && kcf >= std::min<u32>(nk, 8)) {
+    const u64 smem = spf_smem(kcf, I);
+    cudaFuncSetAttribute(k_sp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per_sm = std::max<int>(1, (int)(SPF_SMEM_MAX / smem));
+    const int grid = std::max(1, std::min<int>(c->num_sms * per_sm,
+                                               (int)((n + SPF_NW - 1) / SPF_NW)));
+    for (u32 k0 = 0; k0 < nk; k0 += kcf) {
+      k_sp_fused<<<grid, SPF_NW * 32, smem, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
+                                                        e->e_time, kmap, k0,
+                                                        std::min(kcf, nk - k0), nk, I, cvw, gs,
+                                                        gm, gl, gh);
+      L.count();
+    }
+  } else if (I > 0) {
     const int grid = std::max(1, std::min<int>(c->num_sms * 8, (int)((n + SP_NW - 1) / SP_NW)));
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
       k_sp_within<<<grid, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
@@ -961,7 +1104,8 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     TRY(tmp.get_n(nk, &dper, "per ctx"));
     TRY(tmp.get_n(1, &dtot, "total"));
   }
-  k_sp_final_k<<<blocks(nk, 64), 64, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, cvw, dper);
+  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, cvw,
+                                                                  dper);
   k_sp_total<<<1, 1, 0, L.stream>>>(nk, n, I, excluded, t_app, dper, dtot);
   L.count(2);
   if (a->mem_kind == TA_MEM_HOST) {

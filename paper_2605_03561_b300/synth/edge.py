@@ -120,6 +120,22 @@ def case(name: str, seed: int = 0):
         parent[0] = NONE
         rank_off, ts, ctx = random_traces(rng, 6, C, 150, 800)
         return dict(rank_off=rank_off, ts=ts, ctx=ctx, parent=parent, marker=150)
+    if name == "many_iterations":
+        # 1200 short iterations per rank: cells of every iteration for many
+        # contexts exceed what one pass keeps on chip
+        C = 12
+        R = 3
+        parts_ro, parts_ts, parts_cx = [0], [], []
+        for r in range(R):
+            body = []
+            for _ in range(1200):
+                body += [1] + list(rng.integers(2, C, size=int(rng.integers(1, 4))))
+            n = len(body)
+            parts_cx.append(np.array(body, np.uint32))
+            parts_ts.append(np.cumsum(rng.integers(1, 50, size=n)).astype(np.uint64))
+            parts_ro.append(parts_ro[-1] + n)
+        return dict(rank_off=np.array(parts_ro, np.uint64), ts=np.concatenate(parts_ts),
+                    ctx=np.concatenate(parts_cx), parent=random_tree(rng, C), marker=1)
     if name == "random_small":
         C = int(rng.integers(2, 14))
         marker = int(rng.integers(0, C))

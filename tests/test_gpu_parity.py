@@ -55,6 +55,15 @@ def test_edge_cases(name):
         check_speedup(a, e, ctxs)
 
 
+def test_many_iterations_speedup_paths():
+    # I* = 1200: twelve contexts take the multi-kernel path, three the fused one
+    d = edge.case("many_iterations", 4)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    check_speedup(a, e, list(range(12)))
+    check_speedup(a, e, [2, 5, 7])
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_random_small(seed):
     d = edge.case("random_small", seed)
