@@ -322,9 +322,16 @@ struct RunList {
 // to the list after the nrun already there; returns the warp's head count.
 __device__ __forceinline__ u32 capture_runs(const RunList& rl, u32 nrun, u32 h4, const u32* c,
                                             const u64* t, u64 q, u64 row_s, u32 C, int lane) {
-  const u32 cnt = __popc(h4);
-  const u32 incl = warp_incl_scan(cnt, lane);
-  u32 slot = nrun + incl - cnt;
+  // heads of lower lanes, from one ballot per sample slot
+  const u32 below = (1u << lane) - 1u;
+  u32 before = 0, total = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const u32 b = __ballot_sync(FULL, (h4 >> j) & 1u);
+    before += __popc(b & below);
+    total += __popc(b);
+  }
+  u32 slot = nrun + before;
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if ((h4 >> j) & 1u) {
@@ -335,7 +342,13 @@ __device__ __forceinline__ u32 capture_runs(const RunList& rl, u32 nrun, u32 h4,
       }
       ++slot;
     }
-  return __shfl_sync(FULL, incl, 31);
+  return total;
+}
+
+// Marks the row's contexts from its run list (write pass).
+__device__ __forceinline__ void mark_runs(const Bm& bm, const Touched& tw, const RunList& rl,
+                                          u32 nrun, int lane) {
+  for (u32 k = lane; k < nrun; k += 32) bm_mark<true>(bm, tw, rl.ctx[k]);
 }
 
 // Accumulates the row's runs (nrun <= RL) at their contexts' ranks.
@@ -401,6 +414,29 @@ __device__ __forceinline__ void accumulate_row(const TensorArgs& A, const Bm& bm
   }
 }
 
+// Marks the contexts of row [s, e) by re-reading its samples (rows with more
+// runs than the run list holds).
+__device__ __forceinline__ void mark_row_samples(const TensorArgs& A, const Bm& bm,
+                                                 const Touched& tw, u64 s, u64 e, u32 C,
+                                                 int lane) {
+  u32 carry = NONE32;
+  for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
+    Step x;
+    load_step(A, g0, lane, false, x);
+    const u64 q = g0 + 4 * (u64)lane;
+    u32 pc = __shfl_up_sync(FULL, x.c[3], 1);
+    if (lane == 0) pc = carry;
+    carry = __shfl_sync(FULL, x.c[3], 31);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const u64 qj = q + j;
+      const u32 prev = j ? x.c[j - 1] : pc;
+      if (qj >= s && qj < e && (qj == s || prev != x.c[j]))
+        bm_mark<true>(bm, tw, x.c[j] < C ? x.c[j] : 0u);
+    }
+  }
+}
+
 __device__ __forceinline__ void emit_row(const TensorArgs& A, const Stage& st, u32 nnz, u64 eo,
                                          int lane) {
   for (u32 k = lane; k < nnz; k += 32) {
@@ -418,6 +454,8 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
                                          const Stage& sm, const Stage& gl, const RunList& rl,
                                          u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs, u64 eo,
                                          u32 C, int lane) {
+  if (nrun <= RL) mark_runs(bm, tw, rl, nrun, lane);
+  else mark_row_samples(A, bm, tw, s, e, C, lane);
   __syncwarp();
   const u32 nnz = bm_prefix_warp(bm, lane);
   const Stage& st = (nnz <= RS) ? sm : gl;
@@ -616,8 +654,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
           for (int j = 0; j < 4; ++j)
             if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) {
               h4 |= 1u << j;
-              if (WRITE) bm_mark<true>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
-              else fresh += bm_mark<false>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
+              if (!WRITE) fresh += bm_mark<false>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
             }
           if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
         }
@@ -662,8 +699,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
             if (((valid4 >> j) & 1u) && pos >= seg_lo && pos < end)
               if (q + j == row_s || pc[j] != cur.c[j]) {
                 h4 |= 1u << j;
-                if (WRITE) bm_mark<true>(bm, tw, cc[j]);
-                else fresh += bm_mark<false>(bm, tw, cc[j]);
+                if (!WRITE) fresh += bm_mark<false>(bm, tw, cc[j]);
               }
           }
           if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
