@@ -345,11 +345,6 @@ __device__ __forceinline__ u32 capture_runs(const RunList& rl, u32 nrun, u32 h4,
   return total;
 }
 
-// Marks the row's contexts from its run list (write pass).
-__device__ __forceinline__ void mark_runs(const Bm& bm, const Touched& tw, const RunList& rl,
-                                          u32 nrun, int lane) {
-  for (u32 k = lane; k < nrun; k += 32) bm_mark<true>(bm, tw, rl.ctx[k]);
-}
 
 // Accumulates the row's runs (nrun <= RL) at their contexts' ranks.
 __device__ __forceinline__ void accumulate_runs(const Bm& bm, const Stage& st, const RunList& rl,
@@ -416,10 +411,10 @@ __device__ __forceinline__ void accumulate_row(const TensorArgs& A, const Bm& bm
 
 // Marks the contexts of row [s, e) by re-reading its samples (rows with more
 // runs than the run list holds).
-__device__ __forceinline__ void mark_row_samples(const TensorArgs& A, const Bm& bm,
-                                                 const Touched& tw, u64 s, u64 e, u32 C,
-                                                 int lane) {
-  u32 carry = NONE32;
+__device__ __forceinline__ u32 mark_row_samples(const TensorArgs& A, const Bm& bm,
+                                                const Touched& tw, u64 s, u64 e, u32 C,
+                                                int lane) {
+  u32 carry = NONE32, fresh = 0;
   for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
     Step x;
     load_step(A, g0, lane, false, x);
@@ -432,43 +427,73 @@ __device__ __forceinline__ void mark_row_samples(const TensorArgs& A, const Bm& 
       const u64 qj = q + j;
       const u32 prev = j ? x.c[j - 1] : pc;
       if (qj >= s && qj < e && (qj == s || prev != x.c[j]))
-        bm_mark<true>(bm, tw, x.c[j] < C ? x.c[j] : 0u);
+        fresh += bm_mark<true>(bm, tw, x.c[j] < C ? x.c[j] : 0u);
     }
   }
+  return fresh;
 }
 
-__device__ __forceinline__ void emit_row(const TensorArgs& A, const Stage& st, u32 nnz, u64 eo,
-                                         int lane) {
-  for (u32 k = lane; k < nnz; k += 32) {
-    const u64 g = eo + k;
-    A.e_ctx[g] = st.ctx[k];
-    A.e_time[g] = st.time[k];
-    A.e_cnt[g] = st.cnt[k];
-  }
+
+// Marks the row's contexts from its run list; returns this lane's new bits.
+__device__ __forceinline__ u32 mark_runs_new(const Bm& bm, const Touched& tw, const RunList& rl,
+                                             u32 nrun, int lane) {
+  u32 fresh = 0;
+  for (u32 k = lane; k < nrun; k += 32) fresh += bm_mark<true>(bm, tw, rl.ctx[k]);
+  return fresh;
 }
 
-// Writes the open row [s, e): from its remembered runs when they all fit the
-// run list, else by re-reading its samples.  ts_end is the timestamp the last
-// run lasts until: the sample at e, or the last sample when e ends the rank.
+// Writes the open row [s, e) (write pass).  The warp's bitmap holds the
+// union of the contexts of its recent rows, not only this row's: successive
+// iterations of a rank mostly call the same contexts, so the ranks (the
+// prefix counts over the bitmap) are recomputed only when a row brings a
+// context the union lacks, and the union restarts from the row when it
+// outgrows the shared-memory stage.  Times and counts are staged at union
+// ranks and the contexts the row has are written in order, compacted.  Runs
+// come from the run list, or from re-reading the samples of rows with more
+// runs than it holds.  ts_end is the timestamp the last run lasts until: the
+// sample at e, or the last sample when e ends the rank.
 __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
                                          const Stage& sm, const Stage& gl, const RunList& rl,
-                                         u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs, u64 eo,
-                                         u32 C, int lane) {
-  if (nrun <= RL) mark_runs(bm, tw, rl, nrun, lane);
-  else mark_row_samples(A, bm, tw, s, e, C, lane);
-  __syncwarp();
-  const u32 nnz = bm_prefix_warp(bm, lane);
-  const Stage& st = (nnz <= RS) ? sm : gl;
-  for (u32 k = lane; k < nnz; k += 32) {
+                                         u32& nb, u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs,
+                                         u64 eo, u32 C, int lane) {
+  const bool listed = nrun <= RL;
+  u32 fresh = listed ? mark_runs_new(bm, tw, rl, nrun, lane)
+                     : mark_row_samples(A, bm, tw, s, e, C, lane);
+  fresh = __reduce_add_sync(FULL, fresh);
+  if (fresh && nb + fresh > RS && nb > 0) {  // restart the union from this row
+    bm_clear_touched<true>(bm, tw, lane);
+    fresh = listed ? mark_runs_new(bm, tw, rl, nrun, lane)
+                   : mark_row_samples(A, bm, tw, s, e, C, lane);
+    fresh = __reduce_add_sync(FULL, fresh);
+    nb = 0;
+  }
+  if (fresh) {
+    __syncwarp();
+    nb = bm_prefix_warp(bm, lane);
+  }
+  const Stage& st = (nb <= RS) ? sm : gl;
+  for (u32 k = lane; k < nb; k += 32) {
     st.time[k] = 0;
     st.cnt[k] = 0;
   }
   __syncwarp();
-  if (nrun <= RL) accumulate_runs(bm, st, rl, nrun, ts_end, (u32)(e - s), lane);
+  if (listed) accumulate_runs(bm, st, rl, nrun, ts_end, (u32)(e - s), lane);
   else accumulate_row(A, bm, st, s, e, e_rs, C, lane);
   __syncwarp();
-  emit_row(A, st, nnz, eo, lane);
-  bm_clear_touched<true>(bm, tw, lane);
+  const u32 below = (1u << lane) - 1u;
+  u32 nnz = 0;
+  for (u32 k0 = 0; k0 < nb; k0 += 32) {
+    const u32 k = k0 + lane;
+    const u32 cnt = (k < nb) ? st.cnt[k] : 0u;
+    const u32 bal = __ballot_sync(FULL, cnt != 0);
+    if (cnt) {
+      const u64 g = eo + nnz + __popc(bal & below);
+      A.e_ctx[g] = st.ctx[k];
+      A.e_time[g] = st.time[k];
+      A.e_cnt[g] = cnt;
+    }
+    nnz += __popc(bal);
+  }
   return nnz;
 }
 
@@ -505,6 +530,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     gst.ctx = A.gst_ctx + gw * A.gst_cap;
     gst.cnt = A.gst_cnt + gw * A.gst_cap;
   }
+  u32 nb = 0;  // write pass: contexts in the bitmap's union
   __syncwarp();
   for (u64 t = gw; t < A.n_tiles; t += G) {
     // the tile's trace set (a single experiment is one set)
@@ -569,7 +595,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
         if (row_open) {
           if (WRITE)
-            cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[lim - 1], row_s, lim, true,
+            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[lim - 1], row_s, lim, true,
                              PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
@@ -661,7 +687,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         if (q1 >= b && b == N) {  // the last tile: rows end at N
           if (row_open) {
             if (WRITE)
-              cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[N - 1], row_s, N, true,
+              cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[N - 1], row_s, N, true,
                                PE + cum, C, lane);
             else {
               cum += __reduce_add_sync(FULL, fresh);
@@ -716,7 +742,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
             const u64 tp = __shfl_sync(FULL, sel4(cur.t, bj), src);
             const u64 tm = __shfl_sync(FULL, sel4(cur.t, n1 & 3), (n1 >> 2) & 31);
             const u64 ts_end = p_rs ? (nxt ? tm : tprev) : tp;
-            cum += write_row(A, bm, tw, sst, gst, rl, nrun, ts_end, row_s, p, p_rs, PE + cum, C,
+            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, ts_end, row_s, p, p_rs, PE + cum, C,
                              lane);
           }
           else {
@@ -756,7 +782,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       if (q1 >= b && b == N) {  // the last tile: rows end at N
         if (row_open) {
           if (WRITE)
-            cum += write_row(A, bm, tw, sst, gst, rl, nrun, A.ts[N - 1], row_s, N, true,
+            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[N - 1], row_s, N, true,
                              PE + cum, C, lane);
           else {
             cum += __reduce_add_sync(FULL, fresh);
@@ -785,6 +811,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     }
     __syncwarp();
   }
+  if (WRITE) bm_clear_touched<true>(bm, tw, lane);  // leave a global bitmap clean
 }
 
 constexpr int TENSOR_NW = 8;

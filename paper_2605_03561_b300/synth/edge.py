@@ -136,6 +136,13 @@ def case(name: str, seed: int = 0):
             parts_ro.append(parts_ro[-1] + n)
         return dict(rank_off=np.array(parts_ro, np.uint64), ts=np.concatenate(parts_ts),
                     ctx=np.concatenate(parts_cx), parent=random_tree(rng, C), marker=1)
+    if name == "large_ctx":
+        # enough contexts that per-warp bitmaps live in global memory
+        C = 60000
+        marker = int(rng.integers(0, C))
+        rank_off, ts, ctx = random_traces(rng, 40, C, marker, 4000, p_marker=0.02)
+        return dict(rank_off=rank_off, ts=ts, ctx=ctx, parent=shuffled_tree(rng, C, 16),
+                    marker=marker)
     if name == "random_small":
         C = int(rng.integers(2, 14))
         marker = int(rng.integers(0, C))

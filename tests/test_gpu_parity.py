@@ -55,6 +55,17 @@ def test_edge_cases(name):
         check_speedup(a, e, ctxs)
 
 
+@pytest.mark.parametrize("seed", range(2))
+def test_large_context_count(seed):
+    # 60,000 contexts: the per-warp bitmaps of the tensor and rank passes are
+    # in global memory; two loads in a row check they are left clean
+    d = edge.case("large_ctx", seed)
+    for _ in range(2):
+        tr, a, e = load_both(d)
+        check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE, tau=(2, 1))
+
+
 def test_many_iterations_speedup_paths():
     # I* = 1200: twelve contexts take the multi-kernel path, three the fused one
     d = edge.case("many_iterations", 4)
