@@ -420,7 +420,10 @@ ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off, const
  * exactly, and captures the whole fixed launch sequence -- validation, the
  * iteration tensor (Section V), exclusive and inclusive CSR, and the
  * cross-rank statistics of the exclusive metric over all ranks of each set
- * (Section VI-A/B) -- in one CUDA graph.  ta_batch_run replays that graph on
+ * (Section VI-A/B) -- in one CUDA graph.  Before capture an autotuner times
+ * every launch shape of the tensor passes (4, 8 or 16 warps per CTA, 1 to the
+ * resident maximum of CTAs per SM) on the batch's own data and keeps the
+ * fastest (see ta_batch_info).  ta_batch_run replays that graph on
  * the context's stream (the inputs of the plan, already on the device, are
  * analysed again) and then sorts the outliers by set.
  *   sets[s]   as for ta_load_traces; parent ids and samples' context ids are
@@ -446,6 +449,11 @@ typedef struct ta_batch_info {
   uint64_t graph_nodes;   /* kernels, memsets and copies in the graph */
   uint64_t graph_kernels; /* kernel nodes among them                  */
   uint64_t device_bytes; /* arena owned by the batch                 */
+  /* launch shape the autotuner chose for the tensor passes: warps per CTA
+     and CTAs (count pass, write pass); trials run and their total time */
+  uint32_t count_warps, count_grid, write_warps, write_grid;
+  uint32_t tune_trials, reserved;
+  double tune_ms;
 } ta_batch_info;
 typedef struct ta_batch_set_view {
   uint32_t n_ranks, n_ctx;

@@ -133,7 +133,10 @@ class BatchArgs(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("n_sets", u32), ("n_ranks", u32), ("n_records", u64), ("n_rows", u64),
                 ("tensor_nnz", u64), ("excl_nnz", u64), ("incl_nnz", u64), ("n_outliers", u64),
-                ("graph_nodes", u64), ("graph_kernels", u64), ("device_bytes", u64)]
+                ("graph_nodes", u64), ("graph_kernels", u64), ("device_bytes", u64),
+                ("count_warps", u32), ("count_grid", u32), ("write_warps", u32),
+                ("write_grid", u32), ("tune_trials", u32), ("reserved", u32),
+                ("tune_ms", C.c_double)]
 
 
 class BatchSetView(C.Structure):

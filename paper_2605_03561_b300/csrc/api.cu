@@ -223,13 +223,12 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   TRY(tmp.get(64, (void**)&meta, "tensor meta"));
   TRY(tmp.get_n(2 * scan_scratch_elems(n_tiles), &A.scan_scratch, "tile scan"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
-  const u32 W = P.threads / 32;
-  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.grid * W * bm_words(e->C) * 4;
+  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.warps() * bm_words(e->C) * 4;
   if (gbm_bytes) {
     TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "tensor bitmaps"));
     cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
   }
-  const size_t gn = (size_t)P.grid * W * P.gst_cap;
+  const size_t gn = (size_t)P.write_warps() * P.gst_cap;
   TRY(tmp.get_n(gn, &A.gst_ctx, "tensor stage"));
   TRY(tmp.get_n(gn, &A.gst_cnt, "tensor stage"));
   TRY(tmp.get_n(gn, &A.gst_time, "tensor stage"));

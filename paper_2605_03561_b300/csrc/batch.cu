@@ -93,6 +93,9 @@ struct ta_batch {
   // kernel scratch
   TensorArgs T{};
   TensorPlan TP{};
+  TensorShape shape{};
+  u32 tune_trials = 0;
+  double tune_ms = 0.0;
   RankCsrArgs X[2]{};
   RankCsrPlan XP{};
   u64* meta = nullptr;   // [0] status, [1..2] tensor totals, [3] excl total, [4] incl total,
@@ -210,6 +213,57 @@ ta_status check_flags(ta_batch* b, const char* where) {
   TRY(status_from_flags(f, where));
   b->max_depth = (u32)h[6];
   b->n_out = h[7];
+  return TA_OK;
+}
+
+// Autotuner of the tensor passes' launch shape (warps per CTA, CTAs per SM):
+// every candidate runs the pass on the batch's own data once to warm up and
+// once timed with CUDA events; the fastest is kept for the captured graph.
+// Repeated runs write the same results (the passes are deterministic).
+constexpr int kTuneWarps[] = {4, 8, 16};
+
+ta_status tune_tensor(ta_batch* b, bool write) {
+  ta_ctx* c = b->ctx;
+  const Launch L = launch_of(b);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(TA_ERR_CUDA, "batch: tuning events");
+  float best = 3.4e38f;
+  TensorShape pick = b->shape;
+  for (int nw : kTuneWarps) {
+    const int occ = tensor_max_per_sm(b->Cmax, write, nw);
+    for (int ps = 1; ps <= occ; ++ps) {
+      TensorShape sh = b->shape;
+      if (write) {
+        sh.nw_write = nw;
+        sh.per_sm_write = ps;
+      } else {
+        sh.nw_count = nw;
+        sh.per_sm_count = ps;
+      }
+      const TensorPlan P = plan_tensor(b->Cmax, b->N, c->num_sms, sh);
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        if (write) launch_tensor_write(L, P, b->T);
+        else launch_tensor_count(L, P, b->T);
+        cudaEventRecord(e1, c->stream);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      ++b->tune_trials;
+      b->tune_ms += ms;
+      if (ms < best) {
+        best = ms;
+        pick = sh;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TRY(sync_check(c, "batch: tuning"));
+  b->shape = pick;
+  b->TP = plan_tensor(b->Cmax, b->N, c->num_sms, b->shape);
   return TA_OK;
 }
 
@@ -340,13 +394,21 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(b->own_n(nt, &A.tile_row_off, "tile row offsets"));
   TRY(b->own_n(nt, &A.tile_ent_off, "tile entry offsets"));
   TRY(b->own_n(2 * scan_scratch_elems(nt), &A.scan_scratch, "tile scan"));
-  const u32 W = b->TP.threads / 32;
+  // per-warp scratch for the widest launch shape the autotuner may try
+  u64 max_warps = 0, max_write_warps = 0;
+  for (int nw : kTuneWarps) {
+    max_warps = std::max<u64>(max_warps, (u64)c->num_sms * nw *
+                                             tensor_max_per_sm(b->Cmax, false, nw));
+    max_write_warps = std::max<u64>(max_write_warps, (u64)c->num_sms * nw *
+                                                         tensor_max_per_sm(b->Cmax, true, nw));
+  }
+  max_warps = std::max(max_warps, max_write_warps);
   if (!b->TP.bm_in_smem) {
-    const u64 words = (u64)b->TP.grid * W * bm_words(b->Cmax);
+    const u64 words = max_warps * bm_words(b->Cmax);
     TRY(b->own_n(words, &A.gbm, "tensor bitmaps"));
     cudaMemsetAsync(A.gbm, 0, words * 4, c->stream);
   }
-  const u64 gn = (u64)b->TP.grid * W * b->TP.gst_cap;
+  const u64 gn = max_write_warps * b->TP.gst_cap;
   TRY(b->own_n(gn, &A.gst_ctx, "tensor stage"));
   TRY(b->own_n(gn, &A.gst_cnt, "tensor stage"));
   TRY(b->own_n(gn, &A.gst_time, "tensor stage"));
@@ -363,6 +425,8 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   A.gst_cap = b->TP.gst_cap;
   A.bm_in_smem = b->TP.bm_in_smem ? 1u : 0u;
   A.sets = b->sets;
+  launch_tile_first_rank(L, b->rank_off, b->R, b->TP.tile, (u32)b->n_tiles, (u32*)A.tfr, b->sets);
+  TRY(tune_tensor(b, false));
   enqueue_tensor_count(b);
   u64 h[3];
   TRY(copy(c, h, b->meta, sizeof h));
@@ -379,6 +443,9 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   A.e_ctx = b->e_ctx;
   A.e_time = b->e_time;
   A.e_cnt = b->e_cnt;
+  k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
+  k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->nnz);
+  TRY(tune_tensor(b, true));
   enqueue_tensor_write(b);
   TRY(check_flags(b, "ta_batch_plan"));
   // exclusive and inclusive CSR
@@ -606,6 +673,12 @@ ta_status ta_batch_get_info(const ta_batch* b, ta_batch_info* i) {
   i->n_outliers = b->n_out;
   i->graph_nodes = b->graph_nodes;
   i->graph_kernels = b->graph_kernels;
+  i->count_warps = (u32)b->TP.nw_count;
+  i->count_grid = (u32)b->TP.grid_count;
+  i->write_warps = (u32)b->TP.nw_write;
+  i->write_grid = (u32)b->TP.grid_write;
+  i->tune_trials = b->tune_trials;
+  i->tune_ms = b->tune_ms;
   i->device_bytes = b->device_bytes;
   return TA_OK;
 }

@@ -814,39 +814,65 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
   if (WRITE) bm_clear_touched<true>(bm, tw, lane);  // leave a global bitmap clean
 }
 
-constexpr int TENSOR_NW = 8;
-
 static void set_smem(const void* k, size_t smem) {
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-TensorPlan plan_tensor(u32 C, u64 N, int num_sms) {
+template <bool WRITE>
+static const void* tensor_kernel(int nw, bool bms) {
+  switch (nw) {
+    case 4:
+      return bms ? (const void*)k_tensor_pass<4, WRITE, true> : (const void*)k_tensor_pass<4, WRITE, false>;
+    case 16:
+      return bms ? (const void*)k_tensor_pass<16, WRITE, true> : (const void*)k_tensor_pass<16, WRITE, false>;
+    default:
+      return bms ? (const void*)k_tensor_pass<8, WRITE, true> : (const void*)k_tensor_pass<8, WRITE, false>;
+  }
+}
+
+static bool tensor_bm_in_smem(u32 C) {
+  return WarpSmem::fixed_write + (size_t)bm_words(C) * 4 <= 12 * 1024;
+}
+
+static size_t tensor_smem(u32 C, bool write, int nw) {
+  const size_t bm = tensor_bm_in_smem(C) ? (size_t)bm_words(C) * 4 : 0;
+  return (size_t)((write ? WarpSmem::fixed_write : WarpSmem::fixed_count) + bm) * nw;
+}
+
+int tensor_max_per_sm(u32 C, bool write, int nw) {
+  const void* k = write ? tensor_kernel<true>(nw, tensor_bm_in_smem(C))
+                        : tensor_kernel<false>(nw, tensor_bm_in_smem(C));
+  const size_t smem = tensor_smem(C, write, nw);
+  set_smem(k, smem);
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nw * 32, smem);
+  return std::max(1, occ);
+}
+
+TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape) {
   TensorPlan P;
   P.tile = TW;
-  P.threads = TENSOR_NW * 32;
-  const size_t bm = (size_t)bm_words(C) * 4;
-  P.bm_in_smem = WarpSmem::fixed_write + bm <= 12 * 1024;
-  P.smem_count = (WarpSmem::fixed_count + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
-  P.smem = (WarpSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * TENSOR_NW;
-  const void* kc = P.bm_in_smem ? (const void*)k_tensor_pass<TENSOR_NW, false, true>
-                                 : (const void*)k_tensor_pass<TENSOR_NW, false, false>;
-  const void* kw = P.bm_in_smem ? (const void*)k_tensor_pass<TENSOR_NW, true, true>
-                                 : (const void*)k_tensor_pass<TENSOR_NW, true, false>;
-  set_smem(kc, P.smem_count);
-  set_smem(kw, P.smem);
-  int o1 = 0, o2 = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, kc, P.threads, P.smem_count);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, kw, P.threads, P.smem);
-  const int occ = std::max(1, std::min(o1, o2));
+  P.bm_in_smem = tensor_bm_in_smem(C);
+  P.nw_count = shape.nw_count;
+  P.nw_write = shape.nw_write;
+  P.smem_count = tensor_smem(C, false, P.nw_count);
+  P.smem = tensor_smem(C, true, P.nw_write);
   const u64 n_tiles = std::max<u64>(1, (N + TW - 1) / TW);
-  P.grid = (int)std::min<u64>((u64)num_sms * occ, (n_tiles + TENSOR_NW - 1) / TENSOR_NW);
+  auto grid = [&](bool write, int nw, int per_sm) {
+    const int occ = tensor_max_per_sm(C, write, nw);
+    const int ps = per_sm > 0 ? std::min(per_sm, occ) : occ;
+    return (int)std::max<u64>(1, std::min<u64>((u64)num_sms * ps, (n_tiles + nw - 1) / nw));
+  };
+  P.grid_count = grid(false, P.nw_count, shape.per_sm_count);
+  P.grid_write = grid(true, P.nw_write, shape.per_sm_write);
   P.gst_cap = C;
   return P;
 }
 
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  if (P.bm_in_smem) k_tensor_pass<TENSOR_NW, false, true><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
-  else k_tensor_pass<TENSOR_NW, false, false><<<P.grid, P.threads, P.smem_count, L.stream>>>(A);
+  void* args[] = {(void*)&A};
+  cudaLaunchKernel(tensor_kernel<false>(P.nw_count, P.bm_in_smem), P.grid_count,
+                   P.nw_count * 32, args, P.smem_count, L.stream);
   L.count();
 }
 
@@ -857,8 +883,9 @@ void launch_tile_scan(const Launch& L, const TensorArgs& A) {
 }
 
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  if (P.bm_in_smem) k_tensor_pass<TENSOR_NW, true, true><<<P.grid, P.threads, P.smem, L.stream>>>(A);
-  else k_tensor_pass<TENSOR_NW, true, false><<<P.grid, P.threads, P.smem, L.stream>>>(A);
+  void* args[] = {(void*)&A};
+  cudaLaunchKernel(tensor_kernel<true>(P.nw_write, P.bm_in_smem), P.grid_write, P.nw_write * 32,
+                   args, P.smem, L.stream);
   L.count();
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "ta.h"
@@ -77,13 +78,26 @@ struct TensorArgs {
   SetMap sets;
 };
 
+// Launch shape of the two tensor passes: warps per CTA (4, 8 or 16) and CTAs
+// per SM (0 = as many as fit), chosen separately for the count and the
+// write pass (the batched form tunes them on its data).
+struct TensorShape {
+  int nw_count = 8, per_sm_count = 0, nw_write = 8, per_sm_write = 0;
+};
 struct TensorPlan {
-  int tile, threads, grid;
+  int tile;
+  int nw_count, grid_count, nw_write, grid_write;
   size_t smem, smem_count;
   bool bm_in_smem;
   u32 gst_cap;
+  u64 warps() const {
+    return (u64)std::max(grid_count * nw_count, grid_write * nw_write);
+  }
+  u64 write_warps() const { return (u64)grid_write * nw_write; }
 };
-TensorPlan plan_tensor(u32 C, u64 N, int num_sms);
+TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape = TensorShape{});
+// CTAs of a pass that fit on one SM (occupancy) for warps per CTA nw.
+int tensor_max_per_sm(u32 C, bool write, int nw);
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A);
 void launch_tile_scan(const Launch& L, const TensorArgs& A);
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A);
