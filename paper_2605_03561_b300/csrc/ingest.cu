@@ -190,7 +190,7 @@ namespace {
 
 constexpr u32 TW = 4096;   // samples per tile
 constexpr u32 MASKW = TW / 32 + 4;  // rank-start mask words (positions 0 .. TW)
-constexpr int DEPTH = 3;   // steps prefetched ahead
+constexpr int DEPTH = 3;   // steps prefetched ahead (count pass)
 constexpr u32 STEP = 128;  // samples per warp step (4 per lane)
 constexpr u32 RS = 128;    // staged entries per warp in shared memory
 
@@ -501,6 +501,7 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
 
 template <int NW, bool WRITE, bool BMS>
 __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
+  constexpr int D = WRITE ? 2 : DEPTH;  // steps in flight (the write pass holds timestamps too)
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
@@ -573,10 +574,10 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
     u64 cum = 0;
     bool row_open = false;
     u64 row_s = 0;
-    // ring of steps: ring[0] is processed while ring[1 .. DEPTH] are in flight
-    Step ring[DEPTH + 1];
+    // ring of steps: ring[0] is processed while ring[1 .. D] are in flight
+    Step ring[D + 1];
 #pragma unroll
-    for (int d = 0; d <= DEPTH; ++d) {
+    for (int d = 0; d <= D; ++d) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         ring[d].c[j] = NONE32;
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
       }
     }
 #pragma unroll
-    for (int d = 0; d < DEPTH; ++d) {
+    for (int d = 0; d < D; ++d) {
       const u64 qd = a + (u64)d * STEP;
       if (qd < A.N) load_step(A, qd, lane, WRITE, ring[d]);
     }
@@ -607,11 +608,10 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         break;
       }
       Step& cur = ring[0];
-      const Step& nx = ring[1];
       const u64 q1 = q0 + STEP;
       {
-        const u64 qd = q0 + (u64)DEPTH * STEP;
-        if (qd < A.N) load_step(A, qd, lane, WRITE, ring[DEPTH]);
+        const u64 qd = q0 + (u64)D * STEP;
+        if (qd < A.N) load_step(A, qd, lane, WRITE, ring[D]);
       }
       const u64 q = q0 + 4 * (u64)lane;
       // samples of this step that exist (tile steps: below b; continuation:
@@ -647,26 +647,16 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
             if ((valid4 >> j) & 1u) cmax = max(cmax, cur.c[j]);
           if (cmax >= C) fl |= F_BAD_CTX;
         } else {
-          // timestamp order within ranks: sample i+1 must not be earlier
-          // unless a rank starts at i+1
-          const u32 rs_next_lane = __shfl_down_sync(FULL, rs4, 1) & 1u;
-          u64 t_after = __shfl_down_sync(FULL, cur.t[0], 1);
-          const u64 nx_t0 = __shfl_sync(FULL, nx.t[0], 0);  // all lanes (nx is always set)
-          u32 rsn = (rs4 >> 1) | (rs_next_lane << 3);  // rank start at rel + j + 1
-          if (lane == 31) {
-            if (q + 4 < N) t_after = (q1 < b) ? nx_t0 : A.ts[q + 4];
-            const u32 r4 = rel + 4;
-            const bool r4s = (q + 4 >= N) ? true
-                             : (r4 < TW) ? (((mask[r4 >> 5] >> (r4 & 31)) & 1u) != 0)
-                                         : (qrank == b);
-            rsn = (rsn & 7u) | ((r4s ? 1u : 0u) << 3);
-          }
+          // timestamp order within ranks: no sample earlier than the one
+          // before it, except at a rank start (each pair is checked by the
+          // tile holding its later sample)
+          u64 tp = __shfl_up_sync(FULL, cur.t[3], 1);
+          if (lane == 0) tp = tprev;
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            if (!((valid4 >> j) & 1u) || ((rsn >> j) & 1u)) continue;
-            if (q + j + 1 >= N) continue;
-            const u64 tn = (j < 3) ? cur.t[j + 1] : t_after;
-            if (tn < cur.t[j]) fl |= F_NOT_SORTED;
+            const u64 before = j ? cur.t[j - 1] : tp;
+            if (((valid4 >> j) & 1u) && !((rs4 >> j) & 1u) && cur.t[j] < before)
+              fl |= F_NOT_SORTED;
           }
         }
       }
@@ -699,7 +689,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
           break;
         }
 #pragma unroll
-        for (int d = 0; d < DEPTH; ++d) ring[d] = ring[d + 1];
+        for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
         continue;
       }
       u32 cc[4];
@@ -794,7 +784,7 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
         break;
       }
 #pragma unroll
-      for (int d = 0; d < DEPTH; ++d) ring[d] = ring[d + 1];
+      for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
     }
     fl = __reduce_or_sync(FULL, fl);
     if (lane == 0 && fl) flag(A.status, fl);
