@@ -272,6 +272,26 @@ uint64_t row_time(const RankResult& rr, size_t row, uint32_t c) {
   return x;
 }
 
+// Sum of v in a fixed pairwise order: level by level, element i of the next
+// level is v[2i] + v[2i+1]; an odd last element moves up unchanged.  (The
+// order is part of the definition: with it the result does not depend on how
+// the work is split.)
+double pairwise_sum(std::vector<double> v) {
+  size_t n = v.size();
+  if (n == 0) return 0.0;
+  while (n > 1) {
+    const size_t m = n / 2;
+    for (size_t i = 0; i < m; ++i) v[i] = v[2 * i] + v[2 * i + 1];
+    if (n & 1) {
+      v[m] = v[n - 1];
+      n = m + 1;
+    } else {
+      n = m;
+    }
+  }
+  return v[0];
+}
+
 bool check_subset(const uint32_t* s, uint32_t n, uint32_t limit) {
   for (uint32_t i = 0; i < n; ++i) {
     if (s[i] >= limit) return false;
@@ -646,7 +666,7 @@ int or_speedup(void* hp, const uint32_t* ctxs, uint32_t n_ctxs, const uint32_t* 
                                       u128_to_double((u128)n * (n - 1)));
       across += (mean == 0.0) ? 0.0 : sd / mean;
     }
-    double within = 0.0;
+    std::vector<double> within_terms;  // per rank of S, in order
     for (uint32_t r : S) {
       uint64_t s = 0;
       u128 q = 0;
@@ -660,8 +680,9 @@ int or_speedup(void* hp, const uint32_t* ctxs, uint32_t n_ctxs, const uint32_t* 
       double sd = (I < 2) ? 0.0
                           : std::sqrt(u128_to_double((u128)I * q - (u128)s * s) /
                                       u128_to_double((u128)I * (I - 1)));
-      within += (mean == 0.0) ? 0.0 : sd / mean;
+      within_terms.push_back((mean == 0.0) ? 0.0 : sd / mean);
     }
+    const double within = pairwise_sum(within_terms);
     const u128 G = (u128)n * A - B;
     or_speedup_ctx& p = per[k];
     p.A = A;

@@ -121,3 +121,41 @@ def test_topk_ties_go_to_lower_rank():
     # mean 20, std (ddof 1) = sqrt(400/3): z = +-10 / sqrt(400/3) = +-sqrt(3)/2
     assert z[0] == pytest.approx(math.sqrt(3) / 2, rel=1e-15)
     assert z[3] == pytest.approx(-math.sqrt(3) / 2, rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_cv_terms_against_exact_means(seed):
+    # cv_within = mean over ranks of each rank's CV over iterations, cv_across =
+    # mean over iterations of the CV over ranks (ddof 1); recomputed from a
+    # brute-force tensor with exact variances and an exactly rounded mean.
+    d = edge.case("random_small", seed)
+    tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+    a = oracle.Analysis(tr)
+    dd = dict(rank_off=d["rank_off"], ts=d["ts"], ctx=d["ctx"], parent=d["parent"],
+              marker=d["marker"])
+    rows = bf.tensor(dd)
+    ctxs = list(range(tr.C))
+    per, tot = a.speedup(ctxs)
+    I = tot["i_star"]
+    if I == 0:
+        return
+
+    def cv(xs):
+        n = len(xs)
+        s = sum(xs)
+        if s == 0:
+            return 0.0
+        var = Fraction(n * sum(x * x for x in xs) - s * s, n * (n - 1)) if n > 1 else 0
+        return math.sqrt(var) / (s / n)
+
+    def t(r, i, c):
+        for cc, tt, _ in rows[r][i + 1]:
+            if cc == c:
+                return tt
+        return 0
+
+    for k, c in enumerate(ctxs):
+        within = math.fsum(cv([t(r, i, c) for i in range(I)]) for r in range(tr.R)) / tr.R
+        across = math.fsum(cv([t(r, i, c) for r in range(tr.R)]) for i in range(I)) / I
+        assert per["cv_within"][k] == pytest.approx(within, rel=1e-13, abs=1e-300)
+        assert per["cv_across"][k] == pytest.approx(across, rel=1e-13, abs=1e-300)
