@@ -522,7 +522,7 @@ __global__ void k_sp_istar(const u32* S, u32 n, const u32* n_iter, const u64* sp
 
 constexpr int SP_NW = 8;
 constexpr u32 SP_KC = 256;    // contexts per within-rank chunk (per-warp accumulators)
-constexpr u32 SP_CELLS = 128; // (iteration, context) cells per warp
+constexpr u32 SP_U = 8;       // entries per lane in flight
 
 // (a) Within-rank CV terms: one warp per rank of S; over iterations i < I*,
 // per context k in [k0, k0 + nkc): sum and 128-bit sum of squares of
@@ -542,13 +542,23 @@ __global__ void __launch_bounds__(SP_NW * 32)
     const u32 r = rank_at(S, ri);
     const u64 row0 = row_off[r] + 1;  // skip the prologue row
     const u64 E0 = entry_off[row0], E1 = entry_off[row0 + I];
-    for (u64 j = E0 + lane; j < E1; j += 32) {
-      const u32 k = kmap[e_ctx[j]];
-      if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
-      const u32 kk = k - k0;
-      const u64 t = e_time[j];
-      atomicAdd(&my_sum[kk], (unsigned long long)t);
-      atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t * t);
+    for (u64 jb = E0; jb < E1; jb += 32 * SP_U) {  // SP_U entries per lane in flight
+      u32 c[SP_U];
+      u64 t[SP_U];
+#pragma unroll
+      for (u32 u = 0; u < SP_U; ++u) {
+        const u64 j = jb + u * 32 + lane;
+        c[u] = j < E1 ? e_ctx[j] : NONE32;
+        t[u] = j < E1 ? e_time[j] : 0ull;
+      }
+#pragma unroll
+      for (u32 u = 0; u < SP_U; ++u) {
+        const u32 k = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
+        if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
+        const u32 kk = k - k0;
+        atomicAdd(&my_sum[kk], (unsigned long long)t[u]);
+        atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t[u] * t[u]);
+      }
     }
     __syncwarp();
     for (u32 kk = lane; kk < nkc; kk += 32) {
@@ -565,174 +575,152 @@ __global__ void __launch_bounds__(SP_NW * 32)
   }
 }
 
-// (b) Cells (i, k) over ranks.  A work item is a tile of cells
-// [i0, i0 + di) x [k0, k0 + dk) (di * dk <= SP_CELLS) and a group of ranks;
-// the warp keeps the tile's partial sums private in shared memory.  It
-// processes one row at a time, so the lanes of an instruction touch distinct
-// cells (a row holds each context once) and plain updates suffice; the tile
-// is flushed to the global cells with one set of atomics per item.
-__global__ void __launch_bounds__(SP_NW * 32)
-    k_sp_cells(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
-               const u64* e_time, const u32* kmap, u32 nk, u32 I, u32 di, u32 dk, u32 n_itiles,
-               u32 n_ktiles, u32 rank_group, u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo,
-               u64* g_sqhi) {
-  __shared__ u64 c_sum[SP_NW][SP_CELLS], c_max[SP_NW][SP_CELLS], c_lo[SP_NW][SP_CELLS],
-      c_hi[SP_NW][SP_CELLS];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u64* cs = c_sum[warp];
-  u64* cm = c_max[warp];
-  u64* cl = c_lo[warp];
-  u64* ch = c_hi[warp];
-  const u64 gw = (u64)blockIdx.x * SP_NW + warp, nw = (u64)gridDim.x * SP_NW;
-  for (u64 item = gw; item < n_items; item += nw) {
-    const u64 tile = item % ((u64)n_itiles * n_ktiles);
-    const u64 grp = item / ((u64)n_itiles * n_ktiles);
-    const u32 i0 = (u32)(tile % n_itiles) * di, k0 = (u32)(tile / n_itiles) * dk;
-    const u32 ni = min(di, I - i0), nkk = min(dk, nk - k0);
-    for (u32 q = lane; q < SP_CELLS; q += 32) cs[q] = cm[q] = cl[q] = ch[q] = 0;
-    __syncwarp();
-    const u32 r_begin = (u32)(grp * rank_group);
-    const u32 r_end = min(n, r_begin + rank_group);
-    for (u32 rb = r_begin; rb < r_end; rb += 32) {
-      // 32 ranks' entry ranges for rows i0 .. i0 + ni, fetched in parallel
-      u64 my_row = 0;
-      if (rb + lane < r_end) my_row = row_off[rank_at(S, rb + lane)] + 1 + i0;
-      const u32 cnt = min(32u, r_end - rb);
-      for (u32 x = 0; x < cnt; ++x) {
-        const u64 row = __shfl_sync(FULL, my_row, x);
-        for (u32 ii = 0; ii < ni; ++ii) {
-          const u64 E0 = entry_off[row + ii], E1 = entry_off[row + ii + 1];
-          for (u64 j = E0 + lane; j < E1; j += 32) {
-            const u32 k = kmap[e_ctx[j]];
-            if (k == NONE32 || k < k0 || k >= k0 + nkk) continue;
-            const u32 q = ii * dk + (k - k0);
-            const u64 t = e_time[j];
-            const u128 t2 = (u128)t * t;
-            cs[q] += t;
-            if (t > cm[q]) cm[q] = t;
-            const u64 lo = cl[q] + (u64)t2;
-            ch[q] += (u64)(t2 >> 64) + (lo < cl[q] ? 1ull : 0ull);
-            cl[q] = lo;
-          }
-          __syncwarp();
-        }
-      }
-    }
-    __syncwarp();
-    for (u32 q = lane; q < ni * dk; q += 32) {
-      const u32 ii = q / dk, kk = q % dk;
-      if (kk >= nkk) continue;
-      const u64 gq = (u64)(i0 + ii) * nk + k0 + kk;
-      if (cs[q]) atomicAdd((unsigned long long*)&g_sum[gq], (unsigned long long)cs[q]);
-      if (cm[q]) atomicMax((unsigned long long*)&g_max[gq], (unsigned long long)cm[q]);
-      if (cl[q] | ch[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)ch[q] << 64) | cl[q]);
-    }
-    __syncwarp();
-  }
-}
+// (b) Cells (i, k) over ranks.  A warp owns the cells of SP_IB iterations
+// [i0, i0 + SP_IB) and 64 contexts [k0, k0 + 64) for a group of ranks and
+// keeps them in registers: lane l holds contexts k0 + l and k0 + l + 32
+// (sum, max, 128-bit sum of squares).  It reads the SP_IB rows of SP_PR ranks
+// at a time (one contiguous entry range per rank, all loads issued first),
+// scatters each entry's time to a per-warp shared-memory buffer indexed by
+// (rank, row, context) -- a row holds each context once, so plain stores
+// suffice -- and every lane then folds its contexts' values into its
+// registers, absent ones reading 0.  The group's cells go to the global
+// cells with one set of atomics per warp.
+constexpr u32 SP_IB = 2;   // iterations per warp
+constexpr u32 SP_PR = 4;   // ranks per round
+constexpr u32 SP_CU = 8;   // entries per lane in flight per round
 
-// (a) + (b) in one pass over the tensor, used when the cells of all I*
-// iterations for a chunk of kc contexts fit in shared memory.  Each CTA keeps
-// the cells (i, k) of the chunk (sum, max, 128-bit sum of squares) for the
-// ranks its warps visit and flushes them with one set of atomics at the end;
-// each warp keeps the within-rank sums of its current rank and writes that
-// rank's CV terms when it moves on.  A lane handles 16 entries per round (all
-// loads issued before any update) and follows the row of its entries with a
-// forward cursor over the rank's row offsets.
-constexpr int SPF_NW = 8;
-constexpr u32 SPF_U = 16;
-constexpr u32 SPF_SMEM_MAX = 227 * 1024;
-
-__host__ __device__ inline u64 spf_warp_bytes(u32 kc, u32 I) { return 24ull * kc + 8ull * (I + 1); }
-__host__ __device__ inline u64 spf_smem(u32 kc, u32 I) {
-  return 32ull * I * kc + SPF_NW * spf_warp_bytes(kc, I);
-}
-
-__global__ void __launch_bounds__(SPF_NW * 32, 1)
-    k_sp_fused(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
+__global__ void __launch_bounds__(SP_NW * 32, 2)
+    k_sp_cells(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
                const u64* __restrict__ entry_off, const u32* __restrict__ e_ctx,
-               const u64* __restrict__ e_time, const u32* __restrict__ kmap, u32 k0, u32 kc,
-               u32 nk, u32 I, double* cvw, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi) {
-  extern __shared__ __align__(16) unsigned char spf_sm[];
-  const u32 ncell = I * kc;
-  unsigned long long* cs = (unsigned long long*)spf_sm;
-  unsigned long long* cm = cs + ncell;
-  u64* cl = (u64*)(cm + ncell);
-  u64* ch = cl + ncell;
+               const u64* __restrict__ e_time, const u32* __restrict__ kmap, u32 nk, u32 I,
+               u32 n_ib, u32 n_kb, u32 group, u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo,
+               u64* g_sqhi) {
+  __shared__ u64 rowbuf[SP_NW][SP_PR][SP_IB][64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* wb = (unsigned char*)(ch + ncell) + (u64)warp * spf_warp_bytes(kc, I);
-  unsigned long long* ws = (unsigned long long*)wb;
-  u64* wl = (u64*)(ws + kc);
-  u64* wh = wl + kc;
-  u64* rowo = wh + kc;  // [I + 1] entry offsets of the rank's iteration rows
-  for (u32 q = threadIdx.x; q < ncell; q += blockDim.x) cs[q] = cm[q] = cl[q] = ch[q] = 0;
-  for (u32 q = lane; q < kc; q += 32) ws[q] = wl[q] = wh[q] = 0;
-  __syncthreads();
-  const u32 gw = blockIdx.x * SPF_NW + warp, nw = gridDim.x * SPF_NW;
-  for (u32 ri = gw; ri < n; ri += nw) {
-    const u32 r = rank_at(S, ri);
-    const u64 row0 = row_off[r] + 1;  // skip the prologue row
-    for (u32 i = lane; i <= I; i += 32) rowo[i] = entry_off[row0 + i];
-    __syncwarp();
-    const u64 E0 = rowo[0], E1 = rowo[I];
-    u32 cur = 0;
-    for (u64 jb = E0; jb < E1; jb += 32 * SPF_U) {
-      u32 c[SPF_U], k[SPF_U];
-      u64 t[SPF_U];
+  u64* buf = &rowbuf[warp][0][0][0];
+  for (u32 q = lane; q < SP_PR * SP_IB * 64; q += 32) buf[q] = 0;
+  __syncwarp();
+  const u64 item = (u64)blockIdx.x * SP_NW + warp;
+  if (item >= n_items) return;
+  const u32 ib = (u32)(item % n_ib), kb = (u32)((item / n_ib) % n_kb);
+  const u32 g = (u32)(item / ((u64)n_ib * n_kb));
+  const u32 i0 = ib * SP_IB, k0 = kb * 64;
+  const u32 nrow = min(SP_IB, I - i0);
+  const u32 r_begin = g * group, r_end = min(n, r_begin + group);
+  u64 csum[SP_IB][2], cmax[SP_IB][2], clo[SP_IB][2], chi[SP_IB][2];
 #pragma unroll
-      for (u32 u = 0; u < SPF_U; ++u) {
-        const u64 j = jb + u * 32 + lane;
-        c[u] = j < E1 ? e_ctx[j] : NONE32;
-        t[u] = j < E1 ? e_time[j] : 0ull;
+  for (u32 il = 0; il < SP_IB; ++il)
+#pragma unroll
+    for (u32 h = 0; h < 2; ++h) csum[il][h] = cmax[il][h] = clo[il][h] = chi[il][h] = 0;
+  for (u32 rb = r_begin; rb < r_end; rb += SP_PR) {
+    // entry ranges of the round's ranks: [b, m) row i0, [m, e) row i0 + 1, ...
+    u64 myb = 0, mym = 0, mye = 0;
+    if (lane < SP_PR && rb + lane < r_end) {
+      const u64 row = row_off[rank_at(S, rb + lane)] + 1 + i0;
+      myb = entry_off[row];
+      mym = entry_off[row + min(1u, nrow)];
+      mye = entry_off[row + nrow];
+    }
+    u64 b[SP_PR], m[SP_PR], len[SP_PR + 1];
+    len[0] = 0;
+#pragma unroll
+    for (u32 p = 0; p < SP_PR; ++p) {
+      b[p] = __shfl_sync(FULL, myb, p);
+      m[p] = __shfl_sync(FULL, mym, p);
+      len[p + 1] = len[p] + (__shfl_sync(FULL, mye, p) - b[p]);
+    }
+    const u64 total = len[SP_PR];
+    for (u64 vb = 0; vb < total; vb += 32 * SP_CU) {
+      u32 c[SP_CU];
+      u64 t[SP_CU];
+      u32 slot[SP_CU];
+#pragma unroll
+      for (u32 u = 0; u < SP_CU; ++u) {
+        const u64 v = vb + u * 32 + lane;
+        u32 p = 0;
+#pragma unroll
+        for (u32 q = 1; q < SP_PR; ++q) p += (v >= len[q]) ? 1u : 0u;
+        u64 bp = b[0], lp = len[0], mp = m[0];
+#pragma unroll
+        for (u32 q = 1; q < SP_PR; ++q)
+          if (p == q) {
+            bp = b[q];
+            lp = len[q];
+            mp = m[q];
+          }
+        const u64 jj = bp + (v - lp);
+        slot[u] = p * SP_IB + ((v < total && SP_IB > 1 && jj >= mp) ? 1u : 0u);
+        c[u] = v < total ? e_ctx[jj] : NONE32;
+        t[u] = v < total ? e_time[jj] : 0ull;
       }
 #pragma unroll
-      for (u32 u = 0; u < SPF_U; ++u) k[u] = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
-#pragma unroll
-      for (u32 u = 0; u < SPF_U; ++u) {
-        const u64 j = jb + u * 32 + lane;
-        if (j >= E1) break;
-        while (rowo[cur + 1] <= j) ++cur;
-        if (k[u] == NONE32 || k[u] < k0 || k[u] >= k0 + kc) continue;
-        const u32 kk = k[u] - k0;
-        const u64 tv = t[u];
-        const u128 t2 = (u128)tv * tv;
-        const u32 q = cur * kc + kk;
-        atomicAdd(&cs[q], (unsigned long long)tv);
-        atomicMax(&cm[q], (unsigned long long)tv);
-        atomic_add_u128(&cl[q], &ch[q], t2);
-        atomicAdd(&ws[kk], (unsigned long long)tv);
-        atomic_add_u128(&wl[kk], &wh[kk], t2);
+      for (u32 u = 0; u < SP_CU; ++u) {
+        const u32 k = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
+        if (k != NONE32 && k >= k0 && k < k0 + 64) buf[slot[u] * 64 + (k - k0)] = t[u];
       }
     }
     __syncwarp();
-    for (u32 kk = lane; kk < kc; kk += 32) {
-      const u64 sm_ = ws[kk];
-      const u128 q = ((u128)wh[kk] << 64) | wl[kk];
-      const double mean = u64_to_f64(sm_) / u64_to_f64(I);
-      const double sd = (I < 2) ? 0.0
-                                : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
-                                       u64_to_f64((u64)I * (I - 1)));
-      cvw[(u64)(k0 + kk) * n + ri] = (mean == 0.0) ? 0.0 : sd / mean;
-      ws[kk] = wl[kk] = wh[kk] = 0;
-    }
+#pragma unroll
+    for (u32 p = 0; p < SP_PR; ++p)
+#pragma unroll
+      for (u32 il = 0; il < SP_IB; ++il)
+#pragma unroll
+        for (u32 h = 0; h < 2; ++h) {
+          u64* cell = &buf[(p * SP_IB + il) * 64 + lane + 32 * h];
+          const u64 v = *cell;
+          *cell = 0;
+          const u128 v2 = (u128)v * v;
+          csum[il][h] += v;
+          cmax[il][h] = max(cmax[il][h], v);
+          const u64 lo = clo[il][h] + (u64)v2;
+          chi[il][h] += (u64)(v2 >> 64) + (lo < clo[il][h] ? 1ull : 0ull);
+          clo[il][h] = lo;
+        }
     __syncwarp();
   }
-  __syncthreads();
-  for (u32 q = threadIdx.x; q < ncell; q += blockDim.x) {
-    const u32 i = q / kc, kk = q % kc;
-    const u64 gq = (u64)i * nk + k0 + kk;
-    if (cs[q]) atomicAdd((unsigned long long*)&g_sum[gq], cs[q]);
-    if (cm[q]) atomicMax((unsigned long long*)&g_max[gq], cm[q]);
-    if (cl[q] | ch[q]) atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)ch[q] << 64) | cl[q]);
-  }
+#pragma unroll
+  for (u32 il = 0; il < SP_IB; ++il)
+#pragma unroll
+    for (u32 h = 0; h < 2; ++h) {
+      const u32 k = k0 + lane + 32 * h;
+      if (il >= nrow || k >= nk) continue;
+      const u64 gq = (u64)(i0 + il) * nk + k;
+      if (csum[il][h]) atomicAdd((unsigned long long*)&g_sum[gq], (unsigned long long)csum[il][h]);
+      if (cmax[il][h]) atomicMax((unsigned long long*)&g_max[gq], (unsigned long long)cmax[il][h]);
+      if (clo[il][h] | chi[il][h])
+        atomic_add_u128(&g_sqlo[gq], &g_sqhi[gq], ((u128)chi[il][h] << 64) | clo[il][h]);
+    }
 }
 
-// One warp per context: sums in ascending iteration / rank order (the
-// oracle's rounding).  The lanes fetch 32 consecutive terms at a time and
-// every lane adds them in order from shuffles, so the loads overlap while
-// the additions stay sequential.
+// Sum of each context's per-rank CV terms (a column of n values of cvw,
+// context-major) in the fixed pairwise order of the definition: level by
+// level, element i of the next level is v[2i] + v[2i+1], an odd last element
+// moves up unchanged.  One CTA per context; levels ping-pong between cvw and
+// tmp.
+__global__ void __launch_bounds__(256) k_sp_pairwise(double* cvw, double* tmp, u32 n,
+                                                     double* within) {
+  const u32 k = blockIdx.x;
+  double* src = cvw + (u64)k * n;
+  double* dst = tmp + (u64)k * n;
+  u32 cnt = n;
+  while (cnt > 1) {
+    const u32 m = cnt / 2;
+    for (u32 i = threadIdx.x; i < m; i += blockDim.x) dst[i] = src[2 * i] + src[2 * i + 1];
+    if ((cnt & 1) && threadIdx.x == 0) dst[m] = src[cnt - 1];
+    cnt = m + (cnt & 1);
+    double* x = src;
+    src = dst;
+    dst = x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) within[k] = (n == 0) ? 0.0 : src[0];
+}
+
+// One warp per context: the iteration sums in ascending order (the
+// oracle's rounding; the lanes fetch 32 iterations at a time and every lane
+// adds them in order from shuffles) and the finished per-context results.
 __global__ void k_sp_final_k(u32 nk, u32 n, u32 I, const u64* g_sum, const u64* g_max,
-                             const u64* g_sqlo, const u64* g_sqhi, const double* cvw,
+                             const u64* g_sqlo, const u64* g_sqhi, const double* within,
                              ta_speedup_ctx* per) {
   const int lane = threadIdx.x & 31;
   const u32 k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -761,22 +749,7 @@ __global__ void k_sp_final_k(u32 nk, u32 n, u32 I, const u64* g_sum, const u64* 
       across += __shfl_sync(FULL, term, x);
     }
   }
-  double within = 0.0;
-  if (I > 0) {
-    const double* col = cvw + (u64)k * n;
-    double v = (lane < n) ? col[lane] : 0.0;
-    for (u32 r0 = 0; r0 < n; r0 += 32) {
-      const double nv = (r0 + 32 + lane < n) ? col[r0 + 32 + lane] : 0.0;  // next chunk
-      const u32 m = min(32u, n - r0);
-      double w[32];
-#pragma unroll
-      for (u32 x = 0; x < 32; ++x) w[x] = __shfl_sync(FULL, v, x);  // all issued first
-#pragma unroll
-      for (u32 x = 0; x < 32; ++x)
-        if (x < m) within += w[x];
-      v = nv;
-    }
-  }
+  const double w_sum = (I > 0) ? within[k] : 0.0;
   if (lane != 0) return;
   const u128 G = (u128)n * A - B;
   ta_speedup_ctx p;
@@ -792,7 +765,7 @@ __global__ void k_sp_final_k(u32 nk, u32 n, u32 I, const u64* g_sum, const u64* 
     p.avg_max = u64_to_f64(A) / u64_to_f64(I);
     p.savings_per_iter = u128_to_f64(G) / u128_to_f64((u128)n * I);
     p.cv_across = across / u64_to_f64(I);
-    p.cv_within = within / u64_to_f64(n);
+    p.cv_within = w_sum / u64_to_f64(n);
   }
   p.total_reduction = u128_to_f64(G) / u64_to_f64(n);
   p.share = 0.0;
@@ -1051,26 +1024,7 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
-  // contexts per fused pass: the cells of all I* iterations must fit
-  u32 kcf = 0;
   if (I > 0) {
-    const u64 per = 32ull * I + 24ull * SPF_NW, fixed = 8ull * SPF_NW * (I + 1);
-    if (fixed < SPF_SMEM_MAX) kcf = (u32)std::min<u64>(nk, (SPF_SMEM_MAX - fixed) / per);
-  }
-  if (I > 0 && kcf >= std::min<u32>(nk, 8)) {
-    const u64 smem = spf_smem(kcf, I);
-    cudaFuncSetAttribute(k_sp_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int per_sm = std::max<int>(1, (int)(SPF_SMEM_MAX / smem));
-    const int grid = std::max(1, std::min<int>(c->num_sms * per_sm,
-                                               (int)((n + SPF_NW - 1) / SPF_NW)));
-    for (u32 k0 = 0; k0 < nk; k0 += kcf) {
-      k_sp_fused<<<grid, SPF_NW * 32, smem, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
-                                                        e->e_time, kmap, k0,
-                                                        std::min(kcf, nk - k0), nk, I, cvw, gs,
-                                                        gm, gl, gh);
-      L.count();
-    }
-  } else if (I > 0) {
     const int grid = std::max(1, std::min<int>(c->num_sms * 8, (int)((n + SP_NW - 1) / SP_NW)));
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
       k_sp_within<<<grid, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
@@ -1078,21 +1032,17 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
                                                       nk, I, cvw);
       L.count();
     }
-    const u32 dk = std::min<u32>(nk, SP_CELLS);
-    const u32 di = std::max<u32>(1, std::min<u32>(I, SP_CELLS / dk));
-    const u32 n_itiles = (I + di - 1) / di, n_ktiles = (nk + dk - 1) / dk;
-    // enough items to fill the GPU, each with a sizeable group of ranks
-    const u64 tiles = (u64)n_itiles * n_ktiles;
-    const u64 want_items = (u64)c->num_sms * 32;
-    u64 groups = std::max<u64>(1, want_items / tiles);
-    groups = std::min<u64>(groups, std::max<u64>(1, (n + 255) / 256));
-    const u32 rank_group = (u32)((n + groups - 1) / groups);
-    groups = (n + rank_group - 1) / rank_group;
+    // cells: enough warps to fill the GPU, each with a sizeable group of ranks
+    const u32 n_ib = (I + SP_IB - 1) / SP_IB, n_kb = (nk + 63) / 64;
+    const u64 tiles = (u64)n_ib * n_kb;
+    const u64 want = (u64)c->num_sms * 48;
+    u64 groups = std::max<u64>(1, std::min<u64>((want + tiles - 1) / tiles, (n + 63) / 64));
+    const u32 group = (u32)((n + groups - 1) / groups);
+    groups = (n + group - 1) / group;
     const u64 n_items = tiles * groups;
-    const int grid2 = (int)std::min<u64>((u64)c->num_sms * 8, (n_items + SP_NW - 1) / SP_NW);
-    k_sp_cells<<<grid2, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
-                                                    e->e_time, kmap, nk, I, di, dk, n_itiles,
-                                                    n_ktiles, rank_group, n_items, gs, gm, gl, gh);
+    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, 0, L.stream>>>(
+        dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, kmap, nk, I, n_ib, n_kb, group,
+        n_items, gs, gm, gl, gh);
     L.count();
   }
   ta_speedup_ctx* dper;
@@ -1104,7 +1054,14 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     TRY(tmp.get_n(nk, &dper, "per ctx"));
     TRY(tmp.get_n(1, &dtot, "total"));
   }
-  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, cvw,
+  double *cvw2, *wsum;
+  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw2, "cv terms"));
+  TRY(tmp.get_n(nk, &wsum, "within sums"));
+  if (I > 0) {
+    k_sp_pairwise<<<nk, 256, 0, L.stream>>>(cvw, cvw2, n, wsum);
+    L.count();
+  }
+  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, wsum,
                                                                   dper);
   k_sp_total<<<1, 1, 0, L.stream>>>(nk, n, I, excluded, t_app, dper, dtot);
   L.count(2);
