@@ -457,6 +457,73 @@ __device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, cons
                                          u32& nb, u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs,
                                          u64 eo, u32 C, int lane) {
   const bool listed = nrun <= RL;
+  // Fast path, the common case of iterations that repeat: every context of
+  // the row is already in the union and each appears in one run only.  Then
+  // the runs' union ranks are distinct (checked by storing each run's index
+  // at its rank and reading it back), a 128-bit mask of the ranks present
+  // gives each run its entry position, and every run is written straight to
+  // its entry.
+  if (listed && nb > 0 && nb <= RS) {
+    u32* present = sm.ctx;  // 4 words of the stage serve as the rank mask
+    if (lane < RS / 32) present[lane] = 0;
+    __syncwarp();
+    u32 rk[RL / 32];
+    bool ok = true;
+#pragma unroll
+    for (u32 it = 0; it < RL / 32; ++it) {
+      const u32 k = lane + 32 * it;
+      rk[it] = 0;
+      if (k < nrun) {
+        const u32 c = rl.ctx[k], w = c >> 5, word = bm.L1[w];
+        ok = ok && ((word >> (c & 31)) & 1u);
+        rk[it] = bm.pre[w] + __popc(word & ((1u << (c & 31)) - 1u));
+        if (ok) {
+          sm.cnt[rk[it]] = k;
+          atomicOr(&present[rk[it] >> 5], 1u << (rk[it] & 31));
+        }
+      }
+    }
+    if (__all_sync(FULL, ok)) {
+      __syncwarp();
+#pragma unroll
+      for (u32 it = 0; it < RL / 32; ++it) {
+        const u32 k = lane + 32 * it;
+        if (k < nrun) ok = ok && sm.cnt[rk[it]] == k;
+      }
+      if (__all_sync(FULL, ok)) {
+        u32 pm[RS / 32], before[RS / 32 + 1];
+        before[0] = 0;
+#pragma unroll
+        for (u32 q = 0; q < RS / 32; ++q) {
+          pm[q] = present[q];
+          before[q + 1] = before[q] + __popc(pm[q]);
+        }
+#pragma unroll
+        for (u32 it = 0; it < RL / 32; ++it) {
+          const u32 k = lane + 32 * it;
+          if (k < nrun) {
+            const u32 r = rk[it];
+            u32 pos = 0;
+#pragma unroll
+            for (u32 q = 0; q < RS / 32; ++q)
+              if (q == (r >> 5)) pos = before[q] + __popc(pm[q] & ((1u << (r & 31)) - 1u));
+            const u64 t0 = rl.ts[k];
+            const u32 p0 = rl.pos[k];
+            const bool more = k + 1 < nrun;
+            const u64 t1 = more ? rl.ts[k + 1] : ts_end;
+            const u32 p1 = more ? rl.pos[k + 1] : (u32)(e - s);
+            const u64 g = eo + pos;
+            A.e_ctx[g] = rl.ctx[k];
+            A.e_time[g] = t1 >= t0 ? t1 - t0 : 0ull;
+            A.e_cnt[g] = p1 - p0;
+          }
+        }
+        __syncwarp();
+        return before[RS / 32];
+      }
+    }
+    __syncwarp();
+  }
   u32 fresh = listed ? mark_runs_new(bm, tw, rl, nrun, lane)
                      : mark_row_samples(A, bm, tw, s, e, C, lane);
   fresh = __reduce_add_sync(FULL, fresh);
