@@ -296,13 +296,12 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   u64* meta;
   TRY(tmp.get(64, (void**)&meta, "csr meta"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
-  const size_t gbm_bytes =
-      P.bm_in_smem ? 0 : (size_t)P.grid * (P.threads / 32) * bm_words(e->C) * 4;
+  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.warps() * bm_words(e->C) * 4;
   if (gbm_bytes) {
     TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "csr bitmaps"));
     cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
   }
-  const size_t gn = (size_t)P.grid * (P.threads / 32) * P.gst_cap;
+  const size_t gn = (size_t)P.warps() * P.gst_cap;
   TRY(tmp.get_n(gn, &A.gst_ctx, "csr stage"));
   TRY(tmp.get_n(gn, &A.gst_cnt, "csr stage"));
   TRY(tmp.get_n(gn, &A.gst_time, "csr stage"));

@@ -450,7 +450,7 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(check_flags(b, "ta_batch_plan"));
   // exclusive and inclusive CSR
   b->XP = plan_rank_csr(b->R, b->Cmax, c->num_sms);
-  const u64 rg = (u64)b->XP.grid * (b->XP.threads / 32) * b->XP.gst_cap;
+  const u64 rg = b->XP.warps() * b->XP.gst_cap;
   u32 *xg_ctx, *xg_cnt, *xg_dep, *xg_par, *x_cnt_r, *xgbm = nullptr;
   u64 *xg_time, *x_scan;
   TRY(b->own_n(rg, &xg_ctx, "csr stage"));
@@ -461,7 +461,7 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(b->own_n(b->R, &x_cnt_r, "csr counts"));
   TRY(b->own_n(scan_scratch_elems(b->R), &x_scan, "csr scan"));
   if (!b->XP.bm_in_smem) {
-    const u64 words = (u64)b->XP.grid * (b->XP.threads / 32) * bm_words(b->Cmax);
+    const u64 words = b->XP.warps() * bm_words(b->Cmax);
     TRY(b->own_n(words, &xgbm, "csr bitmaps"));
     cudaMemsetAsync(xgbm, 0, words * 4, c->stream);
   }

@@ -961,6 +961,7 @@ namespace {
 constexpr u32 RSR = 256;           // staged entries per warp in shared memory
 constexpr u32 DEPTH_BUCKETS = 64;  // depth range handled by the bucket sweep
 constexpr u32 BUCKET_MAX = 1024;   // closure size handled by the bucket sweep
+constexpr int RU = 8;              // entries per lane in flight (exclusive)
 
 struct RankSmem {
   static constexpr u32 time_off = 0;                 // u64[RSR]
@@ -971,6 +972,7 @@ struct RankSmem {
   static constexpr u32 bucket_off = par_off + 4 * RSR;  // u32[DEPTH_BUCKETS + 1], u16[BUCKET_MAX]
   static constexpr u32 fixed_write =
       (bucket_off + 4 * (DEPTH_BUCKETS + 1) + 2 * BUCKET_MAX + 15) & ~15u;
+  static constexpr u32 fixed_write0 = dep_off;  // exclusive: time, ctx, cnt only
 };
 
 struct RStage {
@@ -988,7 +990,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
-  const u32 fixed = WRITE ? RankSmem::fixed_write : 0u;
+  const u32 fixed = WRITE ? (MODE == 0 ? RankSmem::fixed_write0 : RankSmem::fixed_write) : 0u;
   const u32 wbytes = fixed + (BMS ? bmw * 4 : 0);
   unsigned char* ws = sm + (size_t)warp * wbytes;
   const u64 gw = (u64)blockIdx.x * NW + warp;
@@ -1002,9 +1004,11 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     ss.time = (u64*)(ws + RankSmem::time_off);
     ss.ctx = (u32*)(ws + RankSmem::ctx_off);
     ss.cnt = (u32*)(ws + RankSmem::cnt_off);
-    ss.dep = (u32*)(ws + RankSmem::dep_off);
-    ss.par = (u32*)(ws + RankSmem::par_off);
-    bucket_base = (u32*)(ws + RankSmem::bucket_off);
+    if (MODE == 1) {
+      ss.dep = (u32*)(ws + RankSmem::dep_off);
+      ss.par = (u32*)(ws + RankSmem::par_off);
+      bucket_base = (u32*)(ws + RankSmem::bucket_off);
+    }
     const u64 gbase = gw * (u64)A.gst_cap;
     gs.time = A.gst_time + gbase;
     gs.ctx = A.gst_ctx + gbase;
@@ -1020,15 +1024,15 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
-      for (u64 j0 = E0; j0 < E1; j0 += 128) {
-        u32 c[4];
+      for (u64 j0 = E0; j0 < E1; j0 += 32 * RU) {
+        u32 c[RU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RU; ++u) {
           const u64 j = j0 + 32 * u + lane;
           c[u] = j < E1 ? A.in_ctx[j] : NONE32;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < RU; ++u)
           if (c[u] != NONE32 && !bm_has(bm, c[u])) bm_set(bm, c[u]);
       }
     } else {
@@ -1058,11 +1062,11 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     }
     __syncwarp();
     if (MODE == 0) {
-      for (u64 j0 = E0; j0 < E1; j0 += 128) {
-        u32 c[4], n[4];
-        u64 t[4];
+      for (u64 j0 = E0; j0 < E1; j0 += 32 * RU) {
+        u32 c[RU], n[RU];
+        u64 t[RU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RU; ++u) {
           const u64 j = j0 + 32 * u + lane;
           const bool ok = j < E1;
           c[u] = ok ? A.in_ctx[j] : NONE32;
@@ -1070,7 +1074,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
           n[u] = ok ? A.in_cnt[j] : 0u;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < RU; ++u) {
           if (c[u] == NONE32) continue;
           const u32 k = bm_rank(bm, c[u]);
           atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t[u]);
@@ -1166,39 +1170,42 @@ RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms) {
   P.threads = RANK_NW * 32;
   const size_t bm = (size_t)bm_words(C) * 4;
   P.bm_in_smem = RankSmem::fixed_write + bm <= 16 * 1024;
-  P.smem_count = (P.bm_in_smem ? bm : 0) * RANK_NW;
-  P.smem = (RankSmem::fixed_write + (P.bm_in_smem ? bm : 0)) * RANK_NW;
-  const void* ks[4];
+  const size_t bms = P.bm_in_smem ? bm : 0;
+  P.smem[0][0] = P.smem[1][0] = bms * RANK_NW;
+  P.smem[0][1] = (RankSmem::fixed_write0 + bms) * RANK_NW;
+  P.smem[1][1] = (RankSmem::fixed_write + bms) * RANK_NW;
+  const void* ks[2][2];
   if (P.bm_in_smem) {
-    ks[0] = (const void*)k_rank_pass<RANK_NW, 0, false, true>;
-    ks[1] = (const void*)k_rank_pass<RANK_NW, 0, true, true>;
-    ks[2] = (const void*)k_rank_pass<RANK_NW, 1, false, true>;
-    ks[3] = (const void*)k_rank_pass<RANK_NW, 1, true, true>;
+    ks[0][0] = (const void*)k_rank_pass<RANK_NW, 0, false, true>;
+    ks[0][1] = (const void*)k_rank_pass<RANK_NW, 0, true, true>;
+    ks[1][0] = (const void*)k_rank_pass<RANK_NW, 1, false, true>;
+    ks[1][1] = (const void*)k_rank_pass<RANK_NW, 1, true, true>;
   } else {
-    ks[0] = (const void*)k_rank_pass<RANK_NW, 0, false, false>;
-    ks[1] = (const void*)k_rank_pass<RANK_NW, 0, true, false>;
-    ks[2] = (const void*)k_rank_pass<RANK_NW, 1, false, false>;
-    ks[3] = (const void*)k_rank_pass<RANK_NW, 1, true, false>;
+    ks[0][0] = (const void*)k_rank_pass<RANK_NW, 0, false, false>;
+    ks[0][1] = (const void*)k_rank_pass<RANK_NW, 0, true, false>;
+    ks[1][0] = (const void*)k_rank_pass<RANK_NW, 1, false, false>;
+    ks[1][1] = (const void*)k_rank_pass<RANK_NW, 1, true, false>;
   }
-  int occ = 1 << 20;
-  for (int i = 0; i < 4; ++i) {
-    const size_t s = (i & 1) ? P.smem : P.smem_count;
-    cudaFuncSetAttribute(ks[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s);
-    int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ks[i], P.threads, s);
-    occ = std::min(occ, std::max(o, 1));
-  }
+  for (int m = 0; m < 2; ++m)
+    for (int w = 0; w < 2; ++w) {
+      cudaFuncSetAttribute(ks[m][w], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)P.smem[m][w]);
+      int o = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, ks[m][w], P.threads, P.smem[m][w]);
+      P.grid[m][w] = (int)std::max<u64>(
+          1, std::min<u64>((u64)num_sms * std::max(o, 1), ((u64)R + RANK_NW - 1) / RANK_NW));
+    }
   P.n_units = R;
-  P.grid = (int)std::min<u64>((u64)num_sms * occ, ((u64)R + RANK_NW - 1) / RANK_NW);
   P.gst_cap = C;
   return P;
 }
 
 template <int MODE, bool WRITE>
 static void rank_launch(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
-  const size_t smem = WRITE ? P.smem : P.smem_count;
-  if (P.bm_in_smem) k_rank_pass<RANK_NW, MODE, WRITE, true><<<P.grid, P.threads, smem, L.stream>>>(A);
-  else k_rank_pass<RANK_NW, MODE, WRITE, false><<<P.grid, P.threads, smem, L.stream>>>(A);
+  const size_t smem = P.smem[MODE][WRITE ? 1 : 0];
+  const int grid = P.grid[MODE][WRITE ? 1 : 0];
+  if (P.bm_in_smem) k_rank_pass<RANK_NW, MODE, WRITE, true><<<grid, P.threads, smem, L.stream>>>(A);
+  else k_rank_pass<RANK_NW, MODE, WRITE, false><<<grid, P.threads, smem, L.stream>>>(A);
 }
 
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {

@@ -148,11 +148,18 @@ struct RankCsrArgs {
   SetMap sets;
 };
 struct RankCsrPlan {
-  int threads, grid;
-  size_t smem, smem_count;
+  int threads;
+  int grid[2][2];     // [mode][write]: CTAs of each kernel (its own occupancy)
+  size_t smem[2][2];  // [mode][write]: dynamic shared memory per CTA
   bool bm_in_smem;
   u32 gst_cap;
   u32 n_units;
+  u64 warps() const {  // per-warp scratch (bitmaps, stages) covers every kernel
+    int g = 0;
+    for (int m = 0; m < 2; ++m)
+      for (int w = 0; w < 2; ++w) g = std::max(g, grid[m][w]);
+    return (u64)g * (threads / 32);
+  }
 };
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
