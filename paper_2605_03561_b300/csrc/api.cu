@@ -202,6 +202,10 @@ void ta_experiment::disown(void* p) {
 
 namespace {
 
+// Longest total of ancestor lists (entries) the inclusive rollup builds;
+// deeper trees use the level-by-level sweep.
+constexpr u64 kAncMax = 1ull << 28;
+
 // Tensor: count pass, scan of per-tile counts, exact allocation, write pass.
 ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   (void)d;
@@ -337,6 +341,25 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   A.gst_cap = P.gst_cap;
   A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
   double* acc = mode == 0 ? &c->prof.exclusive_ms : &c->prof.inclusive_ms;
+  if (mode == 1) {  // ancestor lists of the tree, unless they would be too long
+    PhaseTimer timer(c, acc);
+    u32* len;
+    u64 *aoff, *ascr;
+    TRY(tmp.get_n(std::max<u32>(e->C, 1), &len, "ancestor lengths"));
+    TRY(tmp.get_n((u64)e->C + 1, &aoff, "ancestor offsets"));
+    TRY(tmp.get_n(scan_scratch_elems(e->C), &ascr, "ancestor scan"));
+    launch_anc_offsets(L, e->depth, e->C, len, aoff, meta + 2, ascr);
+    u64 total = 0;
+    TRY(copy(c, &total, meta + 2, 8));
+    TRY(sync_check(c, "inclusive (ancestors)"));
+    if (total <= kAncMax) {
+      u32* anc;
+      TRY(tmp.get_n(std::max<u64>(total, 1), &anc, "ancestor lists"));
+      launch_anc_fill(L, e->parent, e->C, aoff, anc, SetMap{});
+      A.anc_off = aoff;
+      A.anc = anc;
+    }
+  }
   {
     PhaseTimer timer(c, acc);
     launch_rank_count(L, P, A);

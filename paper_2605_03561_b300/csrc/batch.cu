@@ -465,6 +465,29 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
     TRY(b->own_n(words, &xgbm, "csr bitmaps"));
     cudaMemsetAsync(xgbm, 0, words * 4, c->stream);
   }
+  // ancestor lists of every set's tree for the inclusive rollup (the trees do
+  // not change between runs), unless they would be too long
+  u64* anc_off = nullptr;
+  u32* anc = nullptr;
+  {
+    u32* len;
+    u64 *aoff, *ascr, *atot;
+    TRY(b->own_n(b->Ctot, &len, "ancestor lengths"));
+    TRY(b->own_n((u64)b->Ctot + 1, &aoff, "ancestor offsets"));
+    TRY(b->own_n(scan_scratch_elems(b->Ctot), &ascr, "ancestor scan"));
+    TRY(b->own_n(1, &atot, "ancestor total"));
+    launch_anc_offsets(L, b->depth, b->Ctot, len, aoff, atot, ascr);
+    u64 total = 0;
+    TRY(copy(c, &total, atot, 8));
+    TRY(sync_check(c, "batch: ancestors"));
+    if (total <= (1ull << 28)) {
+      TRY(b->own_n(total, &anc, "ancestor lists"));
+      launch_anc_fill(L, b->parent, b->Ctot, aoff, anc, b->sets);
+      anc_off = aoff;
+    } else {
+      anc = nullptr;
+    }
+  }
   for (int mode = 0; mode < 2; ++mode) {
     RankCsrArgs& X = b->X[mode];
     std::memset(&X, 0, sizeof X);
@@ -488,6 +511,10 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
     }
     X.parent = b->parent;
     X.depth = b->depth;
+    if (mode == 1) {
+      X.anc_off = anc_off;
+      X.anc = anc;
+    }
     X.out_off = out.off;
     X.out_cnt = x_cnt_r;
     X.total = b->meta + 3 + mode;

@@ -161,6 +161,43 @@ __global__ void k_n_iter(const u64* __restrict__ row_off_of_rank, u32 R, u32* n_
   if (r < R) n_iter[r] = (u32)(row_off_of_rank[r + 1] - row_off_of_rank[r] - 1);
 }
 
+// ---------------------------------------------------------------------------
+// Ancestor lists: context v's list is v, parent(v), ..., the root.
+__global__ void k_anc_len(const u32* __restrict__ depth, u32 C, u32* len) {
+  const u32 v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < C) len[v] = depth[v] + 1;
+}
+
+__global__ void k_anc_fill(const u32* __restrict__ parent, u32 C, const u64* __restrict__ anc_off,
+                           u32* anc, SetMap sets) {
+  const u32 v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= C) return;
+  const u32 base = sets.S ? sets.set_ctx0[set_of_ctx(sets, v)] : 0u;
+  u64 q = anc_off[v];
+  const u64 q1 = anc_off[v + 1];
+  u32 c = v - base;  // local id
+  while (q < q1) {
+    anc[q++] = c;
+    const u32 p = parent[base + c];
+    if (p == NONE32) break;
+    c = p;
+  }
+}
+
+void launch_anc_offsets(const Launch& L, const u32* depth, u32 C, u32* len, u64* anc_off,
+                        u64* total, u64* scratch) {
+  k_anc_len<<<(C + 255) / 256, 256, 0, L.stream>>>(depth, C, len);
+  L.count();
+  scan_exclusive(L, len, C, anc_off, total, scratch);
+  cudaMemcpyAsync(anc_off + C, total, 8, cudaMemcpyDeviceToDevice, L.stream);
+}
+
+void launch_anc_fill(const Launch& L, const u32* parent, u32 C, const u64* anc_off, u32* anc,
+                     const SetMap& sets) {
+  k_anc_fill<<<(C + 255) / 256, 256, 0, L.stream>>>(parent, C, anc_off, anc, sets);
+  L.count();
+}
+
 void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_iter) {
   k_n_iter<<<(R + 255) / 256, 256, 0, L.stream>>>(row_off_of_rank, R, n_iter);
   L.count();
@@ -975,6 +1012,16 @@ struct RankSmem {
   static constexpr u32 fixed_write0 = dep_off;  // exclusive: time, ctx, cnt only
 };
 
+// Inclusive through ancestor lists: a stage of time, ctx, cnt only, larger
+// (an inclusive set is the closure of the exclusive one).
+constexpr u32 RSR2 = 512;
+struct RankSmem2 {
+  static constexpr u32 time_off = 0;
+  static constexpr u32 ctx_off = 8 * RSR2;
+  static constexpr u32 cnt_off = ctx_off + 4 * RSR2;
+  static constexpr u32 fixed_write = cnt_off + 4 * RSR2;
+};
+
 struct RStage {
   u64* time;
   u32* ctx;
@@ -990,7 +1037,10 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const u32 bmw = bm_words(A.C);
-  const u32 fixed = WRITE ? (MODE == 0 ? RankSmem::fixed_write0 : RankSmem::fixed_write) : 0u;
+  const u32 fixed = !WRITE ? 0u
+                    : MODE == 0 ? RankSmem::fixed_write0
+                    : MODE == 1 ? RankSmem::fixed_write
+                                : RankSmem2::fixed_write;
   const u32 wbytes = fixed + (BMS ? bmw * 4 : 0);
   unsigned char* ws = sm + (size_t)warp * wbytes;
   const u64 gw = (u64)blockIdx.x * NW + warp;
@@ -1000,7 +1050,15 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
   RStage ss, gs;
   u32* bucket_base = nullptr;
-  if (WRITE) {
+  if (WRITE && MODE == 2) {
+    ss.time = (u64*)(ws + RankSmem2::time_off);
+    ss.ctx = (u32*)(ws + RankSmem2::ctx_off);
+    ss.cnt = (u32*)(ws + RankSmem2::cnt_off);
+    const u64 gbase = gw * (u64)A.gst_cap;
+    gs.time = A.gst_time + gbase;
+    gs.ctx = A.gst_ctx + gbase;
+    gs.cnt = A.gst_cnt + gbase;
+  } else if (WRITE) {
     ss.time = (u64*)(ws + RankSmem::time_off);
     ss.ctx = (u32*)(ws + RankSmem::ctx_off);
     ss.cnt = (u32*)(ws + RankSmem::cnt_off);
@@ -1035,7 +1093,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         for (int u = 0; u < RU; ++u)
           if (c[u] != NONE32 && !bm_has(bm, c[u])) bm_set(bm, c[u]);
       }
-    } else {
+    } else if (MODE == 1) {
       E0 = A.in_off[r];
       E1 = A.in_off[r + 1];
       for (u64 j = E0 + lane; j < E1; j += 32) {
@@ -1043,6 +1101,21 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         for (u32 step = 0; c != NONE32 && step <= A.max_depth; ++step) {
           if (bm_test_set(bm, c)) break;
           c = A.parent[cbase + c];
+        }
+      }
+    } else {  // the closure: every ancestor of every exclusive context
+      E0 = A.in_off[r];
+      E1 = A.in_off[r + 1];
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 x = A.in_ctx[j];
+        const u64 a1 = A.anc_off[cbase + x + 1];
+        for (u64 q = A.anc_off[cbase + x]; q < a1; q += 4) {
+          u32 a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = (q + u < a1) ? A.anc[q + u] : NONE32;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (a[u] != NONE32 && !bm_has(bm, a[u])) bm_set(bm, a[u]);
         }
       }
     }
@@ -1080,6 +1153,27 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
           atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t[u]);
           atomicAdd(&st.cnt[k], n[u]);
           st.ctx[k] = c[u];
+        }
+      }
+    } else if (MODE == 2) {
+      // each exclusive value goes to every context on its root path
+      for (u64 j = E0 + lane; j < E1; j += 32) {
+        const u32 x = A.in_ctx[j];
+        const u64 t = A.in_time[j];
+        const u32 n = A.in_cnt[j];
+        const u64 a1 = A.anc_off[cbase + x + 1];
+        for (u64 q = A.anc_off[cbase + x]; q < a1; q += 4) {
+          u32 a[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[u] = (q + u < a1) ? A.anc[q + u] : NONE32;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (a[u] == NONE32) continue;
+            const u32 k = bm_rank(bm, a[u]);
+            atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t);
+            atomicAdd(&st.cnt[k], n);
+            st.ctx[k] = a[u];
+          }
         }
       }
     } else {
@@ -1156,7 +1250,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
     }
     };
-    if (nnz <= RSR) run(ss);
+    if (nnz <= (MODE == 2 ? RSR2 : RSR)) run(ss);
     else run(gs);
     bm_clear_warp(bm, lane);
     __syncwarp();
@@ -1171,22 +1265,27 @@ RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms) {
   const size_t bm = (size_t)bm_words(C) * 4;
   P.bm_in_smem = RankSmem::fixed_write + bm <= 16 * 1024;
   const size_t bms = P.bm_in_smem ? bm : 0;
-  P.smem[0][0] = P.smem[1][0] = bms * RANK_NW;
+  P.smem[0][0] = P.smem[1][0] = P.smem[2][0] = bms * RANK_NW;
   P.smem[0][1] = (RankSmem::fixed_write0 + bms) * RANK_NW;
   P.smem[1][1] = (RankSmem::fixed_write + bms) * RANK_NW;
-  const void* ks[2][2];
+  P.smem[2][1] = (RankSmem2::fixed_write + bms) * RANK_NW;
+  const void* ks[3][2];
   if (P.bm_in_smem) {
     ks[0][0] = (const void*)k_rank_pass<RANK_NW, 0, false, true>;
     ks[0][1] = (const void*)k_rank_pass<RANK_NW, 0, true, true>;
     ks[1][0] = (const void*)k_rank_pass<RANK_NW, 1, false, true>;
     ks[1][1] = (const void*)k_rank_pass<RANK_NW, 1, true, true>;
+    ks[2][0] = (const void*)k_rank_pass<RANK_NW, 2, false, true>;
+    ks[2][1] = (const void*)k_rank_pass<RANK_NW, 2, true, true>;
   } else {
     ks[0][0] = (const void*)k_rank_pass<RANK_NW, 0, false, false>;
     ks[0][1] = (const void*)k_rank_pass<RANK_NW, 0, true, false>;
     ks[1][0] = (const void*)k_rank_pass<RANK_NW, 1, false, false>;
     ks[1][1] = (const void*)k_rank_pass<RANK_NW, 1, true, false>;
+    ks[2][0] = (const void*)k_rank_pass<RANK_NW, 2, false, false>;
+    ks[2][1] = (const void*)k_rank_pass<RANK_NW, 2, true, false>;
   }
-  for (int m = 0; m < 2; ++m)
+  for (int m = 0; m < 3; ++m)
     for (int w = 0; w < 2; ++w) {
       cudaFuncSetAttribute(ks[m][w], cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)P.smem[m][w]);
@@ -1210,6 +1309,7 @@ static void rank_launch(const Launch& L, const RankCsrPlan& P, const RankCsrArgs
 
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
   if (A.mode == 0) rank_launch<0, false>(L, P, A);
+  else if (A.anc) rank_launch<2, false>(L, P, A);
   else rank_launch<1, false>(L, P, A);
   L.count();
   scan_exclusive(L, A.out_cnt, A.R, A.out_off, A.total, A.scan_scratch);
@@ -1218,6 +1318,7 @@ void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs&
 
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
   if (A.mode == 0) rank_launch<0, true>(L, P, A);
+  else if (A.anc) rank_launch<2, true>(L, P, A);
   else rank_launch<1, true>(L, P, A);
   L.count();
 }

@@ -129,6 +129,10 @@ struct RankCsrArgs {
   const u32* in_cnt;
   const u32* parent;
   const u32* depth;
+  // inclusive: per context its ancestors, itself first ([anc_off[v],
+  // anc_off[v+1]) of anc, ids local to the set); null: level-by-level sweep
+  const u64* anc_off;
+  const u32* anc;
   u32* out_cnt;  // [R] count pass
   u64* out_off;  // [R+1] scan
   u32* out_ctx;
@@ -147,16 +151,18 @@ struct RankCsrArgs {
   u32* status;
   SetMap sets;
 };
+// Kernels of the rank passes by variant: 0 exclusive, 1 inclusive by a
+// level-by-level sweep, 2 inclusive through ancestor lists.
 struct RankCsrPlan {
   int threads;
-  int grid[2][2];     // [mode][write]: CTAs of each kernel (its own occupancy)
-  size_t smem[2][2];  // [mode][write]: dynamic shared memory per CTA
+  int grid[3][2];     // [variant][write]: CTAs of each kernel (its own occupancy)
+  size_t smem[3][2];  // [variant][write]: dynamic shared memory per CTA
   bool bm_in_smem;
   u32 gst_cap;
   u32 n_units;
   u64 warps() const {  // per-warp scratch (bitmaps, stages) covers every kernel
     int g = 0;
-    for (int m = 0; m < 2; ++m)
+    for (int m = 0; m < 3; ++m)
       for (int w = 0; w < 2; ++w) g = std::max(g, grid[m][w]);
     return (u64)g * (threads / 32);
   }
@@ -164,6 +170,15 @@ struct RankCsrPlan {
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+
+// Ancestor lists of every context (itself first, then up to the root):
+// anc_off = exclusive scan of depth + 1 (total in *total; len and scratch:
+// C u32 and scan_scratch_elems(C) u64), then the lists.  With sets, parent
+// ids are local to each set's tree and so are the listed ids.
+void launch_anc_offsets(const Launch& L, const u32* depth, u32 C, u32* len, u64* anc_off,
+                        u64* total, u64* scratch);
+void launch_anc_fill(const Launch& L, const u32* parent, u32 C, const u64* anc_off, u32* anc,
+                     const SetMap& sets);
 
 // Batch statistics (stats.cu).
 u64 batch_stats_scratch_bytes(u32 Ctot);

@@ -66,6 +66,26 @@ def test_large_context_count(seed):
     check_stats(a, e, ta.EXCLUSIVE, tau=(2, 1))
 
 
+def test_inclusive_paths_shallow_and_very_deep():
+    # A 30,000-node chain: the ancestor lists of all contexts would exceed the
+    # bound, so the inclusive rollup takes the level-by-level sweep; the other
+    # cases here take the ancestor lists.
+    rng = np.random.default_rng(8)
+    C = 30000
+    parent = np.arange(-1, C - 1, dtype=np.int64).astype(np.uint32)
+    parent[0] = NONE
+    ctx = np.concatenate([rng.integers(C - 200, C, size=60), rng.integers(0, C, size=40)])
+    ctx[0] = 5
+    ctx[60] = 5
+    ts = np.concatenate([np.cumsum(rng.integers(1, 9, size=60)),
+                         np.cumsum(rng.integers(1, 9, size=40))]).astype(np.uint64)
+    d = dict(rank_off=np.array([0, 60, 100], np.uint64), ts=ts, ctx=ctx.astype(np.uint32),
+             parent=parent, marker=5)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.INCLUSIVE, tau=(1, 1))
+
+
 def test_many_iterations_speedup_paths():
     # I* = 1200: twelve contexts take the multi-kernel path, three the fused one
     d = edge.case("many_iterations", 4)
