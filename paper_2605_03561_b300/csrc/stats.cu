@@ -575,7 +575,7 @@ __global__ void __launch_bounds__(SP_NW * 32)
   }
 }
 
-// (b) Cells (i, k) over ranks.  A warp owns the cells of SP_IB iterations
+// (b) Cells (i, k) over ranks.  A warp owns the cells of SP_IB iteration(s)
 // [i0, i0 + SP_IB) and 64 contexts [k0, k0 + 64) for a group of ranks and
 // keeps them in registers: lane l holds contexts k0 + l and k0 + l + 32
 // (sum, max, 128-bit sum of squares).  It reads the SP_IB rows of SP_PR ranks
@@ -585,11 +585,11 @@ __global__ void __launch_bounds__(SP_NW * 32)
 // suffice -- and every lane then folds its contexts' values into its
 // registers, absent ones reading 0.  The group's cells go to the global
 // cells with one set of atomics per warp.
-constexpr u32 SP_IB = 2;   // iterations per warp
+constexpr u32 SP_IB = 1;   // iterations per warp
 constexpr u32 SP_PR = 4;   // ranks per round
 constexpr u32 SP_CU = 8;   // entries per lane in flight per round
 
-__global__ void __launch_bounds__(SP_NW * 32, 2)
+__global__ void __launch_bounds__(SP_NW * 32, 3)
     k_sp_cells(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
                const u64* __restrict__ entry_off, const u32* __restrict__ e_ctx,
                const u64* __restrict__ e_time, const u32* __restrict__ kmap, u32 nk, u32 I,
