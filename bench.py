@@ -257,6 +257,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ----------------------------------------------------------------- replicas --
+def max_over_ranks(ms: float, world: int) -> float:
+    """The slowest rank's time: N independent replicas (weak scaling) finish
+    when the slowest does.  Needs an initialised process group when world > 1."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def aggregate_rate(world: int, units_per_rank: int, steps: int, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return world * units_per_rank * steps / (ms / 1000.0)
+
+
 # --------------------------------------------------------------- baselines --
 def oracle_sample(w, n_ranks, args):
     """Run the oracle on ranks [0, n_ranks) of the workload; returns (records, s)."""
@@ -593,16 +612,12 @@ def run_gpu(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     tc1 = clocks.mark()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t[0])
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     clk = clocks.stop(tc0, tc1)
     prof = ctx.profile(reset=True)
     launches = ctx.launches() - launches0
     ms_step = ms / args.steps
-    value = world * N * args.steps / (ms / 1000.0)
+    value = aggregate_rate(world, N, args.steps, ms)
 
     # dominant kernel: the iteration-tensor kernel, timed with events on its stream
     peaks, peak_kind = measured_peaks()
