@@ -431,7 +431,9 @@ ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off, const
  *   args      tau = tau_num / tau_den (NULL: 3/1); outlier_cap = capacity of
  *             the outlier list over all sets (0: 2^20).
  * Every product of set s is the product ta_load_traces + ta_context_stats
- * (metric exclusive, all ranks, all contexts) would give for that set alone;
+ * (metric exclusive, all ranks, all contexts) -- and, when requested in
+ * set_args, ta_potential_speedup and ta_topology_rollup -- would give for
+ * that set alone;
  * ta_batch_get_set returns zero-copy device views with offsets relative to
  * the set (valid until ta_batch_free).  Errors: as ta_load_traces for any
  * set (the message names the set).  ta_batch_plan ends with one run; when
@@ -439,9 +441,25 @@ ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t* off, const
  * info's n_outliers holds the full count, every set's outlier list is empty
  * and the other products are valid. */
 typedef struct ta_batch ta_batch;
+/* Optional per-set requests, computed for every set in the same graph:
+ * the potential speedup (as ta_potential_speedup over all ranks of the set)
+ * and the rack rollup of one context (as ta_topology_rollup, exclusive
+ * metric, all ranks).  Host arrays, copied at plan time. */
+typedef struct ta_batch_set_args {
+  const uint32_t* speedup_ctxs;    /* sorted, unique set-local contexts; NULL = none */
+  uint32_t n_speedup_ctxs;
+  uint32_t topo_ctx;               /* rollup context (set-local)                     */
+  uint64_t app_time_ns;            /* speedup denominator; 0 = longest rank span     */
+  const uint32_t* node_of_rank;    /* [n_ranks]; NULL = no rollup                    */
+  const uint32_t* rack_of_node;    /* [n_nodes]                                      */
+  const uint32_t* chassis_of_node; /* [n_nodes]                                      */
+  uint32_t n_nodes, n_chassis, n_racks;
+  uint32_t topo_tau_num, topo_tau_den, topo_min_ranks;
+} ta_batch_set_args;
 typedef struct ta_batch_args {
   uint32_t tau_num, tau_den;
   uint64_t outlier_cap;
+  const ta_batch_set_args* set_args; /* [n_sets] or NULL */
 } ta_batch_args;
 typedef struct ta_batch_info {
   uint32_t n_sets, n_ranks;
@@ -463,6 +481,23 @@ typedef struct ta_batch_set_view {
   const ta_ctx_stats* stats;   /* [n_ctx]                           */
   const ta_outlier* outliers;  /* sorted by (ctx, rank); local ids  */
   uint64_t n_outliers;
+  /* potential speedup (NULL / 0 when not requested) */
+  const ta_speedup_ctx* speedup; /* [n_speedup], in the request's order */
+  const ta_speedup_total* speedup_total;
+  uint32_t n_speedup, n_flagged_racks;
+  /* rack rollup (NULL / 0 when not requested), as ta_topo_out */
+  uint32_t n_nodes, n_chassis, n_racks, reserved;
+  const uint32_t* node_outliers;
+  const uint64_t* node_sum;
+  const uint32_t* node_ranks;
+  const uint8_t* node_flag;
+  const uint32_t* chassis_flagged;
+  const uint32_t* chassis_nodes;
+  const uint64_t* chassis_sum;
+  const uint32_t* rack_flagged;
+  const uint32_t* rack_nodes;
+  const uint64_t* rack_sum;
+  const uint32_t* flagged_racks;
 } ta_batch_set_view;
 ta_status ta_batch_plan(ta_ctx* ctx, const ta_trace_desc* sets, uint32_t n_sets,
                         const ta_batch_args* args, ta_batch** out);

@@ -126,8 +126,15 @@ class Profile(C.Structure):
                 ("tensor_rows", u64)]
 
 
+class BatchSetArgs(C.Structure):
+    _fields_ = [("speedup_ctxs", P), ("n_speedup_ctxs", u32), ("topo_ctx", u32),
+                ("app_time_ns", u64), ("node_of_rank", P), ("rack_of_node", P),
+                ("chassis_of_node", P), ("n_nodes", u32), ("n_chassis", u32), ("n_racks", u32),
+                ("topo_tau_num", u32), ("topo_tau_den", u32), ("topo_min_ranks", u32)]
+
+
 class BatchArgs(C.Structure):
-    _fields_ = [("tau_num", u32), ("tau_den", u32), ("outlier_cap", u64)]
+    _fields_ = [("tau_num", u32), ("tau_den", u32), ("outlier_cap", u64), ("set_args", P)]
 
 
 class BatchInfo(C.Structure):
@@ -142,7 +149,12 @@ class BatchInfo(C.Structure):
 class BatchSetView(C.Structure):
     _fields_ = [("n_ranks", u32), ("n_ctx", u32), ("tensor", TensorView),
                 ("exclusive", CsrView), ("inclusive", CsrView), ("stats", P), ("outliers", P),
-                ("n_outliers", u64)]
+                ("n_outliers", u64), ("speedup", P), ("speedup_total", P), ("n_speedup", u32),
+                ("n_flagged_racks", u32), ("n_nodes", u32), ("n_chassis", u32), ("n_racks", u32),
+                ("reserved", u32), ("node_outliers", P), ("node_sum", P), ("node_ranks", P),
+                ("node_flag", P), ("chassis_flagged", P), ("chassis_nodes", P),
+                ("chassis_sum", P), ("rack_flagged", P), ("rack_nodes", P), ("rack_sum", P),
+                ("flagged_racks", P)]
 
 
 class ServeConfig(C.Structure):
@@ -570,9 +582,12 @@ class Batch:
     """Many independent trace sets analysed as one unit (ta_batch_plan): the
     whole analysis is one captured CUDA graph, replayed by run()."""
 
-    def __init__(self, ctx: Context, sets, tau=(3, 1), outlier_cap=1 << 20):
+    def __init__(self, ctx: Context, sets, tau=(3, 1), outlier_cap=1 << 20, set_args=None):
         """sets: sequence of (rank_off, ts, ctx, parent, marker), either all
-        numpy arrays (host) or all torch CUDA tensors (device)."""
+        numpy arrays (host) or all torch CUDA tensors (device).  set_args:
+        optional per-set dicts (or None) with keys speedup_ctxs, app_time_ns,
+        and topology (node_of_rank, rack_of_node, chassis_of_node, n_racks,
+        n_chassis) with topo_ctx, topo_tau, min_ranks."""
         self.ctx = ctx
         keep, descs = [], (TraceDesc * len(sets))()
         for d, (rank_off, ts, cx, parent, marker) in zip(descs, sets):
@@ -596,6 +611,30 @@ class Batch:
         a = BatchArgs()
         a.tau_num, a.tau_den = tau
         a.outlier_cap = outlier_cap
+        sargs = None
+        if set_args is not None:
+            sargs = (BatchSetArgs * len(sets))()
+            for x, sa in zip(sargs, set_args):
+                if not sa:
+                    continue
+                if sa.get("speedup_ctxs") is not None:
+                    kc = _np(sa["speedup_ctxs"], np.uint32)
+                    keep.append(kc)
+                    x.speedup_ctxs, x.n_speedup_ctxs = kc.ctypes.data, len(kc)
+                x.app_time_ns = int(sa.get("app_time_ns", 0))
+                topo = sa.get("topology")
+                if topo is not None:
+                    arrs = [_np(topo[k], np.uint32)
+                            for k in ("node_of_rank", "rack_of_node", "chassis_of_node")]
+                    keep.extend(arrs)
+                    x.node_of_rank, x.rack_of_node, x.chassis_of_node = (
+                        z.ctypes.data for z in arrs)
+                    x.n_nodes, x.n_racks = len(arrs[1]), int(topo["n_racks"])
+                    x.n_chassis = int(topo["n_chassis"])
+                    x.topo_ctx = int(sa.get("topo_ctx", 0))
+                    x.topo_tau_num, x.topo_tau_den = sa.get("topo_tau", (3, 1))
+                    x.topo_min_ranks = int(sa.get("min_ranks", 1))
+            a.set_args = C.cast(sargs, P)
         h = P()
         _check(lib().ta_batch_plan(ctx.h, descs, len(sets), C.byref(a), C.byref(h)))
         self.h = h
@@ -655,6 +694,29 @@ class Batch:
         out["outliers"] = dict(ctx=np.array([x.ctx for x in ol[:m]], np.uint32),
                                rank=np.array([x.rank for x in ol[:m]], np.uint32),
                                z=np.array([x.z for x in ol[:m]], np.float64))
+        if v.n_speedup:
+            ns = int(v.n_speedup)
+            sp = _dev_structs(v.speedup, ns, SpeedupCtx, dev)
+            d = {f: np.array([getattr(x, f) for x in sp[:ns]]) for f, _ in SpeedupCtx._fields_}
+            d["G"] = [int(lo) + (int(hi) << 64) for lo, hi in zip(d["G_lo"], d["G_hi"])]
+            tt = _dev_structs(v.speedup_total, 1, SpeedupTotal, dev)[0]
+            t = {f: getattr(tt, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
+            t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
+            out["speedup"] = (d, t)
+        if v.n_nodes:
+            nn, nc, nr = int(v.n_nodes), int(v.n_chassis), int(v.n_racks)
+            out["topology"] = dict(
+                node_outliers=_dev_to_np(v.node_outliers, nn, np.uint32, dev),
+                node_sum=_dev_to_np(v.node_sum, nn, np.uint64, dev),
+                node_ranks=_dev_to_np(v.node_ranks, nn, np.uint32, dev),
+                node_flag=_dev_to_np(v.node_flag, nn, np.uint8, dev),
+                chassis_flagged=_dev_to_np(v.chassis_flagged, nc, np.uint32, dev),
+                chassis_nodes=_dev_to_np(v.chassis_nodes, nc, np.uint32, dev),
+                chassis_sum=_dev_to_np(v.chassis_sum, nc, np.uint64, dev),
+                rack_flagged=_dev_to_np(v.rack_flagged, nr, np.uint32, dev),
+                rack_nodes=_dev_to_np(v.rack_nodes, nr, np.uint32, dev),
+                rack_sum=_dev_to_np(v.rack_sum, nr, np.uint64, dev),
+                flagged_racks=_dev_to_np(v.flagged_racks, int(v.n_flagged_racks), np.uint32, dev))
         return out
 
 

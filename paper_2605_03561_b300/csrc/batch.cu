@@ -110,6 +110,14 @@ struct ta_batch {
   u64 n_out = 0;
   u64 device_bytes = 0;
   std::vector<Block> owned;
+  // optional per-set speedup and rack rollup
+  const ta_batch_set_args* set_args = nullptr;
+  BatchSpeedupArgs SP{};
+  BatchTopoArgs RT{};
+  bool has_sp = false, has_topo = false;
+  u64 sp_cells = 0, sp_cv = 0, rt_nodes = 0, rt_chassis = 0, rt_racks = 0;
+  std::vector<u32> h_k0, h_nflag;
+  std::vector<u64> h_node0, h_ch0, h_rk0;
 
   ta_status own(size_t bytes, void** p, const char* what) {
     void* q = dalloc(ctx, bytes);
@@ -192,6 +200,8 @@ void enqueue_all(ta_batch* b) {
     launch_rank_write(L, b->XP, b->X[mode]);
   }
   enqueue_stats(b);
+  if (b->has_sp) launch_batch_speedup(L, b->SP, b->sp_cells, b->sp_cv);
+  if (b->has_topo) launch_batch_topology(L, b->RT, b->rt_nodes, b->rt_chassis, b->rt_racks);
   enqueue_views(b);
 }
 
@@ -264,6 +274,213 @@ ta_status tune_tensor(ta_batch* b, bool write) {
   TRY(sync_check(c, "batch: tuning"));
   b->shape = pick;
   b->TP = plan_tensor(b->Cmax, b->N, c->num_sms, b->shape);
+  return TA_OK;
+}
+
+// Per-set speedup and rack-rollup requests: host-side layout of every set's
+// share of the work and outputs, from the products of the plan's first run.
+ta_status plan_rollups(ta_batch* b) {
+  const ta_batch_set_args* sa = b->set_args;
+  if (!sa) return TA_OK;
+  ta_ctx* c = b->ctx;
+  const u32 S = b->S;
+  bool any_sp = false, any_topo = false;
+  for (u32 s = 0; s < S; ++s) {
+    any_sp = any_sp || (sa[s].speedup_ctxs && sa[s].n_speedup_ctxs);
+    any_topo = any_topo || sa[s].node_of_rank;
+  }
+  std::vector<u32> n_iter(b->R);
+  std::vector<u64> span(b->R);
+  TRY(copy(c, n_iter.data(), b->n_iter, (u64)b->R * 4));
+  TRY(copy(c, span.data(), b->span, (u64)b->R * 8));
+  TRY(sync_check(c, "batch: rollup sizes"));
+  if (any_sp) {
+    constexpr u32 GROUP = 256;  // ranks per cells work item
+    std::vector<u32> kmap(b->Ctot, NONE32), k0(S + 1, 0), istar(S, 0);
+    std::vector<u64> cell0(S + 1, 0), cv0(S + 1, 0), item0(S + 1, 0), excl(S, 0), tapp(S, 0);
+    for (u32 s = 0; s < S; ++s) {
+      const u32 nk = (sa[s].speedup_ctxs) ? sa[s].n_speedup_ctxs : 0u;
+      const u32 r0 = b->h_rank0[s], r1 = b->h_rank0[s + 1], n = r1 - r0;
+      for (u32 k = 0; k < nk; ++k) {
+        const u32 cx = sa[s].speedup_ctxs[k];
+        if (cx >= b->h_C[s] || (k && cx <= sa[s].speedup_ctxs[k - 1]))
+          return fail(TA_ERR_INVALID_ARG, "batch: set %u: speedup contexts must be sorted, "
+                      "unique, < n_ctx", s);
+        kmap[b->h_ctx0[s] + cx] = k;
+      }
+      k0[s + 1] = k0[s] + nk;
+      u32 I = 0xFFFFFFFFu;
+      u64 sum_it = 0, mspan = 0;
+      for (u32 r = r0; r < r1; ++r) {
+        I = std::min(I, n_iter[r]);
+        sum_it += n_iter[r];
+        mspan = std::max(mspan, span[r]);
+      }
+      if (nk == 0) I = 0;
+      istar[s] = I;
+      excl[s] = nk ? sum_it - (u64)n * I : 0;
+      tapp[s] = sa[s].app_time_ns ? sa[s].app_time_ns : mspan;
+      cell0[s + 1] = cell0[s] + (u64)I * nk;
+      cv0[s + 1] = cv0[s] + (u64)n * nk;
+      const u64 items = (nk && I) ? (u64)I * ((nk + 63) / 64) * ((n + GROUP - 1) / GROUP) : 0;
+      item0[s + 1] = item0[s] + items;
+    }
+    BatchSpeedupArgs& P = b->SP;
+    P.S = S;
+    P.R = b->R;
+    P.nk_total = k0[S];
+    P.group = GROUP;
+    P.n_items = item0[S];
+    P.rank_set = b->sets.rank_set;
+    P.set_rank0 = b->sets.set_rank0;
+    P.set_ctx0 = b->sets.set_ctx0;
+    P.row_off = b->row_off;
+    P.entry_off = b->entry_off;
+    P.e_ctx = b->e_ctx;
+    P.e_time = b->e_time;
+    u32 *d_kmap = nullptr, *d_k0 = nullptr, *d_istar = nullptr;
+    u64 *d_cell0 = nullptr, *d_cv0 = nullptr, *d_item0 = nullptr, *d_excl = nullptr,
+        *d_tapp = nullptr;
+    TRY(b->own_n(b->Ctot, &d_kmap, "speedup map"));
+    TRY(b->own_n(S + 1, &d_k0, "speedup layout"));
+    TRY(b->own_n(S, &d_istar, "speedup layout"));
+    TRY(b->own_n(S + 1, &d_cell0, "speedup layout"));
+    TRY(b->own_n(S + 1, &d_cv0, "speedup layout"));
+    TRY(b->own_n(S + 1, &d_item0, "speedup layout"));
+    TRY(b->own_n(S, &d_excl, "speedup layout"));
+    TRY(b->own_n(S, &d_tapp, "speedup layout"));
+    TRY(copy(c, d_kmap, kmap.data(), kmap.size() * 4));
+    TRY(copy(c, d_k0, k0.data(), (S + 1) * 4));
+    TRY(copy(c, d_istar, istar.data(), S * 4));
+    TRY(copy(c, d_cell0, cell0.data(), (S + 1) * 8));
+    TRY(copy(c, d_cv0, cv0.data(), (S + 1) * 8));
+    TRY(copy(c, d_item0, item0.data(), (S + 1) * 8));
+    TRY(copy(c, d_excl, excl.data(), S * 8));
+    TRY(copy(c, d_tapp, tapp.data(), S * 8));
+    P.kmap = d_kmap;
+    P.k0 = d_k0;
+    P.istar = d_istar;
+    P.cell0 = d_cell0;
+    P.cv0 = d_cv0;
+    P.item0 = d_item0;
+    P.excluded = d_excl;
+    P.t_app = d_tapp;
+    b->sp_cells = cell0[S];
+    b->sp_cv = cv0[S];
+    TRY(b->own_n(std::max<u64>(b->sp_cells, 1), &P.g_sum, "speedup cells"));
+    TRY(b->own_n(std::max<u64>(b->sp_cells, 1), &P.g_max, "speedup cells"));
+    TRY(b->own_n(std::max<u64>(b->sp_cells, 1), &P.g_sqlo, "speedup cells"));
+    TRY(b->own_n(std::max<u64>(b->sp_cells, 1), &P.g_sqhi, "speedup cells"));
+    TRY(b->own_n(std::max<u64>(b->sp_cv, 1), &P.cvw, "speedup cv terms"));
+    TRY(b->own_n(std::max<u64>(b->sp_cv, 1), &P.cvw2, "speedup cv terms"));
+    TRY(b->own_n(std::max<u32>(P.nk_total, 1), &P.wsum, "speedup sums"));
+    TRY(b->own_n(std::max<u32>(P.nk_total, 1), &P.per, "speedup per context"));
+    TRY(b->own_n(S, &P.tot, "speedup totals"));
+    b->h_k0 = k0;
+    b->has_sp = P.nk_total > 0;
+  }
+  if (any_topo) {
+    std::vector<u32> has(S, 0), tctx(S, 0), tn(S, 1), td(S, 1), mr(S, 1), node(b->R, 0);
+    std::vector<u64> node0(S + 1, 0), ch0(S + 1, 0), rk0(S + 1, 0);
+    std::vector<u32> rack, chassis;
+    for (u32 s = 0; s < S; ++s) {
+      const ta_batch_set_args& a = sa[s];
+      const u32 r0 = b->h_rank0[s], n = b->h_rank0[s + 1] - r0;
+      if (a.node_of_rank) {
+        if (!a.rack_of_node || !a.chassis_of_node || !a.n_nodes || !a.n_racks || !a.n_chassis ||
+            a.topo_ctx >= b->h_C[s] || !a.topo_tau_den || !a.topo_min_ranks)
+          return fail(TA_ERR_INVALID_ARG, "batch: set %u: rack rollup arguments", s);
+        for (u32 i = 0; i < n; ++i) {
+          if (a.node_of_rank[i] >= a.n_nodes)
+            return fail(TA_ERR_INVALID_ARG, "batch: set %u: node_of_rank >= n_nodes", s);
+          node[r0 + i] = a.node_of_rank[i];
+        }
+        for (u32 i = 0; i < a.n_nodes; ++i) {
+          if (a.rack_of_node[i] >= a.n_racks || a.chassis_of_node[i] >= a.n_chassis)
+            return fail(TA_ERR_INVALID_ARG, "batch: set %u: rack or chassis id out of range", s);
+          rack.push_back(a.rack_of_node[i]);
+          chassis.push_back(a.chassis_of_node[i]);
+        }
+        has[s] = 1;
+        tctx[s] = a.topo_ctx;
+        tn[s] = a.topo_tau_num;
+        td[s] = a.topo_tau_den;
+        mr[s] = a.topo_min_ranks;
+      }
+      node0[s + 1] = node0[s] + (has[s] ? a.n_nodes : 0);
+      ch0[s + 1] = ch0[s] + (has[s] ? a.n_chassis : 0);
+      rk0[s + 1] = rk0[s] + (has[s] ? a.n_racks : 0);
+    }
+    BatchTopoArgs& T = b->RT;
+    T.S = S;
+    T.R = b->R;
+    T.rank_set = b->sets.rank_set;
+    T.set_ctx0 = b->sets.set_ctx0;
+    T.x_off = b->x.off;
+    T.x_ctx = b->x.ctx;
+    T.x_time = b->x.time;
+    T.stats = b->stats;
+    b->rt_nodes = node0[S];
+    b->rt_chassis = ch0[S];
+    b->rt_racks = rk0[S];
+    u32 *d_has = nullptr, *d_ctx = nullptr, *d_tn = nullptr, *d_td = nullptr, *d_mr = nullptr,
+        *d_node = nullptr, *d_rack = nullptr, *d_ch = nullptr;
+    u64 *d_n0 = nullptr, *d_c0 = nullptr, *d_r0 = nullptr;
+    TRY(b->own_n(S, &d_has, "rollup layout"));
+    TRY(b->own_n(S, &d_ctx, "rollup layout"));
+    TRY(b->own_n(S, &d_tn, "rollup layout"));
+    TRY(b->own_n(S, &d_td, "rollup layout"));
+    TRY(b->own_n(S, &d_mr, "rollup layout"));
+    TRY(b->own_n(b->R, &d_node, "rollup nodes"));
+    TRY(b->own_n(std::max<u64>(b->rt_nodes, 1), &d_rack, "rollup racks"));
+    TRY(b->own_n(std::max<u64>(b->rt_nodes, 1), &d_ch, "rollup chassis"));
+    TRY(b->own_n(S + 1, &d_n0, "rollup layout"));
+    TRY(b->own_n(S + 1, &d_c0, "rollup layout"));
+    TRY(b->own_n(S + 1, &d_r0, "rollup layout"));
+    TRY(copy(c, d_has, has.data(), S * 4));
+    TRY(copy(c, d_ctx, tctx.data(), S * 4));
+    TRY(copy(c, d_tn, tn.data(), S * 4));
+    TRY(copy(c, d_td, td.data(), S * 4));
+    TRY(copy(c, d_mr, mr.data(), S * 4));
+    TRY(copy(c, d_node, node.data(), (u64)b->R * 4));
+    if (!rack.empty()) {
+      TRY(copy(c, d_rack, rack.data(), rack.size() * 4));
+      TRY(copy(c, d_ch, chassis.data(), chassis.size() * 4));
+    }
+    TRY(copy(c, d_n0, node0.data(), (S + 1) * 8));
+    TRY(copy(c, d_c0, ch0.data(), (S + 1) * 8));
+    TRY(copy(c, d_r0, rk0.data(), (S + 1) * 8));
+    TRY(sync_check(c, "batch: rollup layout"));
+    T.has = d_has;
+    T.ctx = d_ctx;
+    T.tau_num = d_tn;
+    T.tau_den = d_td;
+    T.min_ranks = d_mr;
+    T.node_of_rank = d_node;
+    T.rack_of_node = d_rack;
+    T.chassis_of_node = d_ch;
+    T.node0 = d_n0;
+    T.chassis0 = d_c0;
+    T.rack0 = d_r0;
+    const u64 nn = std::max<u64>(b->rt_nodes, 1), nc = std::max<u64>(b->rt_chassis, 1),
+              nr = std::max<u64>(b->rt_racks, 1);
+    TRY(b->own_n(nn, &T.node_out, "rollup outputs"));
+    TRY(b->own_n(nn, &T.node_sum, "rollup outputs"));
+    TRY(b->own_n(nn, &T.node_ranks, "rollup outputs"));
+    TRY(b->own_n(nn, &T.node_flag, "rollup outputs"));
+    TRY(b->own_n(nc, &T.ch_flag, "rollup outputs"));
+    TRY(b->own_n(nc, &T.ch_nodes, "rollup outputs"));
+    TRY(b->own_n(nc, &T.ch_sum, "rollup outputs"));
+    TRY(b->own_n(nr, &T.rk_flag, "rollup outputs"));
+    TRY(b->own_n(nr, &T.rk_nodes, "rollup outputs"));
+    TRY(b->own_n(nr, &T.rk_sum, "rollup outputs"));
+    TRY(b->own_n(nr, &T.flagged, "rollup outputs"));
+    TRY(b->own_n(S, &T.n_flagged, "rollup outputs"));
+    b->h_node0 = node0;
+    b->h_ch0 = ch0;
+    b->h_rk0 = rk0;
+    b->has_topo = b->rt_nodes > 0;
+  }
   return TA_OK;
 }
 
@@ -552,6 +769,7 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(b->own_n(P2, &b->zs, "outlier z"));
   TRY(b->own_n(std::max<u64>(b->outlier_cap, 1), &b->outl, "outliers"));
   TRY(b->own_n(S + 1, &b->set_out0, "outlier offsets"));
+  TRY(plan_rollups(b));
   // per-set relative offsets
   std::vector<u64> h_ro((u64)b->R + 1), h_xo((u64)b->R + 1), h_io((u64)b->R + 1);
   TRY(copy(c, h_ro.data(), b->row_off, h_ro.size() * 8));
@@ -634,6 +852,7 @@ ta_status ta_batch_plan(ta_ctx* c, const ta_trace_desc* sets, uint32_t n_sets,
     b->tau_num = args->tau_num;
     b->tau_den = args->tau_den;
     b->outlier_cap = args->outlier_cap;
+    b->set_args = args->set_args;
   }
   if (b->tau_den == 0) {
     delete b;
@@ -670,6 +889,10 @@ ta_status ta_batch_run(ta_batch* b) {
                         b->set_out0);
   b->h_out0.resize(b->S + 1);
   TRY(copy(c, b->h_out0.data(), b->set_out0, (b->S + 1) * 8));
+  if (b->has_topo) {
+    b->h_nflag.resize(b->S);
+    TRY(copy(c, b->h_nflag.data(), b->RT.n_flagged, (u64)b->S * 4));
+  }
   TRY(sync_check(c, "ta_batch_run"));
   if (b->n_out > b->outlier_cap)
     return fail(TA_ERR_CAPACITY, "batch: %llu outliers, capacity %llu",
@@ -741,6 +964,39 @@ ta_status ta_batch_get_set(const ta_batch* b, uint32_t s, ta_batch_set_view* v) 
   } else {
     v->outliers = nullptr;
     v->n_outliers = 0;
+  }
+  v->speedup = nullptr;
+  v->speedup_total = nullptr;
+  v->n_speedup = 0;
+  if (b->has_sp && b->h_k0[s + 1] > b->h_k0[s]) {
+    v->speedup = b->SP.per + b->h_k0[s];
+    v->speedup_total = b->SP.tot + s;
+    v->n_speedup = b->h_k0[s + 1] - b->h_k0[s];
+  }
+  v->n_flagged_racks = 0;
+  v->n_nodes = v->n_chassis = v->n_racks = v->reserved = 0;
+  v->node_outliers = v->node_ranks = v->chassis_flagged = v->chassis_nodes = nullptr;
+  v->rack_flagged = v->rack_nodes = v->flagged_racks = nullptr;
+  v->node_sum = v->chassis_sum = v->rack_sum = nullptr;
+  v->node_flag = nullptr;
+  if (b->has_topo && b->h_node0[s + 1] > b->h_node0[s]) {
+    const BatchTopoArgs& T = b->RT;
+    const u64 n0 = b->h_node0[s], c0 = b->h_ch0[s], r0s = b->h_rk0[s];
+    v->n_nodes = (u32)(b->h_node0[s + 1] - n0);
+    v->n_chassis = (u32)(b->h_ch0[s + 1] - c0);
+    v->n_racks = (u32)(b->h_rk0[s + 1] - r0s);
+    v->n_flagged_racks = b->h_nflag.size() == b->S ? b->h_nflag[s] : 0;
+    v->node_outliers = T.node_out + n0;
+    v->node_sum = (const uint64_t*)T.node_sum + n0;
+    v->node_ranks = T.node_ranks + n0;
+    v->node_flag = T.node_flag + n0;
+    v->chassis_flagged = T.ch_flag + c0;
+    v->chassis_nodes = T.ch_nodes + c0;
+    v->chassis_sum = (const uint64_t*)T.ch_sum + c0;
+    v->rack_flagged = T.rk_flag + r0s;
+    v->rack_nodes = T.rk_nodes + r0s;
+    v->rack_sum = (const uint64_t*)T.rk_sum + r0s;
+    v->flagged_racks = T.flagged + r0s;
   }
   return TA_OK;
 }

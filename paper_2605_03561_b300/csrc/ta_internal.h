@@ -189,6 +189,70 @@ void launch_batch_stats(const Launch& L, u32 R, u32 Ctot, const u64* off, const 
 void launch_batch_outliers(const Launch& L, u64* keys, double* zs, u64 n, const SetMap& sets,
                            ta_outlier* out, u64* set_off);
 
+// Potential speedup and rack rollup of every set of a batch (batch_rollup.cu).
+// Per set s: contexts k0[s] .. k0[s+1] of the global context index (kmap maps
+// a set-local context, offset by the set's first context, to its index in
+// the set's list), I* istar[s], cells at cell0[s] (I* x nk), CV terms at
+// cv0[s] (nk x ranks), cells work items at item0[s].
+struct BatchSpeedupArgs {
+  u32 S, R, nk_total, group;
+  u64 n_items;
+  const u32* rank_set;
+  const u32* set_rank0;
+  const u32* set_ctx0;
+  const u64* row_off;
+  const u64* entry_off;
+  const u32* e_ctx;
+  const u64* e_time;
+  const u32* kmap;
+  const u32* k0;
+  const u32* istar;
+  const u64* cell0;
+  const u64* cv0;
+  const u64* item0;
+  const u64* excluded;
+  const u64* t_app;
+  u64 *g_sum, *g_max, *g_sqlo, *g_sqhi;
+  double *cvw, *cvw2, *wsum;
+  ta_speedup_ctx* per;
+  ta_speedup_total* tot;
+};
+struct BatchTopoArgs {
+  u32 S, R;
+  const u32* rank_set;
+  const u32* set_ctx0;
+  const u64* x_off;
+  const u32* x_ctx;
+  const u64* x_time;
+  const ta_ctx_stats* stats;
+  const u32* has;
+  const u32* ctx;
+  const u32* tau_num;
+  const u32* tau_den;
+  const u32* min_ranks;
+  const u32* node_of_rank;     // [R] node within the rank's set
+  const u32* rack_of_node;     // nodes of all sets, concatenated
+  const u32* chassis_of_node;
+  const u64* node0;            // [S+1]
+  const u64* chassis0;         // [S+1]
+  const u64* rack0;            // [S+1]
+  u32* node_out;
+  unsigned long long* node_sum;
+  u32* node_ranks;
+  uint8_t* node_flag;
+  u32* ch_flag;
+  u32* ch_nodes;
+  unsigned long long* ch_sum;
+  u32* rk_flag;
+  u32* rk_nodes;
+  unsigned long long* rk_sum;
+  u32* flagged;
+  u32* n_flagged;  // [S]
+};
+void launch_batch_speedup(const Launch& L, const BatchSpeedupArgs& P, u64 n_cells, u64 n_cv);
+void launch_batch_topology(const Launch& L, const BatchTopoArgs& T, u64 n_nodes, u64 n_chassis,
+                           u64 n_racks);
+
 // Exclusive prefix sums (scan.cu); scratch holds scan_scratch_elems(n) u64.
 u64 scan_scratch_elems(u64 n);
 void scan_exclusive(const Launch& L, const u32* in, u64 n, u64* out, u64* total, u64* scratch);

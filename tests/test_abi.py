@@ -20,6 +20,7 @@ STRUCTS = {"ta_trace_desc": ta.TraceDesc, "ta_experiment_info": ta.ExperimentInf
            "ta_speedup_total": ta.SpeedupTotal, "ta_speedup_out": ta.SpeedupOut,
            "ta_profile": ta.Profile, "ta_batch_args": ta.BatchArgs,
            "ta_batch_info": ta.BatchInfo, "ta_batch_set_view": ta.BatchSetView,
+           "ta_batch_set_args": ta.BatchSetArgs,
            "ta_serve_config": ta.ServeConfig, "ta_query": ta.Query,
            "ta_query_result": ta.QueryResult, "ta_q_stats": ta.QStats,
            "ta_q_topk_entry": ta.QTopkEntry, "ta_q_racks": ta.QRacks}

@@ -142,3 +142,57 @@ def test_batch_rejects_invalid_sets():
     with pytest.raises(ta.TaError) as ei:
         ta.Batch(context(), [_tuple(unsorted), _tuple(good)])
     assert ei.value.status == ta.NOT_SORTED
+
+
+def test_batch_speedup_and_rollup_per_set():
+    # Every set asks for the potential speedup over a context list and a rack
+    # rollup of one context (as ta_potential_speedup / ta_topology_rollup over
+    # all its ranks); sets differ in shape, iterations and topology.
+    from gpu_helpers import SP_FP, SP_INT, simple_topology
+    rng = np.random.default_rng(21)
+    sets = _sets_mixed(4)
+    sets += [synth.generate(synth.preset(1, seed=40 + k, n_ranks=int(rng.integers(8, 40))))
+             for k in range(4)]
+    args = []
+    for k, d in enumerate(sets):
+        R = len(d["rank_off"]) - 1
+        Cn = len(d["parent"])
+        present = np.unique(d["ctx"]) if len(d["ctx"]) else np.array([0], np.uint32)
+        if k % 5 == 4:
+            args.append(None)  # no requests for this set
+            continue
+        kset = np.unique(rng.choice(present, size=min(len(present), 70))).astype(np.uint32)
+        topo = simple_topology(R, int(rng.integers(1, 4)), int(rng.integers(1, 4)), 2)
+        args.append(dict(speedup_ctxs=kset, app_time_ns=0 if k % 2 else 10**9, topology=topo,
+                         topo_ctx=int(rng.choice(present)), topo_tau=(int(rng.integers(1, 3)), 1),
+                         min_ranks=int(rng.integers(1, 3))))
+    b = ta.Batch(context(), [_tuple(d) for d in sets], tau=(2, 1), set_args=args)
+    for s, d in enumerate(sets):
+        got = b.products(s)
+        if args[s] is None:
+            assert "speedup" not in got and "topology" not in got
+            continue
+        tr = oracle.Traces(d["rank_off"], d["ts"], d["ctx"], d["parent"], d["marker"])
+        a = oracle.Analysis(tr)
+        gp, gt = got["speedup"]
+        op, ot = a.speedup(args[s]["speedup_ctxs"], app_time_ns=args[s]["app_time_ns"])
+        for k in SP_INT:
+            assert np.array_equal(gp[k], op[k]), (s, k)
+        for k in SP_FP:
+            close(gp[k], op[k], k)
+        for k in ("i_star", "excluded_iterations", "sum_G", "t_app"):
+            assert gt[k] == ot[k], (s, k)
+        for k in ("total_reduction", "speedup_fraction"):
+            close([gt[k]], [ot[k]], k)
+        t = args[s]["topology"]
+        o = a.topology(args[s]["topo_ctx"], t["node_of_rank"], t["rack_of_node"],
+                       t["chassis_of_node"], t["n_racks"], t["n_chassis"], metric=ta.EXCLUSIVE,
+                       tau=args[s]["topo_tau"], min_ranks=args[s]["min_ranks"])
+        for k in o:
+            assert np.array_equal(got["topology"][k], o[k]), (s, k)
+    # a second replay gives the same results
+    before = b.products(1)
+    b.run()
+    again = b.products(1)
+    if "speedup" in before:
+        assert np.array_equal(before["speedup"][0]["G_lo"], again["speedup"][0]["G_lo"])
