@@ -66,7 +66,9 @@ def make_workload(preset: int, seed: int = 1, pinned: bool = True, ranks: int = 
 
 BATCHED = ("batched: 256 independent trace sets, ranks per set lognormal (median 362, sigma "
            "1.04) in 16..8192, C log-uniform in 100..10,000, trace lengths lognormal (mean 30k, "
-           "sigma 1.0), I=50, jitter 5%, 1% of ranks 1.2-2x on random iterations")
+           "sigma 1.0), I=50, jitter 5%, 1% of ranks 1.2-2x on random iterations; per set: "
+           "tensor, exclusive, inclusive, statistics, potential speedup over its iteration "
+           "program, rack rollup of a communication context")
 SET_ALIGN = 32  # samples; every set of the input arena starts 16-byte aligned
 
 
@@ -90,8 +92,12 @@ def make_batch_workload(n_sets: int, seed: int, device: str, scale: float = 1.0)
                            n_ctx=int(Cn[k]), len_mean=30000.0, len_sigma=1.0,
                            n_segments=int(min(64, Cn[k] - 2)))
         rank_off, parent, info = synth.plan(cfg)
+        truth = synth.truth(cfg, info)
+        segs = np.unique(truth["segment_ctx"]).astype(np.uint32)
+        comm = truth["segment_ctx"][truth["comm_segment"].astype(bool)]
         sets.append(dict(cfg=cfg, rank_off=rank_off, parent=parent, marker=cfg.marker_ctx,
-                         N=int(rank_off[-1])))
+                         N=int(rank_off[-1]), kset=segs, topo=synth.topology(cfg, info),
+                         topo_ctx=int(comm[0]) if len(comm) else int(segs[0])))
         starts.append(total)
         total += (int(rank_off[-1]) + SET_ALIGN - 1) // SET_ALIGN * SET_ALIGN
     t0 = time.time()
@@ -332,7 +338,9 @@ def run_batched(args, ctx, local):
     """The batched form (one graph replay over every set) against plain
     per-experiment calls on the same device-resident sets, same products:
     tensor, exclusive, inclusive, statistics of the exclusive metric over all
-    ranks and contexts (tau = 3) with outliers."""
+    ranks and contexts (tau = 3) with outliers, the potential speedup over
+    each set's iteration-program contexts and the rack rollup of one of its
+    communication contexts (tau = 2)."""
     import torch
     import paper_2605_03561_b300 as ta
     dev = f"cuda:{local}"
@@ -345,8 +353,23 @@ def run_batched(args, ctx, local):
     cap = 1 << 20
     ol = torch.empty(cap * C.sizeof(ta.Outlier), dtype=torch.uint8, device=dev)
 
+    nkmax = max(len(x["kset"]) for x in sets)
+    per = torch.empty(nkmax * C.sizeof(ta.SpeedupCtx), dtype=torch.uint8, device=dev)
+    tot = torch.empty(C.sizeof(ta.SpeedupTotal), dtype=torch.uint8, device=dev)
+    nnmax = max(int(x["topo"]["n_nodes"]) for x in sets)
+    ncmax = max(int(x["topo"]["n_chassis"]) for x in sets)
+    nrmax = max(int(x["topo"]["n_racks"]) for x in sets)
+    tout = {k: torch.empty(n * w, dtype=torch.uint8, device=dev) for k, n, w in [
+        ("node_outliers", nnmax, 4), ("node_sum", nnmax, 8), ("node_ranks", nnmax, 4),
+        ("node_flag", nnmax, 1), ("chassis_flagged", ncmax, 4), ("chassis_nodes", ncmax, 4),
+        ("chassis_sum", ncmax, 8), ("rack_flagged", nrmax, 4), ("rack_nodes", nrmax, 4),
+        ("rack_sum", nrmax, 8), ("flagged_racks", nrmax, 4)]}
+    for x in sets:
+        x["d_kset"] = torch.from_numpy(x["kset"]).to(dev)
+        x["d_topo"] = [torch.from_numpy(x["topo"][k]).to(dev)
+                       for k in ("node_of_rank", "rack_of_node", "chassis_of_node")]
+
     def plain_step():
-        launches = 0
         for x in sets:
             e = ctx.load(x["d_rank_off"], x["ts"], x["ctx"], x["d_parent"], x["marker"],
                          borrow=True)
@@ -355,6 +378,23 @@ def run_batched(args, ctx, local):
             o = ta.StatsOut()
             o.stats, o.outliers, o.outlier_cap = st.data_ptr(), ol.data_ptr(), cap
             ta._check(ta.lib().ta_context_stats(e.h, C.byref(a), C.byref(o)))
+            sa = ta.SpeedupArgs()
+            sa.mem_kind, sa.n_ctxs, sa.ctxs = ta.MEM_DEVICE, len(x["kset"]), x["d_kset"].data_ptr()
+            so = ta.SpeedupOut()
+            so.per_ctx, so.total = per.data_ptr(), tot.data_ptr()
+            ta._check(ta.lib().ta_potential_speedup(e.h, C.byref(sa), C.byref(so)))
+            t = ta.Topology()
+            t.n_nodes, t.n_chassis = int(x["topo"]["n_nodes"]), int(x["topo"]["n_chassis"])
+            t.n_racks, t.mem_kind = int(x["topo"]["n_racks"]), ta.MEM_DEVICE
+            t.node_of_rank, t.rack_of_node, t.chassis_of_node = (z.data_ptr() for z in x["d_topo"])
+            ta_ = ta.TopoArgs()
+            ta_.metric, ta_.ctx, ta_.tau_num, ta_.tau_den, ta_.min_ranks = (
+                ta.EXCLUSIVE, x["topo_ctx"], 2, 1, 1)
+            to = ta.TopoOut()
+            to.mem_kind = ta.MEM_DEVICE
+            for k, v in tout.items():
+                setattr(to, k, v.data_ptr())
+            ta._check(ta.lib().ta_topology_rollup(e.h, C.byref(t), C.byref(ta_), C.byref(to)))
             e.free()
 
     def timed(fn, steps, warmup):
@@ -379,8 +419,10 @@ def run_batched(args, ctx, local):
     steps = max(1, min(args.steps, 3))
     plain_ms, plain_l, plain_clk = timed(plain_step, steps, 1)
     t0 = time.perf_counter()
+    set_args = [dict(speedup_ctxs=x["kset"], topology=x["topo"], topo_ctx=x["topo_ctx"],
+                     topo_tau=(2, 1), min_ranks=1) for x in sets]
     b = ta.Batch(ctx, [(x["d_rank_off"], x["ts"], x["ctx"], x["d_parent"], x["marker"])
-                       for x in sets], tau=(3, 1), outlier_cap=cap)
+                       for x in sets], tau=(3, 1), outlier_cap=cap, set_args=set_args)
     plan_s = time.perf_counter() - t0
     info = b.info()
     batch_ms, batch_l, batch_clk = timed(b.run, args.steps, max(3, args.warmup))
