@@ -1,0 +1,84 @@
+"""Parity at the full plain-at-scale size (100,000 ranks, C = 20,000, about
+2e9 records), in the launch configuration the benchmark times.
+
+The oracle analyses sampled rank ranges one by one (their tensor, exclusive
+and inclusive CSR and spans must match bit for bit); the rest is checked
+through properties that hold at any size: every rank's exclusive times sum to
+its span and its inclusive root equals it, the tensor sums back to the
+exclusive CSR, and the statistics' integer moments equal sums over the
+exclusive CSR."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2605_03561_b300 as ta
+from paper_2605_03561_b300 import synth
+from gpu_helpers import INT_FIELDS, context, per_rank_rows
+
+pytestmark = pytest.mark.gpu
+
+
+def _enough_host_memory(gb):
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024 > gb * 2**30
+    except OSError:
+        pass
+    return False
+
+
+@pytest.mark.skipif(not _enough_host_memory(96), reason="needs ~96 GB of host memory")
+def test_full_size_config3_sampled_and_invariants():
+    cfg = synth.preset(3, seed=1)
+    g = synth.generate(cfg)
+    R = cfg.n_ranks
+    assert R == 100000 and int(g["rank_off"][-1]) > 1.5e9
+    e = context().load(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"])
+    tr = oracle.Traces(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"])
+    t = e.tensor()
+    x = e.csr(ta.EXCLUSIVE)
+    inc = e.csr(ta.INCLUSIVE)
+    span = e.span()
+    rng = np.random.default_rng(5)
+    for r0 in [0, R - 4] + sorted(rng.integers(1, R - 4, size=6).tolist()):
+        a = oracle.Analysis(tr, r0, r0 + 4)
+        ot = a.tensor()
+        assert np.array_equal(t["n_iter"][r0:r0 + 4], ot["n_iter"])
+        for r in range(r0, r0 + 4):
+            assert per_rank_rows(t, r) == per_rank_rows(ot, r - r0), r
+        for g_csr, metric in ((x, ta.EXCLUSIVE), (inc, ta.INCLUSIVE)):
+            o = a.csr(metric)
+            for r in range(r0, r0 + 4):
+                b, q = int(g_csr["off"][r]), int(g_csr["off"][r + 1])
+                ob, oq = int(o["off"][r - r0]), int(o["off"][r - r0 + 1])
+                for k in ("ctx", "time", "cnt"):
+                    assert np.array_equal(g_csr[k][b:q], o[k][ob:oq]), (metric, r, k)
+        assert np.array_equal(span[r0:r0 + 4], a.span())
+    # invariants over every rank
+    xo = x["off"].astype(np.int64)
+    cs = np.concatenate([[0], np.cumsum(x["time"].astype(np.uint64), dtype=np.uint64)])
+    per_rank = cs[xo[1:]] - cs[xo[:-1]]
+    assert np.array_equal(per_rank, span)  # a rank's exclusive times add up to its span
+    io = inc["off"].astype(np.int64)
+    nonempty = np.diff(io) > 0
+    first = io[:-1][nonempty]
+    assert (inc["ctx"][first] == 0).all()  # the root leads every non-empty list
+    assert np.array_equal(inc["time"][first], span[nonempty])
+    tot_t = int(t["e_time"].astype(np.uint64).sum(dtype=np.uint64))
+    assert tot_t == int(x["time"].astype(np.uint64).sum(dtype=np.uint64))
+    assert int(t["e_cnt"].sum(dtype=np.uint64)) == int(g["rank_off"][-1])
+    # statistics of sampled contexts against sums over the exclusive CSR
+    ctxs = np.unique(x["ctx"][rng.integers(0, len(x["ctx"]), size=12)]).astype(np.uint32)
+    gs, _, _, _ = e.stats(ta.EXCLUSIVE, ctxs=ctxs, tau=(3, 1), outlier_cap=1 << 20)
+    for i, c in enumerate(ctxs):
+        sel = x["ctx"] == c
+        vals = x["time"][sel].astype(object)
+        assert int(gs["n"][i]) == R
+        assert int(gs["present"][i]) == int(sel.sum())
+        assert int(gs["s1"][i]) == int(sum(vals))
+        s2 = int(sum(v * v for v in vals))
+        assert int(gs["s2_lo"][i]) + (int(gs["s2_hi"][i]) << 64) == s2
+        assert int(gs["max"][i]) == int(max(vals))
+        assert set(INT_FIELDS) <= set(gs)
