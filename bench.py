@@ -326,9 +326,9 @@ def committed_traffic(preset):
             d = json.load(f)
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_2605_03561_b300", "csrc", "ingest.cu")
+    src = os.path.join(ROOT, "paper_2605_03561_b300", "csrc", "tensor.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if d.get("ingest_cu_sha256_16") != h:
+    if d.get("tensor_cu_sha256_16") != h:
         return None
     return d.get("per_record_bytes")
 

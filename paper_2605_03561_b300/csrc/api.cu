@@ -206,7 +206,9 @@ namespace {
 // deeper trees use the level-by-level sweep.
 constexpr u64 kAncMax = 1ull << 28;
 
-// Tensor: count pass, scan of per-tile counts, exact allocation, write pass.
+// Tensor: count pass, scan of per-tile counts, allocation (rows exactly,
+// entries one slot per run), write pass; compaction when a row repeats a
+// context in several runs.
 ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   (void)d;
   ta_ctx* c = e->ctx;
@@ -223,11 +225,11 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   TRY(tmp.get_n(n_tiles, &A.tile_ents, "tile entries"));
   TRY(tmp.get_n(n_tiles, &A.tile_row_off, "tile row offsets"));
   TRY(tmp.get_n(n_tiles, &A.tile_ent_off, "tile entry offsets"));
-  u64* meta;  // [0] status, [1..2] totals
+  u64* meta;  // [0] status, [1..2] rows, entry slots, [3] distinct entries
   TRY(tmp.get(64, (void**)&meta, "tensor meta"));
   TRY(tmp.get_n(2 * scan_scratch_elems(n_tiles), &A.scan_scratch, "tile scan"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
-  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.warps() * bm_words(e->C) * 4;
+  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.write_warps() * bm_words(e->C) * 4;
   if (gbm_bytes) {
     TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "tensor bitmaps"));
     cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
@@ -246,6 +248,7 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   A.N = N;
   A.status = (u32*)meta;
   A.totals = meta + 1;
+  A.nnz_sum = meta + 3;
   A.gst_cap = P.gst_cap;
   A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
   {
@@ -254,19 +257,19 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     launch_tile_scan(L, A);
     timer.stop_and_sync();
   }
-  u64 h[3];
+  u64 h[4];
   TRY(copy(c, h, meta, sizeof h));
   TRY(sync_check(c, "iteration tensor (count)"));
   TRY(status_from_flags((u32)h[0], "ta_load_traces"));
   e->rows = h[1];
-  e->nnz = h[2];
+  const u64 slots = h[2];
   TRY(e->own((u64)(R + 1) * 8, (void**)&e->row_off, "row_off_of_rank"));
   TRY(e->own((e->rows + 1) * 8, (void**)&e->entry_off, "entry_off"));
-  TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&e->e_ctx, "e_ctx"));
-  TRY(e->own(std::max<u64>(e->nnz, 1) * 8, (void**)&e->e_time, "e_time"));
-  TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&e->e_cnt, "e_cnt"));
+  TRY(e->own(std::max<u64>(slots, 1) * 4, (void**)&e->e_ctx, "e_ctx"));
+  TRY(e->own(std::max<u64>(slots, 1) * 8, (void**)&e->e_time, "e_time"));
+  TRY(e->own(std::max<u64>(slots, 1) * 4, (void**)&e->e_cnt, "e_cnt"));
+  TRY(tmp.get_n(std::max<u64>(e->rows, 1), &A.row_nnz, "row entries"));
   TRY(copy(c, e->row_off + R, &e->rows, 8));
-  TRY(copy(c, e->entry_off + e->rows, &e->nnz, 8));
   A.row_off_of_rank = e->row_off;
   A.entry_off = e->entry_off;
   A.e_ctx = e->e_ctx;
@@ -277,10 +280,49 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     launch_tensor_write(L, P, A);
     timer.stop_and_sync();
   }
-  u64 f = 0;
-  TRY(copy(c, &f, meta, 8));
+  TRY(copy(c, h, meta, sizeof h));
   TRY(sync_check(c, "iteration tensor (write)"));
-  TRY(status_from_flags((u32)f, "ta_load_traces"));
+  TRY(status_from_flags((u32)h[0], "ta_load_traces"));
+  e->nnz = h[3];
+  if (e->nnz > slots) return fail(TA_ERR_STATE, "iteration tensor: %llu entries in %llu slots",
+                                  (unsigned long long)e->nnz, (unsigned long long)slots);
+  if (e->nnz == slots) {  // every row's contexts are distinct across its runs
+    TRY(copy(c, e->entry_off + e->rows, &e->nnz, 8));
+  } else {
+    TensorCompact K{};
+    K.rows = e->rows;
+    K.slot_off = e->entry_off;
+    K.row_nnz = A.row_nnz;
+    K.ctx_in = e->e_ctx;
+    K.time_in = e->e_time;
+    K.cnt_in = e->e_cnt;
+    u64* off;
+    u32 *cx, *cn;
+    u64* tm;
+    TRY(e->own((e->rows + 1) * 8, (void**)&off, "entry_off"));
+    TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&cx, "e_ctx"));
+    TRY(e->own(std::max<u64>(e->nnz, 1) * 8, (void**)&tm, "e_time"));
+    TRY(e->own(std::max<u64>(e->nnz, 1) * 4, (void**)&cn, "e_cnt"));
+    TRY(tmp.get_n(scan_scratch_elems(std::max<u64>(e->rows, 1)), &K.scan_scratch, "row scan"));
+    K.new_off = off;
+    K.ctx_out = cx;
+    K.time_out = tm;
+    K.cnt_out = cn;
+    {
+      PhaseTimer timer(c, &c->prof.tensor_ms);
+      launch_tensor_compact(L, K);
+      timer.stop_and_sync();
+    }
+    TRY(sync_check(c, "iteration tensor (compaction)"));
+    e->disown(e->entry_off);
+    e->disown(e->e_ctx);
+    e->disown(e->e_time);
+    e->disown(e->e_cnt);
+    e->entry_off = off;
+    e->e_ctx = cx;
+    e->e_time = tm;
+    e->e_cnt = cn;
+  }
   c->prof.tensor_launches += 1;
   c->prof.tensor_records += N;
   c->prof.tensor_entries += e->nnz;

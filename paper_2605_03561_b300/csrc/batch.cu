@@ -75,6 +75,11 @@ struct ta_batch {
   u32* e_ctx = nullptr;
   u64* e_time = nullptr;
   u32* e_cnt = nullptr;
+  // tensor slots (one per run) and the compaction into the arrays above, when
+  // some row repeats a context in several runs
+  u64 slots = 0;
+  bool compact = false;
+  TensorCompact TC{};
   Csr x, in;
   ta_ctx_stats* stats = nullptr;
   u64* keys = nullptr;
@@ -163,9 +168,14 @@ void enqueue_tensor_count(ta_batch* b) {
 void enqueue_tensor_write(ta_batch* b) {
   const Launch L = launch_of(b);
   k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
-  k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->nnz);
-  L.count(2);
+  L.count();
+  if (!b->compact) {
+    k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->slots);
+    L.count();
+  }
+  cudaMemsetAsync(b->T.nnz_sum, 0, 8, L.stream);
   launch_tensor_write(L, b->TP, b->T);
+  if (b->compact) launch_tensor_compact(L, b->TC);
   launch_n_iter(L, b->row_off, b->R, b->n_iter);
 }
 
@@ -650,21 +660,49 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(sync_check(c, "batch: tensor count"));
   TRY(status_from_flags((u32)h[0], "ta_batch_plan"));
   b->rows = h[1];
-  b->nnz = h[2];
+  b->slots = h[2];
   TRY(b->own_n(b->rows + 1, &b->entry_off, "entry_off"));
-  TRY(b->own_n(b->nnz, &b->e_ctx, "e_ctx"));
-  TRY(b->own_n(b->nnz, &b->e_time, "e_time"));
-  TRY(b->own_n(b->nnz, &b->e_cnt, "e_cnt"));
+  TRY(b->own_n(b->slots, &b->e_ctx, "e_ctx"));
+  TRY(b->own_n(b->slots, &b->e_time, "e_time"));
+  TRY(b->own_n(b->slots, &b->e_cnt, "e_cnt"));
+  TRY(b->own_n(b->rows, &A.row_nnz, "row entries"));
+  TRY(b->own_n(1, &A.nnz_sum, "tensor entries"));
   A.row_off_of_rank = b->row_off;
   A.entry_off = b->entry_off;
   A.e_ctx = b->e_ctx;
   A.e_time = b->e_time;
   A.e_cnt = b->e_cnt;
   k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
-  k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->nnz);
   TRY(tune_tensor(b, true));
   enqueue_tensor_write(b);
   TRY(check_flags(b, "ta_batch_plan"));
+  TRY(copy(c, &b->nnz, A.nnz_sum, 8));
+  TRY(sync_check(c, "batch: tensor entries"));
+  if (b->nnz > b->slots) return fail(TA_ERR_STATE, "batch: %llu tensor entries in %llu slots",
+                                     (unsigned long long)b->nnz, (unsigned long long)b->slots);
+  if (b->nnz < b->slots) {  // rows that repeat a context: compact into exact arrays
+    TensorCompact& K = b->TC;
+    K.rows = b->rows;
+    K.slot_off = b->entry_off;
+    K.row_nnz = A.row_nnz;
+    K.ctx_in = b->e_ctx;
+    K.time_in = b->e_time;
+    K.cnt_in = b->e_cnt;
+    TRY(b->own_n(b->rows + 1, &b->entry_off, "entry_off"));
+    TRY(b->own_n(b->nnz, &b->e_ctx, "e_ctx"));
+    TRY(b->own_n(b->nnz, &b->e_time, "e_time"));
+    TRY(b->own_n(b->nnz, &b->e_cnt, "e_cnt"));
+    TRY(b->own_n(scan_scratch_elems(std::max<u64>(b->rows, 1)), &K.scan_scratch, "row scan"));
+    K.new_off = b->entry_off;
+    K.ctx_out = b->e_ctx;
+    K.time_out = b->e_time;
+    K.cnt_out = b->e_cnt;
+    b->compact = true;
+    launch_tensor_compact(L, K);
+    TRY(sync_check(c, "batch: tensor compaction"));
+  } else {
+    k_put_u64<<<1, 1, 0, L.stream>>>(b->entry_off + b->rows, b->nnz);
+  }
   // exclusive and inclusive CSR
   b->XP = plan_rank_csr(b->R, b->Cmax, c->num_sms);
   const u64 rg = b->XP.warps() * b->XP.gst_cap;

@@ -1,8 +1,7 @@
 // ingest.cu -- kernels that turn raw traces into the resident products:
 // rank-offset and span validation, calling-context-tree validation and depth,
-// the fused validate + duration + iteration-cut + (rank, iteration, context)
-// aggregation kernel (the iteration tensor of Section V), and the per-rank
-// exclusive / inclusive CSR kernels (Sections II-A and VI-B).
+// ancestor lists, and the per-rank exclusive / inclusive CSR kernels
+// (Sections II-A and VI-B).  The iteration tensor is in tensor.cu.
 #include <algorithm>
 
 #include "ta_internal.h"
@@ -203,131 +202,7 @@ void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_it
   L.count();
 }
 
-// ---------------------------------------------------------------------------
-// The iteration tensor (Section V): two passes over warp tiles, no waiting.
-//
-// A tile is TW consecutive samples; it owns the rows (rank prologues and
-// iterations) that START inside it and reads past its end to finish its last
-// row.  Every warp takes tiles grid-stride and streams a tile 128 samples at a
-// time (4 per lane, 16-byte vector loads, the next step prefetched while the
-// current one is processed): rank starts and marker-run starts cut rows; each
-// run head of a row sets its context's bit in the warp's two-level bitmap.
-//   count pass (contexts only): per tile, rows and distinct entries (bitmap
-//     popcount per row); also validates context ids.
-//   a device scan of the per-tile counts gives every tile its row and entry
-//     offsets and the exact output sizes.
-//   write pass (contexts and timestamps): validates timestamp order; per row a
-//     prefix over the bitmap ranks its contexts in ascending order, a second
-//     pass over the row's samples (cache-resident, consecutive equal contexts
-//     merged in registers first) accumulates time and count at those ranks in
-//     shared memory, and the row is written straight to its final place.
-// No tile ever waits for another, so uneven tiles (long rows, rank
-// boundaries) cost only their own work.
-namespace {
-
-constexpr u32 TW = 4096;   // samples per tile
-constexpr u32 MASKW = TW / 32 + 4;  // rank-start mask words (positions 0 .. TW)
-constexpr int DEPTH = 3;   // steps prefetched ahead (count pass)
-constexpr u32 STEP = 128;  // samples per warp step (4 per lane)
-constexpr u32 RS = 128;    // staged entries per warp in shared memory
-
-constexpr u32 TL = 128;    // touched bitmap words remembered per row
-constexpr u32 RL = 128;    // run heads remembered per row (write pass)
-
-struct WarpSmem {
-  static constexpr u32 mask_off = 0;                  // u32[MASKW] rank-start mask
-  static constexpr u32 tl_off = 4 * MASKW;            // u32[TL + 4] touched words, count
-  static constexpr u32 time_off = tl_off + 4 * (TL + 4);  // u64[RS] (16-byte aligned)
-  static constexpr u32 ctx_off = time_off + 8 * RS;
-  static constexpr u32 cnt_off = ctx_off + 4 * RS;
-  static constexpr u32 run_ts_off = cnt_off + 4 * RS;     // u64[RL] run-head timestamps
-  static constexpr u32 run_ctx_off = run_ts_off + 8 * RL;  // u32[RL] run contexts
-  static constexpr u32 run_pos_off = run_ctx_off + 4 * RL;  // u32[RL] offsets in the row
-  static constexpr u32 bm_off = run_pos_off + 4 * RL;     // bitmap words (16-byte aligned)
-  static constexpr u32 fixed_count = time_off;        // count pass: mask + touched list
-  static constexpr u32 fixed_write = bm_off;
-};
-
-// Bitmap marking that also remembers which words became non-empty, so the
-// row's bitmap can be cleared by visiting only those words.  The count pass
-// keeps no summary level (with_l2 = false): it only needs the number of new
-// bits, and a row that touches more than TL words is cleared in full.
-struct Touched {
-  u32* list;  // [TL]
-  u32* cnt;   // [1]
-};
-
-template <bool WITH_L2>
-__device__ __forceinline__ u32 bm_mark(const Bm& b, const Touched& tw, u32 c) {
-  const u32 w = c >> 5, bit = 1u << (c & 31);
-  const u32 old = atomicOr(&b.L1[w], bit);
-  if (old == 0) {
-    if (WITH_L2) atomicOr(&b.L2[w >> 5], 1u << (w & 31));
-    const u32 i = atomicAdd(tw.cnt, 1u);
-    if (i < TL) tw.list[i] = w;
-  }
-  return (old & bit) ? 0u : 1u;
-}
-
-template <bool WITH_L2>
-__device__ __forceinline__ void bm_clear_touched(const Bm& b, const Touched& tw, int lane) {
-  __syncwarp();
-  const u32 n = *tw.cnt;
-  if (n <= TL) {
-    for (u32 i = lane; i < n; i += 32) {
-      const u32 w = tw.list[i];
-      b.L1[w] = 0;
-      if (WITH_L2) b.L2[w >> 5] = 0;
-    }
-  } else if (WITH_L2) {
-    bm_clear_warp(b, lane);
-  } else {
-    for (u32 i = lane; i < b.W1; i += 32) b.L1[i] = 0;
-  }
-  __syncwarp();
-  if (lane == 0) *tw.cnt = 0;
-  __syncwarp();
-}
-
-// Element j (warp-uniform or per-lane) of a 4-element register array without
-// dynamic register indexing.
-__device__ __forceinline__ u64 sel4(const u64* v, u32 j) {
-  return j == 0 ? v[0] : j == 1 ? v[1] : j == 2 ? v[2] : v[3];
-}
-
-struct Step {
-  u32 c[4];
-  u64 t[4];
-};
-
-// Load samples q0 + 4 lane + j (j < 4); contexts always, timestamps if want_ts.
-__device__ __forceinline__ void load_step(const TensorArgs& A, u64 q0, int lane, bool want_ts,
-                                          Step& s) {
-  const u64 q = q0 + 4 * (u64)lane;
-  if (q + 3 < A.N) {
-    const uint4 cv = *reinterpret_cast<const uint4*>(A.ctx + q);
-    s.c[0] = cv.x;
-    s.c[1] = cv.y;
-    s.c[2] = cv.z;
-    s.c[3] = cv.w;
-    if (want_ts) {
-      const ulonglong2 t0 = *reinterpret_cast<const ulonglong2*>(A.ts + q);
-      const ulonglong2 t1 = *reinterpret_cast<const ulonglong2*>(A.ts + q + 2);
-      s.t[0] = t0.x;
-      s.t[1] = t0.y;
-      s.t[2] = t1.x;
-      s.t[3] = t1.y;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      s.c[j] = (q + j < A.N) ? A.ctx[q + j] : NONE32;
-      if (want_ts) s.t[j] = (q + j < A.N) ? A.ts[q + j] : 0ull;
-    }
-  }
-}
-
-// Distinct contexts of the row in the bitmap (count pass).
+// Set bits of a bitmap (one warp).
 __device__ __forceinline__ u32 bm_count_warp(const Bm& b, int lane) {
   u32 sum = 0;
   for (u32 g = 0; g < b.W2; g += 32) {
@@ -336,651 +211,6 @@ __device__ __forceinline__ u32 bm_count_warp(const Bm& b, int lane) {
     for (u32 x = bits; x; x &= x - 1) sum += __popc(vld(&b.L1[w2 * 32 + __ffs(x) - 1]));
   }
   return __reduce_add_sync(FULL, sum);
-}
-
-struct Stage {
-  u32* ctx;
-  u64* time;
-  u32* cnt;
-};
-
-// The write pass remembers the run heads of the open row (a run = samples of
-// one context in a row, in order): its context, first timestamp and offset in
-// the row.  A run lasts until the next run head, the last one until the row
-// end, so its time is a difference of two head timestamps (the per-sample
-// durations telescope) and its samples a difference of two offsets.
-struct RunList {
-  u64* ts;
-  u32* ctx;
-  u32* pos;
-};
-
-// Appends this lane's run heads (bits j of h4 among its 4 samples at q..q+3)
-// to the list after the nrun already there; returns the warp's head count.
-__device__ __forceinline__ u32 capture_runs(const RunList& rl, u32 nrun, u32 h4, const u32* c,
-                                            const u64* t, u64 q, u64 row_s, u32 C, int lane) {
-  // heads of lower lanes, from one ballot per sample slot
-  const u32 below = (1u << lane) - 1u;
-  u32 before = 0, total = 0;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const u32 b = __ballot_sync(FULL, (h4 >> j) & 1u);
-    before += __popc(b & below);
-    total += __popc(b);
-  }
-  u32 slot = nrun + before;
-#pragma unroll
-  for (int j = 0; j < 4; ++j)
-    if ((h4 >> j) & 1u) {
-      if (slot < RL) {
-        rl.ctx[slot] = c[j] < C ? c[j] : 0u;
-        rl.ts[slot] = t[j];
-        rl.pos[slot] = (u32)(q + j - row_s);
-      }
-      ++slot;
-    }
-  return total;
-}
-
-
-// Accumulates the row's runs (nrun <= RL) at their contexts' ranks.
-__device__ __forceinline__ void accumulate_runs(const Bm& bm, const Stage& st, const RunList& rl,
-                                                u32 nrun, u64 ts_end, u32 len, int lane) {
-  for (u32 k = lane; k < nrun; k += 32) {
-    const u64 t0 = rl.ts[k];
-    const u32 p0 = rl.pos[k];
-    const bool more = k + 1 < nrun;
-    const u64 t1 = more ? rl.ts[k + 1] : ts_end;
-    const u32 p1 = more ? rl.pos[k + 1] : len;
-    const u32 c = rl.ctx[k];
-    const u32 r = bm_rank(bm, c);
-    atomicAdd((unsigned long long*)&st.time[r], (unsigned long long)(t1 >= t0 ? t1 - t0 : 0ull));
-    atomicAdd(&st.cnt[r], p1 - p0);
-    st.ctx[r] = c;
-  }
-}
-
-// Write pass, one row [s, e) whose ranks are in the bitmap: accumulate time
-// and count at each context's rank in the stage, then write the row at entry
-// eo.  The stage is shared memory or the warp's global region (compile time).
-__device__ __forceinline__ void accumulate_row(const TensorArgs& A, const Bm& bm, const Stage& st,
-                                               u64 s, u64 e, bool e_rs, u32 C, int lane) {
-  for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
-    Step x;
-    load_step(A, g0, lane, true, x);
-    const u64 q = g0 + 4 * (u64)lane;
-    u64 t_after = __shfl_down_sync(FULL, x.t[0], 1);  // first timestamp of the next lane
-    if (lane == 31 && q + 4 < e) t_after = A.ts[q + 4];
-    u32 rc = NONE32, rn = 0;
-    u64 rt = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const u64 qj = q + j;
-      if (qj < s || qj >= e) continue;
-      u64 tn;
-      if (qj + 1 < e) tn = (j < 3) ? x.t[j + 1] : t_after;
-      else tn = e_rs ? x.t[j] : A.ts[e];
-      const u64 d = tn >= x.t[j] ? tn - x.t[j] : 0;
-      const u32 c = x.c[j] < C ? x.c[j] : 0u;
-      if (c == rc) {
-        rt += d;
-        ++rn;
-      } else {
-        if (rn) {
-          const u32 k = bm_rank(bm, rc);
-          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)rt);
-          atomicAdd(&st.cnt[k], rn);
-          st.ctx[k] = rc;
-        }
-        rc = c;
-        rt = d;
-        rn = 1;
-      }
-    }
-    if (rn) {
-      const u32 k = bm_rank(bm, rc);
-      atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)rt);
-      atomicAdd(&st.cnt[k], rn);
-      st.ctx[k] = rc;
-    }
-  }
-}
-
-// Marks the contexts of row [s, e) by re-reading its samples (rows with more
-// runs than the run list holds).
-__device__ __forceinline__ u32 mark_row_samples(const TensorArgs& A, const Bm& bm,
-                                                const Touched& tw, u64 s, u64 e, u32 C,
-                                                int lane) {
-  u32 carry = NONE32, fresh = 0;
-  for (u64 g0 = s & ~(u64)(STEP - 1); g0 < e; g0 += STEP) {
-    Step x;
-    load_step(A, g0, lane, false, x);
-    const u64 q = g0 + 4 * (u64)lane;
-    u32 pc = __shfl_up_sync(FULL, x.c[3], 1);
-    if (lane == 0) pc = carry;
-    carry = __shfl_sync(FULL, x.c[3], 31);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const u64 qj = q + j;
-      const u32 prev = j ? x.c[j - 1] : pc;
-      if (qj >= s && qj < e && (qj == s || prev != x.c[j]))
-        fresh += bm_mark<true>(bm, tw, x.c[j] < C ? x.c[j] : 0u);
-    }
-  }
-  return fresh;
-}
-
-
-// Marks the row's contexts from its run list; returns this lane's new bits.
-__device__ __forceinline__ u32 mark_runs_new(const Bm& bm, const Touched& tw, const RunList& rl,
-                                             u32 nrun, int lane) {
-  u32 fresh = 0;
-  for (u32 k = lane; k < nrun; k += 32) fresh += bm_mark<true>(bm, tw, rl.ctx[k]);
-  return fresh;
-}
-
-// Writes the open row [s, e) (write pass).  The warp's bitmap holds the
-// union of the contexts of its recent rows, not only this row's: successive
-// iterations of a rank mostly call the same contexts, so the ranks (the
-// prefix counts over the bitmap) are recomputed only when a row brings a
-// context the union lacks, and the union restarts from the row when it
-// outgrows the shared-memory stage.  Times and counts are staged at union
-// ranks and the contexts the row has are written in order, compacted.  Runs
-// come from the run list, or from re-reading the samples of rows with more
-// runs than it holds.  ts_end is the timestamp the last run lasts until: the
-// sample at e, or the last sample when e ends the rank.
-__device__ __forceinline__ u32 write_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
-                                         const Stage& sm, const Stage& gl, const RunList& rl,
-                                         u32& nb, u32 nrun, u64 ts_end, u64 s, u64 e, bool e_rs,
-                                         u64 eo, u32 C, int lane) {
-  const bool listed = nrun <= RL;
-  // Fast path, the common case of iterations that repeat: every context of
-  // the row is already in the union and each appears in one run only.  Then
-  // the runs' union ranks are distinct (checked by storing each run's index
-  // at its rank and reading it back), a 128-bit mask of the ranks present
-  // gives each run its entry position, and every run is written straight to
-  // its entry.
-  if (listed && nb > 0 && nb <= RS) {
-    u32* present = sm.ctx;  // 4 words of the stage serve as the rank mask
-    if (lane < RS / 32) present[lane] = 0;
-    __syncwarp();
-    u32 rk[RL / 32];
-    bool ok = true;
-#pragma unroll
-    for (u32 it = 0; it < RL / 32; ++it) {
-      const u32 k = lane + 32 * it;
-      rk[it] = 0;
-      if (k < nrun) {
-        const u32 c = rl.ctx[k], w = c >> 5, word = bm.L1[w];
-        ok = ok && ((word >> (c & 31)) & 1u);
-        rk[it] = bm.pre[w] + __popc(word & ((1u << (c & 31)) - 1u));
-        if (ok) {
-          sm.cnt[rk[it]] = k;
-          atomicOr(&present[rk[it] >> 5], 1u << (rk[it] & 31));
-        }
-      }
-    }
-    if (__all_sync(FULL, ok)) {
-      __syncwarp();
-#pragma unroll
-      for (u32 it = 0; it < RL / 32; ++it) {
-        const u32 k = lane + 32 * it;
-        if (k < nrun) ok = ok && sm.cnt[rk[it]] == k;
-      }
-      if (__all_sync(FULL, ok)) {
-        u32 pm[RS / 32], before[RS / 32 + 1];
-        before[0] = 0;
-#pragma unroll
-        for (u32 q = 0; q < RS / 32; ++q) {
-          pm[q] = present[q];
-          before[q + 1] = before[q] + __popc(pm[q]);
-        }
-#pragma unroll
-        for (u32 it = 0; it < RL / 32; ++it) {
-          const u32 k = lane + 32 * it;
-          if (k < nrun) {
-            const u32 r = rk[it];
-            u32 pos = 0;
-#pragma unroll
-            for (u32 q = 0; q < RS / 32; ++q)
-              if (q == (r >> 5)) pos = before[q] + __popc(pm[q] & ((1u << (r & 31)) - 1u));
-            const u64 t0 = rl.ts[k];
-            const u32 p0 = rl.pos[k];
-            const bool more = k + 1 < nrun;
-            const u64 t1 = more ? rl.ts[k + 1] : ts_end;
-            const u32 p1 = more ? rl.pos[k + 1] : (u32)(e - s);
-            const u64 g = eo + pos;
-            A.e_ctx[g] = rl.ctx[k];
-            A.e_time[g] = t1 >= t0 ? t1 - t0 : 0ull;
-            A.e_cnt[g] = p1 - p0;
-          }
-        }
-        __syncwarp();
-        return before[RS / 32];
-      }
-    }
-    __syncwarp();
-  }
-  u32 fresh = listed ? mark_runs_new(bm, tw, rl, nrun, lane)
-                     : mark_row_samples(A, bm, tw, s, e, C, lane);
-  fresh = __reduce_add_sync(FULL, fresh);
-  if (fresh && nb + fresh > RS && nb > 0) {  // restart the union from this row
-    bm_clear_touched<true>(bm, tw, lane);
-    fresh = listed ? mark_runs_new(bm, tw, rl, nrun, lane)
-                   : mark_row_samples(A, bm, tw, s, e, C, lane);
-    fresh = __reduce_add_sync(FULL, fresh);
-    nb = 0;
-  }
-  if (fresh) {
-    __syncwarp();
-    nb = bm_prefix_warp(bm, lane);
-  }
-  const Stage& st = (nb <= RS) ? sm : gl;
-  for (u32 k = lane; k < nb; k += 32) {
-    st.time[k] = 0;
-    st.cnt[k] = 0;
-  }
-  __syncwarp();
-  if (listed) accumulate_runs(bm, st, rl, nrun, ts_end, (u32)(e - s), lane);
-  else accumulate_row(A, bm, st, s, e, e_rs, C, lane);
-  __syncwarp();
-  const u32 below = (1u << lane) - 1u;
-  u32 nnz = 0;
-  for (u32 k0 = 0; k0 < nb; k0 += 32) {
-    const u32 k = k0 + lane;
-    const u32 cnt = (k < nb) ? st.cnt[k] : 0u;
-    const u32 bal = __ballot_sync(FULL, cnt != 0);
-    if (cnt) {
-      const u64 g = eo + nnz + __popc(bal & below);
-      A.e_ctx[g] = st.ctx[k];
-      A.e_time[g] = st.time[k];
-      A.e_cnt[g] = cnt;
-    }
-    nnz += __popc(bal);
-  }
-  return nnz;
-}
-
-}  // namespace
-
-template <int NW, bool WRITE, bool BMS>
-__global__ void __launch_bounds__(NW * 32) k_tensor_pass(const TensorArgs A) {
-  constexpr int D = WRITE ? 2 : DEPTH;  // steps in flight (the write pass holds timestamps too)
-  extern __shared__ __align__(16) unsigned char sm[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const u32 bmw = bm_words(A.C);
-  const u32 fixed = WRITE ? WarpSmem::fixed_write : WarpSmem::fixed_count;
-  const u32 wbytes = fixed + (BMS ? bmw * 4 : 0);
-  unsigned char* ws = sm + (size_t)warp * wbytes;
-  const u64 gw = (u64)blockIdx.x * NW + warp;
-  const u64 G = (u64)gridDim.x * NW;
-  u32* mask = (u32*)(ws + WarpSmem::mask_off);
-  Touched tw;
-  tw.list = (u32*)(ws + WarpSmem::tl_off);
-  tw.cnt = tw.list + TL;
-  if (lane == 0) *tw.cnt = 0;
-  const Bm bm = bm_at(BMS ? (u32*)(ws + fixed) : A.gbm + gw * bmw, A.C);
-  if (BMS)
-    for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
-  Stage sst, gst;
-  RunList rl;
-  if (WRITE) {
-    rl.ts = (u64*)(ws + WarpSmem::run_ts_off);
-    rl.ctx = (u32*)(ws + WarpSmem::run_ctx_off);
-    rl.pos = (u32*)(ws + WarpSmem::run_pos_off);
-    sst.time = (u64*)(ws + WarpSmem::time_off);
-    sst.ctx = (u32*)(ws + WarpSmem::ctx_off);
-    sst.cnt = (u32*)(ws + WarpSmem::cnt_off);
-    gst.time = A.gst_time + gw * A.gst_cap;
-    gst.ctx = A.gst_ctx + gw * A.gst_cap;
-    gst.cnt = A.gst_cnt + gw * A.gst_cap;
-  }
-  u32 nb = 0;  // write pass: contexts in the bitmap's union
-  __syncwarp();
-  for (u64 t = gw; t < A.n_tiles; t += G) {
-    // the tile's trace set (a single experiment is one set)
-    u64 sbase = 0, N = A.N, t0 = 0, t1 = A.n_tiles;
-    u32 rlo = 0, rhi = A.R, C = A.C, m = A.m;
-    if (A.sets.S) {
-      const u32 s = A.sets.tile_set[t];
-      sbase = A.sets.set_rec0[s];
-      N = A.sets.set_rec_end[s];
-      t0 = A.sets.set_tile0[s];
-      t1 = A.sets.set_tile0[s + 1];
-      rlo = A.sets.set_rank0[s];
-      rhi = A.sets.set_rank0[s + 1];
-      C = A.sets.set_C[s];
-      m = A.sets.set_m[s];
-    }
-    const u64 a = sbase + (t - t0) * TW;
-    const u64 b = min(a + (u64)TW, N);
-    const bool last = (t + 1 == t1);
-    const u32 lo = A.tfr[t], hi = last ? rhi : A.tfr[t + 1];
-    const u64 qrank = (hi < rhi) ? A.rank_off[hi] : N;  // first rank start >= b (or N)
-    u32 carry = (a > sbase) ? A.ctx[a - 1] : NONE32;
-    u64 tcarry = (WRITE && a > sbase) ? A.ts[a - 1] : 0ull;  // timestamp before the step
-    u64 PR = 0, PE = 0;
-    if (WRITE) {
-      PR = A.tile_row_off[t];
-      PE = A.tile_ent_off[t];
-    }
-    for (u32 i = lane; i < MASKW; i += 32) mask[i] = 0;
-    __syncwarp();
-    for (u32 r = lo + lane; r < hi; r += 32) {
-      const u32 p = (u32)(A.rank_off[r] - a);
-      atomicOr(&mask[p >> 5], 1u << (p & 31));
-    }
-    __syncwarp();
-
-    u32 rank_ptr = lo, rows_local = 0, fl = 0;
-    u32 fresh = 0;  // count pass: contexts this lane saw first in the open row
-    u32 nrun = 0;   // write pass: run heads of the open row so far
-    u64 cum = 0;
-    bool row_open = false;
-    u64 row_s = 0;
-    // ring of steps: ring[0] is processed while ring[1 .. D] are in flight
-    Step ring[D + 1];
-#pragma unroll
-    for (int d = 0; d <= D; ++d) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        ring[d].c[j] = NONE32;
-        ring[d].t[j] = 0;
-      }
-    }
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const u64 qd = a + (u64)d * STEP;
-      if (qd < A.N) load_step(A, qd, lane, WRITE, ring[d]);
-    }
-    for (u64 q0 = a;; q0 += STEP) {
-      const bool tile_step = q0 < b;
-      if (!tile_step && !row_open) break;
-      const u64 lim = tile_step ? b : qrank;
-      if (q0 >= lim) {  // the open row runs to a rank boundary (or N)
-        if (row_open) {
-          if (WRITE)
-            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[lim - 1], row_s, lim, true,
-                             PE + cum, C, lane);
-          else {
-            cum += __reduce_add_sync(FULL, fresh);
-            fresh = 0;
-            bm_clear_touched<false>(bm, tw, lane);
-          }
-        }
-        row_open = false;
-        break;
-      }
-      Step& cur = ring[0];
-      const u64 q1 = q0 + STEP;
-      {
-        const u64 qd = q0 + (u64)D * STEP;
-        if (qd < A.N) load_step(A, qd, lane, WRITE, ring[D]);
-      }
-      const u64 q = q0 + 4 * (u64)lane;
-      // samples of this step that exist (tile steps: below b; continuation:
-      // below the next rank start)
-      const u32 nvalid = (u32)min(lim - q0, (u64)STEP);
-      const u32 pos0 = 4u * (u32)lane;
-      u32 pc[4];
-      pc[0] = __shfl_up_sync(FULL, cur.c[3], 1);
-      if (lane == 0) pc[0] = carry;
-      pc[1] = cur.c[0];
-      pc[2] = cur.c[1];
-      pc[3] = cur.c[2];
-      carry = __shfl_sync(FULL, cur.c[3], 31);
-      const u64 tprev = tcarry;  // timestamp of sample q0 - 1
-      if (WRITE) tcarry = __shfl_sync(FULL, cur.t[3], 31);
-      const u32 rel = (u32)(q - a);
-      // rank-start bits of this lane's 4 samples (positions rel .. rel + 3)
-      const u32 rs4 = tile_step ? ((mask[rel >> 5] >> (rel & 31)) & 0xFu) : 0u;
-      u32 ms4 = 0, valid4 = 0;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool valid = pos0 + j < nvalid;
-        valid4 |= (valid ? 1u : 0u) << j;
-        const bool ms = cur.c[j] == m && (pc[j] != m || ((rs4 >> j) & 1u));
-        ms4 |= (ms ? 1u : 0u) << j;
-      }
-      ms4 &= valid4;
-      if (tile_step) {
-        if (!WRITE) {
-          u32 cmax = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if ((valid4 >> j) & 1u) cmax = max(cmax, cur.c[j]);
-          if (cmax >= C) fl |= F_BAD_CTX;
-        } else {
-          // timestamp order within ranks: no sample earlier than the one
-          // before it, except at a rank start (each pair is checked by the
-          // tile holding its later sample)
-          u64 tp = __shfl_up_sync(FULL, cur.t[3], 1);
-          if (lane == 0) tp = tprev;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const u64 before = j ? cur.t[j - 1] : tp;
-            if (((valid4 >> j) & 1u) && !((rs4 >> j) & 1u) && cur.t[j] < before)
-              fl |= F_NOT_SORTED;
-          }
-        }
-      }
-      const u32 st4_any = (rs4 & valid4) | ms4;
-      if (!__any_sync(FULL, st4_any != 0)) {
-        // fast path: no row starts in this step; mark the run heads of the
-        // open row
-        if (row_open) {
-          u32 h4 = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (((valid4 >> j) & 1u) && pc[j] != cur.c[j]) {
-              h4 |= 1u << j;
-              if (!WRITE) fresh += bm_mark<false>(bm, tw, cur.c[j] < C ? cur.c[j] : 0u);
-            }
-          if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
-        }
-        if (q1 >= b && b == N) {  // the last tile: rows end at N
-          if (row_open) {
-            if (WRITE)
-              cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[N - 1], row_s, N, true,
-                               PE + cum, C, lane);
-            else {
-              cum += __reduce_add_sync(FULL, fresh);
-              fresh = 0;
-              bm_clear_touched<false>(bm, tw, lane);
-            }
-          }
-          row_open = false;
-          break;
-        }
-#pragma unroll
-        for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
-        continue;
-      }
-      u32 cc[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) cc[j] = cur.c[j] < C ? cur.c[j] : 0u;
-      const u32 st4 = st4_any;
-      u32 seg_lo = 0, from = 0;
-      bool stop = false;
-      for (;;) {
-        u32 mypos = 255;
-#pragma unroll
-        for (int j = 3; j >= 0; --j) {
-          const u32 pos = 4 * lane + j;
-          if (((st4 >> j) & 1u) && pos >= from) mypos = pos;
-        }
-        const u32 nxt = __reduce_min_sync(FULL, mypos);
-        const u32 end = nxt < STEP ? nxt : STEP;
-        if (row_open) {
-          u32 h4 = 0;
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const u32 pos = pos0 + j;
-            if (((valid4 >> j) & 1u) && pos >= seg_lo && pos < end)
-              if (q + j == row_s || pc[j] != cur.c[j]) {
-                h4 |= 1u << j;
-                if (!WRITE) fresh += bm_mark<false>(bm, tw, cc[j]);
-              }
-          }
-          if (WRITE) nrun += capture_runs(rl, nrun, h4, cur.c, cur.t, q, row_s, C, lane);
-        }
-        if (nxt >= STEP) break;
-        const u64 p = q0 + nxt;
-        const u32 src = nxt >> 2, bj = nxt & 3;
-        const bool p_rs = (__shfl_sync(FULL, rs4, src) >> bj) & 1u;
-        const bool p_ms = (__shfl_sync(FULL, ms4, src) >> bj) & 1u;
-        if (row_open) {
-          if (WRITE) {
-            // timestamp the last run lasts until: sample p, or p - 1 at a rank start
-            const u32 n1 = nxt - 1;
-            const u64 tp = __shfl_sync(FULL, sel4(cur.t, bj), src);
-            const u64 tm = __shfl_sync(FULL, sel4(cur.t, n1 & 3), (n1 >> 2) & 31);
-            const u64 ts_end = p_rs ? (nxt ? tm : tprev) : tp;
-            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, ts_end, row_s, p, p_rs, PE + cum, C,
-                             lane);
-          }
-          else {
-            cum += __reduce_add_sync(FULL, fresh);
-            fresh = 0;
-            bm_clear_touched<false>(bm, tw, lane);
-          }
-        }
-        if (!tile_step) {  // the continuation found the end of the row
-          row_open = false;
-          stop = true;
-          break;
-        }
-        u32 nrs = 0, r0 = rank_ptr;
-        if (p_rs) {
-          u32 rp = rank_ptr;
-          if (lane == 0)
-            while (rp < hi && A.rank_off[rp] == p) ++rp;
-          rp = __shfl_sync(FULL, rp, 0);
-          nrs = rp - rank_ptr;
-          rank_ptr = rp;
-        }
-        const u32 nrow = nrs + (p_ms ? 1u : 0u);
-        if (WRITE) {
-          const u64 row0 = PR + rows_local;
-          for (u32 k = lane; k < nrow; k += 32) A.entry_off[row0 + k] = PE + cum;
-          for (u32 k = lane; k < nrs; k += 32) A.row_off_of_rank[r0 + k] = row0 + k;
-        }
-        rows_local += nrow;
-        row_open = true;
-        row_s = p;
-        nrun = 0;
-        seg_lo = nxt;
-        from = nxt + 1;
-      }
-      if (stop) break;
-      if (q1 >= b && b == N) {  // the last tile: rows end at N
-        if (row_open) {
-          if (WRITE)
-            cum += write_row(A, bm, tw, sst, gst, rl, nb, nrun, A.ts[N - 1], row_s, N, true,
-                             PE + cum, C, lane);
-          else {
-            cum += __reduce_add_sync(FULL, fresh);
-            fresh = 0;
-            bm_clear_touched<false>(bm, tw, lane);
-          }
-        }
-        row_open = false;
-        break;
-      }
-#pragma unroll
-      for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
-    }
-    fl = __reduce_or_sync(FULL, fl);
-    if (lane == 0 && fl) flag(A.status, fl);
-    const u32 n_end = last ? hi - rank_ptr : 0u;  // empty ranks starting at N
-    if (WRITE) {
-      const u64 row0 = PR + rows_local;
-      for (u32 k = lane; k < n_end; k += 32) {
-        A.entry_off[row0 + k] = PE + cum;
-        A.row_off_of_rank[rhi - n_end + k] = row0 + k;
-      }
-    } else if (lane == 0) {
-      A.tile_rows[t] = rows_local + n_end;
-      A.tile_ents[t] = cum;
-    }
-    __syncwarp();
-  }
-  if (WRITE) bm_clear_touched<true>(bm, tw, lane);  // leave a global bitmap clean
-}
-
-static void set_smem(const void* k, size_t smem) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-template <bool WRITE>
-static const void* tensor_kernel(int nw, bool bms) {
-  switch (nw) {
-    case 4:
-      return bms ? (const void*)k_tensor_pass<4, WRITE, true> : (const void*)k_tensor_pass<4, WRITE, false>;
-    case 16:
-      return bms ? (const void*)k_tensor_pass<16, WRITE, true> : (const void*)k_tensor_pass<16, WRITE, false>;
-    default:
-      return bms ? (const void*)k_tensor_pass<8, WRITE, true> : (const void*)k_tensor_pass<8, WRITE, false>;
-  }
-}
-
-static bool tensor_bm_in_smem(u32 C) {
-  return WarpSmem::fixed_write + (size_t)bm_words(C) * 4 <= 12 * 1024;
-}
-
-static size_t tensor_smem(u32 C, bool write, int nw) {
-  const size_t bm = tensor_bm_in_smem(C) ? (size_t)bm_words(C) * 4 : 0;
-  return (size_t)((write ? WarpSmem::fixed_write : WarpSmem::fixed_count) + bm) * nw;
-}
-
-int tensor_max_per_sm(u32 C, bool write, int nw) {
-  const void* k = write ? tensor_kernel<true>(nw, tensor_bm_in_smem(C))
-                        : tensor_kernel<false>(nw, tensor_bm_in_smem(C));
-  const size_t smem = tensor_smem(C, write, nw);
-  set_smem(k, smem);
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nw * 32, smem);
-  return std::max(1, occ);
-}
-
-TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape) {
-  TensorPlan P;
-  P.tile = TW;
-  P.bm_in_smem = tensor_bm_in_smem(C);
-  P.nw_count = shape.nw_count;
-  P.nw_write = shape.nw_write;
-  P.smem_count = tensor_smem(C, false, P.nw_count);
-  P.smem = tensor_smem(C, true, P.nw_write);
-  const u64 n_tiles = std::max<u64>(1, (N + TW - 1) / TW);
-  auto grid = [&](bool write, int nw, int per_sm) {
-    const int occ = tensor_max_per_sm(C, write, nw);
-    const int ps = per_sm > 0 ? std::min(per_sm, occ) : occ;
-    return (int)std::max<u64>(1, std::min<u64>((u64)num_sms * ps, (n_tiles + nw - 1) / nw));
-  };
-  P.grid_count = grid(false, P.nw_count, shape.per_sm_count);
-  P.grid_write = grid(true, P.nw_write, shape.per_sm_write);
-  P.gst_cap = C;
-  return P;
-}
-
-void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  void* args[] = {(void*)&A};
-  cudaLaunchKernel(tensor_kernel<false>(P.nw_count, P.bm_in_smem), P.grid_count,
-                   P.nw_count * 32, args, P.smem_count, L.stream);
-  L.count();
-}
-
-void launch_tile_scan(const Launch& L, const TensorArgs& A) {
-  const u64 ns = scan_scratch_elems(A.n_tiles);
-  scan_exclusive(L, A.tile_rows, A.n_tiles, A.tile_row_off, A.totals, A.scan_scratch);
-  scan_exclusive(L, A.tile_ents, A.n_tiles, A.tile_ent_off, A.totals + 1, A.scan_scratch + ns);
-}
-
-void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
-  void* args[] = {(void*)&A};
-  cudaLaunchKernel(tensor_kernel<true>(P.nw_write, P.bm_in_smem), P.grid_write, P.nw_write * 32,
-                   args, P.smem, L.stream);
-  L.count();
 }
 
 // ---------------------------------------------------------------------------

@@ -55,16 +55,19 @@ struct TensorArgs {
   u64 n_tiles;
   u64 N;
   const u32* tfr;  // [n_tiles + 1] first rank starting at or after tile start
-  // per-tile counts (count pass) and their exclusive prefix (scan)
+  // per-tile counts (count pass: rows, run heads) and their exclusive prefix
   u32* tile_rows;
   u64* tile_ents;
   u64* tile_row_off;
   u64* tile_ent_off;
-  u64* totals;  // [2] rows, entries
+  u64* totals;  // [2] rows, entry slots (= run heads)
   u64* scan_scratch;  // 2 x scan_scratch_elems(n_tiles)
-  // outputs (write pass), exactly sized
+  // outputs (write pass): rows exactly sized, entries at slots (one per run;
+  // a row's distinct contexts fill the first row_nnz[row] of its slots)
   u64* row_off_of_rank;
-  u64* entry_off;
+  u64* entry_off;  // first slot of each row
+  u32* row_nnz;    // [rows] distinct contexts of each row
+  u64* nnz_sum;    // [1] total of row_nnz (added to)
   u32* e_ctx;
   u64* e_time;
   u32* e_cnt;
@@ -101,6 +104,22 @@ int tensor_max_per_sm(u32 C, bool write, int nw);
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A);
 void launch_tile_scan(const Launch& L, const TensorArgs& A);
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A);
+// When some row fills fewer slots than it has runs: exact offsets (scan of
+// row_nnz into new_off[rows + 1]) and a copy into exactly sized arrays.
+struct TensorCompact {
+  u64 rows;
+  const u64* slot_off;  // [rows] first slot of each row (the write pass's entry_off)
+  const u32* row_nnz;   // [rows]
+  u64* new_off;         // [rows + 1]
+  u64* scan_scratch;    // scan_scratch_elems(rows)
+  const u32* ctx_in;
+  const u64* time_in;
+  const u32* cnt_in;
+  u32* ctx_out;
+  u64* time_out;
+  u32* cnt_out;
+};
+void launch_tensor_compact(const Launch& L, const TensorCompact& K);
 
 // With sets, the last rank of set s ends at set_rec_end[s] (samples between
 // set_rec_end[s] and set_rec0[s+1] are alignment padding of no rank).
