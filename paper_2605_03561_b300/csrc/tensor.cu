@@ -32,7 +32,7 @@ namespace {
 constexpr u32 TW = 4096;            // samples per tile
 constexpr u32 MASKW = TW / 32 + 4;  // rank-start mask words (positions 0 .. TW)
 constexpr u32 STEP = 128;           // samples per warp step (4 per lane)
-constexpr int DEPTH_COUNT = 4;      // steps in flight, count pass
+constexpr int DEPTH_COUNT = 2;      // steps in flight, count pass (256 samples each)
 constexpr int DEPTH_WRITE = 1;      // steps in flight in registers, write pass (timestamps too)
 constexpr u32 RS = 128;             // staged entries per warp in shared memory
 constexpr u32 TL = 128;             // touched bitmap words remembered
@@ -110,27 +110,10 @@ __device__ __forceinline__ u32 fill_mask(const TensorArgs& A, const Tile& T, u32
   return __reduce_or_sync(FULL, steps);
 }
 
-struct CStep {
-  u32 c[4];
-};
 struct WStep {
   u32 c[4];
   u64 t[4];
 };
-
-__device__ __forceinline__ void load_c(const TensorArgs& A, u64 q0, int lane, CStep& s) {
-  const u64 q = q0 + 4 * (u64)lane;
-  if (q0 + STEP <= A.N) {
-    const uint4 v = *reinterpret_cast<const uint4*>(A.ctx + q);
-    s.c[0] = v.x;
-    s.c[1] = v.y;
-    s.c[2] = v.z;
-    s.c[3] = v.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) s.c[j] = (q + j < A.N) ? A.ctx[q + j] : NONE32;
-  }
-}
 
 __device__ __forceinline__ void load_w(const TensorArgs& A, u64 q0, int lane, WStep& s) {
   const u64 q = q0 + 4 * (u64)lane;
@@ -199,6 +182,41 @@ __device__ __forceinline__ void step_bits(const u32* c, const u32* pc, u32 rs4, 
 }
 
 // ------------------------------------------------------------ count pass --
+// 8 samples per lane, 256 per step: the pass does little per sample, so
+// wider steps spread the per-step work (loop, shuffles, checks) thinner.
+constexpr u32 KC = 8;
+constexpr u32 STEPC = 32 * KC;
+static_assert(STEPC == 2 * STEP, "a count step covers two rank-start mask steps");
+
+struct CStep {
+  u32 c[KC];
+};
+
+__device__ __forceinline__ void load_c(const TensorArgs& A, u64 q0, int lane, CStep& s) {
+  const u64 q = q0 + KC * (u64)lane;
+  if (q0 + STEPC <= A.N) {
+    const uint4 v0 = *reinterpret_cast<const uint4*>(A.ctx + q);
+    const uint4 v1 = *reinterpret_cast<const uint4*>(A.ctx + q + 4);
+    s.c[0] = v0.x;
+    s.c[1] = v0.y;
+    s.c[2] = v0.z;
+    s.c[3] = v0.w;
+    s.c[4] = v1.x;
+    s.c[5] = v1.y;
+    s.c[6] = v1.z;
+    s.c[7] = v1.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < (int)KC; ++j) s.c[j] = (q + j < A.N) ? A.ctx[q + j] : NONE32;
+  }
+}
+
+// Bits of this lane's KC positions (KC lane + j) at or after position f.
+__device__ __forceinline__ u32 from_mask8(u32 f, int lane) {
+  const int s = (int)f - (int)KC * lane;
+  return s <= 0 ? 0xFFu : (s >= (int)KC ? 0u : (0xFFu << s) & 0xFFu);
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
   constexpr int D = DEPTH_COUNT;
@@ -216,68 +234,77 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
     CStep ring[D + 1];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const u64 qd = T.a + (u64)d * STEP;
+      const u64 qd = T.a + (u64)d * STEPC;
       if (qd < A.N) load_c(A, qd, lane, ring[d]);
     }
-    for (u64 q0 = T.a;; q0 += STEP) {
+    for (u64 q0 = T.a;; q0 += STEPC) {
       const bool tile_step = q0 < T.b;
       if (!tile_step && !open) break;
       const u64 lim = tile_step ? T.b : T.qrank;
       if (q0 >= lim) break;
       {
-        const u64 qd = q0 + (u64)D * STEP;
+        const u64 qd = q0 + (u64)D * STEPC;
         if (qd < A.N) load_c(A, qd, lane, ring[D]);
       }
       const CStep& cur = ring[0];
-      u32 pc0 = __shfl_up_sync(FULL, cur.c[3], 1);
+      u32 pc0 = __shfl_up_sync(FULL, cur.c[KC - 1], 1);
       if (lane == 0) pc0 = carry;
-      carry = __shfl_sync(FULL, cur.c[3], 31);
-      const u32 si = (u32)(q0 - T.a) / STEP;
-      if (open && q0 + STEP <= T.b && !((rsteps >> si) & 1u)) {
+      carry = __shfl_sync(FULL, cur.c[KC - 1], 31);
+      const u32 si = (u32)(q0 - T.a) / STEP;  // first of the two mask steps
+      if (open && q0 + STEPC <= T.b && !((rsteps >> si) & 3u)) {
         // a full tile step inside the tile's rows, no rank start: every
         // change of context is a head, every marker after another context
         // an iteration start
         const u32 m = T.m;
-        const u32 c0 = cur.c[0], c1 = cur.c[1], c2 = cur.c[2], c3 = cur.c[3];
-        heads += (u32)(c0 != pc0) + (u32)(c1 != c0) + (u32)(c2 != c1) + (u32)(c3 != c2);
-        ms += (u32)(c0 == m && pc0 != m) + (u32)(c1 == m && c0 != m) + (u32)(c2 == m && c1 != m) +
-              (u32)(c3 == m && c2 != m);
-        cmax = max(cmax, max(max(c0, c1), max(c2, c3)));
-        if (q0 + STEP >= T.b && T.b == T.N) break;  // the set's last tile
-      } else {
-        u32 pc[4];
-        pc[0] = pc0;
-        pc[1] = cur.c[0];
-        pc[2] = cur.c[1];
-        pc[3] = cur.c[2];
-        const u32 nvalid = (u32)min(lim - q0, (u64)STEP);
-        const u32 rel = (u32)(q0 - T.a) + 4u * (u32)lane;
-        const u32 rs4 = tile_step ? ((mask[rel >> 5] >> (rel & 31)) & 0xFu) : 0u;
-        const u32 valid4 = (nvalid >= STEP) ? 0xFu : ~from_mask(nvalid, lane) & 0xFu;
-        u32 ms4, st4, h4;
-        step_bits(cur.c, pc, rs4, valid4, T.m, ms4, st4, h4);
-        u32 take = h4;
-        bool stop = false;
-        if (tile_step) {
-          ms += __popc(ms4);
+        u32 prev = pc0, h = 0, s2 = 0, cm = 0;
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if ((valid4 >> j) & 1u) cmax = max(cmax, cur.c[j]);
+        for (int j = 0; j < (int)KC; ++j) {
+          const u32 c = cur.c[j];
+          h += (u32)(c != prev);
+          s2 += (u32)(c == m && prev != m);
+          cm = max(cm, c);
+          prev = c;
         }
+        heads += h;
+        ms += s2;
+        cmax = max(cmax, cm);
+        if (q0 + STEPC >= T.b && T.b == T.N) break;  // the set's last tile
+      } else {
+        const u32 nvalid = (u32)min(lim - q0, (u64)STEPC);
+        const u32 rel = (u32)(q0 - T.a) + KC * (u32)lane;
+        const u32 rs8 = tile_step ? ((mask[rel >> 5] >> (rel & 31)) & 0xFFu) : 0u;
+        const u32 valid8 = (nvalid >= STEPC) ? 0xFFu : ~from_mask8(nvalid, lane) & 0xFFu;
+        const u32 m = T.m;
+        u32 ms8 = 0, h8 = 0, prev = pc0;
+#pragma unroll
+        for (int j = 0; j < (int)KC; ++j) {
+          const u32 c = cur.c[j];
+          const bool rs = (rs8 >> j) & 1u;
+          ms8 |= (u32)(c == m && (prev != m || rs)) << j;
+          h8 |= (u32)(prev != c || rs) << j;
+          if (tile_step && ((valid8 >> j) & 1u)) cmax = max(cmax, c);
+          prev = c;
+        }
+        ms8 &= valid8;
+        const u32 st8 = (rs8 & valid8) | ms8;
+        h8 = (h8 | st8) & valid8;
+        u32 take = h8;
+        bool stop = false;
+        if (tile_step) ms += __popc(ms8);
         if (!open || !tile_step) {
-          const u32 my = st4 ? 4u * lane + __ffs(st4) - 1u : 255u;
+          const u32 my = st8 ? KC * lane + __ffs(st8) - 1u : 0xFFFFu;
           const u32 f = __reduce_min_sync(FULL, my);
           if (!open) {  // heads from the tile's first row start on
-            take = (f < STEP) ? (h4 & from_mask(f, lane)) : 0u;
-            open = f < STEP;
+            take = (f < STEPC) ? (h8 & from_mask8(f, lane)) : 0u;
+            open = f < STEPC;
           } else {  // continuation: heads before the end of the last row
-            take = h4 & ~from_mask(f, lane);
-            stop = f < STEP || q0 + STEP >= lim;
+            take = h8 & ~from_mask8(f, lane);
+            stop = f < STEPC || q0 + STEPC >= lim;
           }
         }
         heads += __popc(take);
         if (stop) break;
-        if (tile_step && q0 + STEP >= T.b && T.b == T.N) break;  // the set's last tile
+        if (tile_step && q0 + STEPC >= T.b && T.b == T.N) break;  // the set's last tile
       }
 #pragma unroll
       for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
