@@ -488,60 +488,53 @@ __device__ __forceinline__ u32 emit_row(const TensorArgs& A, const Bm& bm, const
   // each run at its rank; otherwise the stamped ranks, as a 128-bit mask,
   // give every run its position.
   if (R.listed && nb > 0 && nb <= RS && n <= FAST_RUNS) {
-    u32 rk[FAST_RUNS / 32];
+    u32* const rkb = sm.ctx;  // each run's union rank (the stage is idle on this path)
     bool ok = true;
-#pragma unroll
-    for (u32 it = 0; it < FAST_RUNS / 32; ++it) {
-      rk[it] = 0;
-      const u32 i = 32 * it + lane;
-      if (32 * it < n && i < n) {
-        const u32 c = ring[(R.k0 + i) & (RING - 1)].ctx;
-        const u32 w = c >> 5, word = bm.L1[w];
-        if ((word >> (c & 31)) & 1u) {
-          rk[it] = bm.pre[w] + __popc(word & ((1u << (c & 31)) - 1u));
-          ok = ok && atomicExch(&stamp[rk[it]], rowid) != rowid;
-        } else {
-          ok = false;
-        }
+    for (u32 i = lane; i < n; i += 32) {
+      const u32 c = ring[(R.k0 + i) & (RING - 1)].ctx;
+      const u32 w = c >> 5, word = bm.L1[w];
+      if ((word >> (c & 31)) & 1u) {
+        const u32 r = bm.pre[w] + __popc(word & ((1u << (c & 31)) - 1u));
+        rkb[i] = r;
+        ok = ok && atomicExch(&stamp[r], rowid) != rowid;
+      } else {
+        ok = false;
       }
     }
     if (__all_sync(FULL, ok)) {
       __syncwarp();
-      u32 pm[4] = {0u, 0u, 0u, 0u};
+      u32 pm0 = 0, pm1 = 0, pm2 = 0, pm3 = 0;
       const bool whole = n == nb;
       if (!whole) {
-#pragma unroll
-        for (u32 w4 = 0; w4 < 4; ++w4)
-          if (32 * w4 < nb) pm[w4] = __ballot_sync(FULL, vld(&stamp[32 * w4 + lane]) == rowid);
+        pm0 = __ballot_sync(FULL, vld(&stamp[lane]) == rowid);
+        if (nb > 32) pm1 = __ballot_sync(FULL, vld(&stamp[32 + lane]) == rowid);
+        if (nb > 64) pm2 = __ballot_sync(FULL, vld(&stamp[64 + lane]) == rowid);
+        if (nb > 96) pm3 = __ballot_sync(FULL, vld(&stamp[96 + lane]) == rowid);
       }
-      const u32 b1 = __popc(pm[0]), b2 = b1 + __popc(pm[1]), b3 = b2 + __popc(pm[2]);
+      const u32 b1 = __popc(pm0), b2 = b1 + __popc(pm1), b3 = b2 + __popc(pm2);
       u32* const ec = A.e_ctx + eo;
       u64* const et = A.e_time + eo;
       u32* const en = A.e_cnt + eo;
-#pragma unroll
-      for (u32 it = 0; it < FAST_RUNS / 32; ++it) {
-        const u32 i = 32 * it + lane;
-        if (32 * it < n && i < n) {
-          const Head h = ring[(R.k0 + i) & (RING - 1)];
-          u64 t1 = R.ts_end;
-          u32 p1 = R.end_pos;
-          if (i + 1 < n) {
-            const Head x = ring[(R.k0 + i + 1) & (RING - 1)];
-            t1 = x.ts;
-            p1 = x.pos;
-          }
-          const u32 r = rk[it];
-          u32 pos = r;
-          if (!whole) {
-            const u32 q = r >> 5;
-            const u32 pmq = q == 0 ? pm[0] : q == 1 ? pm[1] : q == 2 ? pm[2] : pm[3];
-            const u32 bq = q == 0 ? 0u : q == 1 ? b1 : q == 2 ? b2 : b3;
-            pos = bq + __popc(pmq & ((1u << (r & 31)) - 1u));
-          }
-          ec[pos] = h.ctx;
-          et[pos] = t1 >= h.ts ? t1 - h.ts : 0ull;
-          en[pos] = p1 - h.pos;
+      for (u32 i = lane; i < n; i += 32) {
+        const Head h = ring[(R.k0 + i) & (RING - 1)];
+        u64 t1 = R.ts_end;
+        u32 p1 = R.end_pos;
+        if (i + 1 < n) {
+          const Head x = ring[(R.k0 + i + 1) & (RING - 1)];
+          t1 = x.ts;
+          p1 = x.pos;
         }
+        const u32 r = rkb[i];
+        u32 pos = r;
+        if (!whole) {
+          const u32 q = r >> 5;
+          const u32 pmq = q == 0 ? pm0 : q == 1 ? pm1 : q == 2 ? pm2 : pm3;
+          const u32 bq = q == 0 ? 0u : q == 1 ? b1 : q == 2 ? b2 : b3;
+          pos = bq + __popc(pmq & ((1u << (r & 31)) - 1u));
+        }
+        ec[pos] = h.ctx;
+        et[pos] = t1 >= h.ts ? t1 - h.ts : 0ull;
+        en[pos] = p1 - h.pos;
       }
       return n;
     }
