@@ -521,43 +521,91 @@ __global__ void k_sp_istar(const u32* S, u32 n, const u32* n_iter, const u64* sp
 }
 
 constexpr int SP_NW = 8;
-constexpr u32 SP_KC = 256;    // contexts per within-rank chunk (per-warp accumulators)
-constexpr u32 SP_U = 8;       // entries per lane in flight
+constexpr u32 SP_KC = 128;    // contexts per within-rank chunk (8-bit positions, 0xFF absent)
+constexpr u32 SP_U = 4;       // entries per lane per batch (two batches in flight)
+constexpr u32 SP_SMAP = 32768;  // context counts whose 8-bit map fits shared memory
+
+// Context -> position in the requested set's chunk [k0, k0 + nkc) (0xFF:
+// outside), built by every CTA in shared memory from the sorted set itself.
+__device__ __forceinline__ void build_kmap8(unsigned char* kmap8, u32 C, const u32* kset, u32 k0,
+                                            u32 nkc) {
+  uint4* w = reinterpret_cast<uint4*>(kmap8);
+  const uint4 ff = make_uint4(~0u, ~0u, ~0u, ~0u);
+  for (u32 i = threadIdx.x; i < (C + 15) / 16; i += blockDim.x) w[i] = ff;
+  __syncthreads();
+  for (u32 i = threadIdx.x; i < nkc; i += blockDim.x) kmap8[kset[k0 + i]] = (unsigned char)i;
+  __syncthreads();
+}
+
+// Chunk position of context c: the shared 8-bit map, or the global map for
+// context counts beyond it.
+struct KLookup {
+  const unsigned char* kmap8;  // null: use kmap
+  const u32* kmap;
+  u32 k0, nkc;
+  __device__ __forceinline__ u32 operator()(u32 c) const {
+    if (kmap8) {
+      const u32 k = kmap8[c];
+      return k == 0xFFu ? NONE32 : k;
+    }
+    const u32 k = kmap[c];
+    return (k == NONE32 || k < k0 || k >= k0 + nkc) ? NONE32 : k - k0;
+  }
+};
 
 // (a) Within-rank CV terms: one warp per rank of S; over iterations i < I*,
-// per context k in [k0, k0 + nkc): sum and 128-bit sum of squares of
-// t[r][i][k] in warp-private shared memory, then the CV term of (r, k).
+// per context of the chunk: sum and 128-bit sum of squares of t[r][i][k] in
+// warp-private shared memory (a context absent from a row adds 0), then the
+// CV term of (r, k).  The rank's rows are contiguous entries; two batches of
+// them are in flight while one is summed.
 __global__ void __launch_bounds__(SP_NW * 32)
     k_sp_within(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
-                const u64* e_time, const u32* kmap, u32 k0, u32 nkc, u32 nk, u32 I, double* cvw) {
+                const u64* e_time, const u32* kset, const u32* kmap, u32 C, u32 k0, u32 nkc,
+                u32 I, double* cvw) {
   __shared__ unsigned long long s_sum[SP_NW][SP_KC], s_lo[SP_NW][SP_KC], s_hi[SP_NW][SP_KC];
+  extern __shared__ __align__(16) unsigned char kmap8[];
+  const bool smap = C <= SP_SMAP;
+  if (smap) build_kmap8(kmap8, C, kset, k0, nkc);
+  const KLookup look{smap ? kmap8 : nullptr, kmap, k0, nkc};
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned long long* my_sum = s_sum[warp];
   unsigned long long* my_lo = s_lo[warp];
   unsigned long long* my_hi = s_hi[warp];
-  for (u32 q = lane; q < nkc; q += 32) my_sum[q] = my_lo[q] = my_hi[q] = 0;
+  for (u32 q = lane; q < SP_KC; q += 32) my_sum[q] = my_lo[q] = my_hi[q] = 0;
   __syncwarp();
   const u32 gw = blockIdx.x * SP_NW + warp, nw = gridDim.x * SP_NW;
   for (u32 ri = gw; ri < n; ri += nw) {
     const u32 r = rank_at(S, ri);
     const u64 row0 = row_off[r] + 1;  // skip the prologue row
     const u64 E0 = entry_off[row0], E1 = entry_off[row0 + I];
-    for (u64 jb = E0; jb < E1; jb += 32 * SP_U) {  // SP_U entries per lane in flight
-      u32 c[SP_U];
-      u64 t[SP_U];
+    u32 c[SP_U];
+    u64 t[SP_U];
 #pragma unroll
-      for (u32 u = 0; u < SP_U; ++u) {
-        const u64 j = jb + u * 32 + lane;
-        c[u] = j < E1 ? e_ctx[j] : NONE32;
-        t[u] = j < E1 ? e_time[j] : 0ull;
+    for (u32 u = 0; u < SP_U; ++u) {
+      const u64 j = E0 + u * 32 + lane;
+      c[u] = j < E1 ? e_ctx[j] : NONE32;
+      t[u] = j < E1 ? e_time[j] : 0ull;
+    }
+    for (u64 jb = E0; jb < E1; jb += 32 * SP_U) {
+      u32 cn[SP_U];
+      u64 tn[SP_U];
+#pragma unroll
+      for (u32 u = 0; u < SP_U; ++u) {  // the next batch
+        const u64 j = jb + 32 * SP_U + u * 32 + lane;
+        cn[u] = j < E1 ? e_ctx[j] : NONE32;
+        tn[u] = j < E1 ? e_time[j] : 0ull;
       }
 #pragma unroll
       for (u32 u = 0; u < SP_U; ++u) {
-        const u32 k = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
-        if (k == NONE32 || k < k0 || k >= k0 + nkc) continue;
-        const u32 kk = k - k0;
+        const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
+        if (kk == NONE32) continue;
         atomicAdd(&my_sum[kk], (unsigned long long)t[u]);
         atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t[u] * t[u]);
+      }
+#pragma unroll
+      for (u32 u = 0; u < SP_U; ++u) {
+        c[u] = cn[u];
+        t[u] = tn[u];
       }
     }
     __syncwarp();
@@ -589,13 +637,17 @@ constexpr u32 SP_IB = 1;   // iterations per warp
 constexpr u32 SP_PR = 4;   // ranks per round
 constexpr u32 SP_CU = 8;   // entries per lane in flight per round
 
-__global__ void __launch_bounds__(SP_NW * 32, 3)
+__global__ void __launch_bounds__(SP_NW * 32, 2)
     k_sp_cells(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
                const u64* __restrict__ entry_off, const u32* __restrict__ e_ctx,
-               const u64* __restrict__ e_time, const u32* __restrict__ kmap, u32 nk, u32 I,
-               u32 n_ib, u32 n_kb, u32 group, u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo,
-               u64* g_sqhi) {
+               const u64* __restrict__ e_time, const u32* __restrict__ kset,
+               const u32* __restrict__ kmap, u32 C, u32 nk, u32 I, u32 n_ib, u32 n_kb, u32 group,
+               u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi) {
   __shared__ u64 rowbuf[SP_NW][SP_PR][SP_IB][64];
+  extern __shared__ __align__(16) unsigned char kmap8[];
+  // one chunk of 64 contexts (n_kb == 1) maps through shared memory
+  const bool smap = n_kb == 1 && C <= SP_SMAP;
+  if (smap) build_kmap8(kmap8, C, kset, 0, nk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u64* buf = &rowbuf[warp][0][0][0];
   for (u32 q = lane; q < SP_PR * SP_IB * 64; q += 32) buf[q] = 0;
@@ -605,6 +657,7 @@ __global__ void __launch_bounds__(SP_NW * 32, 3)
   const u32 ib = (u32)(item % n_ib), kb = (u32)((item / n_ib) % n_kb);
   const u32 g = (u32)(item / ((u64)n_ib * n_kb));
   const u32 i0 = ib * SP_IB, k0 = kb * 64;
+  const KLookup look{smap ? kmap8 : nullptr, kmap, k0, 64};
   const u32 nrow = min(SP_IB, I - i0);
   const u32 r_begin = g * group, r_end = min(n, r_begin + group);
   u64 csum[SP_IB][2], cmax[SP_IB][2], clo[SP_IB][2], chi[SP_IB][2];
@@ -612,15 +665,22 @@ __global__ void __launch_bounds__(SP_NW * 32, 3)
   for (u32 il = 0; il < SP_IB; ++il)
 #pragma unroll
     for (u32 h = 0; h < 2; ++h) csum[il][h] = cmax[il][h] = clo[il][h] = chi[il][h] = 0;
-  for (u32 rb = r_begin; rb < r_end; rb += SP_PR) {
-    // entry ranges of the round's ranks: [b, m) row i0, [m, e) row i0 + 1, ...
-    u64 myb = 0, mym = 0, mye = 0;
-    if (lane < SP_PR && rb + lane < r_end) {
+  // entry ranges of a round's ranks (lanes < SP_PR): [b, m) row i0, [m, e)
+  // row i0 + 1, ...; the next round's are loaded while a round is summed
+  auto offsets = [&](u32 rb, u64& myb, u64& mym, u64& mye) {
+    myb = mym = mye = 0;
+    if (lane < (int)SP_PR && rb + lane < r_end) {
       const u64 row = row_off[rank_at(S, rb + lane)] + 1 + i0;
       myb = entry_off[row];
       mym = entry_off[row + min(1u, nrow)];
       mye = entry_off[row + nrow];
     }
+  };
+  u64 nb_, nm_, ne_;
+  offsets(r_begin, nb_, nm_, ne_);
+  for (u32 rb = r_begin; rb < r_end; rb += SP_PR) {
+    const u64 myb = nb_, mym = nm_, mye = ne_;
+    if (rb + SP_PR < r_end) offsets(rb + SP_PR, nb_, nm_, ne_);
     u64 b[SP_PR], m[SP_PR], len[SP_PR + 1];
     len[0] = 0;
 #pragma unroll
@@ -655,8 +715,8 @@ __global__ void __launch_bounds__(SP_NW * 32, 3)
       }
 #pragma unroll
       for (u32 u = 0; u < SP_CU; ++u) {
-        const u32 k = (c[u] != NONE32) ? kmap[c[u]] : NONE32;
-        if (k != NONE32 && k >= k0 && k < k0 + 64) buf[slot[u] * 64 + (k - k0)] = t[u];
+        const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
+        if (kk != NONE32) buf[slot[u] * 64 + kk] = t[u];
       }
     }
     __syncwarp();
@@ -1025,11 +1085,14 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
   cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
   if (I > 0) {
-    const int grid = std::max(1, std::min<int>(c->num_sms * 8, (int)((n + SP_NW - 1) / SP_NW)));
+    const size_t map_smem = e->C <= SP_SMAP ? (size_t)(e->C + 15) / 16 * 16 : 0;
+    const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + SP_NW - 1) / SP_NW)));
+    if (map_smem)
+      cudaFuncSetAttribute(k_sp_within, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_smem);
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
-      k_sp_within<<<grid, SP_NW * 32, 0, L.stream>>>(dS, n, e->row_off, e->entry_off, e->e_ctx,
-                                                      e->e_time, kmap, k0, std::min(SP_KC, nk - k0),
-                                                      nk, I, cvw);
+      k_sp_within<<<grid, SP_NW * 32, map_smem, L.stream>>>(
+          dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
+          std::min(SP_KC, nk - k0), I, cvw);
       L.count();
     }
     // cells: enough warps to fill the GPU, each with a sizeable group of ranks
@@ -1040,9 +1103,12 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     const u32 group = (u32)((n + groups - 1) / groups);
     groups = (n + group - 1) / group;
     const u64 n_items = tiles * groups;
-    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, 0, L.stream>>>(
-        dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, kmap, nk, I, n_ib, n_kb, group,
-        n_items, gs, gm, gl, gh);
+    const size_t cmap_smem = (n_kb == 1) ? map_smem : 0;
+    if (cmap_smem)
+      cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cmap_smem);
+    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cmap_smem, L.stream>>>(
+        dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
+        group, n_items, gs, gm, gl, gh);
     L.count();
   }
   ta_speedup_ctx* dper;
