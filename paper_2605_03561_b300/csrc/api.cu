@@ -205,6 +205,9 @@ namespace {
 // Longest total of ancestor lists (entries) the inclusive rollup builds;
 // deeper trees use the level-by-level sweep.
 constexpr u64 kAncMax = 1ull << 28;
+// Per-rank scratch entries of the one-pass exclusive CSR (ranks with more
+// distinct contexts take a second write pass).
+constexpr u64 kXsCap = 256;
 
 // Tensor: count pass, scan of per-tile counts, allocation (rows exactly,
 // entries one slot per run), write pass; compaction when a row repeats a
@@ -401,6 +404,47 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
       A.anc_off = aoff;
       A.anc = anc;
     }
+  }
+  if (mode == 0) {
+    // one pass: the write pass first, into a per-rank scratch of kXsCap
+    // entries; exact counts, scan, allocation, copy; ranks above the cap
+    // are written by a second, restricted write pass
+    const u64 cap = kXsCap;
+    TRY(tmp.get_n((u64)R * cap, &A.xs_ctx, "exclusive scratch"));
+    TRY(tmp.get_n((u64)R * cap, &A.xs_time, "exclusive scratch"));
+    TRY(tmp.get_n((u64)R * cap, &A.xs_cnt, "exclusive scratch"));
+    A.xs_cap = (u32)cap;
+    A.n_over = (unsigned long long*)(meta + 2);
+    {
+      PhaseTimer timer(c, acc);
+      launch_excl_scratch(L, P, A);
+      timer.stop_and_sync();
+    }
+    u64 h[3];
+    TRY(copy(c, h, meta, sizeof h));
+    TRY(sync_check(c, "exclusive (scratch)"));
+    TRY(status_from_flags((u32)h[0], "exclusive"));
+    out.nnz = h[1];
+    const u64 n = std::max<u64>(out.nnz, 1);
+    TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
+    TRY(e->own(n * 8, (void**)&out.time, "csr time"));
+    TRY(e->own(n * 4, (void**)&out.cnt, "csr cnt"));
+    A.out_ctx = out.ctx;
+    A.out_time = out.time;
+    A.out_cnt_e = out.cnt;
+    {
+      PhaseTimer timer(c, acc);
+      launch_excl_copy(L, A);
+      if (h[2]) {
+        A.only_over = 1;
+        launch_rank_write(L, P, A);
+      }
+      timer.stop_and_sync();
+    }
+    u64 f = 0;
+    TRY(copy(c, &f, meta, 8));
+    TRY(sync_check(c, "exclusive"));
+    return status_from_flags((u32)f, "exclusive");
   }
   {
     PhaseTimer timer(c, acc);

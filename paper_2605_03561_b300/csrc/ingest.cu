@@ -306,6 +306,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
   }
   __syncwarp();
   for (u64 r = gw; r < A.R; r += G) {
+    if (MODE == 0 && WRITE && A.only_over && A.out_cnt[r] <= A.xs_cap) continue;
     // context ids are local to the rank's set; tree arrays are concatenated
     const u32 cbase = A.sets.S ? A.sets.set_ctx0[A.sets.rank_set[r]] : 0u;
     u64 E0, E1;
@@ -358,6 +359,18 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       continue;
     }
     const u32 nnz = bm_prefix_warp(bm, lane);
+    const bool scratch = MODE == 0 && A.xs_cap && !A.only_over;
+    if (scratch) {
+      if (lane == 0) {
+        A.out_cnt[r] = nnz;
+        if (nnz > A.xs_cap) atomicAdd(A.n_over, 1ull);
+      }
+      if (nnz > A.xs_cap) {  // left to the write pass over the ranks above the cap
+        bm_clear_warp(bm, lane);
+        __syncwarp();
+        continue;
+      }
+    }
     auto run = [&](const RStage& st) {
     for (u32 k = lane; k < nnz; k += 32) {
       st.time[k] = 0;
@@ -473,11 +486,20 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       }
     }
     __syncwarp();
-    const u64 eo = A.out_off[r];
-    for (u32 k = lane; k < nnz; k += 32) {
-      A.out_ctx[eo + k] = vld(&st.ctx[k]);
-      A.out_time[eo + k] = vld(&st.time[k]);
-      A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
+    if (scratch) {
+      const u64 eo = r * (u64)A.xs_cap;
+      for (u32 k = lane; k < nnz; k += 32) {
+        A.xs_ctx[eo + k] = vld(&st.ctx[k]);
+        A.xs_time[eo + k] = vld(&st.time[k]);
+        A.xs_cnt[eo + k] = vld(&st.cnt[k]);
+      }
+    } else {
+      const u64 eo = A.out_off[r];
+      for (u32 k = lane; k < nnz; k += 32) {
+        A.out_ctx[eo + k] = vld(&st.ctx[k]);
+        A.out_time[eo + k] = vld(&st.time[k]);
+        A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
+      }
     }
     };
     if (nnz <= (MODE == 2 ? RSR2 : RSR)) run(ss);
@@ -544,6 +566,35 @@ void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs&
   L.count();
   scan_exclusive(L, A.out_cnt, A.R, A.out_off, A.total, A.scan_scratch);
   cudaMemcpyAsync(A.out_off + A.R, A.total, 8, cudaMemcpyDeviceToDevice, L.stream);
+}
+
+// Scratch rows of at most xs_cap contexts to their CSR place, warp per rank.
+__global__ void k_excl_copy(const RankCsrArgs A) {
+  const int lane = threadIdx.x & 31;
+  const u64 G = (u64)gridDim.x * (blockDim.x >> 5);
+  for (u64 r = (u64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < A.R; r += G) {
+    const u32 n = A.out_cnt[r];
+    if (n > A.xs_cap) continue;
+    const u64 src = r * (u64)A.xs_cap, dst = A.out_off[r];
+    for (u32 k = lane; k < n; k += 32) {
+      A.out_ctx[dst + k] = A.xs_ctx[src + k];
+      A.out_time[dst + k] = A.xs_time[src + k];
+      A.out_cnt_e[dst + k] = A.xs_cnt[src + k];
+    }
+  }
+}
+
+void launch_excl_scratch(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {
+  rank_launch<0, true>(L, P, A);
+  L.count();
+  scan_exclusive(L, A.out_cnt, A.R, A.out_off, A.total, A.scan_scratch);
+  cudaMemcpyAsync(A.out_off + A.R, A.total, 8, cudaMemcpyDeviceToDevice, L.stream);
+}
+
+void launch_excl_copy(const Launch& L, const RankCsrArgs& A) {
+  const u64 warps = std::min<u64>(std::max<u64>(A.R, 1), (u64)L.num_sms * 64);
+  k_excl_copy<<<(unsigned)((warps + 7) / 8), 256, 0, L.stream>>>(A);
+  L.count();
 }
 
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A) {

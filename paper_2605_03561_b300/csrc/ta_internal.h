@@ -169,6 +169,16 @@ struct RankCsrArgs {
   u32 bm_in_smem;
   u32* status;
   SetMap sets;
+  // exclusive in one pass (mode 0): the write pass runs first, records every
+  // rank's distinct count in out_cnt and writes ranks of at most xs_cap
+  // contexts to a per-rank scratch (r * xs_cap); with only_over set it
+  // writes just the ranks above xs_cap, at out_off
+  u32* xs_ctx;
+  u64* xs_time;
+  u32* xs_cnt;
+  u32 xs_cap;
+  u32 only_over;
+  unsigned long long* n_over;  // [1] ranks above xs_cap
 };
 // Kernels of the rank passes by variant: 0 exclusive, 1 inclusive by a
 // level-by-level sweep, 2 inclusive through ancestor lists.
@@ -189,6 +199,10 @@ struct RankCsrPlan {
 RankCsrPlan plan_rank_csr(u32 R, u32 C, int num_sms);
 void launch_rank_count(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
 void launch_rank_write(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+// Exclusive in one pass: the write pass into the per-rank scratch, the scan
+// of the counts, then (after the caller allocates) the copy to the CSR.
+void launch_excl_scratch(const Launch& L, const RankCsrPlan& P, const RankCsrArgs& A);
+void launch_excl_copy(const Launch& L, const RankCsrArgs& A);
 
 // Ancestor lists of every context (itself first, then up to the root):
 // anc_off = exclusive scan of depth + 1 (total in *total; len and scratch:

@@ -38,7 +38,7 @@ constexpr u32 RS = 128;             // staged entries per warp in shared memory
 constexpr u32 TL = 128;             // touched bitmap words remembered
 constexpr u32 RING = 256;           // run heads remembered per warp (power of two)
 constexpr u32 FAST_RUNS = 128;      // longest row (in runs) of the direct-write path
-constexpr u32 PF = 4;               // steps prefetched into L2 ahead (write pass)
+constexpr u32 PF = 2;               // steps prefetched into L2 ahead (write pass)
 
 struct Head {  // one run head: 16 bytes, one vector store
   u64 ts;
