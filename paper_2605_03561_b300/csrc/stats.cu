@@ -287,6 +287,35 @@ __global__ void k_sort_step(u64* keys, double* vals, u64 P, u64 j, u64 k) {
   }
 }
 
+// Bitonic stages of span below SORT_B inside blocks of SORT_B pairs, one
+// block per CTA in shared memory: every stage k <= SORT_B (k_fixed = 0), or
+// the spans j < SORT_B of stage k_fixed.  Directions follow global indices.
+constexpr u32 SORT_B = 4096;
+
+__global__ void __launch_bounds__(1024) k_sort_block(u64* keys, double* vals, u64 k_fixed) {
+  extern __shared__ __align__(16) u64 sk[];
+  double* sv = reinterpret_cast<double*>(sk + SORT_B);
+  const u64 base = (u64)blockIdx.x * SORT_B;
+  for (u32 i = threadIdx.x; i < SORT_B; i += blockDim.x) {
+    sk[i] = keys[base + i];
+    sv[i] = vals[base + i];
+  }
+  __syncthreads();
+  const u64 k0 = k_fixed ? k_fixed : 2, k1 = k_fixed ? k_fixed : SORT_B;
+  for (u64 k = k0; k <= k1; k <<= 1)
+    for (u32 j = (u32)((k >> 1) < (SORT_B >> 1) ? (k >> 1) : (SORT_B >> 1)); j > 0; j >>= 1) {
+      for (u32 i = threadIdx.x; i < SORT_B; i += blockDim.x) {
+        const u32 l = i ^ j;
+        if (l > i) cmp_swap(sk, sv, i, l, ((base + i) & k) == 0);
+      }
+      __syncthreads();
+    }
+  for (u32 i = threadIdx.x; i < SORT_B; i += blockDim.x) {
+    keys[base + i] = sk[i];
+    vals[base + i] = sv[i];
+  }
+}
+
 // Keys are (slot << 32 | rank); slot_ctx maps a slot back to its context
 // (null: the slot is the context).
 __global__ void k_write_outliers(const u64* keys, const double* zs, u64 n, ta_outlier* out,
@@ -315,11 +344,28 @@ void sort_pairs(const Launch& L, u64* keys, double* vals, u64 n) {
   while (P < n) P <<= 1;
   k_fill_u64<<<blocks(P - n), 256, 0, L.stream>>>(keys + n, P - n, ~0ull);
   L.count();
-  for (u64 k = 2; k <= P; k <<= 1)
-    for (u64 j = k >> 1; j > 0; j >>= 1) {
+  if (P < SORT_B) {
+    for (u64 k = 2; k <= P; k <<= 1)
+      for (u64 j = k >> 1; j > 0; j >>= 1) {
+        k_sort_step<<<blocks(P), 256, 0, L.stream>>>(keys, vals, P, j, k);
+        L.count();
+      }
+    return;
+  }
+  // spans below SORT_B in shared memory, longer ones one global step each
+  const size_t smem = (size_t)SORT_B * 16;
+  cudaFuncSetAttribute(k_sort_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const unsigned nb = (unsigned)(P / SORT_B);
+  k_sort_block<<<nb, 1024, smem, L.stream>>>(keys, vals, 0);
+  L.count();
+  for (u64 k = 2 * (u64)SORT_B; k <= P; k <<= 1) {
+    for (u64 j = k >> 1; j >= SORT_B; j >>= 1) {
       k_sort_step<<<blocks(P), 256, 0, L.stream>>>(keys, vals, P, j, k);
       L.count();
     }
+    k_sort_block<<<nb, 1024, smem, L.stream>>>(keys, vals, k);
+    L.count();
+  }
 }
 
 const Csr* metric_csr(const ta_experiment* e, u32 metric) {
@@ -510,14 +556,28 @@ __global__ void k_topo_racks(u32 nr, const u32* rk_flag, u32* flagged, u32* coun
 }
 
 // -------------------------------------------------------------- speedup --
+// I* = min over S of n_iter, their sum and the longest span: a warp
+// reduction, then one set of atomics per warp.
 __global__ void k_sp_istar(const u32* S, u32 n, const u32* n_iter, const u64* span, u32* istar,
                            unsigned long long* sum_iter, unsigned long long* max_span) {
   const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const u32 r = rank_at(S, i);
-  atomicMin(istar, n_iter[r]);
-  atomicAdd(sum_iter, (unsigned long long)n_iter[r]);
-  atomicMax(max_span, (unsigned long long)span[r]);
+  u32 it = NONE32, sum = 0;
+  u64 sp = 0;
+  if (i < n) {
+    const u32 r = rank_at(S, i);
+    it = n_iter[r];
+    sum = it;
+    sp = span[r];
+  }
+  it = __reduce_min_sync(FULL, it);
+  const u64 sum64 = warp_incl_scan((u64)sum, threadIdx.x & 31);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sp = max(sp, (u64)__shfl_xor_sync(FULL, sp, o));
+  if ((threadIdx.x & 31) == 31) {
+    if (it != NONE32) atomicMin(istar, it);
+    atomicAdd(sum_iter, (unsigned long long)sum64);
+    atomicMax(max_span, (unsigned long long)sp);
+  }
 }
 
 constexpr int SP_NW = 8;
