@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Small and medium cases compare every output element by element; they span
-many 1024-sample tiles with ragged tails, rows that cross tiles, empty and
+many 4096-sample tiles with ragged tails, rows that cross tiles, empty and
 degenerate ranks, and contexts far apart in the tree."""
 import json
 import os
@@ -222,3 +222,48 @@ def test_validation_errors():
     # the context is still usable afterwards
     tr, a, e = load_both(base)
     check_products(tr, a, e)
+
+
+def test_rows_repeating_contexts_across_runs():
+    # Few contexts and long rows: a row returns to a context after others, so
+    # it has more runs than distinct contexts and fills fewer entry slots than
+    # the count pass sized (the compaction step), across many tiles.
+    rng = np.random.default_rng(31)
+    R, C, marker = 48, 20, 3
+    rank_off, ts, ctx = edge.random_traces(rng, R, C, marker, 40000, p_empty=0.05, p_marker=0.004)
+    d = dict(rank_off=rank_off, ts=ts, ctx=ctx, parent=edge.shuffled_tree(rng, C, 5), marker=marker)
+    tr, a, e = load_both(d)
+    assert int(rank_off[-1]) > 50 * 4096
+    check_products(tr, a, e)
+    t = e.tensor()
+    runs = int(np.sum(ctx[1:] != ctx[:-1])) + 1
+    assert len(t["e_ctx"]) < runs  # rows do repeat contexts here
+
+
+def test_exclusive_ranks_above_the_scratch_cap():
+    # Ranks with more than 256 distinct contexts (written by the second,
+    # restricted write pass) mixed with ranks below the cap (the scratch copy).
+    rng = np.random.default_rng(32)
+    R, C, marker = 40, 3000, 7
+    lengths = np.where(np.arange(R) % 3 == 0, 6000, 150)
+    rank_off, ts, ctx = edge.random_traces(rng, R, C, marker, 0, p_marker=0.002, lengths=lengths)
+    d = dict(rank_off=rank_off, ts=ts, ctx=ctx, parent=edge.shuffled_tree(rng, C, 8), marker=marker)
+    tr, a, e = load_both(d)
+    x = e.csr(ta.EXCLUSIVE)
+    per_rank = np.diff(x["off"].astype(np.int64))
+    assert (per_rank > 256).any() and (per_rank <= 256).any()
+    check_products(tr, a, e)
+
+
+def test_large_outlier_sort():
+    # Tens of thousands of outliers: the sort runs its shared-memory blocks of
+    # 4096 pairs and the global steps between them; the list must equal the
+    # oracle's, ordered by (context, rank).
+    cfg = synth.preset(2, seed=33, n_ranks=2000, len_mean=3000.0)
+    d = synth.generate(cfg)
+    tr, a, e = load_both(d)
+    gs, go, gn, _ = e.stats(ta.EXCLUSIVE, tau=(1, 2), outlier_cap=1 << 20)
+    os_, oo, on, _ = a.stats(ta.EXCLUSIVE, tau=(1, 2), want_z=False)
+    assert gn == on and on > 8192
+    assert np.array_equal(go["ctx"], oo["ctx"]) and np.array_equal(go["rank"], oo["rank"])
+
