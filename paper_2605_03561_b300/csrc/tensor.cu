@@ -53,7 +53,9 @@ struct WriteSmem {
   static constexpr u32 ctx_off = time_off + 8 * RS;       // u32[RS]
   static constexpr u32 cnt_off = ctx_off + 4 * RS;        // u32[RS]
   static constexpr u32 stamp_off = cnt_off + 4 * RS;      // u32[RS] row ids (direct path)
-  static constexpr u32 ring_off = stamp_off + 4 * RS;     // Head[RING]
+  static constexpr u32 tctx_off = stamp_off + 4 * RS;     // u32[FAST_RUNS] template contexts
+  static constexpr u32 tpos_off = tctx_off + 4 * FAST_RUNS;  // u8[FAST_RUNS] template positions
+  static constexpr u32 ring_off = tpos_off + FAST_RUNS;   // Head[RING]
   static constexpr u32 fixed = ring_off + 16 * RING;      // bitmap words follow
 };
 static_assert(WriteSmem::time_off % 16 == 0 && WriteSmem::ring_off % 16 == 0 &&
@@ -477,11 +479,45 @@ __device__ __forceinline__ void accumulate_samples(const TensorArgs& A, const Bm
 // rank mostly call the same contexts, so the ranks are recomputed only when a
 // row brings a context the union lacks, and the union restarts from the row
 // when it outgrows the shared-memory stage.
+// Template: the run contexts of the warp's last row written by the direct
+// path and each run's position; tn = its run count (0: none).
+struct Template {
+  u32* ctx;            // [FAST_RUNS]
+  unsigned char* pos;  // [FAST_RUNS]
+};
+
 __device__ __forceinline__ u32 emit_row(const TensorArgs& A, const Bm& bm, const Touched& tw,
                                         const Stage& sm, const Stage& gl, const Head* ring,
-                                        u32* stamp, u32 rowid, u32& nb, const RowEnd& R, u64 eo,
-                                        u32 C, int lane) {
+                                        u32* stamp, u32 rowid, u32& nb, const Template& tp,
+                                        u32& tn, const RowEnd& R, u64 eo, u32 C, int lane) {
   const u32 n = R.k1 - R.k0;
+  // Template path: successive iterations of a rank mostly repeat their run
+  // sequence exactly, and then every run goes where the template's did.  The
+  // runs are written while they are compared; a row that differs anywhere is
+  // rewritten below, over all of its positions (direct path) or within its
+  // first slots (general path, whose remaining slots no one reads).
+  if (R.listed && n == tn) {
+    bool same = true;
+    u32* const ec = A.e_ctx + eo;
+    u64* const et = A.e_time + eo;
+    u32* const en = A.e_cnt + eo;
+    for (u32 i = lane; i < n; i += 32) {
+      const Head h = ring[(R.k0 + i) & (RING - 1)];
+      u64 t1 = R.ts_end;
+      u32 p1 = R.end_pos;
+      if (i + 1 < n) {
+        const Head x = ring[(R.k0 + i + 1) & (RING - 1)];
+        t1 = x.ts;
+        p1 = x.pos;
+      }
+      same = same && h.ctx == tp.ctx[i];
+      const u32 pos = tp.pos[i] < n ? tp.pos[i] : 0u;
+      ec[pos] = h.ctx;
+      et[pos] = t1 >= h.ts ? t1 - h.ts : 0ull;
+      en[pos] = p1 - h.pos;
+    }
+    if (__all_sync(FULL, same)) return n;
+  }
   // Direct path: every run's context is in the union and no two runs share
   // one (each run stamps its union rank with the row's id; finding the id
   // already there means a repeat).  A row holding the whole union writes
@@ -535,10 +571,15 @@ __device__ __forceinline__ u32 emit_row(const TensorArgs& A, const Bm& bm, const
         ec[pos] = h.ctx;
         et[pos] = t1 >= h.ts ? t1 - h.ts : 0ull;
         en[pos] = p1 - h.pos;
+        tp.ctx[i] = h.ctx;
+        tp.pos[i] = (unsigned char)pos;
       }
+      tn = n;
+      __syncwarp();
       return n;
     }
   }
+  tn = 0;  // the general path keeps no template
   // General path: mark the row's contexts into the union (restart it if it
   // would outgrow the stage), recompute ranks if anything was new, sum runs
   // at their ranks, write the present ones in order.
@@ -593,6 +634,8 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_write(const TensorArgs A) {
   const u64 G = (u64)gridDim.x * NW;
   u32* mask = (u32*)(ws + WriteSmem::mask_off);
   u32* stamp = (u32*)(ws + WriteSmem::stamp_off);
+  const Template tpl{(u32*)(ws + WriteSmem::tctx_off), (unsigned char*)(ws + WriteSmem::tpos_off)};
+  u32 tn = 0;  // runs of the template (0: none)
   Touched tw;
   tw.list = (u32*)(ws + WriteSmem::tl_off);
   tw.cnt = tw.list + TL;
@@ -641,7 +684,8 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_write(const TensorArgs A) {
       R.e_rs = e_rs;
       u32 nnz = 0;
       if (PE + cum + (k1 - R.k0) <= slot_end) {
-        nnz = emit_row(A, bm, tw, sst, gst, ring, stamp, rowid, nb, R, PE + cum, T.C, lane);
+        nnz = emit_row(A, bm, tw, sst, gst, ring, stamp, rowid, nb, tpl, tn, R, PE + cum, T.C,
+                       lane);
         if (lane == 0) A.row_nnz[open_row] = nnz;
       } else {
         fl |= F_INTERNAL;
@@ -900,7 +944,7 @@ static void set_smem(const void* k, size_t smem) {
 }
 
 static bool tensor_bm_in_smem(u32 C) {
-  return WriteSmem::fixed + (size_t)bm_words(C) * 4 <= 13 * 1024;
+  return WriteSmem::fixed + (size_t)bm_words(C) * 4 <= 14 * 1024;
 }
 
 // Dynamic shared memory of a pass (the count pass uses static memory only).
