@@ -693,8 +693,8 @@ __global__ void __launch_bounds__(SP_NW * 32)
 // suffice -- and every lane then folds its contexts' values into its
 // registers, absent ones reading 0.  The group's cells go to the global
 // cells with one set of atomics per warp.
-constexpr u32 SP_IB = 1;   // iterations per warp
-constexpr u32 SP_PR = 4;   // ranks per round
+constexpr u32 SP_IB = 4;   // iterations per warp (one contiguous read per rank)
+constexpr u32 SP_PR = 1;   // ranks per round
 constexpr u32 SP_CU = 8;   // entries per lane in flight per round
 
 __global__ void __launch_bounds__(SP_NW * 32, 2)
@@ -725,29 +725,30 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
   for (u32 il = 0; il < SP_IB; ++il)
 #pragma unroll
     for (u32 h = 0; h < 2; ++h) csum[il][h] = cmax[il][h] = clo[il][h] = chi[il][h] = 0;
-  // entry ranges of a round's ranks (lanes < SP_PR): [b, m) row i0, [m, e)
-  // row i0 + 1, ...; the next round's are loaded while a round is summed
-  auto offsets = [&](u32 rb, u64& myb, u64& mym, u64& mye) {
-    myb = mym = mye = 0;
-    if (lane < (int)SP_PR && rb + lane < r_end) {
-      const u64 row = row_off[rank_at(S, rb + lane)] + 1 + i0;
-      myb = entry_off[row];
-      mym = entry_off[row + min(1u, nrow)];
-      mye = entry_off[row + nrow];
+  // entry boundaries of a round's ranks: lane p (SP_IB + 1) + q holds the
+  // start of row i0 + q of rank p (q = nrow: the end of its last row); the
+  // next round's are loaded while a round is summed
+  constexpr u32 NB = SP_IB + 1;
+  auto offsets = [&](u32 rb, u64& mine) {
+    mine = 0;
+    const u32 p = (u32)lane / NB, q = (u32)lane % NB;
+    if ((u32)lane < SP_PR * NB && rb + p < r_end) {
+      const u64 row = row_off[rank_at(S, rb + p)] + 1 + i0;
+      mine = entry_off[row + min(q, nrow)];
     }
   };
-  u64 nb_, nm_, ne_;
-  offsets(r_begin, nb_, nm_, ne_);
+  u64 next_;
+  offsets(r_begin, next_);
   for (u32 rb = r_begin; rb < r_end; rb += SP_PR) {
-    const u64 myb = nb_, mym = nm_, mye = ne_;
-    if (rb + SP_PR < r_end) offsets(rb + SP_PR, nb_, nm_, ne_);
-    u64 b[SP_PR], m[SP_PR], len[SP_PR + 1];
+    const u64 mine = next_;
+    if (rb + SP_PR < r_end) offsets(rb + SP_PR, next_);
+    u64 bnd[SP_PR][NB], len[SP_PR + 1];
     len[0] = 0;
 #pragma unroll
     for (u32 p = 0; p < SP_PR; ++p) {
-      b[p] = __shfl_sync(FULL, myb, p);
-      m[p] = __shfl_sync(FULL, mym, p);
-      len[p + 1] = len[p] + (__shfl_sync(FULL, mye, p) - b[p]);
+#pragma unroll
+      for (u32 q = 0; q < NB; ++q) bnd[p][q] = __shfl_sync(FULL, mine, p * NB + q);
+      len[p + 1] = len[p] + (bnd[p][SP_IB] - bnd[p][0]);
     }
     const u64 total = len[SP_PR];
     for (u64 vb = 0; vb < total; vb += 32 * SP_CU) {
@@ -760,16 +761,21 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
         u32 p = 0;
 #pragma unroll
         for (u32 q = 1; q < SP_PR; ++q) p += (v >= len[q]) ? 1u : 0u;
-        u64 bp = b[0], lp = len[0], mp = m[0];
+        u64 bp[NB], lp = len[0];
 #pragma unroll
-        for (u32 q = 1; q < SP_PR; ++q)
-          if (p == q) {
-            bp = b[q];
-            lp = len[q];
-            mp = m[q];
+        for (u32 q = 0; q < NB; ++q) bp[q] = bnd[0][q];
+#pragma unroll
+        for (u32 pp = 1; pp < SP_PR; ++pp)
+          if (p == pp) {
+            lp = len[pp];
+#pragma unroll
+            for (u32 q = 0; q < NB; ++q) bp[q] = bnd[pp][q];
           }
-        const u64 jj = bp + (v - lp);
-        slot[u] = p * SP_IB + ((v < total && SP_IB > 1 && jj >= mp) ? 1u : 0u);
+        const u64 jj = bp[0] + (v - lp);
+        u32 il = 0;  // the entry's row among the rank's rows of this warp
+#pragma unroll
+        for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bp[q]) ? 1u : 0u;
+        slot[u] = p * SP_IB + il;
         c[u] = v < total ? e_ctx[jj] : NONE32;
         t[u] = v < total ? e_time[jj] : 0ull;
       }
