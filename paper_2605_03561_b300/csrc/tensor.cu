@@ -784,15 +784,17 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_write(const TensorArgs A) {
       for (int j = 0; j < 4; ++j) {
         const u32 hb = __ballot_sync(FULL, (h4 >> j) & 1u);
         before += __popc(hb & below);
-        total += __popc(hb);
       }
+      total = __shfl_sync(FULL, before + __popc(h4), 31);
       const u32 base = nh;
       {
         u32 slot = base + before;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
           if ((h4 >> j) & 1u) {
-            const u32 c = cur.c[j] < T.C ? cur.c[j] : 0u;
+            // contexts are < C here: the count pass validated every sample
+            // before this pass is launched
+            const u32 c = cur.c[j];
             *reinterpret_cast<uint4*>(ring + (slot & (RING - 1))) =
                 make_uint4((u32)cur.t[j], (u32)(cur.t[j] >> 32), c, rel + (u32)j);
             ++slot;
