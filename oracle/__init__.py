@@ -201,6 +201,47 @@ class Analysis:
         lib().or_span_get(self.h, _p(out))
         return out
 
+    def prune(self, keep_num, keep_den, drop=None):
+        """Pruning of the calling context tree on the summary profile (Section
+        III-A, "Pruning Large Calling Context Trees": a strategy is evaluated
+        once on the summary profile, the aggregate of all parallel profiles,
+        then propagated to every parallel profile; Section VI-B drops the
+        regions under 1 % of the total runtime, and MPI internals and line
+        statements by class).
+
+        The summary profile holds, per context, its inclusive time summed
+        over the ranks; the total is the root's.  Context c is kept iff
+        summary[c] * keep_den >= total * keep_num (exact integers) and not
+        drop[c].  Every rank's exclusive and inclusive profile keeps the
+        entries of kept contexts, in order; a dropped context's time is not
+        moved elsewhere.  Returns (kept u8[C], summary u64[C], exclusive CSR,
+        inclusive CSR).  Written as plain loops; for small inputs."""
+        n_ctx = self.tr.C
+        inc = self.csr(INCL)
+        summary = [0] * n_ctx
+        for c, t in zip(inc["ctx"].tolist(), inc["time"].tolist()):
+            summary[c] += int(t)
+        parent = np.asarray(self.tr.parent).tolist()
+        root = parent.index(0xFFFFFFFF)
+        total = summary[root]
+        kept = [1 if summary[c] * keep_den >= total * keep_num and not (drop is not None and drop[c])
+                else 0 for c in range(n_ctx)]
+
+        def restrict(csr):
+            off, ctx, time, cnt = [0], [], [], []
+            for r in range(self.r1 - self.r0):
+                for j in range(int(csr["off"][r]), int(csr["off"][r + 1])):
+                    if kept[int(csr["ctx"][j])]:
+                        ctx.append(int(csr["ctx"][j]))
+                        time.append(int(csr["time"][j]))
+                        cnt.append(int(csr["cnt"][j]))
+                off.append(len(ctx))
+            return dict(off=np.array(off, np.uint64), ctx=np.array(ctx, np.uint32),
+                        time=np.array(time, np.uint64), cnt=np.array(cnt, np.uint32))
+
+        return (np.array(kept, np.uint8), np.array(summary, np.uint64),
+                restrict(self.csr(EXCL)), restrict(inc))
+
     def stats(self, metric=EXCL, ranks=None, ctxs=None, tau=(3, 1), cap=1 << 20, want_z=False):
         ranks, ctxs = _u32(ranks), _u32(ctxs)
         k = self.tr.C if ctxs is None else len(ctxs)
