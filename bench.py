@@ -725,6 +725,23 @@ def run_gpu(args):
                 "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_launch * 1e3}
     step_bytes = alg_bytes  # the step's HBM floor is dominated by the tensor pass
 
+    # next row N1: pruning on the summary profile (the paper's 1 % rule) of one
+    # freshly loaded experiment, timed alone around the call (not in the step)
+    prune = None
+    if not args.no_prune:
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        before = e.info()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr = e.prune(keep=(1, 100))
+        el = time.perf_counter() - t0
+        e.free()
+        prune = {"keep": "1/100 of the summary total", "ms": el * 1e3, "kept": pr["n_kept"],
+                 "contexts": len(w["parent"]),
+                 "exclusive_entries": [before["excl_nnz"], pr["excl_nnz"]],
+                 "inclusive_entries": [before["incl_nnz"], pr["incl_nnz"]],
+                 "timing": "host clock around ta_prune_profiles (it synchronises)"}
+
     # e2e: the user-facing call with host (pinned) inputs and host outputs
     e2e = None
     if not args.no_e2e:
@@ -800,7 +817,7 @@ def run_gpu(args):
                                       ("validate_ms", "tensor_count_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "batched_vs_plain": batched, "serving": serving,
+                "batched_vs_plain": batched, "serving": serving, "prune": prune,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -823,6 +840,7 @@ def main():
                    help="skip the oracle split over all host cores")
     p.add_argument("--ref-records", type=float, default=5e6)
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-prune", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
     p.add_argument("--serve-queries", type=int, default=100000)

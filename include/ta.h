@@ -376,6 +376,49 @@ typedef struct ta_speedup_out {
 } ta_speedup_out;
 ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_speedup_out* o);
 
+/* --------------------------------------------------------------- pruning --- */
+
+/* Pruning of the calling context tree on the summary profile (Section III-A,
+ * "Pruning Large Calling Context Trees": a strategy is evaluated once on the
+ * summary profile, the aggregate of all parallel profiles, then propagated to
+ * every parallel profile; Section VI-B removes library internals, line
+ * statements and regions under 1 % of the total runtime).
+ * The summary profile holds each context's inclusive time summed over all
+ * ranks; the total is the root's.  Context c is kept iff
+ *     summary[c] * keep_den >= total * keep_num      (exact integers)
+ * and drop[c] is 0 (drop: optional per-context flags for classes the caller
+ * removes by name, such as library internals or line statements).  Every
+ * rank's exclusive and inclusive CSR is then compacted IN PLACE to the kept
+ * contexts (order kept; a pruned context's time is not moved elsewhere), so
+ * later calls and views see the pruned profiles; the iteration tensor is
+ * not changed.  Needs the inclusive CSR (loaded without TA_LOAD_NO_INCLUSIVE).
+ *   keep_num / keep_den  threshold fraction of the total (keep_den > 0; 1/100
+ *                        is the paper's 1 %; 0/1 keeps every context).
+ *   drop                 NULL or uint8[n_ctx] (nonzero: drop).
+ *   kept                 NULL or uint8[n_ctx] out: 1 for kept contexts.
+ *   summary              NULL or uint64[n_ctx] out: summary inclusive times.
+ *   n_kept, excl_nnz, incl_nnz  out: kept contexts and the CSRs' new sizes.
+ * mem_kind applies to drop, kept and summary.  Errors: INVALID_ARG (NULL, den
+ * 0, mem kind), STATE (no inclusive CSR, or the experiment is registered with
+ * a server, whose queries read its CSRs), OOM, CUDA. */
+typedef struct ta_prune_args {
+  uint32_t mem_kind;
+  uint32_t keep_num;
+  uint32_t keep_den;
+  uint32_t reserved;
+  const uint8_t* drop;
+} ta_prune_args;
+
+typedef struct ta_prune_out {
+  uint8_t* kept;
+  uint64_t* summary;
+  uint32_t n_kept;
+  uint32_t reserved;
+  uint64_t excl_nnz;
+  uint64_t incl_nnz;
+} ta_prune_out;
+ta_status ta_prune_profiles(ta_experiment* e, const ta_prune_args* a, ta_prune_out* o);
+
 /* ------------------------------------------- allocation-free statistics ---- */
 
 /* ta_context_stats over every context, for callers that must not allocate

@@ -179,6 +179,16 @@ class SpeedupOut(C.Structure):
     _fields_ = [("per_ctx", P), ("total", P)]
 
 
+class PruneArgs(C.Structure):
+    _fields_ = [("mem_kind", u32), ("keep_num", u32), ("keep_den", u32), ("reserved", u32),
+                ("drop", P)]
+
+
+class PruneOut(C.Structure):
+    _fields_ = [("kept", P), ("summary", P), ("n_kept", u32), ("reserved", u32),
+                ("excl_nnz", u64), ("incl_nnz", u64)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -217,6 +227,7 @@ _SIGS = {
     "ta_topology_rollup": (C.c_int, [P, C.POINTER(Topology), C.POINTER(TopoArgs),
                                      C.POINTER(TopoOut)]),
     "ta_potential_speedup": (C.c_int, [P, C.POINTER(SpeedupArgs), C.POINTER(SpeedupOut)]),
+    "ta_prune_profiles": (C.c_int, [P, C.POINTER(PruneArgs), C.POINTER(PruneOut)]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
     "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
@@ -560,6 +571,23 @@ class Experiment:
         t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
         t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
         return d, t
+
+    def prune(self, keep=(1, 100), drop=None):
+        """ta_prune_profiles: keep the contexts whose summary inclusive time is
+        at least keep[0]/keep[1] of the total and not flagged in drop; this
+        experiment's exclusive and inclusive CSRs are compacted in place.
+        Returns dict(kept u8[C], summary u64[C], n_kept, excl_nnz, incl_nnz)."""
+        a = PruneArgs()
+        a.mem_kind, a.keep_num, a.keep_den = MEM_HOST, int(keep[0]), int(keep[1])
+        dr = None if drop is None else _np(drop, np.uint8)
+        a.drop = _ptr(dr)
+        kept = np.zeros(self.C, np.uint8)
+        summary = np.zeros(self.C, np.uint64)
+        o = PruneOut()
+        o.kept, o.summary = _ptr(kept), _ptr(summary)
+        _check(lib().ta_prune_profiles(self.h, C.byref(a), C.byref(o)))
+        return dict(kept=kept, summary=summary, n_kept=int(o.n_kept), excl_nnz=int(o.excl_nnz),
+                    incl_nnz=int(o.incl_nnz))
 
 
 def _dev_to_np(ptr, n, dtype, device):

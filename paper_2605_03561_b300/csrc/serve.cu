@@ -916,6 +916,7 @@ ta_status ta_serve_close(ta_server* s) {
   if (s->h_result) cudaFreeHost(s->h_result);
   cudaStreamSynchronize(s->ctx->stream);
   for (auto& b : s->owned) dfree(s->ctx, b.p, b.n);
+  for (ta_experiment* e : s->exp_handles) --e->serve_refs;
   delete s;
   return TA_OK;
 }
@@ -982,6 +983,7 @@ ta_status ta_serve_add_experiment(ta_server* s, ta_experiment* e, const ta_topol
   if (st != TA_OK) return st;
   s->exps.push_back(d);
   s->exp_handles.push_back(e);
+  ++e->serve_refs;
   s->resident += need;
   *id = k;
   return TA_OK;

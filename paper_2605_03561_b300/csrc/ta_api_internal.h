@@ -97,6 +97,7 @@ struct ta_experiment {
   ta::u64 rows = 0, nnz = 0;
   ta::Csr x, in;
   bool has_incl = false;
+  ta::u32 serve_refs = 0;  // servers holding pointers into its products
   ta::u64 device_bytes = 0;
   std::vector<ta::Block> owned;
 
