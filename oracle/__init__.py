@@ -201,6 +201,53 @@ class Analysis:
         lib().or_span_get(self.h, _p(out))
         return out
 
+    def interval(self, t0, t1, incl=False):
+        """Per-rank profiles of the time window [t0, t1) (Section III-A's
+        trace slices; Section II-A samples: sample i of a rank is in ctx_i
+        during [ts_i, ts_{i+1}), the rank's last sample lasts 0 ns).  A sample
+        adds to its context the length of its interval inside the window and
+        counts as a sample iff ts_i lies in the window; a (rank, context) is
+        listed iff it gets time or samples.  With incl, every value is also
+        added along the context's path to the root.  Returns a CSR over the
+        analysed ranks (contexts ascending).  Plain loops; small inputs."""
+        tr = self.tr
+        parent = np.asarray(tr.parent).tolist()
+        off, ctx, time, cnt = [0], [], [], []
+        for r in range(self.r0, self.r1):
+            b, e = int(tr.rank_off[r]), int(tr.rank_off[r + 1])
+            acc = {}
+            for i in range(b, e):
+                ts = int(tr.ts[i])
+                nxt = int(tr.ts[i + 1]) if i + 1 < e else ts
+                d = max(0, min(nxt, t1) - max(ts, t0))
+                n = 1 if t0 <= ts < t1 else 0
+                if d == 0 and n == 0:
+                    continue
+                c = int(tr.ctx[i])
+                while True:
+                    v = acc.setdefault(c, [0, 0])
+                    v[0] += d
+                    v[1] += n
+                    if not incl or parent[c] == 0xFFFFFFFF:
+                        break
+                    c = parent[c]
+            for c in sorted(acc):
+                ctx.append(c)
+                time.append(acc[c][0])
+                cnt.append(acc[c][1])
+            off.append(len(ctx))
+        return dict(off=np.array(off, np.uint64), ctx=np.array(ctx, np.uint32),
+                    time=np.array(time, np.uint64), cnt=np.array(cnt, np.uint32))
+
+    def call_chain(self, c):
+        """The calling context of node c, bottom up (Section VI-B, "Obtaining
+        Calling Context"): c, its parent, ..., the root."""
+        parent = np.asarray(self.tr.parent).tolist()
+        out = [int(c)]
+        while parent[out[-1]] != 0xFFFFFFFF:
+            out.append(parent[out[-1]])
+        return np.array(out, np.uint32)
+
     def prune(self, keep_num, keep_den, drop=None):
         """Pruning of the calling context tree on the summary profile (Section
         III-A, "Pruning Large Calling Context Trees": a strategy is evaluated
