@@ -104,6 +104,7 @@ typedef struct ta_profile {
   double exclusive_ms, inclusive_ms;
   double stats_ms, topology_ms, speedup_ms;
   uint64_t tensor_launches, tensor_records, tensor_entries, tensor_rows;
+  double interval_ms; /* time-window profiles (ta_interval_profile)      */
 } ta_profile;
 ta_status ta_get_profile(ta_ctx* ctx, ta_profile* out, int reset);
 
@@ -127,13 +128,16 @@ ta_status ta_get_profile(ta_ctx* ctx, ta_profile* out, int reset);
  *                  and must stay valid and unchanged until
  *                  ta_experiment_free() (arrays not 16-byte aligned are
  *                  copied instead); TA_LOAD_NO_INCLUSIVE: skip the
- *                  inclusive rollup.
+ *                  inclusive rollup; TA_LOAD_KEEP_TRACES: keep the copied
+ *                  ts/ctx on the device after ingestion (by default they
+ *                  are released), for ta_interval_profile.
  *   nnz_hint, rows_hint  optional first-try capacities of the tensor (0 =
  *                  library default); a too-small hint only costs a re-run.
  * A sample lasts until the next sample of its rank; a rank's last sample
  * lasts 0 ns but still counts as one sample. */
 #define TA_LOAD_BORROW 1u
 #define TA_LOAD_NO_INCLUSIVE 2u
+#define TA_LOAD_KEEP_TRACES 4u
 
 typedef struct ta_trace_desc {
   uint32_t n_ranks;
@@ -418,6 +422,54 @@ typedef struct ta_prune_out {
   uint64_t incl_nnz;
 } ta_prune_out;
 ta_status ta_prune_profiles(ta_experiment* e, const ta_prune_args* a, ta_prune_out* o);
+
+/* ------------------------------------------------ time-window slices ---- */
+
+/* Per-rank profiles of the time window [t0, t1) (Section III-A: queries of
+ * rank ranges and time ranges over the traces, which hold time-ordered
+ * calling-context events and are searched by binary search on time).  Sample
+ * i of a rank is in ctx_i during [ts_i, ts_{i+1}) (the rank's last sample
+ * during [ts_i, ts_i]).  For ranks r0 <= r < r1 (relative index r - r0):
+ *   exclusive: per context, time = the summed length of its samples'
+ *              intervals inside the window, cnt = its samples whose ts lies
+ *              in the window; a context is listed iff time > 0 or cnt > 0
+ *              (the sample in progress at t0 gives time but no count).
+ *   inclusive: the exclusive window profile rolled up the calling context
+ *              tree as in ta_inclusive_rollup.
+ * Over the whole time range this is ta_exclusive / ta_inclusive_rollup of
+ * the same ranks, and adjacent windows add up exactly.  t1 <= t0 is an
+ * empty window (every rank empty).
+ * Needs the raw traces: loaded with TA_LOAD_KEEP_TRACES, or borrowed
+ * (TA_LOAD_BORROW with aligned device arrays).  Each rank's window is found
+ * by a warp-cooperative 32-ary search of its timestamps.
+ *   o  as for ta_exclusive, over r1 - r0 ranks: off[r1 - r0 + 1]; NULL
+ *      arrays = sizes only; nnz_cap too small = TA_ERR_CAPACITY (nnz set).
+ * The inclusive window needs only the tree, not the experiment's inclusive
+ * CSR.  Errors: INVALID_ARG (NULL, r0 > r1 or r1 > n_ranks, metric,
+ * mem_kind), STATE (the traces were released after loading), OOM, CUDA. */
+typedef struct ta_interval_args {
+  uint64_t t0, t1;
+  uint32_t r0, r1;
+  uint32_t metric; /* ta_metric */
+  uint32_t reserved;
+} ta_interval_args;
+ta_status ta_interval_profile(ta_experiment* e, const ta_interval_args* a, ta_csr_out* o);
+
+/* Calling contexts of n contexts, bottom up (Section VI-B, "Obtaining
+ * Calling Context": from a tree node up to the root, e.g. a communication
+ * leaf to the solver call that issued it): chain i is
+ * chain[off[i] .. off[i+1]) = ctxs[i], its parent, ..., the root; its length
+ * is the node's depth + 1.
+ *   mem_kind  of ctxs, off and chain.
+ *   ctxs[n]   context ids (< n_ctx; any order, repeats allowed).
+ *   off       [n + 1] out, or NULL (sizes only, with chain NULL).
+ *   chain     [chain_cap] out, or NULL.
+ *   total     out: off[n] (always set).
+ * Errors: INVALID_ARG (NULL e/ctxs/total, mem_kind, a context id >= n_ctx),
+ * CAPACITY (chain_cap < total; nothing written), OOM, CUDA. */
+ta_status ta_call_chains(const ta_experiment* e, uint32_t mem_kind, const uint32_t* ctxs,
+                         uint32_t n, uint64_t* off, uint32_t* chain, uint64_t chain_cap,
+                         uint64_t* total);
 
 /* ------------------------------------------- allocation-free statistics ---- */
 

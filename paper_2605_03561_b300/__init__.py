@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "ta.h")
 OK, INVALID_ARG, NOT_SORTED, BAD_CTX, BAD_CCT, OOM, CAPACITY, TIMEOUT, CUDA, STATE = range(10)
 MEM_HOST, MEM_DEVICE = 0, 1
 EXCLUSIVE, INCLUSIVE = 0, 1
-LOAD_BORROW, LOAD_NO_INCLUSIVE = 1, 2
+LOAD_BORROW, LOAD_NO_INCLUSIVE, LOAD_KEEP_TRACES = 1, 2, 4
 NO_PARENT = 0xFFFFFFFF
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "not_sorted", 3: "bad_ctx", 4: "bad_cct", 5: "oom",
                 6: "capacity", 7: "timeout", 8: "cuda", 9: "state"}
@@ -123,7 +123,7 @@ class Profile(C.Structure):
                 ("exclusive_ms", C.c_double), ("inclusive_ms", C.c_double),
                 ("stats_ms", C.c_double), ("topology_ms", C.c_double), ("speedup_ms", C.c_double),
                 ("tensor_launches", u64), ("tensor_records", u64), ("tensor_entries", u64),
-                ("tensor_rows", u64)]
+                ("tensor_rows", u64), ("interval_ms", C.c_double)]
 
 
 class BatchSetArgs(C.Structure):
@@ -184,6 +184,11 @@ class PruneArgs(C.Structure):
                 ("drop", P)]
 
 
+class IntervalArgs(C.Structure):
+    _fields_ = [("t0", u64), ("t1", u64), ("r0", u32), ("r1", u32), ("metric", u32),
+                ("reserved", u32)]
+
+
 class PruneOut(C.Structure):
     _fields_ = [("kept", P), ("summary", P), ("n_kept", u32), ("reserved", u32),
                 ("excl_nnz", u64), ("incl_nnz", u64)]
@@ -228,6 +233,8 @@ _SIGS = {
                                      C.POINTER(TopoOut)]),
     "ta_potential_speedup": (C.c_int, [P, C.POINTER(SpeedupArgs), C.POINTER(SpeedupOut)]),
     "ta_prune_profiles": (C.c_int, [P, C.POINTER(PruneArgs), C.POINTER(PruneOut)]),
+    "ta_interval_profile": (C.c_int, [P, C.POINTER(IntervalArgs), C.POINTER(CsrOut)]),
+    "ta_call_chains": (C.c_int, [P, u32, P, u32, P, P, u64, C.POINTER(u64)]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
     "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
@@ -364,9 +371,10 @@ class Context:
             pass
 
     def load(self, rank_off, ts, ctx, parent, marker: int, borrow: bool = False,
-             inclusive: bool = True, nnz_hint: int = 0, rows_hint: int = 0) -> "Experiment":
+             inclusive: bool = True, nnz_hint: int = 0, rows_hint: int = 0,
+             keep_traces: bool = False) -> "Experiment":
         return Experiment(self, rank_off, ts, ctx, parent, marker, borrow, inclusive, nnz_hint,
-                          rows_hint)
+                          rows_hint, keep_traces)
 
 
 def _np(a, dtype):
@@ -377,7 +385,7 @@ class Experiment:
     """Resident analysis products of one trace set (see ta_load_traces)."""
 
     def __init__(self, ctx: Context, rank_off, ts, cx, parent, marker, borrow=False,
-                 inclusive=True, nnz_hint=0, rows_hint=0):
+                 inclusive=True, nnz_hint=0, rows_hint=0, keep_traces=False):
         self.ctx = ctx
         dev = _is_dev(ts) or _is_dev(rank_off)
         if dev:
@@ -397,7 +405,8 @@ class Experiment:
         d.mem_kind = MEM_DEVICE if dev else MEM_HOST
         d.n_records = ts.shape[0]
         d.rank_off, d.ts, d.ctx, d.parent = _ptr(rank_off), _ptr(ts), _ptr(cx), _ptr(parent)
-        d.flags = (LOAD_BORROW if borrow else 0) | (0 if inclusive else LOAD_NO_INCLUSIVE)
+        d.flags = ((LOAD_BORROW if borrow else 0) | (0 if inclusive else LOAD_NO_INCLUSIVE)
+                   | (LOAD_KEEP_TRACES if keep_traces else 0))
         d.nnz_hint, d.rows_hint = nnz_hint, rows_hint
         h = P()
         _check(lib().ta_load_traces(ctx.h, C.byref(d), C.byref(h)))
@@ -571,6 +580,40 @@ class Experiment:
         t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
         t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
         return d, t
+
+    def interval(self, t0, t1, r0=0, r1=None, metric=EXCLUSIVE, device=False):
+        """ta_interval_profile: per-rank profiles of the time window [t0, t1)
+        for ranks [r0, r1) (the experiment must keep its traces).  Returns a
+        CSR dict like csr(), over r1 - r0 ranks."""
+        a = IntervalArgs()
+        a.t0, a.t1 = int(t0), int(t1)
+        a.r0, a.r1 = int(r0), self.R if r1 is None else int(r1)
+        a.metric = metric
+        o = CsrOut()
+        o.mem_kind = MEM_DEVICE if device else MEM_HOST
+        _check(lib().ta_interval_profile(self.h, C.byref(a), C.byref(o)))
+        nnz = int(o.nnz)
+        n = a.r1 - a.r0
+        out = dict(off=self._alloc(n + 1, np.uint64, device), ctx=self._alloc(nnz, np.uint32, device),
+                   time=self._alloc(nnz, np.uint64, device), cnt=self._alloc(nnz, np.uint32, device))
+        o.off, o.ctx, o.time, o.cnt = (_ptr(out[k]) for k in ("off", "ctx", "time", "cnt"))
+        o.nnz_cap = nnz
+        _check(lib().ta_interval_profile(self.h, C.byref(a), C.byref(o)))
+        return out
+
+    def call_chains(self, ctxs):
+        """ta_call_chains: the bottom-up calling context of each context id.
+        Returns a list of uint32 arrays (context, parent, ..., root)."""
+        cx = _np(ctxs, np.uint32)
+        n = len(cx)
+        off = np.zeros(n + 1, np.uint64)
+        total = u64()
+        _check(lib().ta_call_chains(self.h, MEM_HOST, _ptr(cx), n, _ptr(off), None, 0,
+                                    C.byref(total)))
+        chain = np.zeros(max(int(total.value), 1), np.uint32)
+        _check(lib().ta_call_chains(self.h, MEM_HOST, _ptr(cx), n, _ptr(off), _ptr(chain),
+                                    int(total.value), C.byref(total)))
+        return [chain[int(off[i]):int(off[i + 1])] for i in range(n)]
 
     def prune(self, keep=(1, 100), drop=None):
         """ta_prune_profiles: keep the contexts whose summary inclusive time is

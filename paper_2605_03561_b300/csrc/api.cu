@@ -333,9 +333,10 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   return TA_OK;
 }
 
-// Exclusive (mode 0) or inclusive (mode 1) per-rank CSR: count, scan, exact
-// allocation, write.
-ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
+// Exclusive per-rank CSR from the tensor in one pass: the write pass into a
+// per-rank scratch, exact counts, scan, allocation, copy; ranks above the
+// scratch cap are written by a second, restricted write pass.
+ta_status build_exclusive(ta_experiment* e, Pool& tmp) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const u32 R = e->R;
@@ -354,30 +355,19 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   TRY(tmp.get_n(gn, &A.gst_ctx, "csr stage"));
   TRY(tmp.get_n(gn, &A.gst_cnt, "csr stage"));
   TRY(tmp.get_n(gn, &A.gst_time, "csr stage"));
-  if (mode == 1) {
-    TRY(tmp.get_n(gn, &A.gst_dep, "csr stage"));
-    TRY(tmp.get_n(gn, &A.gst_par, "csr stage"));
-  }
   TRY(tmp.get_n((u64)R, &A.out_cnt, "csr counts"));
   TRY(tmp.get_n(scan_scratch_elems(R), &A.scan_scratch, "csr scan"));
-  Csr& out = mode == 0 ? e->x : e->in;
+  Csr& out = e->x;
   TRY(e->own(((u64)R + 1) * 8, (void**)&out.off, "csr off"));
-  A.mode = (u32)mode;
+  A.mode = 0;
   A.R = R;
   A.C = e->C;
   A.max_depth = e->max_depth;
   A.row_off_of_rank = e->row_off;
   A.entry_off = e->entry_off;
-  if (mode == 0) {
-    A.in_ctx = e->e_ctx;
-    A.in_time = e->e_time;
-    A.in_cnt = e->e_cnt;
-  } else {
-    A.in_off = e->x.off;
-    A.in_ctx = e->x.ctx;
-    A.in_time = e->x.time;
-    A.in_cnt = e->x.cnt;
-  }
+  A.in_ctx = e->e_ctx;
+  A.in_time = e->e_time;
+  A.in_cnt = e->e_cnt;
   A.parent = e->parent;
   A.depth = e->depth;
   A.out_off = out.off;
@@ -385,8 +375,90 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   A.status = (u32*)meta;
   A.gst_cap = P.gst_cap;
   A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
-  double* acc = mode == 0 ? &c->prof.exclusive_ms : &c->prof.inclusive_ms;
-  if (mode == 1) {  // ancestor lists of the tree, unless they would be too long
+  double* acc = &c->prof.exclusive_ms;
+  const u64 cap = kXsCap;
+  TRY(tmp.get_n((u64)R * cap, &A.xs_ctx, "exclusive scratch"));
+  TRY(tmp.get_n((u64)R * cap, &A.xs_time, "exclusive scratch"));
+  TRY(tmp.get_n((u64)R * cap, &A.xs_cnt, "exclusive scratch"));
+  A.xs_cap = (u32)cap;
+  A.n_over = (unsigned long long*)(meta + 2);
+  {
+    PhaseTimer timer(c, acc);
+    launch_excl_scratch(L, P, A);
+    timer.stop_and_sync();
+  }
+  u64 h[3];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, "exclusive (scratch)"));
+  TRY(status_from_flags((u32)h[0], "exclusive"));
+  out.nnz = h[1];
+  const u64 n = std::max<u64>(out.nnz, 1);
+  TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
+  TRY(e->own(n * 8, (void**)&out.time, "csr time"));
+  TRY(e->own(n * 4, (void**)&out.cnt, "csr cnt"));
+  A.out_ctx = out.ctx;
+  A.out_time = out.time;
+  A.out_cnt_e = out.cnt;
+  {
+    PhaseTimer timer(c, acc);
+    launch_excl_copy(L, A);
+    if (h[2]) {
+      A.only_over = 1;
+      launch_rank_write(L, P, A);
+    }
+    timer.stop_and_sync();
+  }
+  u64 f = 0;
+  TRY(copy(c, &f, meta, 8));
+  TRY(sync_check(c, "exclusive"));
+  return status_from_flags((u32)f, "exclusive");
+}
+
+}  // namespace
+
+// Inclusive rollup of a per-rank exclusive CSR over the experiment's tree:
+// ancestor lists (unless too long: level-by-level sweep), count, scan,
+// exact allocation through `alloc`, write.
+ta_status ta::build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out,
+                              const AllocFn& alloc, Pool& tmp, double* acc) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
+  RankCsrPlan P = plan_rank_csr(R, e->C, c->num_sms);
+  RankCsrArgs A;
+  std::memset(&A, 0, sizeof A);
+  u64* meta;
+  TRY(tmp.get(64, (void**)&meta, "csr meta"));
+  cudaMemsetAsync(meta, 0, 64, c->stream);
+  const size_t gbm_bytes = P.bm_in_smem ? 0 : (size_t)P.warps() * bm_words(e->C) * 4;
+  if (gbm_bytes) {
+    TRY(tmp.get(gbm_bytes, (void**)&A.gbm, "csr bitmaps"));
+    cudaMemsetAsync(A.gbm, 0, gbm_bytes, c->stream);
+  }
+  const size_t gn = (size_t)P.warps() * P.gst_cap;
+  TRY(tmp.get_n(gn, &A.gst_ctx, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_cnt, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_time, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_dep, "csr stage"));
+  TRY(tmp.get_n(gn, &A.gst_par, "csr stage"));
+  TRY(tmp.get_n(std::max<u64>(R, 1), &A.out_cnt, "csr counts"));
+  TRY(tmp.get_n(scan_scratch_elems(R), &A.scan_scratch, "csr scan"));
+  TRY(alloc(((u64)R + 1) * 8, (void**)&out.off, "csr off"));
+  A.mode = 1;
+  A.R = R;
+  A.C = e->C;
+  A.max_depth = e->max_depth;
+  A.in_off = in.off;
+  A.in_ctx = in.ctx;
+  A.in_time = in.time;
+  A.in_cnt = in.cnt;
+  A.parent = e->parent;
+  A.depth = e->depth;
+  A.out_off = out.off;
+  A.total = meta + 1;
+  A.status = (u32*)meta;
+  A.gst_cap = P.gst_cap;
+  A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
+  {  // ancestor lists of the tree, unless they would be too long
     PhaseTimer timer(c, acc);
     u32* len;
     u64 *aoff, *ascr;
@@ -405,47 +477,6 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
       A.anc = anc;
     }
   }
-  if (mode == 0) {
-    // one pass: the write pass first, into a per-rank scratch of kXsCap
-    // entries; exact counts, scan, allocation, copy; ranks above the cap
-    // are written by a second, restricted write pass
-    const u64 cap = kXsCap;
-    TRY(tmp.get_n((u64)R * cap, &A.xs_ctx, "exclusive scratch"));
-    TRY(tmp.get_n((u64)R * cap, &A.xs_time, "exclusive scratch"));
-    TRY(tmp.get_n((u64)R * cap, &A.xs_cnt, "exclusive scratch"));
-    A.xs_cap = (u32)cap;
-    A.n_over = (unsigned long long*)(meta + 2);
-    {
-      PhaseTimer timer(c, acc);
-      launch_excl_scratch(L, P, A);
-      timer.stop_and_sync();
-    }
-    u64 h[3];
-    TRY(copy(c, h, meta, sizeof h));
-    TRY(sync_check(c, "exclusive (scratch)"));
-    TRY(status_from_flags((u32)h[0], "exclusive"));
-    out.nnz = h[1];
-    const u64 n = std::max<u64>(out.nnz, 1);
-    TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
-    TRY(e->own(n * 8, (void**)&out.time, "csr time"));
-    TRY(e->own(n * 4, (void**)&out.cnt, "csr cnt"));
-    A.out_ctx = out.ctx;
-    A.out_time = out.time;
-    A.out_cnt_e = out.cnt;
-    {
-      PhaseTimer timer(c, acc);
-      launch_excl_copy(L, A);
-      if (h[2]) {
-        A.only_over = 1;
-        launch_rank_write(L, P, A);
-      }
-      timer.stop_and_sync();
-    }
-    u64 f = 0;
-    TRY(copy(c, &f, meta, 8));
-    TRY(sync_check(c, "exclusive"));
-    return status_from_flags((u32)f, "exclusive");
-  }
   {
     PhaseTimer timer(c, acc);
     launch_rank_count(L, P, A);
@@ -453,12 +484,12 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   }
   u64 h[2];
   TRY(copy(c, h, meta, sizeof h));
-  TRY(sync_check(c, mode == 0 ? "exclusive (count)" : "inclusive (count)"));
+  TRY(sync_check(c, "inclusive (count)"));
   out.nnz = h[1];
   const u64 n = std::max<u64>(out.nnz, 1);
-  TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
-  TRY(e->own(n * 8, (void**)&out.time, "csr time"));
-  TRY(e->own(n * 4, (void**)&out.cnt, "csr cnt"));
+  TRY(alloc(n * 4, (void**)&out.ctx, "csr ctx"));
+  TRY(alloc(n * 8, (void**)&out.time, "csr time"));
+  TRY(alloc(n * 4, (void**)&out.cnt, "csr cnt"));
   A.out_ctx = out.ctx;
   A.out_time = out.time;
   A.out_cnt_e = out.cnt;
@@ -469,9 +500,11 @@ ta_status build_rank_csr(ta_experiment* e, int mode, Pool& tmp) {
   }
   u64 f = 0;
   TRY(copy(c, &f, meta, 8));
-  TRY(sync_check(c, mode == 0 ? "exclusive" : "inclusive"));
-  return status_from_flags((u32)f, mode == 0 ? "exclusive" : "inclusive");
+  TRY(sync_check(c, "inclusive"));
+  return status_from_flags((u32)f, "inclusive");
 }
+
+namespace {
 
 ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& tmp) {
   Launch L{c->stream, c->num_sms, &c->launches};
@@ -529,12 +562,14 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   e->max_span = h[1];
   TRY(build_tensor(e, d, tmp));
   launch_n_iter(L, e->row_off, R, e->n_iter);
-  TRY(build_rank_csr(e, 0, tmp));
+  TRY(build_exclusive(e, tmp));
   if (!(d->flags & TA_LOAD_NO_INCLUSIVE)) {
-    TRY(build_rank_csr(e, 1, tmp));
+    const AllocFn own = [e](size_t n, void** p, const char* w) { return e->own(n, p, w); };
+    TRY(build_inclusive(e, e->x, R, e->in, own, tmp, &c->prof.inclusive_ms));
     e->has_incl = true;
   }
-  if (e->owns_traces) {  // raw traces are not needed after ingestion
+  // raw traces are not needed after ingestion unless kept for time windows
+  if (e->owns_traces && !(d->flags & TA_LOAD_KEEP_TRACES)) {
     e->disown((void*)e->ts);
     e->disown((void*)e->ctxv);
     e->ts = nullptr;

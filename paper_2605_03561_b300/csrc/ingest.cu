@@ -202,17 +202,6 @@ void launch_n_iter(const Launch& L, const u64* row_off_of_rank, u32 R, u32* n_it
   L.count();
 }
 
-// Set bits of a bitmap (one warp).
-__device__ __forceinline__ u32 bm_count_warp(const Bm& b, int lane) {
-  u32 sum = 0;
-  for (u32 g = 0; g < b.W2; g += 32) {
-    const u32 w2 = g + lane;
-    const u32 bits = (w2 < b.W2) ? vld(&b.L2[w2]) : 0u;
-    for (u32 x = bits; x; x &= x - 1) sum += __popc(vld(&b.L1[w2 * 32 + __ffs(x) - 1]));
-  }
-  return __reduce_add_sync(FULL, sum);
-}
-
 // ---------------------------------------------------------------------------
 // Per-rank CSR of distinct contexts, one warp per rank (grid-stride), in two
 // passes with a scan between them (no rank waits for another):

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <vector>
 
 #include "ta.h"
@@ -105,3 +106,13 @@ struct ta_experiment {
   void disown(void* p);
   void drop();
 };
+
+namespace ta {
+// Device allocation for a product (experiment-owned or a call's temporary).
+using AllocFn = std::function<ta_status(size_t, void**, const char*)>;
+// Inclusive rollup (Section II-A) of the per-rank exclusive CSR `in` of R
+// ranks over e's calling context tree into `out` (arrays from `alloc`);
+// device time is added to *acc.
+ta_status build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out, const AllocFn& alloc,
+                          Pool& tmp, double* acc);
+}  // namespace ta

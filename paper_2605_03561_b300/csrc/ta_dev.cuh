@@ -179,6 +179,17 @@ __device__ __forceinline__ void bm_enumerate_warp(const Bm& b, u32* out_ctx, int
   }
 }
 
+// One warp: the number of set bits.
+__device__ __forceinline__ u32 bm_count_warp(const Bm& b, int lane) {
+  u32 sum = 0;
+  for (u32 g = 0; g < b.W2; g += 32) {
+    const u32 w2 = g + lane;
+    const u32 bits = (w2 < b.W2) ? vld(&b.L2[w2]) : 0u;
+    for (u32 x = bits; x; x &= x - 1) sum += __popc(vld(&b.L1[w2 * 32 + __ffs(x) - 1]));
+  }
+  return __reduce_add_sync(FULL, sum);
+}
+
 // One warp: zeroes every set word (cost proportional to what was set).
 __device__ __forceinline__ void bm_clear_warp(const Bm& b, int lane) {
   for (u32 g = 0; g < b.W2; g += 32) {
