@@ -742,6 +742,55 @@ def run_gpu(args):
                  "inclusive_entries": [before["incl_nnz"], pr["incl_nnz"]],
                  "timing": "host clock around ta_prune_profiles (it synchronises)"}
 
+    # next row N2: per-rank profiles of a time window (borrowed traces stay on
+    # the device), all ranks; device time of the window kernels from the
+    # library's stream events.  Algorithmic bytes: the edge samples and inner
+    # tensor entries the kernels must read (counted by the library), the
+    # output entries and per-rank offsets.  Each timed call has new bounds
+    # (t1 moved by 1 ns) so that none reuses the previous result.
+    interval = None
+    if not args.no_interval:
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        ro = w["rank_off"].astype(np.int64)
+        ne = ro[1:] > ro[:-1]
+        ts_np = w["ts"].numpy()
+        first = ts_np[ro[:-1][ne]].astype(np.int64)
+        last = ts_np[ro[1:][ne] - 1].astype(np.int64)
+        med = int(np.median(last - first)) + int(np.median(first))
+        interval = {"timing": "CUDA events on the library stream around the window kernels "
+                              "(count pass, scan, write pass; inclusive adds the rollup); "
+                              "median of 5 calls after 1 warm-up, one computation per call",
+                    "window_10pct": "[45%, 55%) of the median rank's end time",
+                    "whole_range": "[0, 2^64 - 1)"}
+        big = (1 << 64) - 1
+        for name, (t0, t1, step) in (("window_10pct", (med * 45 // 100, med * 55 // 100, 1)),
+                                     ("whole_range", (0, big, -1))):
+            for metric, mname in ((ta.EXCLUSIVE, "exclusive"), (ta.INCLUSIVE, "inclusive")):
+                e.interval(t0, t1, metric=metric, device=True)
+                recs = []
+                for i in range(5):
+                    ctx.profile(reset=True)
+                    out = e.interval(t0, t1 + step * (i + 1), metric=metric, device=True)
+                    p = ctx.profile(reset=True)
+                    recs.append((p["interval_ms"], p["interval_samples"], p["interval_entries"]))
+                    nnz = int(out["ctx"].numel())
+                    samples = int(out["cnt"].to(torch.int64).sum().item()) \
+                        if metric == ta.EXCLUSIVE else None
+                    del out
+                recs.sort()
+                ms, es, ee = recs[2]
+                rec = {"ms": ms, "entries_out": nnz, "edge_samples_read": es,
+                       "inner_entries_read": ee}
+                if metric == ta.EXCLUSIVE:
+                    alg = 12 * es + 16 * ee + 16 * nnz + 40 * R
+                    gbs = alg / (ms / 1e3) / 1e9
+                    rec.update({"samples_in_window": samples, "alg_bytes": alg,
+                                "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"],
+                                "samples_per_s": samples / (ms / 1e3)})
+                interval[f"{name}_{mname}"] = rec
+        e.free()
+        del ts_np
+
     # e2e: the user-facing call with host (pinned) inputs and host outputs
     e2e = None
     if not args.no_e2e:
@@ -818,6 +867,7 @@ def run_gpu(args):
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched_vs_plain": batched, "serving": serving, "prune": prune,
+                "interval": interval,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -841,6 +891,7 @@ def main():
     p.add_argument("--ref-records", type=float, default=5e6)
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-prune", action="store_true")
+    p.add_argument("--no-interval", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
     p.add_argument("--serve-queries", type=int, default=100000)

@@ -105,6 +105,9 @@ typedef struct ta_profile {
   double stats_ms, topology_ms, speedup_ms;
   uint64_t tensor_launches, tensor_records, tensor_entries, tensor_rows;
   double interval_ms; /* time-window profiles (ta_interval_profile)      */
+  /* what the time-window kernels read: edge samples (12 B each) and inner
+     tensor entries (16 B each) */
+  uint64_t interval_samples, interval_entries;
 } ta_profile;
 ta_status ta_get_profile(ta_ctx* ctx, ta_profile* out, int reset);
 
@@ -441,7 +444,13 @@ ta_status ta_prune_profiles(ta_experiment* e, const ta_prune_args* a, ta_prune_o
  * empty window (every rank empty).
  * Needs the raw traces: loaded with TA_LOAD_KEEP_TRACES, or borrowed
  * (TA_LOAD_BORROW with aligned device arrays).  Each rank's window is found
- * by a warp-cooperative 32-ary search of its timestamps.
+ * by a warp-cooperative 32-ary search of its timestamps; iterations wholly
+ * inside the window are taken from the iteration tensor, the samples of the
+ * partial iterations at its edges one by one.  The first call builds an
+ * index of every tensor row's first sample (8 bytes per row, kept with the
+ * experiment).  The result of the last call stays with the experiment in
+ * device memory until a call with other arguments or ta_experiment_free, so
+ * the second call of the two-call pattern only copies it out.
  *   o  as for ta_exclusive, over r1 - r0 ranks: off[r1 - r0 + 1]; NULL
  *      arrays = sizes only; nnz_cap too small = TA_ERR_CAPACITY (nnz set).
  * The inclusive window needs only the tree, not the experiment's inclusive

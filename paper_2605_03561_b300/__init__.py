@@ -123,7 +123,8 @@ class Profile(C.Structure):
                 ("exclusive_ms", C.c_double), ("inclusive_ms", C.c_double),
                 ("stats_ms", C.c_double), ("topology_ms", C.c_double), ("speedup_ms", C.c_double),
                 ("tensor_launches", u64), ("tensor_records", u64), ("tensor_entries", u64),
-                ("tensor_rows", u64), ("interval_ms", C.c_double)]
+                ("tensor_rows", u64), ("interval_ms", C.c_double),
+                ("interval_samples", u64), ("interval_entries", u64)]
 
 
 class BatchSetArgs(C.Structure):

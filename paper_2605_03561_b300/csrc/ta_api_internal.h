@@ -98,6 +98,12 @@ struct ta_experiment {
   ta::u64 rows = 0, nnz = 0;
   ta::Csr x, in;
   bool has_incl = false;
+  // first sample of every tensor row ([rows + 1], global sample index; built
+  // by the first time-window call) and that call's last result
+  ta::u64* row_first = nullptr;
+  bool iv_valid = false;
+  ta_interval_args iv_args{};
+  ta::Csr iv;
   ta::u32 serve_refs = 0;  // servers holding pointers into its products
   ta::u64 device_bytes = 0;
   std::vector<ta::Block> owned;

@@ -35,7 +35,8 @@ def test_full_size_config3_sampled_and_invariants():
     g = synth.generate(cfg)
     R = cfg.n_ranks
     assert R == 100000 and int(g["rank_off"][-1]) > 1.5e9
-    e = context().load(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"])
+    e = context().load(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"],
+                       keep_traces=True)
     tr = oracle.Traces(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"])
     t = e.tensor()
     x = e.csr(ta.EXCLUSIVE)
@@ -82,3 +83,30 @@ def test_full_size_config3_sampled_and_invariants():
         assert int(gs["s2_lo"][i]) + (int(gs["s2_hi"][i]) << 64) == s2
         assert int(gs["max"][i]) == int(max(vals))
         assert set(INT_FIELDS) <= set(gs)
+    # time-window profiles: sampled rank ranges against the oracle, every
+    # rank's totals against the closed form (overlap of the window with the
+    # rank's span; samples with ts in the window)
+    ts, ro = g["ts"], g["rank_off"].astype(np.int64)
+    lo, hi = int(ts[ro[:-1][ro[1:] > ro[:-1]]].min()), int(ts.max()) + 1
+    t0, t1 = lo + (hi - lo) * 45 // 100, lo + (hi - lo) * 55 // 100
+    win = e.interval(t0, t1)
+    for r0 in [0, R - 4] + sorted(rng.integers(1, R - 4, size=4).tolist()):
+        a = oracle.Analysis(tr, r0, r0 + 4, rows=False, incl=False)
+        o = a.interval(t0, t1)
+        for r in range(r0, r0 + 4):
+            b, q = int(win["off"][r]), int(win["off"][r + 1])
+            ob, oq = int(o["off"][r - r0]), int(o["off"][r - r0 + 1])
+            for k in ("ctx", "time", "cnt"):
+                assert np.array_equal(win[k][b:q], o[k][ob:oq]), ("interval", r, k)
+    wo = win["off"].astype(np.int64)
+    ct = np.concatenate([[0], np.cumsum(win["time"].astype(np.uint64), dtype=np.uint64)])
+    cn = np.concatenate([[0], np.cumsum(win["cnt"].astype(np.uint64), dtype=np.uint64)])
+    got_t, got_n = ct[wo[1:]] - ct[wo[:-1]], cn[wo[1:]] - cn[wo[:-1]]
+    for r in range(R):
+        b, q = int(ro[r]), int(ro[r + 1])
+        if q == b:
+            assert got_t[r] == 0 and got_n[r] == 0
+            continue
+        x = ts[b:q]
+        assert int(got_t[r]) == max(0, min(t1, int(x[-1])) - max(t0, int(x[0]))), r
+        assert int(got_n[r]) == int(np.searchsorted(x, t1) - np.searchsorted(x, t0)), r

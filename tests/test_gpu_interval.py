@@ -89,6 +89,47 @@ def test_random_windows_and_rank_ranges(seed):
     _check(tr, e, 0, BIG)
 
 
+def _iteration_starts(d):
+    """Timestamps of every iteration start (first sample of a marker run)."""
+    ts, cx, ro = d["ts"], d["ctx"], d["rank_off"].astype(np.int64)
+    first = np.zeros(len(cx), bool)
+    first[ro[:-1][ro[1:] > ro[:-1]]] = True
+    m = cx == d["marker"]
+    prev = np.concatenate([[False], m[:-1]])
+    return ts[m & (first | ~prev)]
+
+
+@pytest.mark.parametrize("name", ["many_iterations", "random_medium", "all_marker"])
+def test_windows_on_iteration_boundaries(name):
+    # window edges exactly at iteration starts: whole iterations inside the
+    # window come from the tensor, the edges from the samples
+    d = edge.case(name, 2)
+    tr, e = _load(d)
+    starts = np.unique(_iteration_starts(d))
+    rng = np.random.default_rng(7)
+    if len(starts) < 2:
+        pytest.skip("no iterations")
+    for _ in range(6):
+        a, b = sorted(int(x) for x in rng.choice(starts, size=2))
+        for t0, t1 in ((a, b), (a, b + 1), (a + 1, b), (a, BIG), (0, b)):
+            _check(tr, e, t0, t1)
+
+
+def test_repeated_calls_reuse_and_replace_the_result():
+    d = edge.case("random_medium", 5)
+    tr, e = _load(d)
+    ts = d["ts"]
+    t0, t1 = int(ts.max()) // 5, int(ts.max()) // 2
+    first = e.interval(t0, t1)
+    again = e.interval(t0, t1)
+    for k in KEYS:
+        assert np.array_equal(first[k], again[k])
+    _check(tr, e, t0 + 1, t1)  # other arguments: computed anew
+    _check(tr, e, t0, t1)
+    e.prune(keep=(1, 100))  # pruning the profiles does not touch the traces
+    _check(tr, e, t0, t1)
+
+
 def test_whole_range_equals_resident_profiles():
     g = synth.generate(synth.preset(2, seed=3, n_ranks=200, len_mean=6000.0))
     tr, e = _load(g)
