@@ -249,6 +249,22 @@ class Analysis:
             out.append(parent[out[-1]])
         return np.array(out, np.uint32)
 
+    def values(self, ctx, metric=EXCL, ranks=None):
+        """Per-rank value of context ctx over a rank subset (relative rank ids;
+        None: every analysed rank), 0 where the rank has no sample of it --
+        the per-rank series the paper clusters (Section VI-B)."""
+        csr = self.csr(metric)
+        ranks = range(self.r1 - self.r0) if ranks is None else ranks
+        out = []
+        for r in ranks:
+            v = 0
+            for j in range(int(csr["off"][r]), int(csr["off"][r + 1])):
+                if int(csr["ctx"][j]) == ctx:
+                    v = int(csr["time"][j])
+                    break
+            out.append(v)
+        return out
+
     def prune(self, keep_num, keep_den, drop=None):
         """Pruning of the calling context tree on the summary profile (Section
         III-A, "Pruning Large Calling Context Trees": a strategy is evaluated
@@ -370,6 +386,120 @@ class Analysis:
         t = {f: getattr(tot, f) for f, _ in SpeedupTotal._fields_ if f != "pad"}
         t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
         return d, t
+
+
+def dbscan(x, eps, min_pts):
+    """DBSCAN (Ester et al., as applied to per-rank times in Section VI-B) on
+    integer scalars.  The eps-neighbourhood of a point holds every point q
+    with |x_q - x_p| <= eps, itself included; a point is a core point when
+    its neighbourhood has at least min_pts points; clusters are the connected
+    components of core points, two cores being connected when they are
+    neighbours; a non-core point within eps of a core is a border point and
+    joins the cluster of its nearest core (equal distances: the cluster of
+    smaller values); every other point is noise (-1).  Clusters are numbered
+    in ascending order of value.  Returns (labels, core flags)."""
+    import bisect
+    n = len(x)
+    order = sorted(range(n), key=lambda i: x[i])
+    xs = [x[i] for i in order]
+
+    def region(p):
+        lo = bisect.bisect_left(xs, x[p] - eps)
+        hi = bisect.bisect_right(xs, x[p] + eps)
+        return [order[j] for j in range(lo, hi)]
+
+    core = []
+    for p in range(n):
+        lo = bisect.bisect_left(xs, x[p] - eps)
+        hi = bisect.bisect_right(xs, x[p] + eps)
+        core.append(hi - lo >= min_pts)
+    comp = [-1] * n
+    n_comp = 0
+    for p in order:  # expansion from the smallest unvisited core
+        if not core[p] or comp[p] >= 0:
+            continue
+        comp[p] = n_comp
+        stack = [p]
+        while stack:
+            q = stack.pop()
+            for o in region(q):
+                if core[o] and comp[o] < 0:
+                    comp[o] = n_comp
+                    stack.append(o)
+        n_comp += 1
+    labels = []
+    for p in range(n):
+        if core[p]:
+            labels.append(comp[p])
+            continue
+        best = None
+        for o in region(p):
+            if core[o]:
+                key = (abs(x[o] - x[p]), comp[o])
+                if best is None or key < best:
+                    best = key
+        labels.append(-1 if best is None else best[1])
+    return labels, core
+
+
+def kmeans(x, k, max_iter):
+    """K-Means (Lloyd's iteration; Section VI-B's stability check) on integer
+    scalars in exact rational arithmetic.  Start: centroid j is the value at
+    sorted position floor((2j + 1) n / (2k)).  Each assignment step orders
+    the clusters by centroid (stably) and gives every point to the first
+    cluster in that order at the smallest distance; each update step moves a
+    non-empty cluster's centroid to its mean (an empty one keeps its
+    centroid).  Stops when an assignment repeats the previous one or after
+    max_iter updates.  Returns (labels as positions in the final order,
+    centroids in that order as Fractions, updates made)."""
+    from fractions import Fraction
+    n = len(x)
+    xs = sorted(x)
+    cents = [Fraction(xs[(2 * j + 1) * n // (2 * k)]) for j in range(k)]
+
+    def assign(cents):
+        order = sorted(range(k), key=lambda j: cents[j])  # stable
+        cents = [cents[j] for j in order]
+        lab = [min(range(k), key=lambda j: (abs(v - cents[j]), j)) for v in x]
+        return cents, lab
+
+    cents, labels = assign(cents)
+    it = 0
+    while it < max_iter:
+        for j in range(k):
+            members = [v for v, l in zip(x, labels) if l == j]
+            if members:
+                cents[j] = Fraction(sum(members), len(members))
+        it += 1
+        cents, new = assign(cents)
+        same = new == labels
+        labels = new
+        if same:
+            break
+    return labels, cents, it
+
+
+def cluster_nodes(labels, node_of_rank, n_nodes, n_clusters):
+    """Node view of a rank clustering (Section VI-B maps rank clusters to
+    compute nodes): per cluster the nodes holding at least one of its ranks,
+    per pair of clusters i < j the nodes holding ranks of both, and the nodes
+    holding a noise rank."""
+    sets = [set() for _ in range(n_nodes)]
+    for l, nd in zip(labels, node_of_rank):
+        sets[nd].add(l)
+    per = [0] * n_clusters
+    pair = [[0] * n_clusters for _ in range(n_clusters)]
+    noise = 0
+    for s in sets:
+        if -1 in s:
+            noise += 1
+        ls = sorted(l for l in s if l >= 0)
+        for a in ls:
+            per[a] += 1
+        for i in range(len(ls)):
+            for j in range(i + 1, len(ls)):
+                pair[ls[i]][ls[j]] += 1
+    return per, pair, noise
 
 
 def savings_from_averages(avg_mean, avg_max, iterations, app_time):
