@@ -480,6 +480,84 @@ ta_status ta_call_chains(const ta_experiment* e, uint32_t mem_kind, const uint32
                          uint32_t n, uint64_t* off, uint32_t* chain, uint64_t chain_cap,
                          uint64_t* total);
 
+/* ------------------------------------------------ clustering of ranks ---- */
+
+/* Groups of ranks by their value of one context (Section VI-B: the ranks'
+ * times of a communication call site clustered with DBSCAN, the groups
+ * mapped to compute nodes, and K-Means over 2..5 groups as a stability
+ * check).  The value of rank r is x_r = the metric's time of ctx on r, 0
+ * where r has no sample of it (as in ta_context_stats).
+ *   TA_CLUSTER_DBSCAN (eps in ns, min_pts >= 1): the eps-neighbourhood of a
+ *     rank holds every rank of the subset whose value differs by at most eps,
+ *     itself included; a rank with at least min_pts neighbours is a core;
+ *     clusters are the connected components of cores (two cores are
+ *     connected when they are neighbours); a non-core within eps of a core
+ *     joins the cluster of its nearest core (equal distances: the cluster of
+ *     smaller values); every other rank is noise (label -1).
+ *   TA_CLUSTER_KMEANS (1 <= k <= 64; max_iter, 0 = 300): Lloyd's iteration
+ *     in exact rational arithmetic.  Centroid j starts at the value at
+ *     sorted position floor((2j + 1) n / (2k)).  Each assignment orders the
+ *     clusters by centroid (stably) and gives every rank to the first cluster
+ *     at the smallest distance; each update moves a non-empty cluster to its
+ *     mean (an empty one keeps its centroid); the iteration stops when an
+ *     assignment repeats the previous one or after max_iter updates.
+ * Both give clusters that are ranges of the sorted values; they are numbered
+ * in ascending order of value.
+ *   ranks         sorted unique rank subset, or NULL for all ranks; labels
+ *                 follow its order.
+ *   node_of_rank  NULL, or the node of every rank of the experiment (< n_nodes):
+ *                 then, when n_clusters <= 64, the node view is computed
+ *                 (Section VI-B's node-level correlation): per cluster the
+ *                 nodes holding one of its ranks, per pair i < j the nodes
+ *                 holding ranks of both (pair_nodes[i * cluster_cap + j]),
+ *                 and the nodes holding a noise rank.
+ *   mem_kind      of ranks, node_of_rank and every output array.
+ * Outputs: labels[n] (int32, or NULL), clusters[cluster_cap] (n, sum, min,
+ * max of the cluster's values; mean = (double)sum / (double)n; centroid =
+ * the mean for DBSCAN, the K-Means centroid S / c as (double)S / (double)c
+ * of its unreduced sum S and count c), n_clusters, n_noise, iterations
+ * (K-Means updates made), cluster_nodes[cluster_cap], pair_nodes
+ * [cluster_cap * cluster_cap], noise_nodes and node_view (1 when the node
+ * arrays were written).  More clusters than cluster_cap: TA_ERR_CAPACITY
+ * after the labels (n_clusters set).  Errors: INVALID_ARG (NULL, method,
+ * metric, ctx, subset, min_pts 0, k, a node id >= n_nodes), STATE
+ * (inclusive metric without the inclusive rollup), CAPACITY, OOM, CUDA. */
+#define TA_CLUSTER_DBSCAN 1u
+#define TA_CLUSTER_KMEANS 2u
+typedef struct ta_cluster_args {
+  uint32_t method;          /* TA_CLUSTER_DBSCAN or TA_CLUSTER_KMEANS */
+  uint32_t metric;          /* ta_metric                               */
+  uint32_t ctx;
+  uint32_t mem_kind;
+  const uint32_t* ranks;
+  uint32_t n_ranks_subset;
+  uint32_t min_pts;         /* DBSCAN                                  */
+  uint64_t eps;             /* DBSCAN, ns                              */
+  uint32_t k;               /* K-Means                                 */
+  uint32_t max_iter;        /* K-Means                                 */
+  const uint32_t* node_of_rank;
+  uint32_t n_nodes;
+  uint32_t reserved;
+} ta_cluster_args;
+typedef struct ta_cluster_info {
+  uint64_t n, sum, min, max;
+  double mean, centroid;
+} ta_cluster_info;
+typedef struct ta_cluster_out {
+  int32_t* labels;
+  ta_cluster_info* clusters;
+  uint32_t* cluster_nodes;
+  uint32_t* pair_nodes;
+  uint32_t cluster_cap;
+  uint32_t n_clusters;  /* out */
+  uint64_t n_noise;     /* out */
+  uint32_t iterations;  /* out */
+  uint32_t noise_nodes; /* out */
+  uint32_t node_view;   /* out */
+  uint32_t reserved;
+} ta_cluster_out;
+ta_status ta_cluster_ranks(ta_experiment* e, const ta_cluster_args* a, ta_cluster_out* o);
+
 /* ------------------------------------------- allocation-free statistics ---- */
 
 /* ta_context_stats over every context, for callers that must not allocate

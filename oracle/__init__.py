@@ -451,32 +451,34 @@ def kmeans(x, k, max_iter):
     non-empty cluster's centroid to its mean (an empty one keeps its
     centroid).  Stops when an assignment repeats the previous one or after
     max_iter updates.  Returns (labels as positions in the final order,
-    centroids in that order as Fractions, updates made)."""
+    centroids in that order as Fractions, updates made, the centroids as
+    unreduced (sum, count) pairs)."""
     from fractions import Fraction
     n = len(x)
     xs = sorted(x)
-    cents = [Fraction(xs[(2 * j + 1) * n // (2 * k)]) for j in range(k)]
+    pairs = [(xs[(2 * j + 1) * n // (2 * k)], 1) for j in range(k)]
 
-    def assign(cents):
-        order = sorted(range(k), key=lambda j: cents[j])  # stable
-        cents = [cents[j] for j in order]
+    def assign(pairs):
+        order = sorted(range(k), key=lambda j: Fraction(*pairs[j]))  # stable
+        pairs = [pairs[j] for j in order]
+        cents = [Fraction(*p) for p in pairs]
         lab = [min(range(k), key=lambda j: (abs(v - cents[j]), j)) for v in x]
-        return cents, lab
+        return pairs, lab
 
-    cents, labels = assign(cents)
+    pairs, labels = assign(pairs)
     it = 0
     while it < max_iter:
         for j in range(k):
             members = [v for v, l in zip(x, labels) if l == j]
             if members:
-                cents[j] = Fraction(sum(members), len(members))
+                pairs[j] = (sum(members), len(members))
         it += 1
-        cents, new = assign(cents)
+        pairs, new = assign(pairs)
         same = new == labels
         labels = new
         if same:
             break
-    return labels, cents, it
+    return labels, [Fraction(*p) for p in pairs], it, pairs
 
 
 def cluster_nodes(labels, node_of_rank, n_nodes, n_clusters):

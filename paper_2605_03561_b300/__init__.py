@@ -190,6 +190,27 @@ class IntervalArgs(C.Structure):
                 ("reserved", u32)]
 
 
+class ClusterArgs(C.Structure):
+    _fields_ = [("method", u32), ("metric", u32), ("ctx", u32), ("mem_kind", u32),
+                ("ranks", P), ("n_ranks_subset", u32), ("min_pts", u32), ("eps", u64),
+                ("k", u32), ("max_iter", u32), ("node_of_rank", P), ("n_nodes", u32),
+                ("reserved", u32)]
+
+
+class ClusterInfo(C.Structure):
+    _fields_ = [("n", u64), ("sum", u64), ("min", u64), ("max", u64), ("mean", C.c_double),
+                ("centroid", C.c_double)]
+
+
+class ClusterOut(C.Structure):
+    _fields_ = [("labels", P), ("clusters", P), ("cluster_nodes", P), ("pair_nodes", P),
+                ("cluster_cap", u32), ("n_clusters", u32), ("n_noise", u64), ("iterations", u32),
+                ("noise_nodes", u32), ("node_view", u32), ("reserved", u32)]
+
+
+CLUSTER_DBSCAN, CLUSTER_KMEANS = 1, 2
+
+
 class PruneOut(C.Structure):
     _fields_ = [("kept", P), ("summary", P), ("n_kept", u32), ("reserved", u32),
                 ("excl_nnz", u64), ("incl_nnz", u64)]
@@ -236,6 +257,7 @@ _SIGS = {
     "ta_prune_profiles": (C.c_int, [P, C.POINTER(PruneArgs), C.POINTER(PruneOut)]),
     "ta_interval_profile": (C.c_int, [P, C.POINTER(IntervalArgs), C.POINTER(CsrOut)]),
     "ta_call_chains": (C.c_int, [P, u32, P, u32, P, P, u64, C.POINTER(u64)]),
+    "ta_cluster_ranks": (C.c_int, [P, C.POINTER(ClusterArgs), C.POINTER(ClusterOut)]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
     "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
@@ -615,6 +637,44 @@ class Experiment:
         _check(lib().ta_call_chains(self.h, MEM_HOST, _ptr(cx), n, _ptr(off), _ptr(chain),
                                     int(total.value), C.byref(total)))
         return [chain[int(off[i]):int(off[i + 1])] for i in range(n)]
+
+    def cluster(self, ctx, method="dbscan", eps=0, min_pts=1, k=2, max_iter=0, metric=EXCLUSIVE,
+                ranks=None, node_of_rank=None, n_nodes=0):
+        """ta_cluster_ranks: DBSCAN (eps ns, min_pts) or K-Means (k, max_iter)
+        over the ranks' values of ctx.  Returns dict(labels int32[n], clusters
+        (dict of arrays n, sum, min, max, mean, centroid, in ascending value),
+        n_clusters, n_noise, iterations, and with node_of_rank: cluster_nodes,
+        pair_nodes [nc, nc] (entry i, j for i < j), noise_nodes)."""
+        a = ClusterArgs()
+        a.method = CLUSTER_DBSCAN if method == "dbscan" else CLUSTER_KMEANS
+        a.metric, a.ctx, a.mem_kind = metric, int(ctx), MEM_HOST
+        rk = None if ranks is None else _np(ranks, np.uint32)
+        a.ranks, a.n_ranks_subset = _ptr(rk), 0 if rk is None else len(rk)
+        a.min_pts, a.eps, a.k, a.max_iter = int(min_pts), int(eps), int(k), int(max_iter)
+        nd = None if node_of_rank is None else _np(node_of_rank, np.uint32)
+        a.node_of_rank, a.n_nodes = _ptr(nd), int(n_nodes)
+        n = self.R if rk is None else len(rk)
+        labels = np.zeros(max(n, 1), np.int32)
+        o = ClusterOut()
+        o.labels = _ptr(labels)
+        _check(lib().ta_cluster_ranks(self.h, C.byref(a), C.byref(o)))
+        nc = int(o.n_clusters)
+        cl = (ClusterInfo * max(nc, 1))()
+        per = np.zeros(max(nc, 1), np.uint32)
+        pair = np.zeros((max(nc, 1), max(nc, 1)), np.uint32)
+        o = ClusterOut()
+        o.labels, o.clusters, o.cluster_cap = _ptr(labels), C.addressof(cl), nc
+        if nd is not None:
+            o.cluster_nodes, o.pair_nodes = _ptr(per), _ptr(pair)
+        _check(lib().ta_cluster_ranks(self.h, C.byref(a), C.byref(o)))
+        out = dict(labels=labels[:n], n_clusters=nc, n_noise=int(o.n_noise),
+                   iterations=int(o.iterations),
+                   clusters={f: np.array([getattr(x, f) for x in cl[:nc]])
+                             for f, _ in ClusterInfo._fields_})
+        if o.node_view:
+            out.update(cluster_nodes=per[:nc], pair_nodes=pair[:nc, :nc],
+                       noise_nodes=int(o.noise_nodes))
+        return out
 
     def prune(self, keep=(1, 100), drop=None):
         """ta_prune_profiles: keep the contexts whose summary inclusive time is

@@ -1390,6 +1390,15 @@ __global__ void k_write_batch_outliers(const u64* keys, const double* zs, u64 n,
 
 namespace ta {
 
+// Shared with the other entry points (declared in ta_api_internal.h).
+void sort_u64_pairs(const Launch& L, u64* keys, double* vals, u64 n) { sort_pairs(L, keys, vals, n); }
+const Csr* csr_of_metric(const ta_experiment* e, u32 metric) { return metric_csr(e, metric); }
+ta_status rank_subset_to_device(ta_ctx* c, Pool& tmp, const Launch& L, const u32* src, u32 n,
+                                u32 kind, u32 limit, u32* status, const u32** out) {
+  TRY(to_device(c, tmp, src, src ? n : 0, kind, out, "rank subset"));
+  return check_subset(c, L, *out, n, limit, status, "rank subset");
+}
+
 u64 batch_stats_scratch_bytes(u32 Ctot) { return (u64)Ctot * 72 + 64; }
 
 // All ranks, all contexts of every set, threshold tau; outlier keys

@@ -121,4 +121,13 @@ using AllocFn = std::function<ta_status(size_t, void**, const char*)>;
 // device time is added to *acc.
 ta_status build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out, const AllocFn& alloc,
                           Pool& tmp, double* acc);
+// Bitonic sort of n (key, value) pairs ascending by key, in buffers of at
+// least next_pow2(n) entries (stats.cu).
+void sort_u64_pairs(const Launch& L, u64* keys, double* vals, u64 n);
+// The experiment's CSR of a metric, or null (inclusive not built).
+const Csr* csr_of_metric(const ta_experiment* e, u32 metric);
+// A caller rank subset on the device (null stays null), checked sorted,
+// unique and below limit; status: one device u32 of scratch.
+ta_status rank_subset_to_device(ta_ctx* c, Pool& tmp, const Launch& L, const u32* src, u32 n,
+                                u32 kind, u32 limit, u32* status, const u32** out);
 }  // namespace ta

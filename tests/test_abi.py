@@ -19,7 +19,8 @@ STRUCTS = {"ta_trace_desc": ta.TraceDesc, "ta_experiment_info": ta.ExperimentInf
            "ta_speedup_args": ta.SpeedupArgs, "ta_speedup_ctx": ta.SpeedupCtx,
            "ta_speedup_total": ta.SpeedupTotal, "ta_speedup_out": ta.SpeedupOut,
            "ta_prune_args": ta.PruneArgs, "ta_prune_out": ta.PruneOut,
-           "ta_interval_args": ta.IntervalArgs,
+           "ta_interval_args": ta.IntervalArgs, "ta_cluster_args": ta.ClusterArgs,
+           "ta_cluster_info": ta.ClusterInfo, "ta_cluster_out": ta.ClusterOut,
            "ta_profile": ta.Profile, "ta_batch_args": ta.BatchArgs,
            "ta_batch_info": ta.BatchInfo, "ta_batch_set_view": ta.BatchSetView,
            "ta_batch_set_args": ta.BatchSetArgs,

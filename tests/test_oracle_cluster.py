@@ -77,14 +77,14 @@ def test_dbscan_matches_scikit_learn():
 
 
 def test_kmeans_hand_example_and_empty_cluster():
-    labels, cents, it = oracle.kmeans([1, 2, 3, 10, 11, 12], 2, 50)
+    labels, cents, it, _ = oracle.kmeans([1, 2, 3, 10, 11, 12], 2, 50)
     assert labels == [0, 0, 0, 1, 1, 1] and cents == [2, 11] and it == 1
     # duplicate starts: the second centroid equals the first and stays empty
-    labels, cents, it = oracle.kmeans([5, 5, 5, 5, 9], 3, 50)
+    labels, cents, it, _ = oracle.kmeans([5, 5, 5, 5, 9], 3, 50)
     assert cents[0] == cents[1] == 5 and cents[2] == 9
     assert labels == [0, 0, 0, 0, 2]
     # one cluster: the mean
-    labels, cents, it = oracle.kmeans([4, 8, 9], 1, 10)
+    labels, cents, it, _ = oracle.kmeans([4, 8, 9], 1, 10)
     assert labels == [0, 0, 0] and cents == [7]
 
 
@@ -95,7 +95,7 @@ def test_kmeans_fixed_point_and_scikit_learn():
         x = np.unique(_clumps(rng, 400, [100, 900, 1500, 4000, 4100], 200))
         rng.shuffle(x)
         k = int(rng.integers(2, 6))
-        labels, cents, it = oracle.kmeans(x.tolist(), k, 300)
+        labels, cents, it, _ = oracle.kmeans(x.tolist(), k, 300)
         assert it < 300
         lab = np.array(labels)
         for j in range(k):  # centroids are the means; points sit at their nearest
