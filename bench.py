@@ -791,6 +791,42 @@ def run_gpu(args):
         e.free()
         del ts_np
 
+    # next row N3: DBSCAN and K-Means (k = 2..5, the paper's stability check)
+    # over every rank's exclusive time of a communication context, with the
+    # node view; host clock around each call (it synchronises), median of 5
+    cluster = None
+    if not args.no_cluster:
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        c = aa["topo_ctx"]
+        node = w["topo"]["node_of_rank"]
+        nn = int(w["topo"]["n_nodes"])
+        x = e.csr(ta.EXCLUSIVE)
+        vals = x["time"][x["ctx"] == c]
+        med = int(np.median(vals)) if len(vals) else 1
+        cluster = {"ctx": c, "ranks": R, "nodes": nn,
+                   "timing": "host clock around ta_cluster_ranks (host outputs, node view), "
+                             "median of 5 calls after 1 warm-up"}
+        runs = [("dbscan", dict(eps=max(1, med // 100), min_pts=10))] + \
+               [(f"kmeans_k{k}", dict(k=k)) for k in (2, 3, 4, 5)]
+        for name, kw in runs:
+            meth = "dbscan" if name == "dbscan" else "kmeans"
+            e.cluster(c, meth, node_of_rank=node, n_nodes=nn, **kw)
+            el = []
+            for _ in range(5):
+                t0 = time.perf_counter()
+                got = e.cluster(c, meth, node_of_rank=node, n_nodes=nn, **kw)
+                el.append(time.perf_counter() - t0)
+            el.sort()
+            rec = {"ms": el[2] * 1e3, "clusters": got["n_clusters"], "noise": got["n_noise"],
+                   "iterations": got["iterations"],
+                   "cluster_sizes": got["clusters"]["n"].tolist()[:8]}
+            if "pair_nodes" in got:
+                pn = got["pair_nodes"]
+                rec["cluster_nodes"] = got["cluster_nodes"].tolist()[:8]
+                rec["nodes_in_two_clusters"] = int(np.triu(pn, 1).sum())
+            cluster[name] = rec
+        e.free()
+
     # e2e: the user-facing call with host (pinned) inputs and host outputs
     e2e = None
     if not args.no_e2e:
@@ -867,7 +903,7 @@ def run_gpu(args):
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched_vs_plain": batched, "serving": serving, "prune": prune,
-                "interval": interval,
+                "interval": interval, "cluster": cluster,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -892,6 +928,7 @@ def main():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-prune", action="store_true")
     p.add_argument("--no-interval", action="store_true")
+    p.add_argument("--no-cluster", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
     p.add_argument("--serve-queries", type=int, default=100000)
