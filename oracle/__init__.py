@@ -504,6 +504,65 @@ def cluster_nodes(labels, node_of_rank, n_nodes, n_clusters):
     return per, pair, noise
 
 
+# ---------------------------------------------------------------------------
+# Column operations (Section IV, Tables I-III: the DataFrame operation classes
+# the paper times on trace events).  Plain definitions over numpy arrays.
+
+def events_table(tr, r0, r1):
+    """The trace events of ranks [r0, r1) as columns: rank, ts, ctx and the
+    duration (next timestamp of the rank minus this one; 0 for a rank's last
+    event, Section II-A)."""
+    rank, ts, ctx, dur = [], [], [], []
+    for r in range(r0, r1):
+        b, e = int(tr.rank_off[r]), int(tr.rank_off[r + 1])
+        for i in range(b, e):
+            rank.append(r)
+            ts.append(int(tr.ts[i]))
+            ctx.append(int(tr.ctx[i]))
+            dur.append(int(tr.ts[i + 1]) - int(tr.ts[i]) if i + 1 < e else 0)
+    return dict(rank=np.array(rank, np.uint32), ts=np.array(ts, np.uint64),
+                ctx=np.array(ctx, np.uint32), dur=np.array(dur, np.uint64))
+
+
+def col_sort(keys):
+    """Stable ascending sort: (sorted keys, permutation)."""
+    perm = np.argsort(np.asarray(keys, np.uint64), kind="stable").astype(np.uint32)
+    return np.asarray(keys, np.uint64)[perm], perm
+
+
+def col_filter(col, lo, hi):
+    """Ascending indices i with lo <= col[i] <= hi."""
+    return np.array([i for i, v in enumerate(np.asarray(col).tolist()) if lo <= v <= hi],
+                    np.uint32)
+
+
+def col_group(seg_off, key, val):
+    """Per segment s (rows [seg_off[s], seg_off[s+1])) and key: the sum of val
+    and the row count, keys ascending within a segment (a group-by on
+    (segment, key))."""
+    off, keys, sums, cnts = [0], [], [], []
+    key, val = np.asarray(key).tolist(), np.asarray(val).tolist()
+    for s in range(len(seg_off) - 1):
+        acc = {}
+        for i in range(int(seg_off[s]), int(seg_off[s + 1])):
+            a = acc.setdefault(key[i], [0, 0])
+            a[0] += val[i]
+            a[1] += 1
+        for k in sorted(acc):
+            keys.append(k)
+            sums.append(acc[k][0])
+            cnts.append(acc[k][1])
+        off.append(len(keys))
+    return dict(off=np.array(off, np.uint64), key=np.array(keys, np.uint32),
+                sum=np.array(sums, np.uint64), cnt=np.array(cnts, np.uint32))
+
+
+def col_gather(key, dim):
+    """The merge of a fact column with a dimension table on its row id:
+    out[i] = dim[key[i]]."""
+    return np.array([dim[k] for k in np.asarray(key).tolist()], np.uint32)
+
+
 def savings_from_averages(avg_mean, avg_max, iterations, app_time):
     a = np.ascontiguousarray(avg_mean, np.float64)
     b = np.ascontiguousarray(avg_max, np.float64)
