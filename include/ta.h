@@ -558,6 +558,63 @@ typedef struct ta_cluster_out {
 } ta_cluster_out;
 ta_status ta_cluster_ranks(ta_experiment* e, const ta_cluster_args* a, ta_cluster_out* o);
 
+/* ------------------------------------------------ column operations ---- */
+
+/* The operation classes the paper times its DataFrame backends with on
+ * trace events (Section IV, Tables I-III: grouping, sorting, filtering,
+ * merging; scalar compare, vector add, in-place multiply, reduction sum,
+ * cumulative sum), as kernels over columns in device memory.  Every pointer
+ * below is a device pointer; every call runs on the context's stream and
+ * returns after its work is done.  n < 2^32 rows.  Errors: INVALID_ARG
+ * (NULL with n > 0, n too large, ranges), OOM, CUDA. */
+
+/* The trace events of ranks [r0, r1) of an experiment that kept its traces
+ * (TA_LOAD_KEEP_TRACES or borrowed), as columns of n = rank_off[r1] -
+ * rank_off[r0] rows in rank and time order: rank, ts, ctx and dur (the next
+ * timestamp of the rank minus this one, 0 for a rank's last event).  Any
+ * output may be NULL.  *n_out receives n.  STATE if the traces were
+ * released. */
+ta_status ta_events_table(ta_experiment* e, uint32_t r0, uint32_t r1, uint32_t* rank,
+                          uint64_t* ts, uint32_t* ctx, uint64_t* dur, uint64_t* n_out);
+
+/* Sorting: stable ascending sort of keys (LSD radix sort, 8-bit digits,
+ * only as many passes as the largest key needs).  keys_out[n] and perm[n]
+ * (perm[i] = the input row of the i-th smallest key) must not overlap keys. */
+ta_status ta_col_sort(ta_ctx* ctx, const uint64_t* keys, uint64_t n, uint64_t* keys_out,
+                      uint32_t* perm);
+
+/* Filtering: the ascending row ids i with lo <= col[i] <= hi into
+ * idx_out[n] (capacity n); *n_out (host) receives their number. */
+ta_status ta_col_filter(ta_ctx* ctx, const uint64_t* col, uint64_t n, uint64_t lo, uint64_t hi,
+                        uint32_t* idx_out, uint64_t* n_out);
+
+/* Grouping: per segment s (rows [seg_off[s], seg_off[s+1]); seg_off[0] = 0,
+ * non-decreasing, seg_off[n_seg] = n) and key (< n_keys), the sum of val
+ * and the row count, keys ascending within a segment, as a CSR:
+ * off_out[n_seg + 1], key_out / sum_out / cnt_out [out_cap].  A call with
+ * key_out, sum_out and cnt_out NULL reports the size only; *n_out (host)
+ * receives the number of groups; out_cap too small: CAPACITY.  Sums wrap
+ * modulo 2^64. */
+ta_status ta_col_group(ta_ctx* ctx, const uint64_t* seg_off, uint32_t n_seg, const uint32_t* key,
+                       uint32_t n_keys, const uint64_t* val, uint64_t n, uint64_t* off_out,
+                       uint32_t* key_out, uint64_t* sum_out, uint32_t* cnt_out,
+                       uint64_t out_cap, uint64_t* n_out);
+
+/* Merging: the join of a fact column with a dimension table on its row id,
+ * out[i] = dim[key[i]] (every key < n_dim, else INVALID_ARG). */
+ta_status ta_col_gather(ta_ctx* ctx, const uint32_t* key, uint64_t n, const uint32_t* dim,
+                        uint32_t n_dim, uint32_t* out);
+
+/* Scalar compare: mask[i] = col[i] > c.  Vector add: out[i] = a[i] + b[i].
+ * In-place multiply: a[i] *= s.  Reduction sum: *sum (host) = sum of a.
+ * Cumulative sum: out[i] = a[0] + ... + a[i].  Integer arithmetic modulo
+ * 2^64. */
+ta_status ta_col_compare(ta_ctx* ctx, const uint64_t* col, uint64_t n, uint64_t c, uint8_t* mask);
+ta_status ta_col_add(ta_ctx* ctx, const uint64_t* a, const uint64_t* b, uint64_t n, uint64_t* out);
+ta_status ta_col_scale(ta_ctx* ctx, uint64_t* a, uint64_t n, uint64_t s);
+ta_status ta_col_sum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* sum);
+ta_status ta_col_cumsum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* out);
+
 /* ------------------------------------------- allocation-free statistics ---- */
 
 /* ta_context_stats over every context, for callers that must not allocate

@@ -258,6 +258,16 @@ _SIGS = {
     "ta_interval_profile": (C.c_int, [P, C.POINTER(IntervalArgs), C.POINTER(CsrOut)]),
     "ta_call_chains": (C.c_int, [P, u32, P, u32, P, P, u64, C.POINTER(u64)]),
     "ta_cluster_ranks": (C.c_int, [P, C.POINTER(ClusterArgs), C.POINTER(ClusterOut)]),
+    "ta_events_table": (C.c_int, [P, u32, u32, P, P, P, P, C.POINTER(u64)]),
+    "ta_col_sort": (C.c_int, [P, P, u64, P, P]),
+    "ta_col_filter": (C.c_int, [P, P, u64, u64, u64, P, C.POINTER(u64)]),
+    "ta_col_group": (C.c_int, [P, P, u32, P, u32, P, u64, P, P, P, P, u64, C.POINTER(u64)]),
+    "ta_col_gather": (C.c_int, [P, P, u64, P, u32, P]),
+    "ta_col_compare": (C.c_int, [P, P, u64, u64, P]),
+    "ta_col_add": (C.c_int, [P, P, P, u64, P]),
+    "ta_col_scale": (C.c_int, [P, P, u64, u64]),
+    "ta_col_sum": (C.c_int, [P, P, u64, C.POINTER(u64)]),
+    "ta_col_cumsum": (C.c_int, [P, P, u64, P]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
     "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
@@ -402,6 +412,94 @@ class Context:
 
 def _np(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Columns:
+    """The column operations of include/ta.h (ta_events_table, ta_col_*) on
+    torch device tensors of this context's device."""
+
+    def __init__(self, ctx: "Context"):
+        self.ctx = ctx
+
+    def _t(self, n, dtype):
+        torch = _torch()
+        return torch.empty(max(int(n), 1), dtype=dtype, device=f"cuda:{self.ctx.device}")[:int(n)]
+
+    def events(self, e: "Experiment", r0=0, r1=None):
+        """dict(rank, ts, ctx, dur) of the events of ranks [r0, r1)."""
+        torch = _torch()
+        r1 = e.R if r1 is None else r1
+        n = u64()
+        _check(lib().ta_events_table(e.h, r0, r1, None, None, None, None, C.byref(n)))
+        out = dict(rank=self._t(n.value, torch.uint32), ts=self._t(n.value, torch.uint64),
+                   ctx=self._t(n.value, torch.uint32), dur=self._t(n.value, torch.uint64))
+        _check(lib().ta_events_table(e.h, r0, r1, out["rank"].data_ptr(), out["ts"].data_ptr(),
+                                     out["ctx"].data_ptr(), out["dur"].data_ptr(), C.byref(n)))
+        return out
+
+    def sort(self, keys):
+        torch = _torch()
+        n = keys.numel()
+        ko, perm = self._t(n, torch.uint64), self._t(n, torch.uint32)
+        _check(lib().ta_col_sort(self.ctx.h, keys.data_ptr(), n, ko.data_ptr(), perm.data_ptr()))
+        return ko, perm
+
+    def filter(self, col, lo, hi):
+        torch = _torch()
+        n = col.numel()
+        idx = self._t(n, torch.uint32)
+        m = u64()
+        _check(lib().ta_col_filter(self.ctx.h, col.data_ptr(), n, int(lo), int(hi),
+                                   idx.data_ptr(), C.byref(m)))
+        return idx[:m.value]
+
+    def group(self, seg_off, key, n_keys, val):
+        torch = _torch()
+        n_seg = seg_off.numel() - 1
+        off = self._t(n_seg + 1, torch.uint64)
+        m = u64()
+        args = (self.ctx.h, seg_off.data_ptr(), n_seg, key.data_ptr(), int(n_keys), val.data_ptr(),
+                key.numel(), off.data_ptr())
+        _check(lib().ta_col_group(*args, None, None, None, 0, C.byref(m)))
+        k, sm, cn = (self._t(m.value, torch.uint32), self._t(m.value, torch.uint64),
+                     self._t(m.value, torch.uint32))
+        _check(lib().ta_col_group(*args, k.data_ptr(), sm.data_ptr(), cn.data_ptr(), m.value,
+                                  C.byref(m)))
+        return dict(off=off, key=k, sum=sm, cnt=cn)
+
+    def gather(self, key, dim):
+        torch = _torch()
+        out = self._t(key.numel(), torch.uint32)
+        _check(lib().ta_col_gather(self.ctx.h, key.data_ptr(), key.numel(), dim.data_ptr(),
+                                   dim.numel(), out.data_ptr()))
+        return out
+
+    def compare(self, col, c):
+        torch = _torch()
+        m = self._t(col.numel(), torch.uint8)
+        _check(lib().ta_col_compare(self.ctx.h, col.data_ptr(), col.numel(), int(c), m.data_ptr()))
+        return m
+
+    def add(self, a, b):
+        torch = _torch()
+        out = self._t(a.numel(), torch.uint64)
+        _check(lib().ta_col_add(self.ctx.h, a.data_ptr(), b.data_ptr(), a.numel(), out.data_ptr()))
+        return out
+
+    def scale(self, a, s):
+        _check(lib().ta_col_scale(self.ctx.h, a.data_ptr(), a.numel(), int(s)))
+        return a
+
+    def sum(self, a):
+        v = u64()
+        _check(lib().ta_col_sum(self.ctx.h, a.data_ptr(), a.numel(), C.byref(v)))
+        return int(v.value)
+
+    def cumsum(self, a):
+        torch = _torch()
+        out = self._t(a.numel(), torch.uint64)
+        _check(lib().ta_col_cumsum(self.ctx.h, a.data_ptr(), a.numel(), out.data_ptr()))
+        return out
 
 
 class Experiment:

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(u64* sums, u64 nb, u64* to
   if (threadIdx.x == 0) *total = carry;
 }
 
-template <class T>
+template <class T, bool INCL = false>
 __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const T* __restrict__ in, u64 n,
                                                         const u64* block_base, u64* out) {
   __shared__ u64 s[SCAN_NT / 32];
@@ -85,17 +85,17 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const T* __restrict__ in
   u64 run = block_base[blockIdx.x] + (warp ? s[warp - 1] : 0) + x - sum;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    if (base + i < n) out[base + i] = run;
+    if (base + i < n) out[base + i] = INCL ? run + v[i] : run;
     run += v[i];
   }
 }
 
-template <class T>
+template <class T, bool INCL = false>
 void scan_impl(const Launch& L, const T* in, u64 n, u64* out, u64* total, u64* scratch) {
   const u64 nb = std::max<u64>(1, (n + SCAN_TILE - 1) / SCAN_TILE);
   k_scan_reduce<T><<<(unsigned)nb, SCAN_NT, 0, L.stream>>>(in, n, scratch);
   k_scan_blocks<<<1, 1024, 0, L.stream>>>(scratch, nb, total);
-  k_scan_apply<T><<<(unsigned)nb, SCAN_NT, 0, L.stream>>>(in, n, scratch, out);
+  k_scan_apply<T, INCL><<<(unsigned)nb, SCAN_NT, 0, L.stream>>>(in, n, scratch, out);
   L.count(3);
 }
 
@@ -108,6 +108,9 @@ void scan_exclusive(const Launch& L, const u32* in, u64 n, u64* out, u64* total,
 }
 void scan_exclusive(const Launch& L, const u64* in, u64 n, u64* out, u64* total, u64* scratch) {
   scan_impl<u64>(L, in, n, out, total, scratch);
+}
+void scan_inclusive(const Launch& L, const u64* in, u64 n, u64* out, u64* total, u64* scratch) {
+  scan_impl<u64, true>(L, in, n, out, total, scratch);
 }
 
 }  // namespace ta

@@ -290,5 +290,7 @@ void launch_batch_topology(const Launch& L, const BatchTopoArgs& T, u64 n_nodes,
 u64 scan_scratch_elems(u64 n);
 void scan_exclusive(const Launch& L, const u32* in, u64 n, u64* out, u64* total, u64* scratch);
 void scan_exclusive(const Launch& L, const u64* in, u64 n, u64* out, u64* total, u64* scratch);
+// Inclusive prefix sums (out[i] includes in[i]), same scratch.
+void scan_inclusive(const Launch& L, const u64* in, u64 n, u64* out, u64* total, u64* scratch);
 
 }  // namespace ta
