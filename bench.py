@@ -646,6 +646,78 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# cuDF on an A100 (Polaris), seconds, Table I of the paper (context only:
+# other data, other machine)
+PAPER_CUDF_S = {
+    10: dict(grouping=0.000982, sorting=0.000581, filtering=0.003548, merging=0.001739),
+    100: dict(grouping=0.001980, sorting=0.000520, filtering=0.001278, merging=0.002199),
+    1000: dict(grouping=0.002260, sorting=0.002224, filtering=0.002433, merging=0.005326),
+    10000: dict(grouping=0.003993, sorting=0.003165, filtering=0.003908, merging=0.007574),
+    100000: dict(grouping=0.024470, sorting=0.023193, filtering=0.008901, merging=0.046568),
+}
+
+
+def run_columns(ta, ctx, e, w, R, stream, peaks):
+    import torch
+    cols = ta.Columns(ctx)
+    node = torch.from_numpy(w["topo"]["node_of_rank"]).cuda()
+    out = {"rows": "trace events of ranks [0, T) of the workload: rank, ts, ctx, dur columns",
+           "ops": {"grouping": "group-by (rank, ctx): sum of dur and count",
+                   "sorting": "stable sort of dur with its permutation",
+                   "filtering": "row ids with dur >= 20 us",
+                   "merging": "join rank -> node (gather)",
+                   "scalar_compare": "dur > 10 us", "vector_add": "ts + dur",
+                   "inplace_multiply": "dur *= 3 (on a copy)", "reduction_sum": "sum of dur",
+                   "cumulative_sum": "inclusive prefix sum of dur"},
+           "paper_cudf_a100_s": PAPER_CUDF_S, "by_traces": {}}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=10):
+        fn()
+        ms = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            r = fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+            del r
+        ms.sort()
+        return 0.5 * (ms[len(ms) // 2 - 1] + ms[len(ms) // 2])
+
+    for T in (10, 100, 1000, 10000, 100000):
+        if T > R:
+            break
+        t = cols.events(e, 0, T)
+        n = int(t["dur"].numel())
+        seg = torch.from_numpy(w["rank_off"][:T + 1] - w["rank_off"][0]).cuda()
+        dcopy = t["dur"].clone()
+        C = len(w["parent"])
+        res = {"events": n}
+        res["grouping"] = timed(lambda: cols.group(seg, t["ctx"], C, t["dur"]))
+        res["sorting"] = timed(lambda: cols.sort(t["dur"]))
+        res["filtering"] = timed(lambda: cols.filter(t["dur"], 20000, (1 << 64) - 1))
+        res["merging"] = timed(lambda: cols.gather(t["rank"], node))
+        res["scalar_compare"] = timed(lambda: cols.compare(t["dur"], 10000))
+        res["vector_add"] = timed(lambda: cols.add(t["ts"], t["dur"]))
+        res["inplace_multiply"] = timed(lambda: cols.scale(dcopy, 3))
+        res["reduction_sum"] = timed(lambda: cols.sum(t["dur"]))
+        res["cumulative_sum"] = timed(lambda: cols.cumsum(t["dur"]))
+        # sort bytes: per pass 3 key reads, a value read and a key+value write
+        mx = int(t["dur"].view(torch.int64).max().item()) if n else 0
+        passes = (max(mx, 1).bit_length() + 7) // 8
+        res["sort_passes"] = passes
+        res["sorting_gbs"] = (40 * n * passes) / (res["sorting"] / 1e3) / 1e9 if n else 0.0
+        res["cumulative_sum_gbs"] = (16 * n) / (res["cumulative_sum"] / 1e3) / 1e9 if n else 0.0
+        out["by_traces"][str(T)] = res
+        del t, seg, dcopy
+        torch.cuda.empty_cache()
+    out["unit"] = "ms per call (median of 10)"
+    out["hbm_peak_gbs"] = peaks["hbm_gbs"]
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2605_03561_b300 as ta
@@ -827,6 +899,17 @@ def run_gpu(args):
             cluster[name] = rec
         e.free()
 
+    # next row N4: the DataFrame operation classes of Tables I-III as column
+    # kernels over the events of the first T traces (T = 10 .. 100,000),
+    # device time from CUDA events on the library stream, median of 10 runs
+    # (the paper averages 10)
+    columns = None
+    if not args.no_columns:
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        columns = run_columns(ta, ctx, e, w, R, stream, peaks)
+        e.free()
+        torch.cuda.empty_cache()
+
     # e2e: the user-facing call with host (pinned) inputs and host outputs
     e2e = None
     if not args.no_e2e:
@@ -903,7 +986,7 @@ def run_gpu(args):
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched_vs_plain": batched, "serving": serving, "prune": prune,
-                "interval": interval, "cluster": cluster,
+                "interval": interval, "cluster": cluster, "columns": columns,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -929,6 +1012,7 @@ def main():
     p.add_argument("--no-prune", action="store_true")
     p.add_argument("--no-interval", action="store_true")
     p.add_argument("--no-cluster", action="store_true")
+    p.add_argument("--no-columns", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
     p.add_argument("--serve-queries", type=int, default=100000)
