@@ -618,9 +618,10 @@ ta_status ta_col_cumsum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* ou
 /* ------------------------------------------- allocation-free statistics ---- */
 
 /* ta_context_stats over every context, for callers that must not allocate
- * device memory at call time -- for example code that runs while a CUDA
- * graph is being captured, or inside a service whose device memory comes
- * from a fixed budget that may not grow.  It uses no allocator: its
+ * device memory at call time -- for example a host runtime that manages all
+ * device memory itself and hands libraries only buffers it already owns,
+ * or a service whose device memory comes from a fixed budget that may not
+ * grow.  It uses no allocator: its
  * temporaries live in one fixed device array inside this library (about 6 MB,
  * held by every GPU that loads the library until the process exits).  The
  * paper has no counterpart; this is an interface convenience.

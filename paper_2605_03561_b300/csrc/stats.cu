@@ -1208,8 +1208,8 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
 
 // ---------------------------------------------------------------------------
 // Allocation-free statistics.  Callers that may not allocate device memory
-// (code running while a CUDA graph is being captured, or under a
-// fixed-budget allocator that forbids growth) get every temporary from one
+// (a host runtime that owns all device memory and passes only its own
+// buffers, or a fixed-budget allocator that forbids growth) get every temporary from one
 // file-scope device array instead of the allocator.  The array lives in every
 // GPU that loads this library until the process exits.
 namespace {

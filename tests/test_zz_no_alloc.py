@@ -1,13 +1,13 @@
 """The allocation-free statistics entry point (ta_context_stats_noalloc).
 
 Some callers cannot allocate device memory when they call the library -- for
-example while a CUDA graph is being captured, or inside a service held to a
-fixed device-memory budget.  This entry point takes device inputs and
-outputs and keeps its temporaries in a fixed array inside the library.  These
-tests call it through the C ABI twice in a row (the array keeps the previous
-call's contents) and check it against the allocating ta_context_stats,
-integers bit for bit and FP64 within 1e-12 relative.  The file is named to be
-collected last.
+example a host runtime that owns all device memory and hands libraries only
+its own buffers, or a service held to a fixed device-memory budget.  This
+entry point takes device inputs and outputs and keeps its temporaries in a
+fixed array inside the library.  These tests call it through the C ABI twice
+in a row (the array keeps the previous call's contents) and check it against
+the allocating ta_context_stats, integers bit for bit and FP64 within 1e-12
+relative.  The file is named to be collected last.
 """
 import ctypes as C
 
