@@ -46,11 +46,31 @@ __global__ void k_events(const u64* __restrict__ rank_off, const u64* __restrict
 // A pass orders by one 8-bit digit, stably: per tile of 4096 rows a digit
 // histogram (warp-aggregated shared atomics), a digit-major exclusive scan
 // of all tiles' histograms (so tile t's rows of digit d follow every earlier
-// tile's), then a scatter in which each warp owns 512 consecutive rows of
-// the tile: its digit counts, the warps' prefix per digit, and for every 32
-// rows the rank among equal digits in the round (__match_any_sync).
+// tile's), then a scatter.  In the scatter each warp owns 512 consecutive
+// rows of the tile: its digit counts, then per digit the
+// tile-local start (a scan over digits) and each warp's start within it,
+// then each row's rank among equal digits of its 32-row round (nine
+// ballots) places it in a shared-memory copy of the tile ordered
+// by digit; the copy is written out in order, so rows of one digit go to
+// consecutive addresses (coalesced) instead of 4096 scattered stores.
 constexpr int RS_NT = 256, RS_WARPS = RS_NT / 32, RS_PER_WARP = 512;
+constexpr int RS_ITEMS = RS_PER_WARP / 32;
 constexpr u32 RS_TILE = RS_WARPS * RS_PER_WARP;
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 12;  // keys u64 + values u32
+
+// Lanes of the warp holding the same 8-bit digit (valid lanes only match
+// valid lanes): nine ballots, constant time whatever the digit mix.
+__device__ __forceinline__ u32 digit_peers(u32 d, bool v) {
+  u32 peers = __ballot_sync(FULL, v);
+  if (!v) peers = ~peers;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const bool bit = (d >> b) & 1u;
+    const u32 bal = __ballot_sync(FULL, bit);
+    peers &= bit ? bal : ~bal;
+  }
+  return peers;
+}
 
 __global__ void __launch_bounds__(RS_NT) k_rs_count(const u64* __restrict__ keys, u64 n, u32 shift,
                                                     u64 n_tiles, u32* hist) {
@@ -63,58 +83,86 @@ __global__ void __launch_bounds__(RS_NT) k_rs_count(const u64* __restrict__ keys
   for (u32 k = threadIdx.x; k < RS_TILE; k += RS_NT) {
     const u64 i = base + k;
     const bool v = i < n;
-    const u32 d = v ? (u32)(keys[i] >> shift) & 255u : 256u + lane;
-    const u32 peers = __match_any_sync(FULL, d);
+    const u32 d = v ? (u32)(keys[i] >> shift) & 255u : 0u;
+    const u32 peers = digit_peers(d, v);
     if (v && (peers & lt) == 0) atomicAdd(&h[d], (u32)__popc(peers));
   }
   __syncthreads();
   hist[(u64)threadIdx.x * n_tiles + blockIdx.x] = h[threadIdx.x];
 }
 
-__global__ void __launch_bounds__(RS_NT) k_rs_scatter(const u64* __restrict__ keys_in,
+__global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__ keys_in,
                                                       const u32* __restrict__ vals_in, u64 n,
                                                       u32 shift, u64 n_tiles,
                                                       const u64* __restrict__ off, u64* keys_out,
                                                       u32* vals_out) {
+  extern __shared__ __align__(16) unsigned char rs_sm[];
+  u64* skey = (u64*)rs_sm;
+  u32* sval = (u32*)(skey + RS_TILE);
   __shared__ u32 wh[RS_WARPS][256];
+  __shared__ u32 lstart[256];
+  __shared__ u64 gbase[256];
+  __shared__ u32 wsum[RS_WARPS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt = (1u << lane) - 1u;
   for (u32 d = lane; d < 256; d += 32) wh[w][d] = 0;
+  const u64 tbase = (u64)blockIdx.x * RS_TILE;
+  const u64 wbase = tbase + (u64)w * RS_PER_WARP;
   __syncwarp();
-  const u64 wbase = (u64)blockIdx.x * RS_TILE + (u64)w * RS_PER_WARP;
-  for (int rd = 0; rd < RS_PER_WARP / 32; ++rd) {
+#pragma unroll 4
+  for (int rd = 0; rd < RS_ITEMS; ++rd) {
     const u64 i = wbase + (u64)rd * 32 + lane;
     const bool v = i < n;
-    const u32 d = v ? (u32)(keys_in[i] >> shift) & 255u : 256u + lane;
-    const u32 peers = __match_any_sync(FULL, d);
+    const u32 d = v ? (u32)(keys_in[i] >> shift) & 255u : 0u;
+    const u32 peers = digit_peers(d, v);
     if (v && (peers & lt) == 0) wh[w][d] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  {  // thread t: digit t's start for every warp of the tile
+  {  // thread t owns digit t: tile-local start (scan over digits), warp starts
     const u32 d = threadIdx.x;
-    u64 run = off[(u64)d * n_tiles + blockIdx.x];
+    u32 cnt = 0;
+    for (int q = 0; q < RS_WARPS; ++q) cnt += wh[q][d];
+    const u32 incl = warp_incl_scan(cnt, lane);
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    u32 before = 0;
+    for (int q = 0; q < w; ++q) before += wsum[q];
+    const u32 start = before + incl - cnt;
+    lstart[d] = start;
+    gbase[d] = off[(u64)d * n_tiles + blockIdx.x];
+    u32 run = start;
     for (int q = 0; q < RS_WARPS; ++q) {
       const u32 c = wh[q][d];
-      wh[q][d] = (u32)run;
+      wh[q][d] = run;
       run += c;
     }
   }
   __syncthreads();
-  for (int rd = 0; rd < RS_PER_WARP / 32; ++rd) {
+#pragma unroll 4
+  for (int rd = 0; rd < RS_ITEMS; ++rd) {
     const u64 i = wbase + (u64)rd * 32 + lane;
     const bool v = i < n;
-    const u64 key = v ? keys_in[i] : 0ull;
-    const u32 d = v ? (u32)(key >> shift) & 255u : 256u + lane;
-    const u32 peers = __match_any_sync(FULL, d);
+    const u64 key = v ? keys_in[i] : 0ull;  // a second read of the tile, from L2
+    const u32 d = (u32)(key >> shift) & 255u;
+    const u32 peers = digit_peers(d, v);
     const u32 pos = v ? wh[w][d] + __popc(peers & lt) : 0u;
     __syncwarp();
     if (v && (peers & lt) == 0) wh[w][d] += __popc(peers);
     __syncwarp();
     if (v) {
-      keys_out[pos] = key;
-      vals_out[pos] = vals_in ? vals_in[i] : (u32)i;
+      skey[pos] = key;
+      sval[pos] = vals_in ? vals_in[i] : (u32)i;
     }
+  }
+  __syncthreads();
+  const u32 m = (u32)min((u64)RS_TILE, n - tbase);
+  for (u32 j = threadIdx.x; j < m; j += RS_NT) {
+    const u64 key = skey[j];
+    const u32 d = (u32)(key >> shift) & 255u;
+    const u64 g = gbase[d] + (j - lstart[d]);
+    keys_out[g] = key;
+    vals_out[g] = sval[j];
   }
 }
 
@@ -430,6 +478,7 @@ extern "C" ta_status ta_col_sort(ta_ctx* c, const uint64_t* keys, uint64_t n, ui
   TRY(S.tmp.get_n(256 * n_tiles, &hist, "sort histograms"));
   TRY(S.tmp.get_n(256 * n_tiles + 1, &off, "sort offsets"));
   TRY(S.tmp.get_n(scan_scratch_elems(256 * n_tiles), &scratch, "sort scan"));
+  cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
   u64* kb[2] = {keys_out, tk};
   u32* vb[2] = {perm, tv};
   for (int p = 0; p < P; ++p) {
@@ -440,8 +489,8 @@ extern "C" ta_status ta_col_sort(ta_ctx* c, const uint64_t* keys, uint64_t n, ui
     k_rs_count<<<(unsigned)n_tiles, RS_NT, 0, c->stream>>>(kin, n, shift, n_tiles, hist);
     S.L.count();
     scan_exclusive(S.L, hist, 256 * n_tiles, off, off + 256 * n_tiles, scratch);
-    k_rs_scatter<<<(unsigned)n_tiles, RS_NT, 0, c->stream>>>(kin, vin, n, shift, n_tiles, off,
-                                                             kb[o], vb[o]);
+    k_rs_scatter<<<(unsigned)n_tiles, RS_NT, RS_SMEM, c->stream>>>(kin, vin, n, shift, n_tiles,
+                                                                   off, kb[o], vb[o]);
     S.L.count();
   }
   return sync_check(c, "ta_col_sort");

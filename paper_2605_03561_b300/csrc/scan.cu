@@ -23,11 +23,11 @@ template <class T>
 __global__ void __launch_bounds__(SCAN_NT) k_scan_reduce(const T* __restrict__ in, u64 n,
                                                          u64* block_sums) {
   __shared__ u64 s[SCAN_NT / 32];
-  const u64 base = (u64)blockIdx.x * SCAN_TILE + (u64)threadIdx.x * SCAN_ITEMS;
+  const u64 base = (u64)blockIdx.x * SCAN_TILE + threadIdx.x;  // coalesced: order is free
   u64 sum = 0;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i)
-    if (base + i < n) sum += in[base + i];
+    if (base + (u64)i * SCAN_NT < n) sum += in[base + (u64)i * SCAN_NT];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   sum = warp_sum(sum);
   if (lane == 0) s[warp] = sum;
@@ -60,16 +60,28 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(u64* sums, u64 nb, u64* to
   if (threadIdx.x == 0) *total = carry;
 }
 
+// The tile goes through shared memory twice so that global loads and stores
+// are coalesced while each thread scans SCAN_ITEMS consecutive elements (one
+// padding word per 16 keeps the per-thread runs on different banks).
+__device__ __forceinline__ u32 scan_pad(u32 x) { return x + (x >> 4); }
+
 template <class T, bool INCL = false>
 __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const T* __restrict__ in, u64 n,
                                                         const u64* block_base, u64* out) {
   __shared__ u64 s[SCAN_NT / 32];
-  const u64 base = (u64)blockIdx.x * SCAN_TILE + (u64)threadIdx.x * SCAN_ITEMS;
+  __shared__ u64 t[SCAN_TILE + SCAN_TILE / 16];
+  const u64 tile = (u64)blockIdx.x * SCAN_TILE;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const u32 j = (u32)i * SCAN_NT + threadIdx.x;
+    t[scan_pad(j)] = (tile + j < n) ? (u64)in[tile + j] : 0ull;
+  }
+  __syncthreads();
   u64 v[SCAN_ITEMS];
   u64 sum = 0;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    v[i] = (base + i < n) ? (u64)in[base + i] : 0ull;
+    v[i] = t[scan_pad(threadIdx.x * SCAN_ITEMS + i)];
     sum += v[i];
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -85,8 +97,14 @@ __global__ void __launch_bounds__(SCAN_NT) k_scan_apply(const T* __restrict__ in
   u64 run = block_base[blockIdx.x] + (warp ? s[warp - 1] : 0) + x - sum;
 #pragma unroll
   for (int i = 0; i < SCAN_ITEMS; ++i) {
-    if (base + i < n) out[base + i] = INCL ? run + v[i] : run;
+    t[scan_pad(threadIdx.x * SCAN_ITEMS + i)] = INCL ? run + v[i] : run;
     run += v[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const u32 j = (u32)i * SCAN_NT + threadIdx.x;
+    if (tile + j < n) out[tile + j] = t[scan_pad(j)];
   }
 }
 

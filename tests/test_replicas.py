@@ -38,7 +38,7 @@ def _rank(rank, world, port, times, out):
 def test_max_over_two_gloo_ranks():
     world = 2
     times = [12.5, 30.25]
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()  # no fork of a threaded process
     mp.spawn(_rank, args=(world, _free_port(), times, out), nprocs=world, join=True)
     assert out[0] == out[1] == max(times)
 
