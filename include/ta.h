@@ -763,7 +763,7 @@ ta_status ta_batch_get_set(const ta_batch* b, uint32_t set, ta_batch_set_view* v
  *
  * Query kinds (slices and per-context views of the tri-dimensional model,
  * Sections V and VI; statistics as ta_context_stats, rollup as
- * ta_topology_rollup):
+ * ta_topology_rollup; time windows of the traces, Section III-A):
  *   TA_Q_STATS   statistics of context ctx over a rank subset (sorted, unique,
  *                host array, copied at submit), threshold tau:
  *                payload ta_q_stats = the ta_ctx_stats ta_context_stats gives
@@ -781,6 +781,13 @@ ta_status ta_batch_get_set(const ta_batch* b, uint32_t set, ta_batch_set_view* v
  *                ta_q_racks header, uint64 rack_sum[n_racks],
  *                uint32 rack_flagged[n_racks], uint32 rack_nodes[n_racks],
  *                uint32 flagged_racks[n_flagged_racks].
+ *   TA_Q_WINDOW  exclusive time and samples of ctx in the time window
+ *                [t0, t1) on every rank of [r0, r1), as ta_interval_profile
+ *                (exclusive) would list them (0 where ctx is absent):
+ *                payload uint64 time[r1 - r0] then uint64 cnt[r1 - r0].
+ *                The experiment must have kept its traces
+ *                (TA_LOAD_KEEP_TRACES or borrowed) when it was added; metric
+ *                is ignored.
  * metric selects the exclusive or inclusive value (the inclusive rollup must
  * have been built).  Invalid queries are refused by ta_serve_submit
  * (TA_ERR_INVALID_ARG); a query larger than an arena returns
@@ -790,6 +797,7 @@ typedef struct ta_server ta_server;
 #define TA_Q_SLICE 2u
 #define TA_Q_TOPK 3u
 #define TA_Q_RACKS 4u
+#define TA_Q_WINDOW 5u
 typedef struct ta_serve_config {
   uint32_t max_batch;     /* queries per batch (0: 1024)                    */
   uint32_t n_streams;     /* batches in flight (0: 3)                       */
@@ -809,6 +817,7 @@ typedef struct ta_query {
   const uint32_t* ranks;     /* STATS (host)        */
   uint32_t n_ranks;          /* STATS              */
   uint32_t reserved;
+  uint64_t t0, t1;           /* WINDOW (r0, r1 too) */
 } ta_query;
 typedef struct ta_q_stats {
   ta_ctx_stats stats;

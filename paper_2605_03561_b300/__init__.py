@@ -168,7 +168,7 @@ class Query(C.Structure):
     _fields_ = [("kind", u32), ("experiment", u32), ("metric", u32), ("ctx", u32),
                 ("tau_num", u32), ("tau_den", u32), ("k", u32), ("min_ranks", u32), ("r0", u32),
                 ("r1", u32), ("i0", u32), ("i1", u32), ("ranks", P), ("n_ranks", u32),
-                ("reserved", u32)]
+                ("reserved", u32), ("t0", u64), ("t1", u64)]
 
 
 class QueryResult(C.Structure):
@@ -231,7 +231,7 @@ class QRacks(C.Structure):
     _fields_ = [("n_racks", u32), ("n_flagged_racks", u32)]
 
 
-Q_STATS, Q_SLICE, Q_TOPK, Q_RACKS = 1, 2, 3, 4
+Q_STATS, Q_SLICE, Q_TOPK, Q_RACKS, Q_WINDOW = 1, 2, 3, 4, 5
 
 _SIGS = {
     "ta_create": (C.c_int, [C.c_int, P, C.POINTER(P)]),
@@ -951,12 +951,13 @@ class Batch:
 
 
 def make_query(kind, experiment=0, ctx=0, metric=EXCLUSIVE, ranks=None, tau=(3, 1), k=10,
-               min_ranks=1, r0=0, r1=0, i0=0, i1=0):
+               min_ranks=1, r0=0, r1=0, i0=0, i1=0, t0=0, t1=0):
     """A ta_query; keeps the rank subset alive on the returned object."""
     q = Query()
     q.kind, q.experiment, q.metric, q.ctx = kind, experiment, metric, ctx
     q.tau_num, q.tau_den, q.k, q.min_ranks = tau[0], tau[1], k, min_ranks
     q.r0, q.r1, q.i0, q.i1 = r0, r1, i0, i1
+    q.t0, q.t1 = int(t0), int(t1)
     if ranks is not None:
         arr = _np(ranks, np.uint32)
         q._ranks = arr
@@ -973,6 +974,9 @@ def parse_payload(kind, data, nbytes):
         return d
     if kind == Q_SLICE:
         return np.frombuffer(data, np.uint64).copy()
+    if kind == Q_WINDOW:
+        v = np.frombuffer(data[:nbytes], np.uint64).copy()
+        return dict(time=v[: len(v) // 2], cnt=v[len(v) // 2:])
     if kind == Q_TOPK:
         n = int(np.frombuffer(data[:8], np.uint64)[0])
         ent = (QTopkEntry * max(n, 1)).from_buffer_copy(data[8: 8 + max(n, 1) * C.sizeof(QTopkEntry)]

@@ -71,35 +71,6 @@ struct WinArgs {
   u32 gst_cap;
 };
 
-// First i in [lo, hi) with v[i] >= t, or hi.  One warp; each step probes 32
-// evenly spaced positions and keeps the gap between the last probe below t
-// and the first at or above it (v is non-decreasing).
-__device__ __forceinline__ u64 warp_lower_bound(const u64* __restrict__ v, u64 lo, u64 hi, u64 t,
-                                                int lane) {
-  while (hi - lo > 32) {
-    const u64 n = hi - lo;
-    const u64 s = (n + 31) / 32;
-    const u64 q = lo + min((u64)(lane + 1) * s, n) - 1;
-    const u32 ge = __ballot_sync(FULL, v[q] >= t);
-    if (ge == 0) return hi;
-    const u64 k = (u64)(__ffs(ge) - 1);
-    const u64 qk = lo + min((k + 1) * s, n) - 1;
-    lo = k ? lo + min(k * s, n) : lo;
-    hi = qk + 1;
-  }
-  const u64 i = lo + lane;
-  const u32 ge = __ballot_sync(FULL, i < hi && v[i] >= t);
-  return ge ? lo + (u64)(__ffs(ge) - 1) : hi;
-}
-
-// Time inside [t0, t1) of the sample in progress at t0 (sample b - 1, b > rb).
-__device__ __forceinline__ u64 head_time(const u64* __restrict__ ts, u64 b, u64 re, u64 t0,
-                                         u64 t1) {
-  const u64 nx = b < re ? ts[b] : ts[b - 1];
-  const u64 hi = min(nx, t1);
-  return hi > t0 ? hi - t0 : 0ull;
-}
-
 // A rank's window: samples [rb, re), window samples [b, u), inner rows
 // [k0, k1) covering samples [s0, s1) (k0 == k1: none, [b, u) all edge).
 struct Win {
@@ -411,6 +382,21 @@ ta_status ensure_row_first(ta_experiment* e, const Launch& L, Pool& tmp) {
   e->row_first = rf;
   return TA_OK;
 }
+
+}  // namespace
+
+ta_status ta::ensure_row_index(ta_experiment* e) {
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  Pool tmp{c, {}};
+  const ta_status s = ensure_row_first(e, L, tmp);
+  cudaStreamSynchronize(c->stream);
+  tmp.release();
+  return s;
+}
+
+namespace {
 
 bool same_window(const ta_interval_args& x, const ta_interval_args& y) {
   return x.t0 == y.t0 && x.t1 == y.t1 && x.r0 == y.r0 && x.r1 == y.r1 && x.metric == y.metric;

@@ -5,7 +5,8 @@
 // query is cut into work items (a chunk of ranks or of slice cells), so a
 // large query spreads over many CTAs and small ones share a launch:
 //   A  per-rank value lookup (stored with a presence bit) and exact partial
-//      moments (u64 / u128 atomics); slice cells are answered here;
+//      moments (u64 / u128 atomics); slice cells and time windows are
+//      answered here;
 //   B  everything that needs the finished moments: outlier counts and the
 //      argmax of STATS, per-node outlier / rank / sum counts of RACKS, and
 //      the whole top-k selection of TOPK (one CTA: radix select on the
@@ -39,6 +40,7 @@ namespace {
 constexpr int SV_NT = 256;
 constexpr u32 CHUNK_R = 2048;      // ranks per work item
 constexpr u32 CHUNK_CELLS = 8192;  // slice cells per work item
+constexpr u32 CHUNK_WIN = 64;      // window ranks per work item (a warp per rank)
 constexpr u32 TOPK_MAX = 1024;
 constexpr u32 MAX_EXPS = 64;
 constexpr u64 PRESENT = 1ull << 63;  // values are < 2^63 (R * span < 2^63)
@@ -51,7 +53,7 @@ __host__ __device__ inline u64 align_up(u64 x) { return (x + ALIGN - 1) / ALIGN 
 __host__ __device__ inline u64 xs_off() { return align_up(64); }
 __host__ __device__ inline u64 nodes_off(u32 n) { return xs_off() + align_up((u64)n * 8); }
 __host__ __device__ inline u64 scratch_bytes_for(u32 kind, u32 n, u32 n_nodes) {
-  if (kind == TA_Q_SLICE) return 0;
+  if (kind == TA_Q_SLICE || kind == TA_Q_WINDOW) return 0;
   u64 b = nodes_off(n);
   if (kind == TA_Q_RACKS) b += 2 * align_up((u64)n_nodes * 8);
   return b;
@@ -64,6 +66,13 @@ struct ExpDev {
   const u64* entry_off;
   const u32* e_ctx;
   const u64* e_time;
+  const u32* e_cnt;
+  // raw traces and the first sample of every tensor row (window queries;
+  // null when the experiment released its traces)
+  const u64* rank_off;
+  const u64* ts;
+  const u32* tctx;
+  const u64* row_first;
   const u64* off[2];
   const u32* ctx[2];
   const u64* time[2];
@@ -77,6 +86,7 @@ struct QDev {
   u32 tau_num, tau_den, k, min_ranks;
   u32 r0, r1, i0, i1;
   u32 n, pad;  // ranks the query runs over (subset size or R)
+  u64 t0, t1;  // window
   const u32* ranks;
   unsigned char* out;
   unsigned char* scratch;  // zeroed before phase A
@@ -185,6 +195,56 @@ __global__ void __launch_bounds__(SV_NT) k_serve_a(const QDev* __restrict__ qs,
   const Item it = items[blockIdx.x];
   const QDev q = qs[it.q];
   const ExpDev& E = exps[q.exp];
+  if (q.kind == TA_Q_WINDOW) {
+    // a warp per rank: the window's ends by 32-ary searches of the rank's
+    // timestamps, its inner iterations by the same search of the rows'
+    // first samples; inner rows add their tensor entry of ctx (a binary
+    // search in the context-ascending row), edge samples of ctx their
+    // clipped durations (the sample in progress at t0: its part after t0)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const u32 n = q.r1 - q.r0;
+    const u32 k0 = it.part * CHUNK_WIN, k1 = min(n, k0 + CHUNK_WIN);
+    u64* out_t = (u64*)q.out;
+    u64* out_n = out_t + n;
+    for (u32 k = k0 + w; k < k1; k += SV_NT / 32) {
+      const u32 r = q.r0 + k;
+      const u64 rb = E.rank_off[r], re = E.rank_off[r + 1];
+      const u64 b = warp_lower_bound(E.ts, rb, re, q.t0, lane);
+      const u64 u = warp_lower_bound(E.ts, b, re, q.t1, lane);
+      const u64 q1 = E.row_off[r + 1];
+      const u64 a0 = warp_lower_bound(E.row_first, E.row_off[r], q1, b, lane);
+      const u64 a1 = warp_lower_bound(E.row_first, a0 + 1, q1 + 1, u == re ? re + 1 : u, lane) - 1;
+      const u64 s0 = a1 > a0 ? E.row_first[a0] : u, s1 = a1 > a0 ? E.row_first[a1] : u;
+      u64 t = 0, c = 0;
+      for (u64 row = a0 + lane; row < a1; row += 32) {
+        const u64 eb = E.entry_off[row], ee = E.entry_off[row + 1];
+        u64 p;
+        csr_find(E.e_ctx, eb, ee, q.ctx, &p);
+        if (p < ee && E.e_ctx[p] == q.ctx) {
+          t += E.e_time[p];
+          c += E.e_cnt[p];
+        }
+      }
+      for (int side = 0; side < 2; ++side) {
+        const u64 lo = side ? s1 : b, hi = side ? u : s0;
+        for (u64 i = lo + lane; i < hi; i += 32) {
+          if (E.tctx[i] != q.ctx) continue;
+          const u64 ti = E.ts[i];
+          const u64 nx = i + 1 < re ? E.ts[i + 1] : ti;
+          t += min(nx, q.t1) - ti;
+          ++c;
+        }
+      }
+      if (lane == 0 && b > rb && E.tctx[b - 1] == q.ctx) t += head_time(E.ts, b, re, q.t0, q.t1);
+      t = warp_sum(t);
+      c = warp_sum(c);
+      if (lane == 0) {
+        out_t[k] = t;
+        out_n[k] = c;
+      }
+    }
+    return;
+  }
   if (q.kind == TA_Q_SLICE) {
     const u64 W = q.i1 - q.i0;
     const u64 total = (u64)(q.r1 - q.r0) * W;
@@ -645,6 +705,13 @@ void size_query(const ta_server* s, QState& st) {
       st.items_b = st.items_c = 0;
       break;
     }
+    case TA_Q_WINDOW: {
+      const u64 n = q.r1 - q.r0;
+      st.res_bytes = n * 16;
+      st.items_a = (n + CHUNK_WIN - 1) / CHUNK_WIN;
+      st.items_b = st.items_c = 0;
+      break;
+    }
     case TA_Q_TOPK:
       st.res_bytes = 8 + (u64)std::min(q.k, E.R) * sizeof(ta_q_topk_entry);
       st.items_a = (st.n + CHUNK_R - 1) / CHUNK_R;
@@ -702,6 +769,8 @@ void launch_batch(ta_server* s, Slot& sl, std::vector<QState*>& B, u64 res_block
     d.i1 = q.i1;
     d.n = st.n;
     d.pad = 0;
+    d.t0 = q.t0;
+    d.t1 = q.t1;
     d.ranks = nullptr;
     if (st.pay_bytes) {
       std::memcpy(sl.h_stage + p, st.ranks.data(), st.ranks.size() * 4);
@@ -814,7 +883,7 @@ ta_status validate_query(const ta_server* s, const ta_query* q) {
   if (q->experiment >= s->exps.size()) return fail(TA_ERR_INVALID_ARG, "query: experiment id");
   const ExpDev& E = s->exps[q->experiment];
   if (q->ctx >= E.C) return fail(TA_ERR_INVALID_ARG, "query: ctx >= n_ctx");
-  if (q->kind != TA_Q_SLICE) {
+  if (q->kind != TA_Q_SLICE && q->kind != TA_Q_WINDOW) {
     if (q->metric > 1) return fail(TA_ERR_INVALID_ARG, "query: metric");
     if (E.off[q->metric] == nullptr)
       return fail(TA_ERR_INVALID_ARG, "query: the inclusive rollup was not built");
@@ -833,6 +902,13 @@ ta_status validate_query(const ta_server* s, const ta_query* q) {
       return TA_OK;
     case TA_Q_TOPK:
       if (q->k == 0 || q->k > TOPK_MAX) return fail(TA_ERR_INVALID_ARG, "top-k query: 1 <= k <= 1024");
+      return TA_OK;
+    case TA_Q_WINDOW:
+      if (q->r0 > q->r1 || q->r1 > E.R)
+        return fail(TA_ERR_INVALID_ARG, "window query: r0 <= r1 <= R");
+      if (!E.row_first)
+        return fail(TA_ERR_INVALID_ARG,
+                    "window query: the experiment's traces were released when it was loaded");
       return TA_OK;
     case TA_Q_RACKS:
       if (q->tau_den == 0 || q->min_ranks == 0 || !E.node_of_rank)
@@ -934,6 +1010,15 @@ ta_status ta_serve_add_experiment(ta_server* s, ta_experiment* e, const ta_topol
   d.entry_off = e->entry_off;
   d.e_ctx = e->e_ctx;
   d.e_time = e->e_time;
+  d.e_cnt = e->e_cnt;
+  if (e->ts || e->N == 0) {  // traces kept or borrowed: window queries
+    const ta_status st = ensure_row_index(e);
+    if (st != TA_OK) return st;
+    d.rank_off = e->rank_off;
+    d.ts = e->ts;
+    d.tctx = e->ctxv;
+    d.row_first = e->row_first;
+  }
   d.off[0] = e->x.off;
   d.ctx[0] = e->x.ctx;
   d.time[0] = e->x.time;

@@ -121,6 +121,8 @@ using AllocFn = std::function<ta_status(size_t, void**, const char*)>;
 // device time is added to *acc.
 ta_status build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out, const AllocFn& alloc,
                           Pool& tmp, double* acc);
+// The first-sample index of every tensor row (e->row_first), built once.
+ta_status ensure_row_index(ta_experiment* e);
 // Bitonic sort of n (key, value) pairs ascending by key, in buffers of at
 // least next_pow2(n) entries (stats.cu).
 void sort_u64_pairs(const Launch& L, u64* keys, double* vals, u64 n);
