@@ -863,6 +863,41 @@ def run_gpu(args):
         e.free()
         del ts_np
 
+    # the serving form's window query (N2) on this experiment: 2,000 queries,
+    # each the time of one segment context in a window of 10 % of the median
+    # rank's time on 1,000 consecutive ranks; all queued at once (saturated)
+    serve_window = None
+    if not args.no_serve_window:
+        e = ctx.load(d_ro, d_ts, d_cx, d_par, w["marker"], borrow=True)
+        rng = np.random.default_rng(31)
+        ro = w["rank_off"].astype(np.int64)
+        ne = ro[1:] > ro[:-1]
+        ts_np = w["ts"].numpy()
+        med = int(np.median(ts_np[ro[1:][ne] - 1].astype(np.int64)
+                            - ts_np[ro[:-1][ne]].astype(np.int64)))
+        span_r = min(1000, R)
+        qs = []
+        for _ in range(2000):
+            t0 = int(rng.integers(0, max(1, med * 9 // 10)))
+            r0 = int(rng.integers(0, R - span_r + 1))
+            qs.append(ta.make_query(ta.Q_WINDOW, 0, int(rng.choice(aa["kset"])), r0=r0,
+                                    r1=r0 + span_r, t0=t0, t1=t0 + med // 10))
+        serve_window = {"queries": len(qs), "ranks_per_query": span_r,
+                        "window": "10 % of the median rank's time at a random start"}
+        for name, mb, ns in (("plain", 1, 1), ("serving", 256, 3)):
+            srv = ta.Server(ctx, max_batch=mb, n_streams=ns, result_bytes=1 << 30,
+                            scratch_bytes=1 << 28)
+            srv.add(e, None)
+            srv.replay(qs[:100], np.zeros(100, np.uint64))
+            _, wall = srv.replay(qs, np.zeros(len(qs), np.uint64))
+            serve_window[name] = {"saturated_qps": len(qs) / (wall * 1e-9),
+                                  "us_per_query": wall / len(qs) / 1e3}
+            srv.close()
+        serve_window["saturated_serving_over_plain"] = (
+            serve_window["serving"]["saturated_qps"] / serve_window["plain"]["saturated_qps"])
+        e.free()
+        del ts_np
+
     # next row N3: DBSCAN and K-Means (k = 2..5, the paper's stability check)
     # over every rank's exclusive time of a communication context, with the
     # node view; host clock around each call (it synchronises), median of 5
@@ -986,7 +1021,8 @@ def run_gpu(args):
                                        "stats_ms", "topology_ms", "speedup_ms")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "batched_vs_plain": batched, "serving": serving, "prune": prune,
-                "interval": interval, "cluster": cluster, "columns": columns,
+                "interval": interval, "serve_window": serve_window, "cluster": cluster,
+                "columns": columns,
                 "gpu_launches": launches, "clocks": clk}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -1012,6 +1048,7 @@ def main():
     p.add_argument("--no-prune", action="store_true")
     p.add_argument("--no-interval", action="store_true")
     p.add_argument("--no-cluster", action="store_true")
+    p.add_argument("--no-serve-window", action="store_true")
     p.add_argument("--no-columns", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
