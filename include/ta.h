@@ -11,7 +11,14 @@
  *     coefficient of variation, argmax rank, z-score outliers (Section VI-A,
  *     the group-by listing and Table IV; Section VI-B, outlier ranks),
  *   - the node/chassis/rack rollup of outlier ranks (Section VI-B),
- *   - the imbalance-derived potential speedup (Section VI-A, Table V).
+ *   - the imbalance-derived potential speedup (Section VI-A, Table V),
+ *   - pruning of the calling context tree on the summary profile, profiles
+ *     of time windows and bottom-up calling contexts (Section III-A,
+ *     Section VI-B), clusters of ranks by DBSCAN / K-Means with their node
+ *     view (Section VI-B), and the DataFrame operation classes the paper
+ *     benchmarks (Section IV) as column kernels,
+ *   - a batched form (many trace sets in one CUDA graph) and a serving form
+ *     (resident experiments, continuous batching of queries).
  *
  * Every computation runs in the library's own CUDA kernels on one GPU.
  *

@@ -4,7 +4,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``oracle.cpp`` (plain,
 single-threaded C++, written from the paper's definitions; see the header of
 that file for the section each function follows) through ctypes; pruning, time
-windows and call chains are plain Python loops in this file.  It shares no
+windows, call chains, the clustering of ranks (DBSCAN, K-Means, node view) and
+the column operations are plain Python loops in this file.  It shares no
 code with the CUDA path and never imports it.
 
 Parity pins live in ``tests/test_oracle_*.py``.  The per-group CV definitions
