@@ -101,8 +101,9 @@ __global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__
   u32* sval = (u32*)(skey + RS_TILE);
   __shared__ u32 wh[RS_WARPS][256];
   __shared__ u32 lstart[256];
-  __shared__ u64 gbase[256];
+  __shared__ u32 gbase[256];  // n < 2^32: offsets fit 32 bits (3 CTAs per SM fit)
   __shared__ u32 wsum[RS_WARPS];
+  __shared__ u32 speers[RS_WARPS][RS_ITEMS][32];  // each row's equal-digit lanes
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt = (1u << lane) - 1u;
   for (u32 d = lane; d < 256; d += 32) wh[w][d] = 0;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__
     const bool v = i < n;
     const u32 d = v ? (u32)(keys_in[i] >> shift) & 255u : 0u;
     const u32 peers = digit_peers(d, v);
+    speers[w][rd][lane] = peers;
     if (v && (peers & lt) == 0) wh[w][d] += __popc(peers);
     __syncwarp();
   }
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__
     for (int q = 0; q < w; ++q) before += wsum[q];
     const u32 start = before + incl - cnt;
     lstart[d] = start;
-    gbase[d] = off[(u64)d * n_tiles + blockIdx.x];
+    gbase[d] = (u32)off[(u64)d * n_tiles + blockIdx.x];
     u32 run = start;
     for (int q = 0; q < RS_WARPS; ++q) {
       const u32 c = wh[q][d];
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__
     const bool v = i < n;
     const u64 key = v ? keys_in[i] : 0ull;  // a second read of the tile, from L2
     const u32 d = (u32)(key >> shift) & 255u;
-    const u32 peers = digit_peers(d, v);
+    const u32 peers = speers[w][rd][lane];  // own lane's entry: no barrier needed
     const u32 pos = v ? wh[w][d] + __popc(peers & lt) : 0u;
     __syncwarp();
     if (v && (peers & lt) == 0) wh[w][d] += __popc(peers);
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(RS_NT, 2) k_rs_scatter(const u64* __restrict__
   for (u32 j = threadIdx.x; j < m; j += RS_NT) {
     const u64 key = skey[j];
     const u32 d = (u32)(key >> shift) & 255u;
-    const u64 g = gbase[d] + (j - lstart[d]);
+    const u64 g = (u64)gbase[d] + (j - lstart[d]);
     keys_out[g] = key;
     vals_out[g] = sval[j];
   }
