@@ -451,10 +451,11 @@ ta_status ta_prune_profiles(ta_experiment* e, const ta_prune_args* a, ta_prune_o
  * empty window (every rank empty).
  * Needs the raw traces: loaded with TA_LOAD_KEEP_TRACES, or borrowed
  * (TA_LOAD_BORROW with aligned device arrays).  Each rank's window is found
- * by a warp-cooperative 32-ary search of its timestamps; iterations wholly
- * inside the window are taken from the iteration tensor, the samples of the
- * partial iterations at its edges one by one.  The first call builds an
- * index of every tensor row's first sample (8 bytes per row, kept with the
+ * by warp-cooperative 32-ary searches (of its iterations' start times, then
+ * of one iteration's timestamps); iterations wholly inside the window are
+ * taken from the iteration tensor, the samples of the partial iterations at
+ * its edges one by one.  The first call builds an index of every tensor
+ * row's first sample and its time (16 bytes per row, kept with the
  * experiment).  The result of the last call stays with the experiment in
  * device memory until a call with other arguments or ta_experiment_free, so
  * the second call of the two-call pattern only copies it out.

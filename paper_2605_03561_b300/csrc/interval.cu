@@ -55,6 +55,7 @@ struct WinArgs {
   const u64* e_time;
   const u32* e_cnt;
   const u64* row_first;  // [rows + 1] first sample of every row
+  const u64* row_ts;     // [rows] its timestamp (rows of empty ranks: unused)
   u32 r0, n, C, bm_in_smem;
   u64 t0, t1;
   u64* win;  // [4n] b, u, first inner row, end of inner rows
@@ -127,14 +128,33 @@ __global__ void __launch_bounds__(IW * 32) k_win_count(const WinArgs A) {
     Win w;
     w.rb = A.rank_off[r];
     w.re = A.rank_off[r + 1];
-    w.b = warp_lower_bound(A.ts, w.rb, w.re, A.t0, lane);
-    w.u = warp_lower_bound(A.ts, w.b, w.re, A.t1, lane);
-    // inner rows: first sample at or after b; the sample after the last one
-    // before u (or the rank's end when the window reaches it)
-    const u64 q1 = A.row_off_of_rank[r + 1];
-    w.k0 = warp_lower_bound(A.row_first, A.row_off_of_rank[r], q1, w.b, lane);
-    const u64 uu = w.u == w.re ? w.re + 1 : w.u;
-    w.k1 = warp_lower_bound(A.row_first, w.k0 + 1, q1 + 1, uu, lane) - 1;
+    const u64 q0 = A.row_off_of_rank[r], q1 = A.row_off_of_rank[r + 1];
+    if (w.re == w.rb) {  // no samples: an empty window
+      w.b = w.u = w.rb;
+      w.k0 = w.k1 = q0;
+    } else {
+      // the rows tile the rank's time: find the first row starting at or
+      // after the bound (row start times are contiguous per rank), then
+      // the bound inside the row before it (a few hundred samples)
+      const u64 f0 = warp_lower_bound(A.row_ts, q0, q1, A.t0, lane);
+      const u64 f1 = warp_lower_bound(A.row_ts, q0, q1, A.t1, lane);
+      w.b = f0 == q0 ? w.rb
+                     : warp_lower_bound(A.ts, A.row_first[f0 - 1], A.row_first[f0], A.t0, lane);
+      w.u = f1 == q0 ? w.rb
+                     : warp_lower_bound(A.ts, A.row_first[f1 - 1], A.row_first[f1], A.t1, lane);
+      // inner rows: from the first row starting at or after b (row f0) to
+      // the row before the one holding u's predecessor (its last sample ends
+      // at or after t1), or every row to the end when u is the rank's end
+      w.k0 = f0;
+      if (w.u <= w.b) {
+        w.u = w.b;
+        w.k1 = w.k0;
+      } else if (w.u == w.re) {
+        w.k1 = q1;
+      } else {
+        w.k1 = max(w.k0, f1 - 1);
+      }
+    }
     if (lane == 0) {
       A.win[4 * k] = w.b;
       A.win[4 * k + 1] = w.u;
@@ -317,6 +337,16 @@ WinPlan plan_window(u32 n, u32 C, int num_sms) {
   return P;
 }
 
+// Start time of every row.  The row of an empty rank points at the next
+// rank's first sample (or at N: then the largest value); the window kernels
+// skip empty ranks, so those values are never used.
+__global__ void k_row_ts(const u64* __restrict__ row_first, const u64* __restrict__ ts, u64 rows,
+                         u64 N, u64* row_ts) {
+  const u64 G = (u64)gridDim.x * blockDim.x;
+  for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < rows; k += G)
+    row_ts[k] = row_first[k] < N ? ts[row_first[k]] : ~0ull;
+}
+
 // Samples of every tensor row (the sum of its entries' counts).
 __global__ void k_row_samples(const u64* __restrict__ entry_off, const u32* __restrict__ e_cnt,
                               u64 rows, u32* n) {
@@ -378,8 +408,15 @@ ta_status ensure_row_first(ta_experiment* e, const Launch& L, Pool& tmp) {
   k_row_samples<<<(unsigned)nb, 256, 0, c->stream>>>(e->entry_off, e->e_cnt, e->rows, n);
   L.count();
   scan_exclusive(L, n, e->rows, rf, rf + e->rows, scratch);
+  u64* rt = nullptr;
+  if (e->ts) {
+    TRY(e->own(std::max<u64>(e->rows, 1) * 8, (void**)&rt, "row start times"));
+    k_row_ts<<<(unsigned)nb, 256, 0, c->stream>>>(rf, e->ts, e->rows, e->N, rt);
+    L.count();
+  }
   TRY(sync_check(c, "ta_interval_profile (row index)"));
   e->row_first = rf;
+  e->row_ts = rt;
   return TA_OK;
 }
 
@@ -427,6 +464,7 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
   A.e_time = e->e_time;
   A.e_cnt = e->e_cnt;
   A.row_first = e->row_first;
+  A.row_ts = e->row_ts;
   A.r0 = a->r0;
   A.n = n;
   A.C = e->C;

@@ -101,6 +101,7 @@ struct ta_experiment {
   // first sample of every tensor row ([rows + 1], global sample index; built
   // by the first time-window call) and that call's last result
   ta::u64* row_first = nullptr;
+  ta::u64* row_ts = nullptr;  // [rows] timestamp of each row's first sample
   bool iv_valid = false;
   ta_interval_args iv_args{};
   ta::Csr iv;
