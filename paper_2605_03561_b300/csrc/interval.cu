@@ -59,7 +59,7 @@ struct WinArgs {
   u32 r0, n, C, bm_in_smem;
   u64 t0, t1;
   u64* win;  // [4n] b, u, first inner row, end of inner rows
-  unsigned long long* units;  // [2] edge samples and inner entries read
+  unsigned long long* units;  // [3] edge samples, inner entries read, max entries of a rank
   u32* cnt;  // [n] entries of every rank
   const u64* off;
   u32* out_ctx;
@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(IW * 32) k_win_count(const WinArgs A) {
     const u32 n = bm_count_warp(bm, lane);
     if (lane == 0) {
       A.cnt[k] = n;
+      atomicMax(&A.units[2], (unsigned long long)n);
       atomicAdd(&A.units[0], (unsigned long long)((w.s0 - w.b) + (w.u - w.s1)));
       if (w.k1 > w.k0)
         atomicAdd(&A.units[1],
@@ -266,7 +267,9 @@ __global__ void __launch_bounds__(IW * 32, 3) k_win_write(const WinArgs A) {
     for (u32 i = lane; i < bmw; i += 32) bm.L1[i] = 0;
   const Stage sst{(u64*)ws, (u32*)(ws + 8 * WSR), (u32*)(ws + 12 * WSR)};
   const u64 gbase = gw * (u64)A.gst_cap;
-  const Stage gst{A.gst_time + gbase, A.gst_ctx + gbase, A.gst_cnt + gbase};
+  // the global stage exists only when some rank has more than WSR entries
+  const Stage gst = A.gst_time ? Stage{A.gst_time + gbase, A.gst_ctx + gbase, A.gst_cnt + gbase}
+                               : sst;
   __syncwarp();
   for (u64 k = gw; k < A.n; k += G) {
     const u64 r = (u64)A.r0 + k;
@@ -477,13 +480,13 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
   const AllocFn& xalloc = incl ? scratch : own;  // the exclusive window is the result or a step
   Csr xtmp;
   Csr& x = incl ? xtmp : e->iv;  // exclusive: written in place as the result
-  u64* total;  // [0] entries, [1..2] units read
+  u64* total;  // [0] entries, [1..2] units read, [3] most entries of one rank
   u64* scan_scratch;
   TRY(tmp.get_n(4 * std::max<u64>(n, 1), &A.win, "window bounds"));
   TRY(tmp.get_n(std::max<u64>(n, 1), &A.cnt, "window counts"));
   TRY(xalloc(((u64)n + 1) * 8, (void**)&x.off, "window offsets"));
-  TRY(tmp.get_n(3, &total, "window total"));
-  cudaMemsetAsync(total, 0, 24, c->stream);
+  TRY(tmp.get_n(4, &total, "window total"));
+  cudaMemsetAsync(total, 0, 32, c->stream);
   A.units = (unsigned long long*)(total + 1);
   TRY(tmp.get_n(scan_scratch_elems(n), &scan_scratch, "window scan"));
   if (!P.bms) {
@@ -491,10 +494,6 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
     TRY(tmp.get(gbm, (void**)&A.gbm, "window bitmaps"));
     cudaMemsetAsync(A.gbm, 0, gbm, c->stream);
   }
-  const size_t gn = (size_t)P.warps() * e->C;
-  TRY(tmp.get_n(gn, &A.gst_ctx, "window stage"));
-  TRY(tmp.get_n(gn, &A.gst_time, "window stage"));
-  TRY(tmp.get_n(gn, &A.gst_cnt, "window stage"));
   A.gst_cap = e->C;
   {
     PhaseTimer timer(c, &c->prof.interval_ms);
@@ -507,12 +506,18 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
     cudaMemcpyAsync(x.off + n, total, 8, cudaMemcpyDeviceToDevice, c->stream);
     timer.stop_and_sync();
   }
-  u64 h[3];
+  u64 h[4];
   TRY(copy(c, h, total, sizeof h));
   TRY(sync_check(c, "ta_interval_profile (count)"));
   x.nnz = h[0];
   c->prof.interval_samples += h[1];
   c->prof.interval_entries += h[2];
+  if (h[3] > WSR) {  // some rank's window overflows the shared-memory stage
+    const size_t gn = (size_t)P.warps() * e->C;
+    TRY(tmp.get_n(gn, &A.gst_ctx, "window stage"));
+    TRY(tmp.get_n(gn, &A.gst_time, "window stage"));
+    TRY(tmp.get_n(gn, &A.gst_cnt, "window stage"));
+  }
   const u64 m = std::max<u64>(x.nnz, 1);
   TRY(xalloc(m * 4, (void**)&x.ctx, "window ctx"));
   TRY(xalloc(m * 8, (void**)&x.time, "window time"));
