@@ -636,7 +636,10 @@ ta_status ta_col_cumsum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* ou
  *   cuda_stream     stream to run on; the current device must be its device.
  *   off, ctx, time  a per-rank CSR on the device (e.g. ta_csr_get_view of an
  *                   experiment): rank r owns [off[r], off[r+1]), contexts
- *                   ascending, times in ns.
+ *                   ascending, times in ns.  Checked on the device before
+ *                   use: offsets that decrease return TA_ERR_INVALID_ARG, a
+ *                   context id >= n_ctx returns TA_ERR_BAD_CTX (nothing is
+ *                   computed).  The offsets must address the caller's arrays.
  *   n_ranks, n_ctx  R and C; n_ctx must not exceed 65536.
  *   ranks           sorted unique device rank ids, or NULL for all ranks.
  *   tau_num/tau_den outlier threshold, as in ta_context_stats.

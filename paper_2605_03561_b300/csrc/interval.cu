@@ -70,6 +70,7 @@ struct WinArgs {
   u64* gst_time;
   u32* gst_cnt;
   u32 gst_cap;
+  u32* status;  // F_INTERNAL: the write pass found a count the count pass did not
 };
 
 // A rank's window: samples [rb, re), window samples [b, u), inner rows
@@ -284,6 +285,15 @@ __global__ void __launch_bounds__(IW * 32, 3) k_win_write(const WinArgs A) {
     mark_window(A, bm, w, lane);
     __syncwarp();
     const u32 nnz = bm_prefix_warp(bm, lane);
+    // the count pass sized both the output and the stage: a rank whose count
+    // differs (or would need a global stage that was not allocated) is
+    // reported and skipped, never written past
+    if (nnz != A.cnt[k] || (nnz > WSR && !A.gst_time)) {
+      if (lane == 0) flag(A.status, F_INTERNAL);
+      bm_clear_warp(bm, lane);
+      __syncwarp();
+      continue;
+    }
     const Stage st = nnz <= WSR ? sst : gst;
     for (u32 q = lane; q < nnz; q += 32) {
       st.time[q] = 0;
@@ -480,14 +490,15 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
   const AllocFn& xalloc = incl ? scratch : own;  // the exclusive window is the result or a step
   Csr xtmp;
   Csr& x = incl ? xtmp : e->iv;  // exclusive: written in place as the result
-  u64* total;  // [0] entries, [1..2] units read, [3] most entries of one rank
+  u64* total;  // [0] entries, [1..2] units read, [3] most entries of one rank, [4] status
   u64* scan_scratch;
   TRY(tmp.get_n(4 * std::max<u64>(n, 1), &A.win, "window bounds"));
   TRY(tmp.get_n(std::max<u64>(n, 1), &A.cnt, "window counts"));
   TRY(xalloc(((u64)n + 1) * 8, (void**)&x.off, "window offsets"));
-  TRY(tmp.get_n(4, &total, "window total"));
-  cudaMemsetAsync(total, 0, 32, c->stream);
+  TRY(tmp.get_n(5, &total, "window total"));
+  cudaMemsetAsync(total, 0, 40, c->stream);
   A.units = (unsigned long long*)(total + 1);
+  A.status = (u32*)(total + 4);
   TRY(tmp.get_n(scan_scratch_elems(n), &scan_scratch, "window scan"));
   if (!P.bms) {
     const size_t gbm = (size_t)P.warps() * bm_words(e->C) * 4;
@@ -533,7 +544,10 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
     L.count();
     timer.stop_and_sync();
   }
+  u64 f = 0;
+  TRY(copy(c, &f, total + 4, 8));
   TRY(sync_check(c, "ta_interval_profile (write)"));
+  TRY(status_from_flags((u32)f, "ta_interval_profile"));
   if (!incl) return TA_OK;
   return build_inclusive(e, x, n, e->iv, own, tmp, &c->prof.interval_ms);
 }

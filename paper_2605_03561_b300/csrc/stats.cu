@@ -1222,6 +1222,29 @@ constexpr u64 NA_BYTES = NA_MAX_CTX * 4 + NA_MAX_CTX * 72 + NA_MAX_OUTLIERS * 16
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
+// The caller's CSR, checked before any kernel indexes the slot map or the
+// partials with it: rank r's offsets non-decreasing (F_INVALID) and every
+// context id below n_ctx (F_BAD_CTX).  Warp per rank of the subset.
+__global__ void k_check_csr(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
+                            const u32* __restrict__ ctx, u32 n_ctx, u32* status) {
+  const int lane = threadIdx.x & 31;
+  const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const u32 nw = (gridDim.x * blockDim.x) >> 5;
+  u32 fl = 0;
+  for (u32 i = gw; i < n; i += nw) {
+    const u32 r = rank_at(S, i);
+    const u64 E0 = off[r], E1 = off[r + 1];
+    if (E1 < E0) {
+      fl |= F_INVALID;
+      continue;
+    }
+    for (u64 j = E0 + lane; j < E1; j += 32)
+      if (ctx[j] >= n_ctx) fl |= F_BAD_CTX;
+  }
+  fl = __reduce_or_sync(FULL, fl);
+  if (lane == 0 && fl) flag(status, fl);
+}
+
 constexpr int NA_MAX_DEVICES = 64;
 unsigned char* g_noalloc_ptr[NA_MAX_DEVICES];
 std::mutex g_noalloc_mu;
@@ -1272,8 +1295,10 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   unsigned long long launches = 0;
   int num_sms = 1;
   int dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr == cudaSuccess)
+    derr = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (derr != cudaSuccess) return cuda_fail(derr, "ta_context_stats_noalloc (device)");
   Launch L{st, num_sms, &launches};
   const u64 C = n_ctx;
   // carve the scratch array
@@ -1309,47 +1334,73 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   const u32 n = ranks ? n_ranks_subset : n_ranks;
   // everything that accumulates starts from zero (the array keeps the last
   // call's contents)
-  cudaMemsetAsync(q, 0, 16, st);
-  if (ranks) {  // the subset is checked before any kernel reads through it
+  const int grid = std::max(1, std::min<int>(num_sms * 4, (int)((n + 7) / 8)));
+  cudaError_t err = cudaMemsetAsync(q, 0, 16, st);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+  // the subset and the caller's CSR are checked before any kernel reads
+  // through them (a context id >= n_ctx would index past the slot map)
+  if (ranks) {
     k_check_sorted<<<blocks(n), 256, 0, st>>>(ranks, n, n_ranks, status);
     L.count();
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc (subset check)");
     u32 hs = 0;
-    cudaError_t e2 = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
-    if (e2 != cudaSuccess) return cuda_fail(e2, "ta_context_stats_noalloc");
+    err = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
     if (hs) return fail(TA_ERR_INVALID_ARG, "rank subset must be sorted, unique and < n_ranks");
   }
-  cudaMemsetAsync(slot_of_ctx, 0xFF, C * 4, st);
-  k_slot_map<<<blocks(C), 256, 0, st>>>(nullptr, 0, n_ctx, slot_of_ctx);
-  cudaMemsetAsync(P.present, 0, C * 4, st);
-  cudaMemsetAsync(P.mn, 0xFF, C * 8, st);
-  cudaMemsetAsync(P.mx, 0, C * 8, st);
-  cudaMemsetAsync(P.s1, 0, C * 8, st);
-  cudaMemsetAsync(P.s2lo, 0, C * 8, st);
-  cudaMemsetAsync(P.s2hi, 0, C * 8, st);
-  const int grid = std::max(1, std::min<int>(num_sms * 4, (int)((n + 7) / 8)));
+  k_check_csr<<<grid, 256, 0, st>>>(ranks, n, off, ctx, n_ctx, status);
+  L.count();
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc (CSR check)");
+  {
+    u32 hs = 0;
+    err = cudaMemcpyAsync(&hs, status, 4, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
+    if (hs & F_INVALID) return fail(TA_ERR_INVALID_ARG, "off decreases within the CSR");
+    if (hs & F_BAD_CTX) return fail(TA_ERR_BAD_CTX, "a context id of the CSR is >= n_ctx");
+  }
+  struct Fill {
+    void* p;
+    int v;
+    size_t bytes;
+  };
+  const Fill fills[] = {{slot_of_ctx, 0xFF, C * 4}, {P.present, 0, C * 4}, {P.mn, 0xFF, C * 8},
+                        {P.mx, 0, C * 8},           {P.s1, 0, C * 8},      {P.s2lo, 0, C * 8},
+                        {P.s2hi, 0, C * 8}};
+  for (const Fill& f : fills) {
+    err = cudaMemsetAsync(f.p, f.v, f.bytes, st);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync");
+  }
   const u64 kcap = std::max<u64>(1, outlier_cap);
+  k_slot_map<<<blocks(C), 256, 0, st>>>(nullptr, 0, n_ctx, slot_of_ctx);
   k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, SetMap{});
   k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats, SetMap{});
   k_stats_z<<<grid, 256, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, tau_num, tau_den,
                                   nullptr, keys, zs, kcap, n_out, nullptr, SetMap{});
   k_stats_argmax<<<blocks(C), 256, 0, st>>>((u32)C, P.argmax, stats);
-  u64 h[2] = {0, 0};
-  cudaError_t err = cudaMemcpyAsync(h, n_out, 16, cudaMemcpyDeviceToHost, st);
+  L.count(5);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc (launch)");
+  u64 h = 0;
+  err = cudaMemcpyAsync(&h, n_out, 8, cudaMemcpyDeviceToHost, st);
   if (err != cudaSuccess) return cuda_fail(err, "cudaMemcpyAsync");
   err = cudaStreamSynchronize(st);
   if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
-  *n_outliers = h[0];
-  if (h[0] > outlier_cap)
-    return fail(TA_ERR_CAPACITY, "%llu outliers, capacity %llu", (unsigned long long)h[0],
+  *n_outliers = h;
+  if (h > outlier_cap)
+    return fail(TA_ERR_CAPACITY, "%llu outliers, capacity %llu", (unsigned long long)h,
                 (unsigned long long)outlier_cap);
-  if (h[0] > 0) {
-    sort_pairs(L, keys, zs, h[0]);  // the key buffer holds NA_MAX_OUTLIERS (a power of two)
-    k_write_outliers<<<blocks(h[0]), 256, 0, st>>>(keys, zs, h[0], outliers, nullptr);
+  if (h > 0) {
+    sort_pairs(L, keys, zs, h);  // the key buffer holds NA_MAX_OUTLIERS (a power of two)
+    k_write_outliers<<<blocks(h), 256, 0, st>>>(keys, zs, h, outliers, nullptr);
+    L.count();
   }
-  err = cudaStreamSynchronize(st);
-  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
   err = cudaGetLastError();
+  if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc (sort)");
+  err = cudaStreamSynchronize(st);
   if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
   return TA_OK;
 }

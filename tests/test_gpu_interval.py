@@ -151,6 +151,30 @@ def test_many_contexts_global_stage_and_bitmaps():
         _check(tr, e, t0, t1)
 
 
+def test_one_rank_over_the_shared_stage():
+    # rank 3 of 8 visits 600 distinct contexts, the others 20 each: only
+    # that rank's window needs the global stage (sized by the count pass)
+    rng = np.random.default_rng(41)
+    Cn = 700
+    parent = np.full(Cn, 0, np.uint32)
+    parent[0] = NONE
+    ro, ts, cx = [0], [], []
+    for r in range(8):
+        k = 600 if r == 3 else 20
+        seq = rng.permutation(np.arange(1, Cn))[:k].astype(np.uint32)
+        seq = np.concatenate([seq, seq[: k // 2]])
+        t = np.cumsum(rng.integers(1, 50, len(seq))).astype(np.uint64)
+        ts.append(t)
+        cx.append(seq)
+        ro.append(ro[-1] + len(seq))
+    d = dict(rank_off=np.array(ro, np.uint64), ts=np.concatenate(ts), ctx=np.concatenate(cx),
+             parent=parent, marker=1)
+    tr, e = _load(d)
+    hi = int(d["ts"].max())
+    for t0, t1 in ((0, BIG), (hi // 4, 3 * hi // 4), (5, hi // 2)):
+        _check(tr, e, t0, t1)
+
+
 def test_generated_windows_closed_form_totals():
     # every rank's window times add up to the overlap of the window with its
     # span; its counts to the samples whose ts lies in the window; adjacent

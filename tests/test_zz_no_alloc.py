@@ -85,6 +85,58 @@ def test_noalloc_rank_subset_twice(experiment):
         _check_equal(ref_stats, ref_out, got_stats, got_out)
 
 
+@pytest.fixture(scope="module")
+def many_outliers():
+    # 256 ranks and a low threshold: thousands of outliers, more than the
+    # one-block sort holds, so the padded multi-block sort runs
+    cfg = synth.preset(1, seed=22, n_ranks=256)
+    g = synth.generate(cfg)
+    ctx = ta.Context(0)
+    e = ctx.load(g["rank_off"], g["ts"], g["ctx"], g["parent"], g["marker"])
+    return ctx, e
+
+
+def test_noalloc_many_outliers_twice(many_outliers):
+    ctx, e = many_outliers
+    ref_stats, ref_out, ref_n, _ = e.stats(ta.EXCLUSIVE, tau=(1, 10))
+    assert ref_n > 4096
+    for _ in range(2):
+        s, got_stats, got_out = _noalloc(e, tau=(1, 10), cap=1 << 16)
+        assert s == ta.OK, ta.lib().ta_last_error_message()
+        _check_equal(ref_stats, ref_out, got_stats, got_out)
+
+
+def test_noalloc_capacity_error_reports_full_count_twice(many_outliers):
+    import torch
+    ctx, e = many_outliers
+    _, _, ref_n, _ = e.stats(ta.EXCLUSIVE, tau=(1, 10))
+    v = ta.CsrView()
+    ta._check(ta.lib().ta_csr_get_view(e.h, ta.EXCLUSIVE, C.byref(v)))
+    stats = torch.zeros(e.C * C.sizeof(ta.CtxStats), dtype=torch.uint8, device="cuda")
+    outl = torch.zeros(100 * C.sizeof(ta.Outlier), dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        n = C.c_uint64(0)
+        s = ta.lib().ta_context_stats_noalloc(
+            e.ctx.stream.cuda_stream, v.off, v.ctx, v.time, e.R, e.C, None, 0, 1, 10,
+            stats.data_ptr(), outl.data_ptr(), 100, C.byref(n))
+        assert s == ta.CAPACITY
+        assert int(n.value) == ref_n
+
+
+def test_noalloc_rejects_context_ids_beyond_n_ctx(experiment):
+    ctx, e = experiment
+    ref_stats, ref_out, _, _ = e.stats(ta.EXCLUSIVE, tau=(2, 1))
+    s, got_stats, got_out = _noalloc(e, tau=(2, 1))  # leaves a full slot map behind
+    assert s == ta.OK
+    x = e.csr(ta.EXCLUSIVE)
+    small = int(x["ctx"].max())  # the largest id used is then out of range
+    s, _, _ = _noalloc(e, tau=(2, 1), n_ctx=small)
+    assert s == ta.BAD_CTX, ta.lib().ta_last_error_message()
+    s, got_stats, got_out = _noalloc(e, tau=(2, 1))
+    assert s == ta.OK
+    _check_equal(ref_stats, ref_out, got_stats, got_out)
+
+
 def test_noalloc_rejects_sizes_beyond_its_array(experiment):
     ctx, e = experiment
     s, _, _ = _noalloc(e, cap=(1 << 16) + 1)
