@@ -344,6 +344,25 @@ def oracle_sample_threads(w, n_ranks, args, n_threads):
     return n, time.perf_counter() - t0, len(jobs)
 
 
+def host_info():
+    """The host's thread count and CPU model (for the CPU baselines)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+# Both CPU legs (the reference arm and the bench line's cpu_baseline) time the
+# oracle on the same sample: the ranks holding the first SAMPLE_RECORDS records.
+SAMPLE_RECORDS = 2e7
+
+
 def pick_sample(w, target_records):
     ro = w["rank_off"]
     k = int(np.searchsorted(ro, target_records))
@@ -624,7 +643,7 @@ def run_reference(args):
         return
     w = make_workload(args.config, pinned=False, ranks=args.ranks)
     aa = analysis_args(w)
-    k = pick_sample(w, args.ref_records)
+    k = pick_sample(w, SAMPLE_RECORDS)
     recs = 0
     secs = 0.0
     for i in range(args.warmup + args.steps):
@@ -640,7 +659,9 @@ def run_reference(args):
             "config": {"workload": WORKLOADS[args.config] + (f" (ranks={args.ranks})" if args.ranks else ""), "sample_ranks": k,
                        "sample_records": recs // args.steps},
             "cpu_baseline": {"value": v, "unit": "records/s", "cores": 1, "kind": "oracle",
-                             "sample": f"ranks [0, {k}) of the workload per step"},
+                             "sample": f"ranks [0, {k}) of the workload per step "
+                                       f"({recs // args.steps} records; the same sample as the "
+                                       f"GPU line's cpu_baseline)", **host_info()},
             "e2e": {"value": v, "unit": "records/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -972,11 +993,16 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        k = pick_sample(w, args.cpu_records)
-        n, s = oracle_sample(w, k, aa)
+        k = pick_sample(w, SAMPLE_RECORDS)
+        n, s, reps = 0, 0.0, 0
+        while reps < 3 or (s < args.cpu_seconds and reps < 20):
+            n1, s1 = oracle_sample(w, k, aa)
+            n, s, reps = n + n1, s + s1, reps + 1
         cpu = {"value": n / s, "unit": "records/s", "cores": 1, "kind": "oracle",
-               "sample": f"ranks [0, {k}) = {n} records of the same workload, whole path "
-                         f"(analysis, stats over all contexts, rack rollup, speedup); {s:.1f} s"}
+               "sample": f"ranks [0, {k}) = {n // reps} records of the same workload (the "
+                         f"reference arm's sample), whole path (analysis, stats over all "
+                         f"contexts, rack rollup, speedup), {reps} runs, {s:.1f} s",
+               **host_info()}
         if not args.no_cpu_threads:
             n_thr = max(1, os.cpu_count() or 1)
             kt = pick_sample(w, args.cpu_records * min(n_thr, 8))
@@ -1040,10 +1066,12 @@ def main():
                    help="override the rank count (smaller cases for profiling)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-records", type=float, default=1.5e8)
+    p.add_argument("--cpu-records", type=float, default=1.5e8,
+                   help="records per thread of the all-cores oracle baseline")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="CPU time the single-core oracle baseline repeats its sample for")
     p.add_argument("--no-cpu-threads", action="store_true",
                    help="skip the oracle split over all host cores")
-    p.add_argument("--ref-records", type=float, default=5e6)
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-prune", action="store_true")
     p.add_argument("--no-interval", action="store_true")

@@ -6,14 +6,18 @@ and inclusive CSR and spans must match bit for bit); the rest is checked
 through properties that hold at any size: every rank's exclusive times sum to
 its span and its inclusive root equals it, the tensor sums back to the
 exclusive CSR, and the statistics' integer moments equal sums over the
-exclusive CSR."""
+exclusive CSR.  The FP64 statistics (mean, std, cv, balance, every outlier's
+z), the outlier lists, the rack rollup and the potential speedup are compared
+with the oracle over a contiguous subset of 3,000 ranks, which the oracle
+analyses on its own."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2605_03561_b300 as ta
 from paper_2605_03561_b300 import synth
-from gpu_helpers import INT_FIELDS, context, per_rank_rows
+from gpu_helpers import (INT_FIELDS, check_speedup, check_stats, check_topology, context,
+                         per_rank_rows)
 
 pytestmark = pytest.mark.gpu
 
@@ -83,6 +87,21 @@ def test_full_size_config3_sampled_and_invariants():
         assert int(gs["s2_lo"][i]) + (int(gs["s2_hi"][i]) << 64) == s2
         assert int(gs["max"][i]) == int(max(vals))
         assert set(INT_FIELDS) <= set(gs)
+    # FP64 statistics, outliers, rack rollup and speedup over a contiguous
+    # subset of ranks the oracle analyses by itself (global rank ids)
+    s0 = int(rng.integers(0, R - 3000))
+    S = np.arange(s0, s0 + 3000, dtype=np.uint32)
+    a = oracle.Analysis(tr, s0, s0 + 3000)
+    check_stats(a, e, ta.EXCLUSIVE, ranks=S, tau=(3, 1), want_z=False)
+    check_stats(a, e, ta.EXCLUSIVE, ranks=S, tau=(2, 1), want_z=False)
+    check_stats(a, e, ta.INCLUSIVE, ranks=S, tau=(3, 1), want_z=False)
+    truth = synth.truth(cfg, g["info"])
+    kset = np.unique(truth["segment_ctx"]).astype(np.uint32)
+    check_speedup(a, e, kset, ranks=S)
+    topo = synth.topology(cfg, g["info"])
+    comm = truth["segment_ctx"][truth["comm_segment"].astype(bool)]
+    check_topology(a, e, int(comm[0]), topo, tau=(2, 1), ranks=S)
+    del a
     # time-window profiles: sampled rank ranges against the oracle, every
     # rank's totals against the closed form (overlap of the window with the
     # rank's span; samples with ts in the window)
