@@ -68,6 +68,32 @@ void Pool::release() {
   items.clear();
 }
 
+cudaEvent_t ta::take_event(ta_ctx* c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+void ta::resolve_phases(ta_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      *p.acc += ms;
+    cudaGetLastError();
+    c->ev_pool.push_back(p.a);
+    c->ev_pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
 ta_status ta::sync_check(ta_ctx* c, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, what);
@@ -128,8 +154,6 @@ ta_status ta_create(int device, void* stream, ta_ctx** out) {
   c->device = device;
   c->stream = (cudaStream_t)stream;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-  cudaEventCreate(&c->ev[0]);
-  cudaEventCreate(&c->ev[1]);
   *out = c;
   return TA_OK;
 }
@@ -137,8 +161,8 @@ ta_status ta_create(int device, void* stream, ta_ctx** out) {
 ta_status ta_destroy(ta_ctx* c) {
   if (!c) return TA_OK;
   cudaStreamSynchronize(c->stream);
-  if (c->ev[0]) cudaEventDestroy(c->ev[0]);
-  if (c->ev[1]) cudaEventDestroy(c->ev[1]);
+  resolve_phases(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   delete c;
   return TA_OK;
 }
@@ -162,6 +186,7 @@ uint64_t ta_kernel_launches(const ta_ctx* c) { return c ? c->launches : 0; }
 
 ta_status ta_get_profile(ta_ctx* c, ta_profile* out, int reset) {
   if (!c) return fail(TA_ERR_INVALID_ARG, "ta_get_profile: ctx is NULL");
+  resolve_phases(c);
   if (out) *out = c->prof;
   if (reset) c->prof = ta_profile{};
   return TA_OK;
@@ -209,11 +234,17 @@ constexpr u64 kAncMax = 1ull << 28;
 // distinct contexts take a second write pass).
 constexpr u64 kXsCap = 256;
 
-// Tensor: count pass, scan of per-tile counts, allocation (rows exactly,
-// entries one slot per run), write pass; compaction when a row repeats a
-// context in several runs.
-ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
-  (void)d;
+// What the tensor's write pass leaves for its finish step.
+struct TensorPending {
+  u64* meta;  // [0] status, [1..2] rows, entry slots, [3] distinct entries
+  u64 slots;
+  u32* row_nnz;
+};
+
+// Tensor, first half: count pass, scan of per-tile counts, allocation (rows
+// exactly, entries one slot per run), write pass.  Nothing waits for the
+// write pass: tensor_finish reads its results.
+ta_status tensor_begin(ta_experiment* e, Pool& tmp, TensorPending* tp) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const u64 N = e->N;
@@ -228,7 +259,7 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   TRY(tmp.get_n(n_tiles, &A.tile_ents, "tile entries"));
   TRY(tmp.get_n(n_tiles, &A.tile_row_off, "tile row offsets"));
   TRY(tmp.get_n(n_tiles, &A.tile_ent_off, "tile entry offsets"));
-  u64* meta;  // [0] status, [1..2] rows, entry slots, [3] distinct entries
+  u64* meta;
   TRY(tmp.get(64, (void**)&meta, "tensor meta"));
   TRY(tmp.get_n(2 * scan_scratch_elems(n_tiles), &A.scan_scratch, "tile scan"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
@@ -258,7 +289,6 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     PhaseTimer timer(c, &c->prof.tensor_count_ms);
     launch_tensor_count(L, P, A);
     launch_tile_scan(L, A);
-    timer.stop_and_sync();
   }
   u64 h[4];
   TRY(copy(c, h, meta, sizeof h));
@@ -281,12 +311,21 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
   {
     PhaseTimer timer(c, &c->prof.tensor_ms);
     launch_tensor_write(L, P, A);
-    timer.stop_and_sync();
   }
-  TRY(copy(c, h, meta, sizeof h));
-  TRY(sync_check(c, "iteration tensor (write)"));
+  tp->meta = meta;
+  tp->slots = slots;
+  tp->row_nnz = A.row_nnz;
+  return TA_OK;
+}
+
+// Tensor, second half (h = the write pass's meta, read back): status, the
+// distinct entry count, and the compaction when some row repeats a context.
+ta_status tensor_finish(ta_experiment* e, Pool& tmp, const TensorPending& tp, const u64* h) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
   TRY(status_from_flags((u32)h[0], "ta_load_traces"));
   e->nnz = h[3];
+  const u64 slots = tp.slots;
   if (e->nnz > slots) return fail(TA_ERR_STATE, "iteration tensor: %llu entries in %llu slots",
                                   (unsigned long long)e->nnz, (unsigned long long)slots);
   if (e->nnz == slots) {  // every row's contexts are distinct across its runs
@@ -295,7 +334,7 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     TensorCompact K{};
     K.rows = e->rows;
     K.slot_off = e->entry_off;
-    K.row_nnz = A.row_nnz;
+    K.row_nnz = tp.row_nnz;
     K.ctx_in = e->e_ctx;
     K.time_in = e->e_time;
     K.cnt_in = e->e_cnt;
@@ -314,7 +353,6 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     {
       PhaseTimer timer(c, &c->prof.tensor_ms);
       launch_tensor_compact(L, K);
-      timer.stop_and_sync();
     }
     TRY(sync_check(c, "iteration tensor (compaction)"));
     e->disown(e->entry_off);
@@ -327,16 +365,23 @@ ta_status build_tensor(ta_experiment* e, const ta_trace_desc* d, Pool& tmp) {
     e->e_cnt = cn;
   }
   c->prof.tensor_launches += 1;
-  c->prof.tensor_records += N;
+  c->prof.tensor_records += e->N;
   c->prof.tensor_entries += e->nnz;
   c->prof.tensor_rows += e->rows;
   return TA_OK;
 }
 
-// Exclusive per-rank CSR from the tensor in one pass: the write pass into a
-// per-rank scratch, exact counts, scan, allocation, copy; ranks above the
-// scratch cap are written by a second, restricted write pass.
-ta_status build_exclusive(ta_experiment* e, Pool& tmp) {
+// What the exclusive scratch pass leaves for its finish step.
+struct ExclPending {
+  RankCsrArgs A;
+  RankCsrPlan P;
+  u64* meta;  // [0] status, [1] total entries, [2] ranks above the scratch cap
+};
+
+// Exclusive per-rank CSR in one pass over the tensor's rows, first half: the
+// write pass into a per-rank scratch with exact counts, and their scan.
+// Nothing waits for it: excl_finish reads the meta.
+ta_status excl_begin(ta_experiment* e, Pool& tmp, ExclPending* xq) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const u32 R = e->R;
@@ -375,7 +420,6 @@ ta_status build_exclusive(ta_experiment* e, Pool& tmp) {
   A.status = (u32*)meta;
   A.gst_cap = P.gst_cap;
   A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
-  double* acc = &c->prof.exclusive_ms;
   const u64 cap = kXsCap;
   TRY(tmp.get_n((u64)R * cap, &A.xs_ctx, "exclusive scratch"));
   TRY(tmp.get_n((u64)R * cap, &A.xs_time, "exclusive scratch"));
@@ -383,14 +427,24 @@ ta_status build_exclusive(ta_experiment* e, Pool& tmp) {
   A.xs_cap = (u32)cap;
   A.n_over = (unsigned long long*)(meta + 2);
   {
-    PhaseTimer timer(c, acc);
+    PhaseTimer timer(c, &c->prof.exclusive_ms);
     launch_excl_scratch(L, P, A);
-    timer.stop_and_sync();
   }
-  u64 h[3];
-  TRY(copy(c, h, meta, sizeof h));
-  TRY(sync_check(c, "exclusive (scratch)"));
+  xq->A = A;
+  xq->P = P;
+  xq->meta = meta;
+  return TA_OK;
+}
+
+// Second half (h = the scratch pass's meta, read back): exact allocation, the
+// copy of the scratch rows, the pass over ranks above the cap.  Its status
+// word (meta[0]) is left for the caller to read at its next synchronisation.
+ta_status excl_finish(ta_experiment* e, ExclPending& xq, const u64* h) {
+  ta_ctx* c = e->ctx;
+  Launch L{c->stream, c->num_sms, &c->launches};
   TRY(status_from_flags((u32)h[0], "exclusive"));
+  Csr& out = e->x;
+  RankCsrArgs& A = xq.A;
   out.nnz = h[1];
   const u64 n = std::max<u64>(out.nnz, 1);
   TRY(e->own(n * 4, (void**)&out.ctx, "csr ctx"));
@@ -399,28 +453,26 @@ ta_status build_exclusive(ta_experiment* e, Pool& tmp) {
   A.out_ctx = out.ctx;
   A.out_time = out.time;
   A.out_cnt_e = out.cnt;
-  {
-    PhaseTimer timer(c, acc);
-    launch_excl_copy(L, A);
-    if (h[2]) {
-      A.only_over = 1;
-      launch_rank_write(L, P, A);
-    }
-    timer.stop_and_sync();
+  PhaseTimer timer(c, &c->prof.exclusive_ms);
+  launch_excl_copy(L, A);
+  if (h[2]) {
+    A.only_over = 1;
+    launch_rank_write(L, xq.P, A);
   }
-  u64 f = 0;
-  TRY(copy(c, &f, meta, 8));
-  TRY(sync_check(c, "exclusive"));
-  return status_from_flags((u32)f, "exclusive");
+  return TA_OK;
 }
 
 }  // namespace
 
 // Inclusive rollup of a per-rank exclusive CSR over the experiment's tree:
 // ancestor lists (unless too long: level-by-level sweep), count, scan,
-// exact allocation through `alloc`, write.
+// exact allocation through `alloc`, write.  `anc` may carry the list offsets
+// and their total already computed (the load computes them beside the tree
+// checks); with `status_out` set, the final status word is left there for the
+// caller to read at its next synchronisation instead of being waited for.
 ta_status ta::build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out,
-                              const AllocFn& alloc, Pool& tmp, double* acc) {
+                              const AllocFn& alloc, Pool& tmp, double* acc, const AncOffsets* anc,
+                              u64** status_out) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   RankCsrPlan P = plan_rank_csr(R, e->C, c->num_sms);
@@ -460,27 +512,29 @@ ta_status ta::build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out,
   A.bm_in_smem = P.bm_in_smem ? 1u : 0u;
   {  // ancestor lists of the tree, unless they would be too long
     PhaseTimer timer(c, acc);
-    u32* len;
-    u64 *aoff, *ascr;
-    TRY(tmp.get_n(std::max<u32>(e->C, 1), &len, "ancestor lengths"));
-    TRY(tmp.get_n((u64)e->C + 1, &aoff, "ancestor offsets"));
-    TRY(tmp.get_n(scan_scratch_elems(e->C), &ascr, "ancestor scan"));
-    launch_anc_offsets(L, e->depth, e->C, len, aoff, meta + 2, ascr);
-    u64 total = 0;
-    TRY(copy(c, &total, meta + 2, 8));
-    TRY(sync_check(c, "inclusive (ancestors)"));
-    if (total <= kAncMax) {
-      u32* anc;
-      TRY(tmp.get_n(std::max<u64>(total, 1), &anc, "ancestor lists"));
-      launch_anc_fill(L, e->parent, e->C, aoff, anc, SetMap{});
-      A.anc_off = aoff;
-      A.anc = anc;
+    AncOffsets own{};
+    if (!anc) {
+      u32* len;
+      u64* ascr;
+      TRY(tmp.get_n(std::max<u32>(e->C, 1), &len, "ancestor lengths"));
+      TRY(tmp.get_n((u64)e->C + 1, &own.off, "ancestor offsets"));
+      TRY(tmp.get_n(scan_scratch_elems(e->C), &ascr, "ancestor scan"));
+      launch_anc_offsets(L, e->depth, e->C, len, own.off, meta + 2, ascr);
+      TRY(copy(c, &own.total, meta + 2, 8));
+      TRY(sync_check(c, "inclusive (ancestors)"));
+      anc = &own;
+    }
+    if (anc->total <= kAncMax) {
+      u32* lists;
+      TRY(tmp.get_n(std::max<u64>(anc->total, 1), &lists, "ancestor lists"));
+      launch_anc_fill(L, e->parent, e->C, anc->off, lists, SetMap{});
+      A.anc_off = anc->off;
+      A.anc = lists;
     }
   }
   {
     PhaseTimer timer(c, acc);
     launch_rank_count(L, P, A);
-    timer.stop_and_sync();
   }
   u64 h[2];
   TRY(copy(c, h, meta, sizeof h));
@@ -496,7 +550,10 @@ ta_status ta::build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out,
   {
     PhaseTimer timer(c, acc);
     launch_rank_write(L, P, A);
-    timer.stop_and_sync();
+  }
+  if (status_out) {
+    *status_out = meta;
+    return TA_OK;
   }
   u64 f = 0;
   TRY(copy(c, &f, meta, 8));
@@ -534,18 +591,29 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   TRY(e->own((u64)R * 8, (void**)&e->span, "span"));
   TRY(e->own((u64)C * 4, (void**)&e->depth, "depth"));
   TRY(e->own((u64)R * 4 + 4, (void**)&e->n_iter, "n_iter"));
-  u64* meta;  // [0] status|pad, [1] max_span, [2] roots|max_depth
+  u64* meta;  // [0] status|pad, [1] max_span, [2] roots|max_depth, [3] ancestor-list total
   TRY(tmp.get(64, (void**)&meta, "load meta"));
   u32* scratch;
   TRY(tmp.get((u64)C * 16, (void**)&scratch, "tree scratch"));
   cudaMemsetAsync(meta, 0, 64, c->stream);
   u32* status = (u32*)meta;
-  PhaseTimer timer(c, &c->prof.validate_ms);
-  launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status, SetMap{});
-  launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status,
-             SetMap{});
-  timer.stop_and_sync();
-  u64 h[3];
+  const bool incl = !(d->flags & TA_LOAD_NO_INCLUSIVE);
+  AncOffsets anc{};
+  {
+    PhaseTimer timer(c, &c->prof.validate_ms);
+    launch_rank_off(L, e->rank_off, R, N, e->ts, e->span, meta + 1, status, SetMap{});
+    launch_cct(L, e->parent, C, e->depth, (u32*)(meta + 2) + 1, (u32*)(meta + 2), scratch, status,
+               SetMap{});
+    if (incl) {  // the inclusive rollup's ancestor-list offsets, read back with the checks
+      u32* len;
+      u64* ascr;
+      TRY(tmp.get_n(std::max<u32>(C, 1), &len, "ancestor lengths"));
+      TRY(tmp.get_n((u64)C + 1, &anc.off, "ancestor offsets"));
+      TRY(tmp.get_n(scan_scratch_elems(C), &ascr, "ancestor scan"));
+      launch_anc_offsets(L, e->depth, C, len, anc.off, meta + 3, ascr);
+    }
+  }
+  u64 h[4];
   TRY(copy(c, h, meta, sizeof h));
   TRY(sync_check(c, "validation"));
   const u32 f = (u32)h[0];
@@ -560,14 +628,32 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
                 (unsigned long long)h[1]);
   e->max_depth = maxd;
   e->max_span = h[1];
-  TRY(build_tensor(e, d, tmp));
+  anc.total = h[3];
+  TensorPending tq;
+  ExclPending xq;
+  TRY(tensor_begin(e, tmp, &tq));
+  u64 ht[8];
+  TRY(copy(c, ht, tq.meta, 4 * 8));
+  TRY(sync_check(c, "iteration tensor (write)"));
+  TRY(tensor_finish(e, tmp, tq, ht));
   launch_n_iter(L, e->row_off, R, e->n_iter);
-  TRY(build_exclusive(e, tmp));
-  if (!(d->flags & TA_LOAD_NO_INCLUSIVE)) {
+  TRY(excl_begin(e, tmp, &xq));  // from the finished tensor's rows
+  TRY(copy(c, ht + 4, xq.meta, 3 * 8));
+  TRY(sync_check(c, "exclusive (scratch)"));
+  TRY(excl_finish(e, xq, ht + 4));
+  u64* incl_status = nullptr;
+  if (incl) {
     const AllocFn own = [e](size_t n, void** p, const char* w) { return e->own(n, p, w); };
-    TRY(build_inclusive(e, e->x, R, e->in, own, tmp, &c->prof.inclusive_ms));
+    TRY(build_inclusive(e, e->x, R, e->in, own, tmp, &c->prof.inclusive_ms, &anc, &incl_status));
     e->has_incl = true;
   }
+  // the status words left by the last passes, read at the one final wait
+  u64 fin[2] = {0, 0};
+  TRY(copy(c, &fin[0], xq.meta, 8));
+  if (incl_status) TRY(copy(c, &fin[1], incl_status, 8));
+  TRY(sync_check(c, "ta_load_traces"));
+  TRY(status_from_flags((u32)fin[0], "exclusive"));
+  TRY(status_from_flags((u32)fin[1], "inclusive"));
   // raw traces are not needed after ingestion unless kept for time windows
   if (e->owns_traces && !(d->flags & TA_LOAD_KEEP_TRACES)) {
     e->disown((void*)e->ts);
@@ -575,7 +661,7 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
     e->ts = nullptr;
     e->ctxv = nullptr;
   }
-  return sync_check(c, "ta_load_traces");
+  return TA_OK;
 }
 
 }  // namespace

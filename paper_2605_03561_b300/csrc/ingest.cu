@@ -302,16 +302,25 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
+      // the next batch's contexts are loaded before this batch is marked
+      u32 c[RU];
+#pragma unroll
+      for (int u = 0; u < RU; ++u) {
+        const u64 j = E0 + 32 * u + lane;
+        c[u] = j < E1 ? A.in_ctx[j] : NONE32;
+      }
       for (u64 j0 = E0; j0 < E1; j0 += 32 * RU) {
-        u32 c[RU];
+        u32 cn[RU];
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
-          const u64 j = j0 + 32 * u + lane;
-          c[u] = j < E1 ? A.in_ctx[j] : NONE32;
+          const u64 j = j0 + 32 * RU + 32 * u + lane;
+          cn[u] = j < E1 ? A.in_ctx[j] : NONE32;
         }
 #pragma unroll
         for (int u = 0; u < RU; ++u)
           if (c[u] != NONE32 && !bm_has(bm, c[u])) bm_set(bm, c[u]);
+#pragma unroll
+        for (int u = 0; u < RU; ++u) c[u] = cn[u];
       }
     } else if (MODE == 1) {
       E0 = A.in_off[r];
@@ -367,24 +376,39 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     }
     __syncwarp();
     if (MODE == 0) {
-      for (u64 j0 = E0; j0 < E1; j0 += 32 * RU) {
-        u32 c[RU], n[RU];
-        u64 t[RU];
+      // two batches of RA entries per lane: the next is loaded while this
+      // one is added
+      constexpr int RA = RU / 2;
+      u32 c[RA], n[RA];
+      u64 t[RA];
+      auto load = [&](u64 j0, u32* cc, u64* tt, u32* nn) {
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
+        for (int u = 0; u < RA; ++u) {
           const u64 j = j0 + 32 * u + lane;
           const bool ok = j < E1;
-          c[u] = ok ? A.in_ctx[j] : NONE32;
-          t[u] = ok ? A.in_time[j] : 0ull;
-          n[u] = ok ? A.in_cnt[j] : 0u;
+          cc[u] = ok ? A.in_ctx[j] : NONE32;
+          tt[u] = ok ? A.in_time[j] : 0ull;
+          nn[u] = ok ? A.in_cnt[j] : 0u;
         }
+      };
+      load(E0, c, t, n);
+      for (u64 j0 = E0; j0 < E1; j0 += 32 * RA) {
+        u32 cn[RA], nn[RA];
+        u64 tn[RA];
+        load(j0 + 32 * RA, cn, tn, nn);
 #pragma unroll
-        for (int u = 0; u < RU; ++u) {
+        for (int u = 0; u < RA; ++u) {
           if (c[u] == NONE32) continue;
           const u32 k = bm_rank(bm, c[u]);
           atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t[u]);
           atomicAdd(&st.cnt[k], n[u]);
           st.ctx[k] = c[u];
+        }
+#pragma unroll
+        for (int u = 0; u < RA; ++u) {
+          c[u] = cn[u];
+          t[u] = tn[u];
+          n[u] = nn[u];
         }
       }
     } else if (MODE == 2) {

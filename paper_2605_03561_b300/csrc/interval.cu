@@ -515,7 +515,7 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
     }
     scan_exclusive(L, A.cnt, n, x.off, total, scan_scratch);
     cudaMemcpyAsync(x.off + n, total, 8, cudaMemcpyDeviceToDevice, c->stream);
-    timer.stop_and_sync();
+    timer.stop();
   }
   u64 h[4];
   TRY(copy(c, h, total, sizeof h));
@@ -542,7 +542,7 @@ ta_status compute_window(ta_experiment* e, const ta_interval_args* a, Pool& tmp)
     if (P.bms) k_win_write<true><<<P.grid_write, IW * 32, P.smem_write, c->stream>>>(A);
     else k_win_write<false><<<P.grid_write, IW * 32, P.smem_write, c->stream>>>(A);
     L.count();
-    timer.stop_and_sync();
+    timer.stop();
   }
   u64 f = 0;
   TRY(copy(c, &f, total + 4, 8));

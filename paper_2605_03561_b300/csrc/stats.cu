@@ -683,37 +683,54 @@ __global__ void __launch_bounds__(SP_NW * 32)
   }
 }
 
-// (b) Cells (i, k) over ranks.  A warp owns the cells of SP_IB iteration(s)
+// (b) Cells (i, k) over ranks.  A warp owns the cells of SP_IB iterations
 // [i0, i0 + SP_IB) and 64 contexts [k0, k0 + 64) for a group of ranks and
 // keeps them in registers: lane l holds contexts k0 + l and k0 + l + 32
-// (sum, max, 128-bit sum of squares).  It reads the SP_IB rows of SP_PR ranks
-// at a time (one contiguous entry range per rank, all loads issued first),
-// scatters each entry's time to a per-warp shared-memory buffer indexed by
-// (rank, row, context) -- a row holds each context once, so plain stores
-// suffice -- and every lane then folds its contexts' values into its
-// registers, absent ones reading 0.  The group's cells go to the global
-// cells with one set of atomics per warp.
-constexpr u32 SP_IB = 4;   // iterations per warp (one contiguous read per rank)
-constexpr u32 SP_PR = 1;   // ranks per round
-constexpr u32 SP_CU = 8;   // entries per lane in flight per round
+// (sum, max, 128-bit sum of squares).  A round is one rank: its SP_IB rows
+// are one contiguous entry range, which the warp's lane 0 copies into a
+// shared-memory stage with two bulk copies (contexts, times) completing on
+// the stage's mbarrier; SPC_ST stages are in flight, so while one round is
+// summed the next ones are on their way.  Each entry's time is scattered to
+// a per-warp buffer indexed by (row, context) -- a row holds each context
+// once, so plain stores suffice -- and every lane then folds its contexts'
+// values into its registers, absent ones reading 0.  A round too long for a
+// stage is read from global memory directly.  The group's cells go to the
+// global cells with one set of atomics per warp.
+constexpr u32 SP_IB = 4;      // iterations per warp (one contiguous read per rank)
+constexpr u32 SP_CU = 8;      // entries per lane in flight (rounds read directly)
+constexpr u32 SPC_ST = 2;     // stages per warp
+constexpr u32 SPC_CAP = 320;  // entries per stage
+// per stage: contexts (cap + 4 for the 16-byte rounding), times (cap + 2)
+constexpr u32 SPC_CTX_BYTES = 4 * (SPC_CAP + 4);
+constexpr u32 SPC_TIME_BYTES = 8 * (SPC_CAP + 2);
+constexpr u32 SPC_STAGE_BYTES = SPC_CTX_BYTES + SPC_TIME_BYTES;
+constexpr u32 SPC_WARP_BYTES = SPC_ST * SPC_STAGE_BYTES + 16 * SPC_ST;  // + mbarriers
+static_assert(SPC_CTX_BYTES % 16 == 0 && SPC_STAGE_BYTES % 16 == 0, "stage alignment");
 
 __global__ void __launch_bounds__(SP_NW * 32, 2)
     k_sp_cells(const u32* __restrict__ S, u32 n, const u64* __restrict__ row_off,
                const u64* __restrict__ entry_off, const u32* __restrict__ e_ctx,
                const u64* __restrict__ e_time, const u32* __restrict__ kset,
                const u32* __restrict__ kmap, u32 C, u32 nk, u32 I, u32 n_ib, u32 n_kb, u32 group,
-               u64 n_items, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi) {
-  __shared__ u64 rowbuf[SP_NW][SP_PR][SP_IB][64];
-  extern __shared__ __align__(16) unsigned char kmap8[];
-  // one chunk of 64 contexts (n_kb == 1) maps through shared memory
-  const bool smap = n_kb == 1 && C <= SP_SMAP;
+               u64 n_items, u32 map_bytes, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi,
+               u32* status) {
+  __shared__ u64 rowbuf[SP_NW][SP_IB][64];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  unsigned char* kmap8 = dsm;  // [map_bytes]: one chunk of 64 contexts maps through it
+  const bool smap = map_bytes > 0;
   if (smap) build_kmap8(kmap8, C, kset, 0, nk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  u64* buf = &rowbuf[warp][0][0][0];
-  for (u32 q = lane; q < SP_PR * SP_IB * 64; q += 32) buf[q] = 0;
-  __syncwarp();
+  unsigned char* ws = dsm + map_bytes + (size_t)warp * SPC_WARP_BYTES;
+  u64* bar = reinterpret_cast<u64*>(ws + SPC_ST * SPC_STAGE_BYTES);
+  u64* buf = &rowbuf[warp][0][0];
+  for (u32 q = lane; q < SP_IB * 64; q += 32) buf[q] = 0;
   const u64 item = (u64)blockIdx.x * SP_NW + warp;
   if (item >= n_items) return;
+  if (lane == 0) {
+    for (u32 s = 0; s < SPC_ST; ++s) mbar_init(&bar[s], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
   const u32 ib = (u32)(item % n_ib), kb = (u32)((item / n_ib) % n_kb);
   const u32 g = (u32)(item / ((u64)n_ib * n_kb));
   const u32 i0 = ib * SP_IB, k0 = kb * 64;
@@ -725,74 +742,117 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
   for (u32 il = 0; il < SP_IB; ++il)
 #pragma unroll
     for (u32 h = 0; h < 2; ++h) csum[il][h] = cmax[il][h] = clo[il][h] = chi[il][h] = 0;
-  // entry boundaries of a round's ranks: lane p (SP_IB + 1) + q holds the
-  // start of row i0 + q of rank p (q = nrow: the end of its last row); the
-  // next round's are loaded while a round is summed
   constexpr u32 NB = SP_IB + 1;
-  auto offsets = [&](u32 rb, u64& mine) {
-    mine = 0;
+  // entry boundaries of SPC_OB rounds at once: lane p NB + q holds the start
+  // of row i0 + q of rank rb0 + p (q = nrow: the end of its last row); two
+  // batches ahead of the round being summed are resolved or in flight, so a
+  // stage is refilled without waiting on these loads
+  constexpr u32 SPC_OB = 6;
+  static_assert(SPC_OB * NB <= 32 && SPC_OB % SPC_ST == 0, "offset batch");
+  auto batch = [&](u32 rb0) -> u64 {
     const u32 p = (u32)lane / NB, q = (u32)lane % NB;
-    if ((u32)lane < SP_PR * NB && rb + p < r_end) {
-      const u64 row = row_off[rank_at(S, rb + p)] + 1 + i0;
+    u64 mine = 0;
+    if (p < SPC_OB && rb0 + p < r_end) {
+      const u64 row = row_off[rank_at(S, rb0 + p)] + 1 + i0;
       mine = entry_off[row + min(q, nrow)];
     }
+    return mine;
   };
-  u64 next_;
-  offsets(r_begin, next_);
-  for (u32 rb = r_begin; rb < r_end; rb += SP_PR) {
-    const u64 mine = next_;
-    if (rb + SP_PR < r_end) offsets(rb + SP_PR, next_);
-    u64 bnd[SP_PR][NB], len[SP_PR + 1];
-    len[0] = 0;
-#pragma unroll
-    for (u32 p = 0; p < SP_PR; ++p) {
-#pragma unroll
-      for (u32 q = 0; q < NB; ++q) bnd[p][q] = __shfl_sync(FULL, mine, p * NB + q);
-      len[p + 1] = len[p] + (bnd[p][SP_IB] - bnd[p][0]);
+  // stage s takes round rb (its bounds in lanes p NB .. p NB + SP_IB of ob)
+  u32 phase = 0;      // bit s: parity of stage s's next completion
+  u32 staged = 0;     // bit s: stage s holds a copy in flight
+  u64 sbase[SPC_ST];  // first entry of each stage's range
+  auto issue = [&](u32 s, u32 rb, u64 ob, u32 p) {
+    const u64 e0 = __shfl_sync(FULL, ob, p * NB), e1 = __shfl_sync(FULL, ob, p * NB + nrow);
+    staged &= ~(1u << s);
+    if (rb >= r_end || e1 <= e0 || e1 - e0 > SPC_CAP) return;
+    const u64 c0 = e0 & ~(u64)3, c1 = (e1 + 3) & ~(u64)3;  // 16-byte rounded ranges
+    const u64 t0 = e0 & ~(u64)1, t1 = (e1 + 1) & ~(u64)1;
+    sbase[s] = e0;
+    staged |= 1u << s;
+    if (lane == 0) {
+      unsigned char* st = ws + s * SPC_STAGE_BYTES;
+      fence_proxy_async_smem();  // the stage's last reads come before its refill
+      mbar_arrive_expect_tx(&bar[s], (u32)((c1 - c0) * 4 + (t1 - t0) * 8));
+      bulk_g2s(st, e_ctx + c0, (u32)((c1 - c0) * 4), &bar[s]);
+      bulk_g2s(st + SPC_CTX_BYTES, e_time + t0, (u32)((t1 - t0) * 8), &bar[s]);
     }
-    const u64 total = len[SP_PR];
-    for (u64 vb = 0; vb < total; vb += 32 * SP_CU) {
-      u32 c[SP_CU];
-      u64 t[SP_CU];
-      u32 slot[SP_CU];
+  };
+  bool failed = false;
+  u64 ob0 = batch(r_begin), ob1 = batch(r_begin + SPC_OB);
 #pragma unroll
-      for (u32 u = 0; u < SP_CU; ++u) {
-        const u64 v = vb + u * 32 + lane;
-        u32 p = 0;
+  for (u32 s = 0; s < SPC_ST; ++s) issue(s, r_begin + s, ob0, s);
+  for (u32 rb0 = r_begin; rb0 < r_end && !failed; rb0 += SPC_OB) {
+    const u64 ob2 = batch(rb0 + 2 * SPC_OB);
 #pragma unroll
-        for (u32 q = 1; q < SP_PR; ++q) p += (v >= len[q]) ? 1u : 0u;
-        u64 bp[NB], lp = len[0];
+    for (u32 p = 0; p < SPC_OB; ++p) {
+      const u32 rb = rb0 + p, s = p % SPC_ST;
+      if (rb >= r_end || failed) break;
+      u64 bnd[NB];
 #pragma unroll
-        for (u32 q = 0; q < NB; ++q) bp[q] = bnd[0][q];
+      for (u32 q = 0; q < NB; ++q) bnd[q] = __shfl_sync(FULL, ob0, p * NB + q);
+      const u64 total = bnd[SP_IB] - bnd[0];
+      if ((staged >> s) & 1u) {
+        if (!mbar_wait(&bar[s], (phase >> s) & 1u)) {
+          failed = true;
+          continue;
+        }
+        phase ^= 1u << s;
+        const unsigned char* st = ws + s * SPC_STAGE_BYTES;
+        const u32* sctx = reinterpret_cast<const u32*>(st) + (sbase[s] & 3);
+        const u64* stime = reinterpret_cast<const u64*>(st + SPC_CTX_BYTES) + (sbase[s] & 1);
+        // all of the stage's loads first (independent), then the lookups,
+        // then the scatter: no chain of dependent shared-memory loads
+        constexpr u32 SPC_U = SPC_CAP / 32;
+        u32 kk[SPC_U];
 #pragma unroll
-        for (u32 pp = 1; pp < SP_PR; ++pp)
-          if (p == pp) {
-            lp = len[pp];
+        for (u32 u = 0; u < SPC_U; ++u) {
+          const u32 v = (u32)lane + 32 * u;
+          kk[u] = v < (u32)total ? sctx[v] : NONE32;
+        }
 #pragma unroll
-            for (u32 q = 0; q < NB; ++q) bp[q] = bnd[pp][q];
+        for (u32 u = 0; u < SPC_U; ++u) kk[u] = kk[u] != NONE32 ? look(kk[u]) : NONE32;
+#pragma unroll
+        for (u32 u = 0; u < SPC_U; ++u) {
+          const u32 v = (u32)lane + 32 * u;
+          if (kk[u] == NONE32) continue;
+          const u64 jj = bnd[0] + v;
+          u32 il = 0;
+#pragma unroll
+          for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bnd[q]) ? 1u : 0u;
+          buf[il * 64 + kk[u]] = stime[v];
+        }
+      } else {
+        for (u64 vb = 0; vb < total; vb += 32 * SP_CU) {
+          u32 c[SP_CU], slot[SP_CU];
+          u64 t[SP_CU];
+#pragma unroll
+          for (u32 u = 0; u < SP_CU; ++u) {
+            const u64 v = vb + u * 32 + lane;
+            const u64 jj = bnd[0] + v;
+            u32 il = 0;
+#pragma unroll
+            for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bnd[q]) ? 1u : 0u;
+            slot[u] = il;
+            c[u] = v < total ? e_ctx[jj] : NONE32;
+            t[u] = v < total ? e_time[jj] : 0ull;
           }
-        const u64 jj = bp[0] + (v - lp);
-        u32 il = 0;  // the entry's row among the rank's rows of this warp
 #pragma unroll
-        for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bp[q]) ? 1u : 0u;
-        slot[u] = p * SP_IB + il;
-        c[u] = v < total ? e_ctx[jj] : NONE32;
-        t[u] = v < total ? e_time[jj] : 0ull;
+          for (u32 u = 0; u < SP_CU; ++u) {
+            const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
+            if (kk != NONE32) buf[slot[u] * 64 + kk] = t[u];
+          }
+        }
       }
-#pragma unroll
-      for (u32 u = 0; u < SP_CU; ++u) {
-        const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
-        if (kk != NONE32) buf[slot[u] * 64 + kk] = t[u];
-      }
-    }
-    __syncwarp();
-#pragma unroll
-    for (u32 p = 0; p < SP_PR; ++p)
+      __syncwarp();
+      // the stage is free: it takes the round SPC_ST ahead
+      if (p + SPC_ST < SPC_OB) issue(s, rb + SPC_ST, ob0, p + SPC_ST);
+      else issue(s, rb + SPC_ST, ob1, p + SPC_ST - SPC_OB);
 #pragma unroll
       for (u32 il = 0; il < SP_IB; ++il)
 #pragma unroll
         for (u32 h = 0; h < 2; ++h) {
-          u64* cell = &buf[(p * SP_IB + il) * 64 + lane + 32 * h];
+          u64* cell = &buf[il * 64 + lane + 32 * h];
           const u64 v = *cell;
           *cell = 0;
           const u128 v2 = (u128)v * v;
@@ -802,7 +862,16 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
           chi[il][h] += (u64)(v2 >> 64) + (lo < clo[il][h] ? 1ull : 0ull);
           clo[il][h] = lo;
         }
-    __syncwarp();
+      __syncwarp();
+    }
+    ob0 = ob1;
+    ob1 = ob2;
+  }
+  if (failed) {  // report; let the copies still in flight land before leaving
+    if (lane == 0) flag(status, F_TIMEOUT);
+    for (u32 q = 0; q < SPC_ST; ++q)
+      if ((staged >> q) & 1u) mbar_wait(&bar[q], (phase >> q) & 1u);
+    return;
   }
 #pragma unroll
   for (u32 il = 0; il < SP_IB; ++il)
@@ -1119,6 +1188,7 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   TRY(tmp.get_n(1, &status, "status"));
   TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
   TRY(check_subset(c, L, dK, nk, e->C, status, "ctx set"));
+  cudaMemsetAsync(status, 0, 4, c->stream);  // the cells kernel reports a stalled copy here
   u64* meta;  // [0] istar, [1] sum n_iter, [2] max span
   TRY(tmp.get_n(4, &meta, "speedup meta"));
   cudaMemsetAsync(meta, 0, 32, c->stream);
@@ -1170,11 +1240,11 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     groups = (n + group - 1) / group;
     const u64 n_items = tiles * groups;
     const size_t cmap_smem = (n_kb == 1) ? map_smem : 0;
-    if (cmap_smem)
-      cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cmap_smem);
-    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cmap_smem, L.stream>>>(
+    const size_t cells_smem = cmap_smem + (size_t)SP_NW * SPC_WARP_BYTES;
+    cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem);
+    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cells_smem, L.stream>>>(
         dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
-        group, n_items, gs, gm, gl, gh);
+        group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
     L.count();
   }
   ta_speedup_ctx* dper;
@@ -1201,7 +1271,10 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     TRY(copy(c, o->per_ctx, dper, (size_t)nk * sizeof(ta_speedup_ctx)));
     TRY(copy(c, o->total, dtot, sizeof(ta_speedup_total)));
   }
-  return sync_check(c, "ta_potential_speedup");
+  u32 f = 0;
+  TRY(copy(c, &f, status, 4));
+  TRY(sync_check(c, "ta_potential_speedup"));
+  return status_from_flags(f, "ta_potential_speedup");
 }
 
 }  // extern "C"

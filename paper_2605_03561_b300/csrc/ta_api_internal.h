@@ -17,7 +17,14 @@ struct ta_ctx {
   void* user = nullptr;
   unsigned long long launches = 0;
   ta_profile prof{};
-  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // phase timing: event pairs recorded on the stream and read only when the
+  // profile is asked for (no synchronisation on the work path)
+  struct PendingPhase {
+    cudaEvent_t a, b;
+    double* acc;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<PendingPhase> pending;
 };
 
 namespace ta {
@@ -55,22 +62,36 @@ ta_status sync_check(ta_ctx* c, const char* what);
 ta_status copy(ta_ctx* c, void* dst, const void* src, size_t bytes);
 ta_status status_from_flags(u32 f, const char* where);
 
-// Device time between two points on the context's stream (profiling).
+// Adds the device time of every recorded phase to its profile field and
+// recycles the events (waits for the last phase to finish).
+void resolve_phases(ta_ctx* c);
+cudaEvent_t take_event(ta_ctx* c);
+
+// Device time between two points on the context's stream (profiling): two
+// events on the stream, resolved by resolve_phases; nothing waits here.
 struct PhaseTimer {
   ta_ctx* c;
   double* acc;
+  cudaEvent_t a;
   bool done = false;
-  PhaseTimer(ta_ctx* c_, double* acc_) : c(c_), acc(acc_) { cudaEventRecord(c->ev[0], c->stream); }
-  ~PhaseTimer() {
-    if (!done) stop_and_sync();
+  PhaseTimer(ta_ctx* c_, double* acc_) : c(c_), acc(acc_), a(take_event(c_)) {
+    if (a) cudaEventRecord(a, c->stream);
   }
-  // Records the end of the phase on the stream and waits for it.
-  void stop_and_sync() {
+  ~PhaseTimer() {
+    if (!done) stop();
+  }
+  // Records the end of the phase on the stream.
+  void stop() {
     done = true;
-    cudaEventRecord(c->ev[1], c->stream);
-    cudaEventSynchronize(c->ev[1]);
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]) == cudaSuccess) *acc += ms;
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) {
+      c->ev_pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({a, b, acc});
+    if (c->pending.size() > 4096) resolve_phases(c);
   }
 };
 
@@ -117,11 +138,19 @@ struct ta_experiment {
 namespace ta {
 // Device allocation for a product (experiment-owned or a call's temporary).
 using AllocFn = std::function<ta_status(size_t, void**, const char*)>;
+// Offsets of every context's ancestor list (exclusive scan of depth + 1) and
+// their total, when already computed.
+struct AncOffsets {
+  u64* off;
+  u64 total;
+};
 // Inclusive rollup (Section II-A) of the per-rank exclusive CSR `in` of R
 // ranks over e's calling context tree into `out` (arrays from `alloc`);
-// device time is added to *acc.
+// device time is added to *acc.  anc: precomputed ancestor-list offsets (or
+// null); status_out: receives the device status word instead of a wait.
 ta_status build_inclusive(ta_experiment* e, const Csr& in, u32 R, Csr& out, const AllocFn& alloc,
-                          Pool& tmp, double* acc);
+                          Pool& tmp, double* acc, const AncOffsets* anc = nullptr,
+                          u64** status_out = nullptr);
 // The first-sample index of every tensor row (e->row_first), built once.
 ta_status ensure_row_index(ta_experiment* e);
 // Bitonic sort of n (key, value) pairs ascending by key, in buffers of at

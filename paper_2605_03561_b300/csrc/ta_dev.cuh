@@ -30,6 +30,57 @@ __device__ __forceinline__ void flag(u32* status, u32 bits) { atomicOr(status, b
 __device__ __forceinline__ u32 vld(const u32* p) { return *(const volatile u32*)p; }
 __device__ __forceinline__ u64 vld(const u64* p) { return *(const volatile u64*)p; }
 
+// ---- bulk copies (TMA, non-tensor form) into shared memory, completed on an
+// mbarrier.  Addresses and sizes of cp.async.bulk must be multiples of 16 B.
+__device__ __forceinline__ u32 smem_u32(const void* p) {
+  return (u32)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(u64* bar, u32 count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+// Makes initialised mbarriers visible to the async proxy (the bulk copies).
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Orders this thread's earlier generic accesses of shared memory before
+// later async-proxy writes to it (a stage read, then refilled).
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(u64* bar, u32 bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Copies bytes (a multiple of 16, both addresses 16-byte aligned) from global
+// src to shared dst; completion is counted on bar.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, u32 bytes, u64* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(u64* bar, u32 parity) {
+  u32 done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for phase `parity` of bar to complete, at most MBAR_SPIN polls (each
+// poll may suspend the thread briefly; about a second in all); returns false
+// if it gave up.
+constexpr u32 MBAR_SPIN = 1u << 20;
+__device__ __forceinline__ bool mbar_wait(u64* bar, u32 parity) {
+  for (u32 i = 0; i < MBAR_SPIN; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 __device__ __forceinline__ u32 ld_acquire(const u32* p) {
   u32 v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
