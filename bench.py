@@ -393,6 +393,105 @@ def committed_traffic(preset):
     return d.get("per_record_bytes")
 
 
+# ------------------------------------------ more plain workloads, timed --
+def device_workload(preset, seed=1, ranks=0, **overrides):
+    """A generated trace set resident on the device (host copy dropped)."""
+    import torch
+    from paper_2605_03561_b300 import synth
+    cfg = synth.preset(preset, seed=seed, **overrides)
+    if ranks:
+        cfg.n_ranks = ranks
+    rank_off, parent, info = synth.plan(cfg)
+    N = int(rank_off[-1])
+    ts = torch.empty(N, dtype=torch.uint64, pin_memory=True)
+    cx = torch.empty(N, dtype=torch.uint32, pin_memory=True)
+    synth.fill(cfg, rank_off, 0, cfg.n_ranks, ts.data_ptr(), cx.data_ptr(), 0)
+    w = dict(cfg=cfg, info=info, rank_off=rank_off, parent=parent, N=N, marker=cfg.marker_ctx,
+             truth=synth.truth(cfg, info), topo=synth.topology(cfg, info))
+    w["d_ro"] = torch.from_numpy(rank_off).cuda()
+    w["d_par"] = torch.from_numpy(parent).cuda()
+    w["d_ts"] = ts.cuda()
+    w["d_cx"] = cx.cuda()
+    torch.cuda.synchronize()
+    return w
+
+
+def tensor_roofline(prof, R, peak):
+    """The write pass's algorithmic bytes per launch over its event time."""
+    n_l = max(1, prof["tensor_launches"])
+    t = prof["tensor_ms"] / n_l / 1000.0
+    alg = (12 * prof["tensor_records"] + 16 * prof["tensor_entries"] + 8 * prof["tensor_rows"]
+           + 8 * (R + 1) * prof["tensor_launches"]) / n_l
+    return {"ms_per_launch": t * 1e3, "achieved_gbs": alg / t / 1e9,
+            "frac": alg / t / 1e9 / peak, "alg_bytes_per_launch": alg}
+
+
+def run_plain_config(ctx, w, steps, warmup, peak, stream, device=0):
+    """The whole step (ingest + statistics + rack rollup + speedup) on a
+    device-resident workload, timed with CUDA events on the library stream."""
+    import torch
+    import paper_2605_03561_b300 as ta
+    aa = analysis_args(w)
+    calls = DeviceCalls(ta, w, aa, device)
+    R = len(w["rank_off"]) - 1
+
+    def step():
+        e = ctx.load(w["d_ro"], w["d_ts"], w["d_cx"], w["d_par"], w["marker"], borrow=True)
+        calls.run(e)
+        e.free()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile(reset=True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    prof = ctx.profile(reset=True)
+    out = {"records": w["N"], "ranks": R, "ms_per_step": ms,
+           "records_per_s": w["N"] / (ms / 1e3), "steps": steps,
+           "phase_ms_per_step": {k: prof[k] / steps for k in
+                                 ("tensor_count_ms", "tensor_ms", "exclusive_ms",
+                                  "inclusive_ms", "stats_ms", "topology_ms", "speedup_ms")},
+           "tensor_write": tensor_roofline(prof, R, peak)}
+    del calls
+    return out
+
+
+def run_shuffled(ctx, ranks, steps, peak):
+    """The tensor passes on the plain-at-scale generator cut to `ranks` ranks,
+    as generated (consecutive iterations repeat their run sequence) and with
+    every iteration's segments in a fresh random order (no row repeats the
+    previous row's runs, so the write pass's template path never applies):
+    load time and the write pass's roofline for both."""
+    import torch
+    out = {"ranks": ranks}
+    for name, shuffle in (("repeating", 0), ("shuffled", 1)):
+        w = device_workload(3, ranks=ranks, shuffle_segments=shuffle)
+        R = len(w["rank_off"]) - 1
+        for _ in range(2):
+            ctx.load(w["d_ro"], w["d_ts"], w["d_cx"], w["d_par"], w["marker"], borrow=True).free()
+        torch.cuda.synchronize()
+        ctx.profile(reset=True)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.load(w["d_ro"], w["d_ts"], w["d_cx"], w["d_par"], w["marker"], borrow=True).free()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+        prof = ctx.profile(reset=True)
+        out[name] = {"records": w["N"], "load_ms": wall * 1e3,
+                     "records_per_s_load": w["N"] / wall,
+                     "tensor_count_ms": prof["tensor_count_ms"] / steps,
+                     "tensor_write": tensor_roofline(prof, R, peak)}
+        del w
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------ batched vs plain --
 def run_batched(args, ctx, local):
     """The batched form (one graph replay over every set) against plain
@@ -739,6 +838,85 @@ def run_columns(ta, ctx, e, w, R, stream, peaks):
     return out
 
 
+def rounded(x, sig=5):
+    """Floats to `sig` significant digits (keeps the JSON line short)."""
+    if isinstance(x, float):
+        return float(f"{x:.{sig}g}")
+    if isinstance(x, dict):
+        return {k: rounded(v, sig) for k, v in x.items()}
+    if isinstance(x, list):
+        return [rounded(v, sig) for v in x]
+    return x
+
+
+def cpu_summary(cpu):
+    if not cpu:
+        return cpu
+    out = {k: v for k, v in cpu.items() if k != "all_cores"}
+    if cpu.get("all_cores"):
+        a = cpu["all_cores"]
+        out["all_cores"] = {"value": a["value"], "cores": a["cores"], "kind": a["kind"]}
+    return out
+
+
+def block_summaries(d):
+    """The headline numbers of every extra block (the full blocks go to
+    stderr as 'bench detail')."""
+    out = {}
+    c2 = d.get("config2")
+    if c2:
+        out["config2"] = {"records_per_s": c2["records_per_s"], "ms_per_step": c2["ms_per_step"],
+                          "records": c2["records"],
+                          "tensor_write_frac": c2["tensor_write"]["frac"]}
+    sh = d.get("shuffled")
+    if sh:
+        out["shuffled_rows"] = {
+            "ranks": sh["ranks"],
+            **{k: {"records": sh[k]["records"], "write_ms": sh[k]["tensor_write"]["ms_per_launch"],
+                   "write_frac": sh[k]["tensor_write"]["frac"],
+                   "records_per_s_load": sh[k]["records_per_s_load"]}
+               for k in ("repeating", "shuffled")}}
+    b = d.get("batched_vs_plain")
+    if b:
+        out["batched"] = {"records_per_s": b["batched"]["value"],
+                          "ms_per_step": b["batched"]["ms_per_step"],
+                          "plain_ms_per_step": b["plain"]["ms_per_step"],
+                          "speedup_over_plain": b["speedup_batched_over_plain"],
+                          "launches_per_step": b["batched"]["gpu_launches_per_step"],
+                          "plain_launches_per_step": b["plain"]["gpu_launches_per_step"],
+                          "hbm_gbs_tensor_floor": b["batched"]["hbm_gbs_tensor_floor"],
+                          "tuned": b.get("tuned")}
+    sv = d.get("serving")
+    if sv:
+        out["serving"] = {"p50_us": sv["serving"]["p50_us"], "p99_us": sv["serving"]["p99_us"],
+                          "plain_p50_us": sv["plain"]["p50_us"],
+                          "plain_p99_us": sv["plain"]["p99_us"],
+                          "saturated_qps": sv["serving"]["saturated_qps"],
+                          "plain_saturated_qps": sv["plain"]["saturated_qps"],
+                          "arrival_rate_qps": sv["arrival_rate_qps"]}
+    pr = d.get("prune")
+    if pr:
+        out["prune"] = {"ms": pr["ms"], "kept": pr["kept"], "contexts": pr["contexts"]}
+    iv = d.get("interval")
+    if iv:
+        out["interval"] = {k: {"ms": iv[k]["ms"], "frac": iv[k].get("frac_of_measured_hbm")}
+                           for k in iv if isinstance(iv[k], dict)}
+    sw = d.get("serve_window")
+    if sw:
+        out["serve_window"] = {"qps": sw["serving"]["saturated_qps"],
+                               "plain_qps": sw["plain"]["saturated_qps"]}
+    cl = d.get("cluster")
+    if cl:
+        out["cluster_ms"] = {k: cl[k]["ms"] for k in cl if isinstance(cl[k], dict)}
+    co = d.get("columns")
+    if co and co.get("by_traces"):
+        last = max(co["by_traces"], key=int)
+        out["columns_ms"] = {"traces": int(last),
+                             **{k: v for k, v in co["by_traces"][last].items()
+                                if k not in ("events", "sort_passes")}}
+    return out
+
+
 def run_gpu(args):
     import torch
     import paper_2605_03561_b300 as ta
@@ -817,6 +995,23 @@ def run_gpu(args):
                 "frac_of_8TBs_nominal": achieved / 8000.0,
                 "alg_bytes_per_launch": alg_bytes, "ms_per_launch": t_launch * 1e3}
     step_bytes = alg_bytes  # the step's HBM floor is dominated by the tensor pass
+    roofline["step_hbm_gbs"] = step_bytes / (ms_step / 1000.0) / 1e9
+    roofline["step_frac"] = roofline["step_hbm_gbs"] / peaks["hbm_gbs"]
+    roofline["step_note"] = ("the write pass's algorithmic bytes (the step's HBM floor) over "
+                             "the whole step's time")
+
+    # the 4,096-rank workload at its stated size, and the write pass on
+    # traces whose rows never repeat their predecessor's run sequence
+    config2 = shuffled = None
+    if world == 1 and args.config == 3 and not args.no_config2:
+        w2 = device_workload(2)
+        config2 = run_plain_config(ctx, w2, max(3, args.steps // 2), 2, peaks["hbm_gbs"],
+                                   stream, local)
+        config2["workload"] = WORKLOADS[2]
+        del w2
+        torch.cuda.empty_cache()
+    if world == 1 and args.config == 3 and not args.no_shuffled:
+        shuffled = run_shuffled(ctx, 10000, 5, peaks["hbm_gbs"])
 
     # next row N1: pruning on the summary profile (the paper's 1 % rule) of one
     # freshly loaded experiment, timed alone around the call (not in the step)
@@ -1026,6 +1221,11 @@ def run_gpu(args):
         serving = run_serving(args, ctx, local)
 
     if rank == 0:
+        detail = {"batched_vs_plain": batched, "serving": serving, "prune": prune,
+                  "interval": interval, "serve_window": serve_window, "cluster": cluster,
+                  "columns": columns, "config2": config2, "shuffled": shuffled,
+                  "cpu_baseline": cpu}
+        log("bench detail " + json.dumps(detail))
         line = {"metric": METRIC, "value": value, "unit": "records/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "ms_per_step_median": ms_median,
@@ -1045,12 +1245,10 @@ def run_gpu(args):
                 "phase_ms_per_step": {k: prof[k] / args.steps for k in
                                       ("validate_ms", "tensor_count_ms", "tensor_ms", "exclusive_ms", "inclusive_ms",
                                        "stats_ms", "topology_ms", "speedup_ms")},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "batched_vs_plain": batched, "serving": serving, "prune": prune,
-                "interval": interval, "serve_window": serve_window, "cluster": cluster,
-                "columns": columns,
+                "roofline": roofline, "cpu_baseline": cpu_summary(cpu), "e2e": e2e,
+                "blocks": block_summaries(detail),
                 "gpu_launches": launches, "clocks": clk}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(rounded(line)), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
@@ -1078,6 +1276,10 @@ def main():
     p.add_argument("--no-cluster", action="store_true")
     p.add_argument("--no-serve-window", action="store_true")
     p.add_argument("--no-columns", action="store_true")
+    p.add_argument("--no-config2", action="store_true",
+                   help="skip the 4,096-rank workload at its stated size")
+    p.add_argument("--no-shuffled", action="store_true",
+                   help="skip the write pass on traces whose rows never repeat")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-exps", type=int, default=8)
     p.add_argument("--serve-queries", type=int, default=100000)

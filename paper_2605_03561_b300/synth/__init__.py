@@ -32,7 +32,7 @@ class Config(C.Structure):
                 ("imb_iter_prob", C.c_double), ("imb_lo", C.c_double), ("imb_hi", C.c_double),
                 ("comm_frac", C.c_double), ("ranks_per_node", C.c_uint32),
                 ("n_racks", C.c_uint32), ("nodes_per_chassis", C.c_uint32),
-                ("n_slow_racks", C.c_uint32)]
+                ("n_slow_racks", C.c_uint32), ("shuffle_segments", C.c_uint32)]
 
 
 class Info(C.Structure):

@@ -216,6 +216,8 @@ struct Experiment {
       return;
     }
     const uint64_t base = body / I, extra = body % I;
+    std::vector<uint32_t> order(K);
+    for (uint32_t k = 0; k < K; ++k) order[k] = k;
     std::vector<uint64_t> split_lo, split_hi;
     if (base >= 1) split(base - 1, split_lo);
     split(base, split_hi);  // used by the +1 iterations: (base + 1) - 1 samples
@@ -232,7 +234,10 @@ struct Experiment {
       if (L_it == 0) continue;
       emit(c.marker_ctx, s);
       const std::vector<uint64_t>& n = (L_it == base) ? split_lo : split_hi;
-      for (uint32_t k = 0; k < K; ++k) {
+      if (c.shuffle_segments)  // Fisher-Yates over the segment order
+        for (uint32_t k = K; k > 1; --k) std::swap(order[k - 1], order[g.below(k)]);
+      for (uint32_t kk = 0; kk < K; ++kk) {
+        const uint32_t k = order[kk];
         double sk = (rack_slow && seg_comm[k]) ? s * c.slow_factor : s;
         for (uint64_t q = 0; q < n[k]; ++q) emit(seg_ctx[k], sk);
       }

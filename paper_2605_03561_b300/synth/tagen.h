@@ -67,6 +67,9 @@ typedef struct tagen_config {
   uint32_t n_racks;
   uint32_t nodes_per_chassis;
   uint32_t n_slow_racks;      /* TAGEN_SLOW_RACK_COMM                         */
+  uint32_t shuffle_segments;  /* 1: every iteration runs its segments in a    */
+                              /* fresh random order (rows never repeat the     */
+                              /* previous row's run sequence)                  */
 } tagen_config;
 
 /* Experiment description that does not depend on the record arrays. */

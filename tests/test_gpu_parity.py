@@ -178,6 +178,20 @@ def test_generated_configs(preset, R):
     check_topology(a, e, int(comm[0]), topo, tau=(2, 1))
 
 
+def test_shuffled_segments_every_product():
+    """Iterations that run their segments in a fresh random order: no row
+    repeats its predecessor's run sequence, so the tensor write pass takes its
+    direct path (contexts in the warp's union, each once per row) instead of
+    the template path, for 300 ranks of the plain-at-scale generator."""
+    cfg = synth.preset(3, seed=12, n_ranks=300, len_mean=8000.0, shuffle_segments=1)
+    g = synth.generate(cfg)
+    tr, a, e = load_both(g)
+    check_products(tr, a, e)
+    check_stats(a, e, ta.EXCLUSIVE)
+    truth = synth.truth(cfg, g["info"])
+    check_speedup(a, e, np.unique(truth["segment_ctx"]).astype(np.uint32))
+
+
 def test_validation_errors():
     base = edge.case("random_small", 2)
     from gpu_helpers import context
