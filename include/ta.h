@@ -623,6 +623,114 @@ ta_status ta_col_scale(ta_ctx* ctx, uint64_t* a, uint64_t n, uint64_t s);
 ta_status ta_col_sum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* sum);
 ta_status ta_col_cumsum(ta_ctx* ctx, const uint64_t* a, uint64_t n, uint64_t* out);
 
+/* ------------------------------------------------------ sharded form ---- */
+
+/* One job's ranks split into contiguous shards, each loaded as its own
+ * experiment (on its own GPU, or one after another): Section VI-B analyses
+ * 100,000 ranks, the case sharding by rank serves.  Every per-rank product
+ * (tensor, exclusive, inclusive) needs nothing from other shards.  The
+ * cross-rank steps -- context statistics and outliers (Sections VI-A/B), the
+ * rack rollup (Section VI-B) and the potential speedup (Section VI-A, Table
+ * V) -- need one exchange of partials.  Every partial array below merges
+ * element by element with SUM, MIN or MAX as stated, in any order or
+ * grouping (an all-reduce, e.g. torch.distributed over NCCL), and the merge
+ * is exact: integers only, 128-bit sums carried as four 32-bit limbs in
+ * 64-bit words (limb l weighs 2^(32 l); a SUM of up to 2^32 shards cannot
+ * overflow a limb).  The one exception is cv_within, a sum of FP64 terms:
+ * merged across shards it agrees with the unsharded value to about 1e-15
+ * relative per term added, not bit for bit.  The job's exactness contract is
+ * the load contract applied to the whole job: n_total x longest span < 2^63.
+ *
+ * Protocol, with rank_base the global id of the shard's first rank and
+ * n_total the job's rank count:
+ *   1. ta_shard_stats_partials on every shard; merge sums (SUM), mins (MIN),
+ *      maxs (MAX).
+ *   2. ta_shard_stats_finalize with the merged arrays: every shard gets the
+ *      job's per-context statistics and its own ranks' outliers (global rank
+ *      ids, sorted by (ctx, rank); the shards' lists merged by (ctx, rank)
+ *      are the job's list) and argmax candidates; merge the candidates (MIN)
+ *      and write them with ta_shard_set_argmax.
+ *   3. rack rollup: ta_shard_topology_partials on every shard (the same
+ *      merged arrays), merge node_parts (SUM), ta_topology_finalize.
+ *   4. speedup: ta_shard_speedup_bounds on every shard, merge (MIN, SUM,
+ *      MAX); ta_shard_speedup_partials with the job's I*; merge (SUM, MAX,
+ *      SUM); ta_speedup_finalize.
+ * All arrays are device memory owned by the caller; calls run on the
+ * experiment's (or context's) stream and return after their work. */
+
+/* Reducible statistics partials of all n_ctx contexts over the shard's ranks
+ * (a rank without the context counts 0, as in ta_context_stats). */
+typedef struct ta_shard_stats_parts {
+  uint64_t* sums; /* [6 n_ctx] SUM: per context present, S1 = sum x, S2 = sum x^2 as 4 limbs */
+  uint64_t* mins; /* [n_ctx] MIN: min x over the shard's ranks */
+  uint64_t* maxs; /* [n_ctx] MAX: max x */
+} ta_shard_stats_parts;
+ta_status ta_shard_stats_partials(ta_experiment* e, uint32_t metric, const ta_shard_stats_parts* out);
+
+/* The merged partials every finishing call reads. */
+typedef struct ta_shard_merged {
+  uint32_t metric;
+  uint32_t rank_base;       /* global id of this shard's first rank */
+  uint32_t n_total;         /* ranks of the whole job */
+  uint32_t tau_num, tau_den;
+  const uint64_t* sums;     /* merged arrays of ta_shard_stats_parts */
+  const uint64_t* mins;
+  const uint64_t* maxs;
+} ta_shard_merged;
+
+/* Statistics of the whole job for every context (stats[n_ctx], argmax =
+ * this shard's candidate until ta_shard_set_argmax), this shard's outliers
+ * (global ids, sorted; TA_ERR_CAPACITY with n_outliers set when above
+ * outlier_cap) and argmax[n_ctx]: the lowest global rank of this shard whose
+ * value is the job's max (MIN-reducible; 0xFFFFFFFF: none here). */
+typedef struct ta_shard_stats_out {
+  ta_ctx_stats* stats;
+  uint32_t* argmax;
+  ta_outlier* outliers;
+  uint64_t outlier_cap;
+  uint64_t n_outliers; /* out */
+} ta_shard_stats_out;
+ta_status ta_shard_stats_finalize(ta_experiment* e, const ta_shard_merged* m, ta_shard_stats_out* o);
+/* stats[c].argmax = argmax[c] for c < n_ctx (the merged candidates). */
+ta_status ta_shard_set_argmax(ta_ctx* ctx, ta_ctx_stats* stats, const uint32_t* argmax,
+                              uint32_t n_ctx);
+
+/* Node partials of one context for the rack rollup (ta_topology_rollup over
+ * the job): node_parts[3 n_nodes] SUM: per node its outlier ranks, sum of x
+ * and ranks, over this shard's ranks; node_of_rank[shard R] maps the shard's
+ * ranks to global node ids. */
+ta_status ta_shard_topology_partials(ta_experiment* e, const ta_shard_merged* m, uint32_t ctx,
+                                     const uint32_t* node_of_rank, uint32_t n_nodes,
+                                     uint64_t* node_parts);
+/* The rollup from merged node partials: flags (>= min_ranks outlier ranks),
+ * chassis and rack counts and sums, flagged racks (t and o device, as in
+ * ta_topology_rollup; t->node_of_rank unused). */
+ta_status ta_topology_finalize(ta_ctx* ctx, const uint64_t* node_parts, const ta_topology* t,
+                               uint32_t min_ranks, ta_topo_out* o);
+
+/* bounds[3] (host): min n_iter (MIN), sum of n_iter (SUM) and longest span
+ * (MAX) over the shard's ranks. */
+ta_status ta_shard_speedup_bounds(ta_experiment* e, uint64_t* bounds);
+/* Reducible speedup partials for contexts ctxs[nk] (device, sorted unique)
+ * over iterations i < i_star (the job's I*): cells[5 i_star nk] SUM (per
+ * (i, k): sum over ranks and the sum of squares as 4 limbs), cell_max[i_star
+ * nk] MAX, within[nk] SUM (per context the shard's sum of its ranks' CV
+ * terms, in the pairwise order of ta_potential_speedup). */
+typedef struct ta_shard_speedup_parts {
+  uint64_t* cells;
+  uint64_t* cell_max;
+  double* within;
+} ta_shard_speedup_parts;
+ta_status ta_shard_speedup_partials(ta_experiment* e, const uint32_t* ctxs, uint32_t nk,
+                                    uint32_t i_star, const ta_shard_speedup_parts* out);
+/* The speedup of the job from merged partials (outputs device, as in
+ * ta_potential_speedup): excluded = sum of n_iter - n_total i_star, t_app =
+ * app_time_ns or the merged longest span. */
+ta_status ta_speedup_finalize(ta_ctx* ctx, uint32_t nk, uint32_t n_total, uint32_t i_star,
+                              uint64_t excluded, uint64_t t_app,
+                              const ta_shard_speedup_parts* merged, ta_speedup_ctx* per_ctx,
+                              ta_speedup_total* total);
+
 /* ------------------------------------------- allocation-free statistics ---- */
 
 /* ta_context_stats over every context, for callers that must not allocate

@@ -117,6 +117,24 @@ class SpeedupTotal(C.Structure):
                 ("total_reduction", C.c_double), ("speedup_fraction", C.c_double)]
 
 
+class ShardStatsParts(C.Structure):
+    _fields_ = [("sums", P), ("mins", P), ("maxs", P)]
+
+
+class ShardMerged(C.Structure):
+    _fields_ = [("metric", u32), ("rank_base", u32), ("n_total", u32), ("tau_num", u32),
+                ("tau_den", u32), ("sums", P), ("mins", P), ("maxs", P)]
+
+
+class ShardStatsOut(C.Structure):
+    _fields_ = [("stats", P), ("argmax", P), ("outliers", P), ("outlier_cap", u64),
+                ("n_outliers", u64)]
+
+
+class ShardSpeedupParts(C.Structure):
+    _fields_ = [("cells", P), ("cell_max", P), ("within", P)]
+
+
 class Profile(C.Structure):
     _fields_ = [("validate_ms", C.c_double), ("tensor_count_ms", C.c_double),
                 ("tensor_ms", C.c_double),
@@ -270,6 +288,15 @@ _SIGS = {
     "ta_col_cumsum": (C.c_int, [P, P, u64, P]),
     "ta_context_stats_noalloc": (C.c_int, [P, P, P, P, u32, u32, P, u32, u32, u32, P, P, u64,
                                            C.POINTER(u64)]),
+    "ta_shard_stats_partials": (C.c_int, [P, u32, C.POINTER(ShardStatsParts)]),
+    "ta_shard_stats_finalize": (C.c_int, [P, C.POINTER(ShardMerged), C.POINTER(ShardStatsOut)]),
+    "ta_shard_set_argmax": (C.c_int, [P, P, P, u32]),
+    "ta_shard_topology_partials": (C.c_int, [P, C.POINTER(ShardMerged), u32, P, u32, P]),
+    "ta_topology_finalize": (C.c_int, [P, P, C.POINTER(Topology), u32, C.POINTER(TopoOut)]),
+    "ta_shard_speedup_bounds": (C.c_int, [P, C.POINTER(u64)]),
+    "ta_shard_speedup_partials": (C.c_int, [P, P, u32, u32, C.POINTER(ShardSpeedupParts)]),
+    "ta_speedup_finalize": (C.c_int, [P, u32, u32, u32, u64, u64, C.POINTER(ShardSpeedupParts),
+                                      P, P]),
     "ta_batch_plan": (C.c_int, [P, C.POINTER(TraceDesc), u32, C.POINTER(BatchArgs),
                                 C.POINTER(P)]),
     "ta_batch_run": (C.c_int, [P]),
@@ -1077,3 +1104,151 @@ class Server:
         _check(lib().ta_serve_replay(self.h, C.cast(arr, P), arrival.ctypes.data, n,
                                      lat.ctypes.data, C.byref(wall)))
         return lat[:n], int(wall.value)
+
+
+class Shard:
+    """One contiguous rank range [rank_base, rank_base + R) of a job of
+    n_total ranks, loaded as its own experiment: the sharded form's calls
+    (include/ta.h, "sharded form").  Partials are int64 device tensors holding
+    the library's u64 words (two's complement views: SUM, MIN and MAX over
+    them equal the unsigned ones, every value being below 2^63), so any
+    all-reduce merges them, e.g. torch.distributed.all_reduce or a sum over
+    shards on one GPU."""
+
+    def __init__(self, exp: Experiment, rank_base: int, n_total: int):
+        self.e, self.rank_base, self.n_total = exp, int(rank_base), int(n_total)
+
+    def _i64(self, n):
+        torch = _torch()
+        return torch.zeros(max(int(n), 1), dtype=torch.int64, device="cuda")
+
+    def stats_partials(self, metric=EXCLUSIVE):
+        """dict(sums [6 C] SUM, mins [C] MIN, maxs [C] MAX)."""
+        C_ = self.e.C
+        out = dict(sums=self._i64(6 * C_), mins=self._i64(C_), maxs=self._i64(C_))
+        p = ShardStatsParts()
+        p.sums, p.mins, p.maxs = (out[k].data_ptr() for k in ("sums", "mins", "maxs"))
+        _check(lib().ta_shard_stats_partials(self.e.h, metric, C.byref(p)))
+        return out
+
+    def _merged(self, merged, metric, tau):
+        m = ShardMerged()
+        m.metric, m.rank_base, m.n_total = metric, self.rank_base, self.n_total
+        m.tau_num, m.tau_den = tau
+        m.sums, m.mins, m.maxs = (merged[k].data_ptr() for k in ("sums", "mins", "maxs"))
+        return m
+
+    def stats_finalize(self, merged, metric=EXCLUSIVE, tau=(3, 1), outlier_cap=1 << 20):
+        """The job's statistics (device bytes of ta_ctx_stats[C]), this
+        shard's argmax candidates (int64 [C], MIN) and outliers (host arrays,
+        global rank ids)."""
+        torch = _torch()
+        C_ = self.e.C
+        m = self._merged(merged, metric, tau)
+        stats = torch.zeros(C_ * C.sizeof(CtxStats), dtype=torch.uint8, device="cuda")
+        arg32 = torch.zeros(max(C_, 1), dtype=torch.int32, device="cuda")
+        outl = torch.zeros(max(outlier_cap, 1) * C.sizeof(Outlier), dtype=torch.uint8,
+                           device="cuda")
+        o = ShardStatsOut()
+        o.stats, o.argmax, o.outliers = stats.data_ptr(), arg32.data_ptr(), outl.data_ptr()
+        o.outlier_cap = outlier_cap
+        _check(lib().ta_shard_stats_finalize(self.e.h, C.byref(m), C.byref(o)))
+        k = int(o.n_outliers)
+        ol = (Outlier * max(k, 1)).from_buffer_copy(outl[: max(k, 1) * C.sizeof(Outlier)]
+                                                    .cpu().numpy().tobytes())
+        outliers = dict(ctx=np.array([x.ctx for x in ol[:k]], np.uint32),
+                        rank=np.array([x.rank for x in ol[:k]], np.uint32),
+                        z=np.array([x.z for x in ol[:k]], np.float64))
+        argmax = arg32.to(torch.int64) & 0xFFFFFFFF
+        return stats, argmax, outliers
+
+    def set_argmax(self, stats, argmax):
+        """Writes the merged argmax candidates into the statistics; returns
+        them as a host dict like Experiment.stats()."""
+        torch = _torch()
+        a32 = argmax.to(torch.int32).contiguous()
+        _check(lib().ta_shard_set_argmax(self.e.ctx.h, stats.data_ptr(), a32.data_ptr(),
+                                         self.e.C))
+        st = (CtxStats * self.e.C).from_buffer_copy(stats.cpu().numpy().tobytes())
+        return {f: np.array([getattr(x, f) for x in st]) for f, _ in CtxStats._fields_
+                if f != "reserved"}
+
+    def topology_partials(self, merged, ctx, node_of_rank, n_nodes, metric=EXCLUSIVE, tau=(3, 1)):
+        """node_parts int64 [3 n_nodes] (SUM); node_of_rank: this shard's
+        ranks' global node ids."""
+        torch = _torch()
+        m = self._merged(merged, metric, tau)
+        node = torch.as_tensor(np.asarray(node_of_rank, np.uint32).view(np.int32)).cuda()
+        parts = self._i64(3 * n_nodes)
+        _check(lib().ta_shard_topology_partials(self.e.h, C.byref(m), int(ctx), node.data_ptr(),
+                                                int(n_nodes), parts.data_ptr()))
+        return parts
+
+    def speedup_bounds(self):
+        """(min n_iter, sum of n_iter, longest span) of this shard."""
+        b = (u64 * 3)()
+        _check(lib().ta_shard_speedup_bounds(self.e.h, b))
+        return int(b[0]), int(b[1]), int(b[2])
+
+    def speedup_partials(self, ctxs, i_star):
+        """dict(cells [5 I* nk] SUM, cell_max [I* nk] MAX, within [nk] f64 SUM)."""
+        torch = _torch()
+        cx = torch.as_tensor(np.asarray(ctxs, np.uint32).view(np.int32)).cuda()
+        nk = len(ctxs)
+        out = dict(cells=self._i64(5 * i_star * nk), cell_max=self._i64(i_star * nk),
+                   within=torch.zeros(nk, dtype=torch.float64, device="cuda"))
+        p = ShardSpeedupParts()
+        p.cells, p.cell_max, p.within = (out[k].data_ptr() for k in ("cells", "cell_max", "within"))
+        _check(lib().ta_shard_speedup_partials(self.e.h, cx.data_ptr(), nk, int(i_star),
+                                               C.byref(p)))
+        return out
+
+
+def topology_finalize(ctx: Context, node_parts, rack_of_node, chassis_of_node, n_racks,
+                      n_chassis, min_ranks=1):
+    """The rack rollup from merged node partials (host dict like
+    Experiment.topology())."""
+    torch = _torch()
+    nn = len(rack_of_node)
+    rack = torch.as_tensor(np.asarray(rack_of_node, np.uint32).view(np.int32)).cuda()
+    ch = torch.as_tensor(np.asarray(chassis_of_node, np.uint32).view(np.int32)).cuda()
+    t = Topology()
+    t.n_nodes, t.n_chassis, t.n_racks, t.mem_kind = nn, int(n_chassis), int(n_racks), MEM_DEVICE
+    t.node_of_rank, t.rack_of_node, t.chassis_of_node = None, rack.data_ptr(), ch.data_ptr()
+    spec = dict(node_outliers=(nn, np.uint32), node_sum=(nn, np.uint64),
+                node_ranks=(nn, np.uint32), node_flag=(nn, np.uint8),
+                chassis_flagged=(n_chassis, np.uint32), chassis_nodes=(n_chassis, np.uint32),
+                chassis_sum=(n_chassis, np.uint64), rack_flagged=(n_racks, np.uint32),
+                rack_nodes=(n_racks, np.uint32), rack_sum=(n_racks, np.uint64),
+                flagged_racks=(n_racks, np.uint32))
+    dev = {k: torch.zeros(max(int(n), 1) * np.dtype(dt).itemsize, dtype=torch.uint8,
+                          device="cuda") for k, (n, dt) in spec.items()}
+    o = TopoOut()
+    o.mem_kind = MEM_DEVICE
+    for k, v in dev.items():
+        setattr(o, k, v.data_ptr())
+    _check(lib().ta_topology_finalize(ctx.h, node_parts.data_ptr(), C.byref(t), int(min_ranks),
+                                      C.byref(o)))
+    out = {k: np.frombuffer(dev[k].cpu().numpy().tobytes(), dt)[: int(n)]
+           for k, (n, dt) in spec.items()}
+    out["flagged_racks"] = out["flagged_racks"][: int(o.n_flagged_racks)]
+    return out
+
+
+def speedup_finalize(ctx: Context, merged, n_total, i_star, excluded, t_app, nk):
+    """The job's speedup from merged partials (host dicts like
+    Experiment.speedup())."""
+    torch = _torch()
+    per = torch.zeros(nk * C.sizeof(SpeedupCtx), dtype=torch.uint8, device="cuda")
+    tot = torch.zeros(C.sizeof(SpeedupTotal), dtype=torch.uint8, device="cuda")
+    p = ShardSpeedupParts()
+    p.cells, p.cell_max, p.within = (merged[k].data_ptr() for k in ("cells", "cell_max", "within"))
+    _check(lib().ta_speedup_finalize(ctx.h, nk, int(n_total), int(i_star), int(excluded),
+                                     int(t_app), C.byref(p), per.data_ptr(), tot.data_ptr()))
+    pc = (SpeedupCtx * nk).from_buffer_copy(per.cpu().numpy().tobytes())
+    tc = SpeedupTotal.from_buffer_copy(tot.cpu().numpy().tobytes())
+    d = {f: np.array([getattr(x, f) for x in pc]) for f, _ in SpeedupCtx._fields_}
+    d["G"] = [int(lo) + (int(hi) << 64) for lo, hi in zip(d["G_lo"], d["G_hi"])]
+    t = {f: getattr(tc, f) for f, _ in SpeedupTotal._fields_ if f != "reserved"}
+    t["sum_G"] = t["sum_G_lo"] + (t["sum_G_hi"] << 64)
+    return d, t

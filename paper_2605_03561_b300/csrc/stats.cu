@@ -186,13 +186,14 @@ __global__ void k_stats_z(const u32* __restrict__ S, u32 n_all, const u64* __res
                           const u32* __restrict__ ctx, const u64* __restrict__ time,
                           const u32* __restrict__ slot_of_ctx, Partials P, u32 tn, u32 td,
                           double* z_out, u64* keys, double* zs, u64 cap,
-                          unsigned long long* n_out, uint8_t* rank_flag, SetMap sets) {
+                          unsigned long long* n_out, uint8_t* rank_flag, SetMap sets,
+                          u64 n_stat) {
   const int lane = threadIdx.x & 31;
   const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
   for (u32 i = gw; i < n_all; i += nw) {
     const u32 r = rank_at(S, i);
-    u64 n = n_all;
+    u64 n = n_stat ? n_stat : n_all;  // the moments' rank count (a shard's job: all shards)
     u32 cbase = 0;
     if (sets.S) {
       const u32 set = sets.rank_set[r];
@@ -319,13 +320,13 @@ __global__ void __launch_bounds__(1024) k_sort_block(u64* keys, double* vals, u6
 // Keys are (slot << 32 | rank); slot_ctx maps a slot back to its context
 // (null: the slot is the context).
 __global__ void k_write_outliers(const u64* keys, const double* zs, u64 n, ta_outlier* out,
-                                 const u32* slot_ctx) {
+                                 const u32* slot_ctx, u32 rank_base) {
   const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   ta_outlier o;
   const u32 slot = (u32)(keys[i] >> 32);
   o.ctx = slot_ctx ? slot_ctx[slot] : slot;
-  o.rank = (u32)keys[i];
+  o.rank = (u32)keys[i] + rank_base;
   o.z = zs[i];
   out[i] = o;
 }
@@ -465,7 +466,7 @@ ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 
                                                    SetMap{});
   k_stats_finalize<<<blocks(ns), 256, 0, L.stream>>>(ns, n, dS, P, R.stats, SetMap{});
   k_stats_z<<<grid, 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P, tn, td,
-                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag, SetMap{});
+                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag, SetMap{}, 0);
   k_stats_argmax<<<blocks(ns), 256, 0, L.stream>>>(ns, P.argmax, R.stats);
   L.count(4);
   u64 h = 0;
@@ -481,8 +482,8 @@ ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 
 __global__ void k_topo_check(const u32* node_of_rank, u32 R, u32 nn, const u32* rack, u32 nr,
                              const u32* chassis, u32 nc, u32* status) {
   const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < R && node_of_rank[i] >= nn) flag(status, F_INVALID);
-  if (i < nn && (rack[i] >= nr || chassis[i] >= nc)) flag(status, F_INVALID);
+  if (node_of_rank && i < R && node_of_rank[i] >= nn) flag(status, F_INVALID);
+  if (rack && chassis && i < nn && (rack[i] >= nr || chassis[i] >= nc)) flag(status, F_INVALID);
 }
 
 __device__ __forceinline__ u64 csr_lookup(const u64* off, const u32* ctx, const u64* time, u32 r,
@@ -991,6 +992,77 @@ __global__ void k_sp_total(u32 nk, u32 n, u32 I, u64 excluded, u64 t_app, ta_spe
 
 }  // namespace
 
+namespace {
+
+// The speedup's parts over ranks S (n of them), contexts dK[nk] and
+// iterations i < I: the cells (per (i, k) sum, max and 128-bit sum of
+// squares over ranks) and every context's pairwise sum of per-rank CV terms.
+struct SpeedupParts {
+  u64 *gs, *gm, *gl, *gh;
+  double* wsum;
+};
+
+ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32* dS, u32 n,
+                        const u32* dK, u32 nk, u32 I, u32* status, SpeedupParts& sp) {
+  ta_ctx* c = e->ctx;
+  u32* kmap;
+  TRY(tmp.get_n(e->C, &kmap, "kmap"));
+  cudaMemsetAsync(kmap, 0xFF, (size_t)e->C * 4, c->stream);
+  k_slot_map<<<blocks(nk), 256, 0, L.stream>>>(dK, nk, e->C, kmap);
+  L.count();
+  const u64 ncell = std::max<u64>(1, (u64)I * nk);
+  u64 *&gs = sp.gs, *&gm = sp.gm, *&gl = sp.gl, *&gh = sp.gh;
+  double* cvw;
+  TRY(tmp.get_n(ncell, &gs, "cells"));
+  TRY(tmp.get_n(ncell, &gm, "cells"));
+  TRY(tmp.get_n(ncell, &gl, "cells"));
+  TRY(tmp.get_n(ncell, &gh, "cells"));
+  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw, "cv terms"));
+  cudaMemsetAsync(gs, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
+  cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
+  if (I > 0) {
+    const size_t map_smem = e->C <= SP_SMAP ? (size_t)(e->C + 15) / 16 * 16 : 0;
+    const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + SP_NW - 1) / SP_NW)));
+    if (map_smem)
+      cudaFuncSetAttribute(k_sp_within, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_smem);
+    for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
+      k_sp_within<<<grid, SP_NW * 32, map_smem, L.stream>>>(
+          dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
+          std::min(SP_KC, nk - k0), I, cvw);
+      L.count();
+    }
+    // cells: enough warps to fill the GPU, each with a sizeable group of ranks
+    const u32 n_ib = (I + SP_IB - 1) / SP_IB, n_kb = (nk + 63) / 64;
+    const u64 tiles = (u64)n_ib * n_kb;
+    const u64 want = (u64)c->num_sms * 48;
+    u64 groups = std::max<u64>(1, std::min<u64>((want + tiles - 1) / tiles, (n + 63) / 64));
+    const u32 group = (u32)((n + groups - 1) / groups);
+    groups = (n + group - 1) / group;
+    const u64 n_items = tiles * groups;
+    const size_t cmap_smem = (n_kb == 1) ? map_smem : 0;
+    const size_t cells_smem = cmap_smem + (size_t)SP_NW * SPC_WARP_BYTES;
+    cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem);
+    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cells_smem, L.stream>>>(
+        dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
+        group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
+    L.count();
+  }
+  double* cvw2;
+  double*& wsum = sp.wsum;
+  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw2, "cv terms"));
+  TRY(tmp.get_n(nk, &wsum, "within sums"));
+  cudaMemsetAsync(wsum, 0, (size_t)nk * 8, c->stream);
+  if (I > 0) {
+    k_sp_pairwise<<<nk, 256, 0, L.stream>>>(cvw, cvw2, n, wsum);
+    L.count();
+  }
+  return TA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_out* o) {
@@ -1037,7 +1109,7 @@ ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_ou
   if (fits && R.kept > 0 && o->outliers) {
     if (a->mem_kind == TA_MEM_DEVICE) dout = o->outliers;
     else TRY(tmp.get_n(R.kept, &dout, "outliers"));
-    k_write_outliers<<<blocks(R.kept), 256, 0, L.stream>>>(R.keys, R.zs, R.kept, dout, dK);
+    k_write_outliers<<<blocks(R.kept), 256, 0, L.stream>>>(R.keys, R.zs, R.kept, dout, dK, 0);
     L.count();
     if (a->mem_kind == TA_MEM_HOST) TRY(copy(c, o->outliers, dout, R.kept * sizeof(ta_outlier)));
   }
@@ -1203,50 +1275,8 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   const u32 I = (u32)h[0];
   const u64 excluded = h[1] - (u64)n * I;
   const u64 t_app = a->app_time_ns ? a->app_time_ns : h[2];
-  u32* kmap;
-  TRY(tmp.get_n(e->C, &kmap, "kmap"));
-  cudaMemsetAsync(kmap, 0xFF, (size_t)e->C * 4, c->stream);
-  k_slot_map<<<blocks(nk), 256, 0, L.stream>>>(dK, nk, e->C, kmap);
-  L.count();
-  const u64 ncell = std::max<u64>(1, (u64)I * nk);
-  u64 *gs, *gm, *gl, *gh;
-  double* cvw;
-  TRY(tmp.get_n(ncell, &gs, "cells"));
-  TRY(tmp.get_n(ncell, &gm, "cells"));
-  TRY(tmp.get_n(ncell, &gl, "cells"));
-  TRY(tmp.get_n(ncell, &gh, "cells"));
-  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw, "cv terms"));
-  cudaMemsetAsync(gs, 0, ncell * 8, c->stream);
-  cudaMemsetAsync(gm, 0, ncell * 8, c->stream);
-  cudaMemsetAsync(gl, 0, ncell * 8, c->stream);
-  cudaMemsetAsync(gh, 0, ncell * 8, c->stream);
-  if (I > 0) {
-    const size_t map_smem = e->C <= SP_SMAP ? (size_t)(e->C + 15) / 16 * 16 : 0;
-    const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + SP_NW - 1) / SP_NW)));
-    if (map_smem)
-      cudaFuncSetAttribute(k_sp_within, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_smem);
-    for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
-      k_sp_within<<<grid, SP_NW * 32, map_smem, L.stream>>>(
-          dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
-          std::min(SP_KC, nk - k0), I, cvw);
-      L.count();
-    }
-    // cells: enough warps to fill the GPU, each with a sizeable group of ranks
-    const u32 n_ib = (I + SP_IB - 1) / SP_IB, n_kb = (nk + 63) / 64;
-    const u64 tiles = (u64)n_ib * n_kb;
-    const u64 want = (u64)c->num_sms * 48;
-    u64 groups = std::max<u64>(1, std::min<u64>((want + tiles - 1) / tiles, (n + 63) / 64));
-    const u32 group = (u32)((n + groups - 1) / groups);
-    groups = (n + group - 1) / group;
-    const u64 n_items = tiles * groups;
-    const size_t cmap_smem = (n_kb == 1) ? map_smem : 0;
-    const size_t cells_smem = cmap_smem + (size_t)SP_NW * SPC_WARP_BYTES;
-    cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem);
-    k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cells_smem, L.stream>>>(
-        dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
-        group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
-    L.count();
-  }
+  SpeedupParts sp;
+  TRY(speedup_parts(e, tmp, L, dS, n, dK, nk, I, status, sp));
   ta_speedup_ctx* dper;
   ta_speedup_total* dtot;
   if (a->mem_kind == TA_MEM_DEVICE) {
@@ -1256,14 +1286,8 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     TRY(tmp.get_n(nk, &dper, "per ctx"));
     TRY(tmp.get_n(1, &dtot, "total"));
   }
-  double *cvw2, *wsum;
-  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw2, "cv terms"));
-  TRY(tmp.get_n(nk, &wsum, "within sums"));
-  if (I > 0) {
-    k_sp_pairwise<<<nk, 256, 0, L.stream>>>(cvw, cvw2, n, wsum);
-    L.count();
-  }
-  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n, I, gs, gm, gl, gh, wsum,
+  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n, I, sp.gs, sp.gm, sp.gl,
+                                                                  sp.gh, sp.wsum,
                                                                   dper);
   k_sp_total<<<1, 1, 0, L.stream>>>(nk, n, I, excluded, t_app, dper, dtot);
   L.count(2);
@@ -1452,7 +1476,7 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, SetMap{});
   k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats, SetMap{});
   k_stats_z<<<grid, 256, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, tau_num, tau_den,
-                                  nullptr, keys, zs, kcap, n_out, nullptr, SetMap{});
+                                  nullptr, keys, zs, kcap, n_out, nullptr, SetMap{}, 0);
   k_stats_argmax<<<blocks(C), 256, 0, st>>>((u32)C, P.argmax, stats);
   L.count(5);
   err = cudaGetLastError();
@@ -1468,7 +1492,7 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
                 (unsigned long long)outlier_cap);
   if (h > 0) {
     sort_pairs(L, keys, zs, h);  // the key buffer holds NA_MAX_OUTLIERS (a power of two)
-    k_write_outliers<<<blocks(h), 256, 0, st>>>(keys, zs, h, outliers, nullptr);
+    k_write_outliers<<<blocks(h), 256, 0, st>>>(keys, zs, h, outliers, nullptr, 0);
     L.count();
   }
   err = cudaGetLastError();
@@ -1477,6 +1501,439 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   if (err != cudaSuccess) return cuda_fail(err, "ta_context_stats_noalloc");
   return TA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Sharded form: reducible partials of the cross-rank steps and their
+// finishing from merged partials (one exchange: SUM, MIN or MAX element-wise;
+// 128-bit sums as four 32-bit limbs in 64-bit words).
+namespace {
+
+__device__ __forceinline__ void put_limbs(u64* q, u128 v) {
+  q[0] = (u64)(v & 0xFFFFFFFFull);
+  q[1] = (u64)((v >> 32) & 0xFFFFFFFFull);
+  q[2] = (u64)((v >> 64) & 0xFFFFFFFFull);
+  q[3] = (u64)(v >> 96);
+}
+// Sum of limb l times 2^(32 l); merged limbs may exceed 32 bits (carried here).
+__device__ __forceinline__ u128 get_limbs(const u64* q) {
+  return (u128)q[0] + ((u128)q[1] << 32) + ((u128)q[2] << 64) + ((u128)q[3] << 96);
+}
+
+// Per context of the shard's partials: present, S1, S2 limbs; min (absent
+// ranks count 0) and max.
+__global__ void k_shard_export(u32 ns, Partials P, u32 R, u64* sums, u64* mins, u64* maxs) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const u32 present = P.present[s];
+  sums[6 * (u64)s] = present;
+  sums[6 * (u64)s + 1] = P.s1[s];
+  put_limbs(sums + 6 * (u64)s + 2, ((u128)P.s2hi[s] << 64) | P.s2lo[s]);
+  mins[s] = present < R ? 0ull : P.mn[s];
+  maxs[s] = P.mx[s];
+}
+
+// Merged partials -> the finishing kernels' partials (slot s = ctx c0 + s).
+__global__ void k_shard_import(u32 ns, u32 c0, const u64* sums, const u64* mins, const u64* maxs,
+                               Partials P) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const u64 c = (u64)c0 + s;
+  P.present[s] = (u32)sums[6 * c];
+  P.s1[s] = sums[6 * c + 1];
+  const u128 S2 = get_limbs(sums + 6 * c + 2);
+  P.s2lo[s] = (u64)S2;
+  P.s2hi[s] = (u64)(S2 >> 64);
+  P.mn[s] = mins[c];
+  P.mx[s] = maxs[c];
+}
+
+// Argmax candidates as global rank ids (none: 0xFFFFFFFF), also written into
+// the statistics records.
+__global__ void k_shard_argmax(u32 ns, const u32* argmax, u32 rank_base, u32* out,
+                               ta_ctx_stats* stats) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ns) return;
+  const u32 a = argmax[s] == NONE32 ? NONE32 : argmax[s] + rank_base;
+  out[s] = a;
+  stats[s].argmax = a;
+}
+
+__global__ void k_set_argmax(u32 n, const u32* argmax, ta_ctx_stats* stats) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) stats[s].argmax = argmax[s];
+}
+
+// Node partials of one context over the shard's ranks: outlier ranks, sum of
+// x, ranks (u64 SUM-reducible).
+__global__ void k_shard_nodes(u32 R, const u64* off, const u32* ctx, const u64* time, u32 c,
+                              const uint8_t* rank_flag, const u32* node_of_rank,
+                              unsigned long long* parts, u32 nn) {
+  const u32 r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  const u32 nd = node_of_rank[r];
+  const u64 x = csr_lookup(off, ctx, time, r, c);
+  if (rank_flag[r]) atomicAdd(&parts[nd], 1ull);
+  atomicAdd(&parts[(u64)nn + nd], (unsigned long long)x);
+  atomicAdd(&parts[2 * (u64)nn + nd], 1ull);
+}
+
+__global__ void k_nodes_unpack(u32 nn, const u64* parts, u32* node_out,
+                               unsigned long long* node_sum, u32* node_ranks) {
+  const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  node_out[i] = (u32)parts[i];
+  node_sum[i] = parts[(u64)nn + i];
+  node_ranks[i] = (u32)parts[2 * (u64)nn + i];
+}
+
+// Speedup cells -> reducible (sum, sum of squares as limbs; max apart), and back.
+__global__ void k_cells_export(u64 ncell, const u64* gs, const u64* gl, const u64* gh, u64* cells) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  cells[5 * i] = gs[i];
+  put_limbs(cells + 5 * i + 1, ((u128)gh[i] << 64) | gl[i]);
+}
+__global__ void k_cells_import(u64 ncell, const u64* cells, u64* gs, u64* gl, u64* gh) {
+  const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ncell) return;
+  gs[i] = cells[5 * i];
+  const u128 q = get_limbs(cells + 5 * i + 1);
+  gl[i] = (u64)q;
+  gh[i] = (u64)(q >> 64);
+}
+
+// The finishing kernels' partial arrays for ns slots.
+ta_status alloc_partials(Pool& tmp, u32 ns, Partials& P) {
+  TRY(tmp.get_n(ns, &P.present, "partials"));
+  TRY(tmp.get_n(ns, &P.mn, "partials"));
+  TRY(tmp.get_n(ns, &P.mx, "partials"));
+  TRY(tmp.get_n(ns, &P.s1, "partials"));
+  TRY(tmp.get_n(ns, &P.s2lo, "partials"));
+  TRY(tmp.get_n(ns, &P.s2hi, "partials"));
+  TRY(tmp.get_n(ns, &P.argmax, "partials"));
+  TRY(tmp.get_n(ns, &P.sd, "partials"));
+  TRY(tmp.get_n(ns, &P.Mlo, "partials"));
+  TRY(tmp.get_n(ns, &P.Mhi, "partials"));
+  return TA_OK;
+}
+
+ta_status shard_check(const ta_experiment* e, const ta_shard_merged* m) {
+  if (!m || !m->sums || !m->mins || !m->maxs) return fail(TA_ERR_INVALID_ARG, "merged partials NULL");
+  if (m->metric > 1 || !metric_csr(e, m->metric))
+    return fail(m->metric > 1 ? TA_ERR_INVALID_ARG : TA_ERR_STATE, "metric");
+  if (m->tau_den == 0) return fail(TA_ERR_INVALID_ARG, "tau_den = 0");
+  if (m->n_total < e->R || (u64)m->rank_base + e->R > m->n_total)
+    return fail(TA_ERR_INVALID_ARG, "shard ranks [%u, %llu) outside the job's %u ranks",
+                m->rank_base, (unsigned long long)m->rank_base + e->R, m->n_total);
+  return TA_OK;
+}
+
+struct ShardCall {
+  Pool tmp;
+  explicit ShardCall(ta_ctx* c) : tmp{c, {}} {}
+  ~ShardCall() {
+    cudaStreamSynchronize(tmp.ctx->stream);
+    tmp.release();
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+ta_status ta_shard_stats_partials(ta_experiment* e, uint32_t metric, const ta_shard_stats_parts* o) {
+  if (!e || !o || !o->sums || !o->mins || !o->maxs)
+    return fail(TA_ERR_INVALID_ARG, "ta_shard_stats_partials: NULL argument");
+  if (metric > 1 || !metric_csr(e, metric))
+    return fail(metric > 1 ? TA_ERR_INVALID_ARG : TA_ERR_STATE, "metric");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.stats_ms);
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  const Csr* m = metric_csr(e, metric);
+  const u32 C = e->C;
+  Partials P;
+  TRY(alloc_partials(tmp, C, P));
+  u32* slot_of_ctx;
+  TRY(tmp.get_n(C, &slot_of_ctx, "slot map"));
+  k_slot_map<<<blocks(C), 256, 0, L.stream>>>(nullptr, 0, C, slot_of_ctx);
+  cudaMemsetAsync(P.present, 0, (size_t)C * 4, c->stream);
+  cudaMemsetAsync(P.mn, 0xFF, (size_t)C * 8, c->stream);
+  cudaMemsetAsync(P.mx, 0, (size_t)C * 8, c->stream);
+  cudaMemsetAsync(P.s1, 0, (size_t)C * 8, c->stream);
+  cudaMemsetAsync(P.s2lo, 0, (size_t)C * 8, c->stream);
+  cudaMemsetAsync(P.s2hi, 0, (size_t)C * 8, c->stream);
+  const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((e->R + 7) / 8)));
+  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(nullptr, e->R, m->off, m->ctx, m->time,
+                                                   slot_of_ctx, P, SetMap{});
+  k_shard_export<<<blocks(C), 256, 0, L.stream>>>(C, P, e->R, o->sums, o->mins, o->maxs);
+  L.count(3);
+  return sync_check(c, "ta_shard_stats_partials");
+}
+
+ta_status ta_shard_stats_finalize(ta_experiment* e, const ta_shard_merged* mg,
+                                  ta_shard_stats_out* o) {
+  if (!e || !o || !o->stats || !o->argmax || (o->outlier_cap && !o->outliers))
+    return fail(TA_ERR_INVALID_ARG, "ta_shard_stats_finalize: NULL argument");
+  TRY(shard_check(e, mg));
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.stats_ms);
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  const Csr* m = metric_csr(e, mg->metric);
+  const u32 C = e->C;
+  Partials P;
+  TRY(alloc_partials(tmp, C, P));
+  u32* slot_of_ctx;
+  TRY(tmp.get_n(C, &slot_of_ctx, "slot map"));
+  k_slot_map<<<blocks(C), 256, 0, L.stream>>>(nullptr, 0, C, slot_of_ctx);
+  k_shard_import<<<blocks(C), 256, 0, L.stream>>>(C, 0, mg->sums, mg->mins, mg->maxs, P);
+  k_stats_finalize<<<blocks(C), 256, 0, L.stream>>>(C, mg->n_total, nullptr, P, o->stats,
+                                                    SetMap{});
+  const u64 kcap = std::max<u64>(1, o->outlier_cap);
+  u64 P2 = 1;
+  while (P2 < kcap) P2 <<= 1;
+  u64* keys;
+  double* zs;
+  unsigned long long* n_out;
+  TRY(tmp.get_n(P2, &keys, "outlier keys"));
+  TRY(tmp.get_n(P2, &zs, "outlier z"));
+  TRY(tmp.get_n(1, &n_out, "outlier count"));
+  cudaMemsetAsync(n_out, 0, 8, c->stream);
+  const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((e->R + 7) / 8)));
+  k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, e->R, m->off, m->ctx, m->time, slot_of_ctx, P,
+                                        mg->tau_num, mg->tau_den, nullptr, keys, zs, kcap, n_out,
+                                        nullptr, SetMap{}, mg->n_total);
+  k_shard_argmax<<<blocks(C), 256, 0, L.stream>>>(C, P.argmax, mg->rank_base, o->argmax,
+                                                  o->stats);
+  L.count(5);
+  u64 h = 0;
+  TRY(copy(c, &h, n_out, 8));
+  TRY(sync_check(c, "ta_shard_stats_finalize"));
+  o->n_outliers = h;
+  if (h > o->outlier_cap)
+    return fail(TA_ERR_CAPACITY, "%llu outliers, capacity %llu", (unsigned long long)h,
+                (unsigned long long)o->outlier_cap);
+  if (h > 0) {
+    sort_pairs(L, keys, zs, h);
+    k_write_outliers<<<blocks(h), 256, 0, L.stream>>>(keys, zs, h, o->outliers, nullptr,
+                                                      mg->rank_base);
+    L.count();
+  }
+  return sync_check(c, "ta_shard_stats_finalize");
+}
+
+ta_status ta_shard_set_argmax(ta_ctx* c, ta_ctx_stats* stats, const uint32_t* argmax,
+                              uint32_t n_ctx) {
+  if (!c || !stats || !argmax) return fail(TA_ERR_INVALID_ARG, "ta_shard_set_argmax: NULL argument");
+  cudaSetDevice(c->device);
+  k_set_argmax<<<blocks(n_ctx), 256, 0, c->stream>>>(n_ctx, argmax, stats);
+  ++c->launches;
+  return sync_check(c, "ta_shard_set_argmax");
+}
+
+ta_status ta_shard_topology_partials(ta_experiment* e, const ta_shard_merged* mg, uint32_t ctx,
+                                     const uint32_t* node_of_rank, uint32_t n_nodes,
+                                     uint64_t* node_parts) {
+  if (!e || !node_of_rank || !node_parts || n_nodes == 0)
+    return fail(TA_ERR_INVALID_ARG, "ta_shard_topology_partials: NULL argument");
+  TRY(shard_check(e, mg));
+  if (ctx >= e->C) return fail(TA_ERR_INVALID_ARG, "ctx >= n_ctx");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.topology_ms);
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  const Csr* m = metric_csr(e, mg->metric);
+  u32* status;
+  TRY(tmp.get_n(1, &status, "status"));
+  cudaMemsetAsync(status, 0, 4, c->stream);
+  k_topo_check<<<blocks(e->R), 256, 0, L.stream>>>(node_of_rank, e->R, n_nodes, nullptr, 0,
+                                                   nullptr, 0, status);
+  L.count();
+  u32 hs = 0;
+  TRY(copy(c, &hs, status, 4));
+  TRY(sync_check(c, "topology check"));
+  if (hs) return fail(TA_ERR_INVALID_ARG, "node ids out of range");
+  // the job's statistics of ctx (slot 0), then this shard's outlier ranks
+  Partials P;
+  TRY(alloc_partials(tmp, 1, P));
+  u32* slot_of_ctx;
+  TRY(tmp.get_n(e->C, &slot_of_ctx, "slot map"));
+  cudaMemsetAsync(slot_of_ctx, 0xFF, (size_t)e->C * 4, c->stream);
+  u32* dk;
+  TRY(tmp.get_n(1, &dk, "ctx"));
+  TRY(copy(c, dk, &ctx, 4));
+  k_slot_map<<<1, 32, 0, L.stream>>>(dk, 1, e->C, slot_of_ctx);
+  ta_ctx_stats* st;
+  TRY(tmp.get_n(1, &st, "stats"));
+  k_shard_import<<<1, 32, 0, L.stream>>>(1, ctx, mg->sums, mg->mins, mg->maxs, P);
+  k_stats_finalize<<<1, 32, 0, L.stream>>>(1, mg->n_total, nullptr, P, st, SetMap{});
+  uint8_t* rank_flag;
+  TRY(tmp.get_n(std::max<u32>(e->R, 1), &rank_flag, "rank flags"));
+  cudaMemsetAsync(rank_flag, 0, e->R, c->stream);
+  u64* keys;
+  double* zs;
+  unsigned long long* n_out;
+  TRY(tmp.get_n(1, &keys, "outlier keys"));
+  TRY(tmp.get_n(1, &zs, "outlier z"));
+  TRY(tmp.get_n(1, &n_out, "outlier count"));
+  cudaMemsetAsync(n_out, 0, 8, c->stream);
+  const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((e->R + 7) / 8)));
+  k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, e->R, m->off, m->ctx, m->time, slot_of_ctx, P,
+                                        mg->tau_num, mg->tau_den, nullptr, keys, zs, 1, n_out,
+                                        rank_flag, SetMap{}, mg->n_total);
+  cudaMemsetAsync(node_parts, 0, (size_t)n_nodes * 24, c->stream);
+  k_shard_nodes<<<blocks(e->R), 256, 0, L.stream>>>(e->R, m->off, m->ctx, m->time, ctx, rank_flag,
+                                                    node_of_rank,
+                                                    (unsigned long long*)node_parts, n_nodes);
+  L.count(5);
+  return sync_check(c, "ta_shard_topology_partials");
+}
+
+ta_status ta_topology_finalize(ta_ctx* c, const uint64_t* node_parts, const ta_topology* t,
+                               uint32_t min_ranks, ta_topo_out* o) {
+  if (!c || !node_parts || !t || !o || !t->rack_of_node || !t->chassis_of_node || t->n_nodes == 0 ||
+      t->n_racks == 0 || t->n_chassis == 0)
+    return fail(TA_ERR_INVALID_ARG, "ta_topology_finalize: NULL argument");
+  if (min_ranks == 0) return fail(TA_ERR_INVALID_ARG, "min_ranks = 0");
+  if (t->mem_kind != TA_MEM_DEVICE || o->mem_kind != TA_MEM_DEVICE)
+    return fail(TA_ERR_INVALID_ARG, "ta_topology_finalize takes device arrays");
+  if (!o->node_outliers || !o->node_sum || !o->node_ranks || !o->node_flag || !o->chassis_flagged ||
+      !o->chassis_nodes || !o->chassis_sum || !o->rack_flagged || !o->rack_nodes || !o->rack_sum ||
+      !o->flagged_racks)
+    return fail(TA_ERR_INVALID_ARG, "ta_topology_finalize: output NULL");
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  const u32 nn = t->n_nodes, nc = t->n_chassis, nr = t->n_racks;
+  u32* status;
+  TRY(tmp.get_n(2, &status, "status"));
+  cudaMemsetAsync(status, 0, 8, c->stream);
+  k_topo_check<<<blocks(nn), 256, 0, L.stream>>>(nullptr, 0, nn, t->rack_of_node, nr,
+                                                 t->chassis_of_node, nc, status);
+  L.count();
+  u32 hs = 0;
+  TRY(copy(c, &hs, status, 4));
+  TRY(sync_check(c, "topology check"));
+  if (hs) return fail(TA_ERR_INVALID_ARG, "topology ids out of range");
+  cudaMemsetAsync(o->chassis_flagged, 0, (size_t)nc * 4, c->stream);
+  cudaMemsetAsync(o->chassis_nodes, 0, (size_t)nc * 4, c->stream);
+  cudaMemsetAsync(o->chassis_sum, 0, (size_t)nc * 8, c->stream);
+  cudaMemsetAsync(o->rack_flagged, 0, (size_t)nr * 4, c->stream);
+  cudaMemsetAsync(o->rack_nodes, 0, (size_t)nr * 4, c->stream);
+  cudaMemsetAsync(o->rack_sum, 0, (size_t)nr * 8, c->stream);
+  k_nodes_unpack<<<blocks(nn), 256, 0, L.stream>>>(nn, node_parts, o->node_outliers,
+                                                  (unsigned long long*)o->node_sum, o->node_ranks);
+  k_topo_up<<<blocks(nn), 256, 0, L.stream>>>(
+      nn, o->node_outliers, (const unsigned long long*)o->node_sum, min_ranks, t->rack_of_node,
+      t->chassis_of_node, o->node_flag, o->chassis_flagged, o->chassis_nodes,
+      (unsigned long long*)o->chassis_sum, o->rack_flagged, o->rack_nodes,
+      (unsigned long long*)o->rack_sum);
+  k_topo_racks<<<1, 1024, 0, L.stream>>>(nr, o->rack_flagged, o->flagged_racks, status + 1);
+  L.count(3);
+  u32 nf = 0;
+  TRY(copy(c, &nf, status + 1, 4));
+  TRY(sync_check(c, "ta_topology_finalize"));
+  o->n_flagged_racks = nf;
+  return TA_OK;
+}
+
+ta_status ta_shard_speedup_bounds(ta_experiment* e, uint64_t* bounds) {
+  if (!e || !bounds) return fail(TA_ERR_INVALID_ARG, "ta_shard_speedup_bounds: NULL argument");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  u64* meta;  // [0] istar, [1] sum n_iter, [2] max span
+  TRY(tmp.get_n(4, &meta, "speedup meta"));
+  cudaMemsetAsync(meta, 0, 32, c->stream);
+  cudaMemsetAsync(meta, 0xFF, 4, c->stream);
+  k_sp_istar<<<blocks(e->R), 256, 0, L.stream>>>(nullptr, e->R, e->n_iter, e->span, (u32*)meta,
+                                                 (unsigned long long*)meta + 1,
+                                                 (unsigned long long*)meta + 2);
+  L.count();
+  u64 h[3];
+  TRY(copy(c, h, meta, sizeof h));
+  TRY(sync_check(c, "ta_shard_speedup_bounds"));
+  bounds[0] = (u32)h[0];
+  bounds[1] = h[1];
+  bounds[2] = h[2];
+  return TA_OK;
+}
+
+ta_status ta_shard_speedup_partials(ta_experiment* e, const uint32_t* ctxs, uint32_t nk,
+                                    uint32_t i_star, const ta_shard_speedup_parts* o) {
+  if (!e || !ctxs || nk == 0 || !o || !o->cells || !o->cell_max || !o->within)
+    return fail(TA_ERR_INVALID_ARG, "ta_shard_speedup_partials: NULL argument");
+  ta_ctx* c = e->ctx;
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  PhaseTimer call_timer(c, &c->prof.speedup_ms);
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  u32* status;
+  TRY(tmp.get_n(1, &status, "status"));
+  TRY(check_subset(c, L, ctxs, nk, e->C, status, "ctx set"));
+  cudaMemsetAsync(status, 0, 4, c->stream);
+  {  // every rank of the shard must hold i_star iterations
+    u64 b[3];
+    TRY(ta_shard_speedup_bounds(e, b));
+    if (b[0] < i_star)
+      return fail(TA_ERR_INVALID_ARG, "i_star = %u above the shard's fewest iterations %llu",
+                  i_star, (unsigned long long)b[0]);
+  }
+  SpeedupParts sp;
+  TRY(speedup_parts(e, tmp, L, nullptr, e->R, ctxs, nk, i_star, status, sp));
+  const u64 ncell = (u64)i_star * nk;
+  if (ncell) {
+    k_cells_export<<<blocks(ncell), 256, 0, L.stream>>>(ncell, sp.gs, sp.gl, sp.gh, o->cells);
+    L.count();
+    cudaMemcpyAsync(o->cell_max, sp.gm, ncell * 8, cudaMemcpyDeviceToDevice, c->stream);
+  }
+  cudaMemcpyAsync(o->within, sp.wsum, (size_t)nk * 8, cudaMemcpyDeviceToDevice, c->stream);
+  u32 f = 0;
+  TRY(copy(c, &f, status, 4));
+  TRY(sync_check(c, "ta_shard_speedup_partials"));
+  return status_from_flags(f, "ta_shard_speedup_partials");
+}
+
+ta_status ta_speedup_finalize(ta_ctx* c, uint32_t nk, uint32_t n_total, uint32_t i_star,
+                              uint64_t excluded, uint64_t t_app,
+                              const ta_shard_speedup_parts* mg, ta_speedup_ctx* per,
+                              ta_speedup_total* tot) {
+  if (!c || nk == 0 || n_total == 0 || !mg || !mg->cells || !mg->cell_max || !mg->within || !per ||
+      !tot)
+    return fail(TA_ERR_INVALID_ARG, "ta_speedup_finalize: NULL argument");
+  cudaSetDevice(c->device);
+  Launch L{c->stream, c->num_sms, &c->launches};
+  ShardCall call(c);
+  Pool& tmp = call.tmp;
+  const u64 ncell = std::max<u64>(1, (u64)i_star * nk);
+  u64 *gs, *gl, *gh;
+  TRY(tmp.get_n(ncell, &gs, "cells"));
+  TRY(tmp.get_n(ncell, &gl, "cells"));
+  TRY(tmp.get_n(ncell, &gh, "cells"));
+  if (i_star) {
+    k_cells_import<<<blocks(ncell), 256, 0, L.stream>>>((u64)i_star * nk, mg->cells, gs, gl, gh);
+    L.count();
+  }
+  k_sp_final_k<<<(unsigned)((nk + 3) / 4), 128, 0, L.stream>>>(nk, n_total, i_star, gs,
+                                                                  mg->cell_max, gl, gh,
+                                                                  mg->within, per);
+  k_sp_total<<<1, 1, 0, L.stream>>>(nk, n_total, i_star, excluded, t_app, per, tot);
+  L.count(2);
+  return sync_check(c, "ta_speedup_finalize");
+}
+
+}  // extern "C"
 
 // ---------------------------------------------------------------------------
 // Statistics of every context of every set of a batch (set-aware kernels).
@@ -1562,7 +2019,7 @@ void launch_batch_stats(const Launch& L, u32 R, u32 Ctot, const u64* off, const 
   k_stats_finalize<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, R, nullptr, P, stats, sets);
   k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, R, off, ctx, time, nullptr, P, tau_num, tau_den,
                                         nullptr, keys, zs, std::max<u64>(cap, 1), n_out, nullptr,
-                                        sets);
+                                        sets, 0);
   k_stats_argmax<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, P.argmax, stats, sets);
   L.count(4);
 }

@@ -24,6 +24,9 @@ STRUCTS = {"ta_trace_desc": ta.TraceDesc, "ta_experiment_info": ta.ExperimentInf
            "ta_profile": ta.Profile, "ta_batch_args": ta.BatchArgs,
            "ta_batch_info": ta.BatchInfo, "ta_batch_set_view": ta.BatchSetView,
            "ta_batch_set_args": ta.BatchSetArgs,
+           "ta_shard_stats_parts": ta.ShardStatsParts, "ta_shard_merged": ta.ShardMerged,
+           "ta_shard_stats_out": ta.ShardStatsOut,
+           "ta_shard_speedup_parts": ta.ShardSpeedupParts,
            "ta_serve_config": ta.ServeConfig, "ta_query": ta.Query,
            "ta_query_result": ta.QueryResult, "ta_q_stats": ta.QStats,
            "ta_q_topk_entry": ta.QTopkEntry, "ta_q_racks": ta.QRacks}
