@@ -598,7 +598,12 @@ def run_batched(args, ctx, local):
                        "clocks": batch_clk,
                        "plan_s": plan_s, "hbm_gbs_tensor_floor": alg / (batch_ms / 1e3) / 1e9},
            "speedup_batched_over_plain": plain_ms / batch_ms,
-           "device_bytes_batch": info["device_bytes"]}
+           "device_bytes_batch": info["device_bytes"],
+           "tuned": {"tile_width": info["tile_width"], "count_warps": info["count_warps"],
+                     "count_grid": info["count_grid"], "write_warps": info["write_warps"],
+                     "write_grid": info["write_grid"], "trials": info["tune_trials"]}}
+    out["batched"]["hbm_frac_tensor_floor"] = (out["batched"]["hbm_gbs_tensor_floor"]
+                                               / measured_peaks()[0]["hbm_gbs"])
     b.free()
     del arena, sets
     torch.cuda.empty_cache()
@@ -885,6 +890,7 @@ def block_summaries(d):
                           "launches_per_step": b["batched"]["gpu_launches_per_step"],
                           "plain_launches_per_step": b["plain"]["gpu_launches_per_step"],
                           "hbm_gbs_tensor_floor": b["batched"]["hbm_gbs_tensor_floor"],
+                          "hbm_frac_tensor_floor": b["batched"].get("hbm_frac_tensor_floor"),
                           "tuned": b.get("tuned")}
     sv = d.get("serving")
     if sv:

@@ -827,9 +827,10 @@ typedef struct ta_batch_info {
   uint64_t graph_kernels; /* kernel nodes among them                  */
   uint64_t device_bytes; /* arena owned by the batch                 */
   /* launch shape the autotuner chose for the tensor passes: warps per CTA
-     and CTAs (count pass, write pass); trials run and their total time */
+     and CTAs (count pass, write pass); trials run, the tile width (samples
+     per tile: 4096 or 2048) and their total time */
   uint32_t count_warps, count_grid, write_warps, write_grid;
-  uint32_t tune_trials, reserved;
+  uint32_t tune_trials, tile_width;
   double tune_ms;
 } ta_batch_info;
 typedef struct ta_batch_set_view {

@@ -161,7 +161,7 @@ class BatchInfo(C.Structure):
                 ("tensor_nnz", u64), ("excl_nnz", u64), ("incl_nnz", u64), ("n_outliers", u64),
                 ("graph_nodes", u64), ("graph_kernels", u64), ("device_bytes", u64),
                 ("count_warps", u32), ("count_grid", u32), ("write_warps", u32),
-                ("write_grid", u32), ("tune_trials", u32), ("reserved", u32),
+                ("write_grid", u32), ("tune_trials", u32), ("tile_width", u32),
                 ("tune_ms", C.c_double)]
 
 

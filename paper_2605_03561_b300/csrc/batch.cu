@@ -101,6 +101,9 @@ struct ta_batch {
   TensorShape shape{};
   u32 tune_trials = 0;
   double tune_ms = 0.0;
+  u64 n_tiles_max = 0;       // tiles at the narrowest width (sizes the tile arrays)
+  u32* d_tile_set = nullptr; // the set map's tile arrays, rewritten per tile width
+  u64* d_tile0 = nullptr;
   RankCsrArgs X[2]{};
   RankCsrPlan XP{};
   u64* meta = nullptr;   // [0] status, [1..2] tensor totals, [3] excl total, [4] incl total,
@@ -242,7 +245,7 @@ ta_status check_flags(ta_batch* b, const char* where) {
 // Repeated runs write the same results (the passes are deterministic).
 constexpr int kTuneWarps[] = {4, 8, 16};
 
-ta_status tune_tensor(ta_batch* b, bool write) {
+ta_status tune_tensor(ta_batch* b, bool write, float* best_ms = nullptr) {
   ta_ctx* c = b->ctx;
   const Launch L = launch_of(b);
   cudaEvent_t e0, e1;
@@ -284,6 +287,32 @@ ta_status tune_tensor(ta_batch* b, bool write) {
   TRY(sync_check(c, "batch: tuning"));
   b->shape = pick;
   b->TP = plan_tensor(b->Cmax, b->N, c->num_sms, b->shape);
+  if (best_ms) *best_ms = best;
+  return TA_OK;
+}
+
+// Tile widths the autotuner tries (samples per tile).
+constexpr int kTuneTiles[] = {4096, 2048};
+
+// The set layout's tiles at width tw: every set's first tile (host and
+// device) and every tile's set; tiles never span two sets.
+ta_status set_tiles(ta_batch* b, int tw) {
+  ta_ctx* c = b->ctx;
+  const u32 S = b->S;
+  b->h_tile0.assign(S + 1, 0);
+  for (u32 s = 0; s < S; ++s) {
+    const u64 n = b->h_rec_end[s] - b->h_rec0[s];
+    b->h_tile0[s + 1] = b->h_tile0[s] + std::max<u64>(1, (n + tw - 1) / tw);
+  }
+  b->n_tiles = b->h_tile0[S];
+  if (b->n_tiles > b->n_tiles_max) return fail(TA_ERR_STATE, "batch: tile map");
+  std::vector<u32> tile_set(b->n_tiles);
+  for (u32 s = 0; s < S; ++s)
+    for (u64 t = b->h_tile0[s]; t < b->h_tile0[s + 1]; ++t) tile_set[t] = s;
+  TRY(copy(c, b->d_tile_set, tile_set.data(), tile_set.size() * 4));
+  TRY(copy(c, b->d_tile0, b->h_tile0.data(), (S + 1) * 8));
+  TRY(sync_check(c, "batch: tile map"));
+  b->T.n_tiles = b->n_tiles;
   return TA_OK;
 }
 
@@ -506,8 +535,6 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   b->h_ctx0.assign(S + 1, 0);
   b->h_C.resize(S);
   b->h_m.resize(S);
-  b->TP = plan_tensor(1, 1, c->num_sms);  // for the tile size
-  const u64 TWt = (u64)b->TP.tile;
   for (u32 s = 0; s < S; ++s) {
     const ta_trace_desc& d = sets[s];
     if (d.n_ranks == 0 || d.n_ctx == 0 || d.marker_ctx >= d.n_ctx || !d.rank_off || !d.parent ||
@@ -519,7 +546,7 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
     b->h_rec_end[s] = b->h_rec0[s] + d.n_records;
     b->h_rec0[s + 1] = (b->h_rec_end[s] + SET_ALIGN - 1) / SET_ALIGN * SET_ALIGN;
     b->n_samples += d.n_records;
-    b->h_tile0[s + 1] = b->h_tile0[s] + std::max<u64>(1, (d.n_records + TWt - 1) / TWt);
+    b->n_tiles_max += std::max<u64>(1, (d.n_records + 2047) / 2048);
     if ((u64)b->h_rank0[s] + d.n_ranks >= 0xFFFFFFFFull)
       return fail(TA_ERR_INVALID_ARG, "batch: too many ranks");
     b->h_rank0[s + 1] = b->h_rank0[s] + d.n_ranks;
@@ -533,7 +560,6 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   b->N = b->h_rec0[S];
   b->R = b->h_rank0[S];
   b->Ctot = b->h_ctx0[S];
-  b->n_tiles = b->h_tile0[S];
   // ---- inputs ---------------------------------------------------------------
   TRY(b->own_n((u64)b->R + 1, &b->rank_off, "rank_off"));
   TRY(b->own_n(b->N, &b->ts, "ts"));
@@ -561,38 +587,34 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   ro[b->R] = b->N;
   TRY(copy(c, b->rank_off, ro.data(), ro.size() * 8));
   // ---- set map on the device ------------------------------------------------
-  std::vector<u32> tile_set(b->n_tiles), rank_set(b->R);
-  for (u32 s = 0; s < S; ++s) {
-    for (u64 t = b->h_tile0[s]; t < b->h_tile0[s + 1]; ++t) tile_set[t] = s;
+  std::vector<u32> rank_set(b->R);
+  for (u32 s = 0; s < S; ++s)
     for (u32 r = b->h_rank0[s]; r < b->h_rank0[s + 1]; ++r) rank_set[r] = s;
-  }
-  u32 *d_tile_set, *d_rank_set, *d_rank0, *d_ctx0, *d_C, *d_m;
-  u64 *d_tile0, *d_rec0, *d_rec_end;
-  TRY(b->own_n(b->n_tiles, &d_tile_set, "set map"));
+  u32 *d_rank_set, *d_rank0, *d_ctx0, *d_C, *d_m;
+  u64 *d_rec0, *d_rec_end;
+  TRY(b->own_n(b->n_tiles_max, &b->d_tile_set, "set map"));
   TRY(b->own_n(b->R, &d_rank_set, "set map"));
   TRY(b->own_n(S + 1, &d_rank0, "set map"));
   TRY(b->own_n(S + 1, &d_ctx0, "set map"));
   TRY(b->own_n(S, &d_C, "set map"));
   TRY(b->own_n(S, &d_m, "set map"));
-  TRY(b->own_n(S + 1, &d_tile0, "set map"));
+  TRY(b->own_n(S + 1, &b->d_tile0, "set map"));
   TRY(b->own_n(S + 1, &d_rec0, "set map"));
   TRY(b->own_n(S, &d_rec_end, "set map"));
   TRY(b->own_n(S + 1, &b->d_rank0_64, "set map"));
-  TRY(copy(c, d_tile_set, tile_set.data(), tile_set.size() * 4));
   TRY(copy(c, d_rank_set, rank_set.data(), rank_set.size() * 4));
   TRY(copy(c, d_rank0, b->h_rank0.data(), (S + 1) * 4));
   TRY(copy(c, d_ctx0, b->h_ctx0.data(), (S + 1) * 4));
   TRY(copy(c, d_C, b->h_C.data(), S * 4));
   TRY(copy(c, d_m, b->h_m.data(), S * 4));
-  TRY(copy(c, d_tile0, b->h_tile0.data(), (S + 1) * 8));
   TRY(copy(c, d_rec0, b->h_rec0.data(), (S + 1) * 8));
   TRY(copy(c, d_rec_end, b->h_rec_end.data(), S * 8));
   std::vector<u64> rank0_64(b->h_rank0.begin(), b->h_rank0.end());
   TRY(copy(c, b->d_rank0_64, rank0_64.data(), (S + 1) * 8));
   TRY(sync_check(c, "batch: upload"));
   b->sets.S = S;
-  b->sets.tile_set = d_tile_set;
-  b->sets.set_tile0 = d_tile0;
+  b->sets.tile_set = b->d_tile_set;
+  b->sets.set_tile0 = b->d_tile0;
   b->sets.set_rec0 = d_rec0;
   b->sets.set_rec_end = d_rec_end;
   b->sets.set_rank0 = d_rank0;
@@ -610,11 +632,13 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(b->own_n((u64)b->R + 1, &b->row_off, "row_off_of_rank"));
   enqueue_validate(b);
   TRY(check_flags(b, "ta_batch_plan"));
-  // tensor: count, size, write
+  // tensor: count, size, write -- tile width and launch shapes tuned on the
+  // batch's own data (every width: its layout, the count pass's shapes, one
+  // count, the write pass's shapes; the fastest width with its shapes wins)
   b->TP = plan_tensor(b->Cmax, b->N, c->num_sms);
   TensorArgs& A = b->T;
   std::memset(&A, 0, sizeof A);
-  const u64 nt = b->n_tiles;
+  const u64 nt = b->n_tiles_max;
   TRY(b->own_n(nt + 1, (u32**)&A.tfr, "tile map"));
   TRY(b->own_n(nt, &A.tile_rows, "tile rows"));
   TRY(b->own_n(nt, &A.tile_ents, "tile entries"));
@@ -623,12 +647,13 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   TRY(b->own_n(2 * scan_scratch_elems(nt), &A.scan_scratch, "tile scan"));
   // per-warp scratch for the widest launch shape the autotuner may try
   u64 max_warps = 0, max_write_warps = 0;
-  for (int nw : kTuneWarps) {
-    max_warps = std::max<u64>(max_warps, (u64)c->num_sms * nw *
-                                             tensor_max_per_sm(b->Cmax, false, nw));
-    max_write_warps = std::max<u64>(max_write_warps, (u64)c->num_sms * nw *
-                                                         tensor_max_per_sm(b->Cmax, true, nw));
-  }
+  for (int tw : kTuneTiles)
+    for (int nw : kTuneWarps) {
+      max_warps = std::max<u64>(max_warps, (u64)c->num_sms * nw *
+                                               tensor_max_per_sm(b->Cmax, false, nw, tw));
+      max_write_warps = std::max<u64>(
+          max_write_warps, (u64)c->num_sms * nw * tensor_max_per_sm(b->Cmax, true, nw, tw));
+    }
   max_warps = std::max(max_warps, max_write_warps);
   if (!b->TP.bm_in_smem) {
     const u64 words = max_warps * bm_words(b->Cmax);
@@ -645,35 +670,58 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
   A.R = b->R;
   A.C = b->Cmax;
   A.m = 0;
-  A.n_tiles = nt;
   A.N = b->N;
   A.status = (u32*)b->meta;
   A.totals = b->meta + 1;
   A.gst_cap = b->TP.gst_cap;
   A.bm_in_smem = b->TP.bm_in_smem ? 1u : 0u;
   A.sets = b->sets;
-  launch_tile_first_rank(L, b->rank_off, b->R, b->TP.tile, (u32)b->n_tiles, (u32*)A.tfr, b->sets);
-  TRY(tune_tensor(b, false));
-  enqueue_tensor_count(b);
-  u64 h[3];
-  TRY(copy(c, h, b->meta, sizeof h));
-  TRY(sync_check(c, "batch: tensor count"));
-  TRY(status_from_flags((u32)h[0], "ta_batch_plan"));
-  b->rows = h[1];
-  b->slots = h[2];
-  TRY(b->own_n(b->rows + 1, &b->entry_off, "entry_off"));
-  TRY(b->own_n(b->slots, &b->e_ctx, "e_ctx"));
-  TRY(b->own_n(b->slots, &b->e_time, "e_time"));
-  TRY(b->own_n(b->slots, &b->e_cnt, "e_cnt"));
-  TRY(b->own_n(b->rows, &A.row_nnz, "row entries"));
   TRY(b->own_n(1, &A.nnz_sum, "tensor entries"));
-  A.row_off_of_rank = b->row_off;
-  A.entry_off = b->entry_off;
-  A.e_ctx = b->e_ctx;
-  A.e_time = b->e_time;
-  A.e_cnt = b->e_cnt;
-  k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
-  TRY(tune_tensor(b, true));
+  float best_total = 3.4e38f;
+  TensorShape best_shape = b->shape;
+  bool sized = false;
+  for (int tw : kTuneTiles) {
+    TRY(set_tiles(b, tw));
+    b->shape.tile = tw;
+    b->TP = plan_tensor(b->Cmax, b->N, c->num_sms, b->shape);
+    launch_tile_first_rank(L, b->rank_off, b->R, tw, (u32)b->n_tiles, (u32*)A.tfr, b->sets);
+    float t_count = 0.f, t_write = 0.f;
+    TRY(tune_tensor(b, false, &t_count));
+    enqueue_tensor_count(b);
+    u64 h[3];
+    TRY(copy(c, h, b->meta, sizeof h));
+    TRY(sync_check(c, "batch: tensor count"));
+    TRY(status_from_flags((u32)h[0], "ta_batch_plan"));
+    if (!sized) {  // rows and slots do not depend on the tile width
+      b->rows = h[1];
+      b->slots = h[2];
+      TRY(b->own_n(b->rows + 1, &b->entry_off, "entry_off"));
+      TRY(b->own_n(b->slots, &b->e_ctx, "e_ctx"));
+      TRY(b->own_n(b->slots, &b->e_time, "e_time"));
+      TRY(b->own_n(b->slots, &b->e_cnt, "e_cnt"));
+      TRY(b->own_n(b->rows, &A.row_nnz, "row entries"));
+      A.row_off_of_rank = b->row_off;
+      A.entry_off = b->entry_off;
+      A.e_ctx = b->e_ctx;
+      A.e_time = b->e_time;
+      A.e_cnt = b->e_cnt;
+      sized = true;
+    } else if (h[1] != b->rows || h[2] != b->slots) {
+      return fail(TA_ERR_STATE, "batch: tile widths disagree on the tensor's size");
+    }
+    k_put_u64<<<1, 1, 0, L.stream>>>(b->row_off + b->R, b->rows);
+    TRY(tune_tensor(b, true, &t_write));
+    if (t_count + t_write < best_total) {
+      best_total = t_count + t_write;
+      best_shape = b->shape;
+    }
+  }
+  // the chosen width's layout and offsets, then the plan's first write
+  b->shape = best_shape;
+  TRY(set_tiles(b, b->shape.tile));
+  b->TP = plan_tensor(b->Cmax, b->N, c->num_sms, b->shape);
+  enqueue_tensor_count(b);
+  TRY(check_flags(b, "ta_batch_plan"));
   enqueue_tensor_write(b);
   TRY(check_flags(b, "ta_batch_plan"));
   TRY(copy(c, &b->nnz, A.nnz_sum, 8));
@@ -966,6 +1014,7 @@ ta_status ta_batch_get_info(const ta_batch* b, ta_batch_info* i) {
   i->write_warps = (u32)b->TP.nw_write;
   i->write_grid = (u32)b->TP.grid_write;
   i->tune_trials = b->tune_trials;
+  i->tile_width = (u32)b->TP.tile;
   i->tune_ms = b->tune_ms;
   i->device_bytes = b->device_bytes;
   return TA_OK;

@@ -81,10 +81,12 @@ struct TensorArgs {
   SetMap sets;
 };
 
-// Launch shape of the two tensor passes: warps per CTA (4, 8 or 16) and CTAs
-// per SM (0 = as many as fit), chosen separately for the count and the
-// write pass (the batched form tunes them on its data).
+// Launch shape of the two tensor passes: the tile width (samples per tile:
+// 4096, or 2048), warps per CTA (4, 8 or 16) and CTAs per SM (0 = as many as
+// fit), the latter two chosen separately for the count and the write pass
+// (the batched form tunes all of them on its data).
 struct TensorShape {
+  int tile = 4096;
   int nw_count = 8, per_sm_count = 0, nw_write = 8, per_sm_write = 0;
 };
 struct TensorPlan {
@@ -100,7 +102,7 @@ struct TensorPlan {
 };
 TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape = TensorShape{});
 // CTAs of a pass that fit on one SM (occupancy) for warps per CTA nw.
-int tensor_max_per_sm(u32 C, bool write, int nw);
+int tensor_max_per_sm(u32 C, bool write, int nw, int tile = 4096);
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A);
 void launch_tile_scan(const Launch& L, const TensorArgs& A);
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A);

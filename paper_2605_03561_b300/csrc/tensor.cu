@@ -29,8 +29,14 @@
 namespace ta {
 namespace {
 
-constexpr u32 TW = 4096;            // samples per tile
-constexpr u32 MASKW = TW / 32 + 4;  // rank-start mask words (positions 0 .. TW)
+// Tile widths (samples per tile) the passes are built for: 4096 by default,
+// 2048 for the batched form's autotuner.  Rank-start mask words cover
+// positions 0 .. TW.
+constexpr u32 TW_DEFAULT = 4096;
+template <u32 TW>
+struct TileW {
+  static constexpr u32 MASKW = TW / 32 + 4;
+};
 constexpr u32 STEP = 128;           // samples per warp step (4 per lane)
 constexpr int DEPTH_COUNT = 2;      // steps in flight, count pass (256 samples each)
 constexpr int DEPTH_WRITE = 1;      // steps in flight in registers, write pass (timestamps too)
@@ -46,9 +52,10 @@ struct Head {  // one run head: 16 bytes, one vector store
   u32 pos;  // offset from the tile start
 };
 
+template <u32 TW>
 struct WriteSmem {
   static constexpr u32 mask_off = 0;                      // u32[MASKW]
-  static constexpr u32 tl_off = 4 * MASKW;                // u32[TL + 4] touched words, count
+  static constexpr u32 tl_off = 4 * TileW<TW>::MASKW;     // u32[TL + 4] touched words, count
   static constexpr u32 time_off = tl_off + 4 * (TL + 4);  // u64[RS]
   static constexpr u32 ctx_off = time_off + 8 * RS;       // u32[RS]
   static constexpr u32 cnt_off = ctx_off + 4 * RS;        // u32[RS]
@@ -58,8 +65,9 @@ struct WriteSmem {
   static constexpr u32 ring_off = tpos_off + FAST_RUNS;   // Head[RING]
   static constexpr u32 fixed = ring_off + 16 * RING;      // bitmap words follow
 };
-static_assert(WriteSmem::time_off % 16 == 0 && WriteSmem::ring_off % 16 == 0 &&
-                  WriteSmem::fixed % 16 == 0,
+static_assert(WriteSmem<4096>::time_off % 16 == 0 && WriteSmem<4096>::ring_off % 16 == 0 &&
+                  WriteSmem<4096>::fixed % 16 == 0 && WriteSmem<2048>::time_off % 16 == 0 &&
+                  WriteSmem<2048>::ring_off % 16 == 0 && WriteSmem<2048>::fixed % 16 == 0,
               "vector alignment of the write pass's shared memory");
 
 // The tile's place in its trace set (a single experiment is one set).
@@ -69,6 +77,7 @@ struct Tile {
   bool last;
 };
 
+template <u32 TW>
 __device__ __forceinline__ Tile tile_of(const TensorArgs& A, u64 t) {
   Tile T;
   T.sbase = 0;
@@ -98,9 +107,10 @@ __device__ __forceinline__ Tile tile_of(const TensorArgs& A, u64 t) {
 
 // Rank starts of the tile as a bit mask over positions 0 .. TW; returns the
 // steps (bit s: samples s STEP .. s STEP + STEP - 1) that hold one.
-static_assert(TW == 32 * STEP, "one bit per step of a tile");
+template <u32 TW>
 __device__ __forceinline__ u32 fill_mask(const TensorArgs& A, const Tile& T, u32* mask, int lane) {
-  for (u32 i = lane; i < MASKW; i += 32) mask[i] = 0;
+  static_assert(TW <= 32 * STEP && TW % (2 * STEP) == 0, "one bit per step of a tile");
+  for (u32 i = lane; i < TileW<TW>::MASKW; i += 32) mask[i] = 0;
   __syncwarp();
   u32 steps = 0;
   for (u32 r = T.lo + lane; r < T.hi; r += 32) {
@@ -219,17 +229,17 @@ __device__ __forceinline__ u32 from_mask8(u32 f, int lane) {
   return s <= 0 ? 0xFFu : (s >= (int)KC ? 0u : (0xFFu << s) & 0xFFu);
 }
 
-template <int NW>
+template <int NW, u32 TW>
 __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
   constexpr int D = DEPTH_COUNT;
-  __shared__ u32 masks[NW][MASKW];
+  __shared__ u32 masks[NW][TileW<TW>::MASKW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   u32* mask = masks[warp];
   const u64 gw = (u64)blockIdx.x * NW + warp;
   const u64 G = (u64)gridDim.x * NW;
   for (u64 t = gw; t < A.n_tiles; t += G) {
-    const Tile T = tile_of(A, t);
-    const u32 rsteps = fill_mask(A, T, mask, lane);
+    const Tile T = tile_of<TW>(A, t);
+    const u32 rsteps = fill_mask<TW>(A, T, mask, lane);
     u32 carry = (T.a > T.sbase) ? A.ctx[T.a - 1] : NONE32;
     u32 heads = 0, ms = 0, cmax = 0;
     bool open = false;  // a row of this tile has started
@@ -622,8 +632,9 @@ __device__ __forceinline__ u32 emit_row(const TensorArgs& A, const Bm& bm, const
   return nnz;
 }
 
-template <int NW, bool BMS>
+template <int NW, bool BMS, u32 TW>
 __global__ void __launch_bounds__(NW * 32) k_tensor_write(const TensorArgs A) {
+  using WriteSmem = ::ta::WriteSmem<TW>;
   constexpr int D = DEPTH_WRITE;
   extern __shared__ __align__(16) unsigned char sm[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -657,8 +668,8 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_write(const TensorArgs A) {
   u64 nnz_warp = 0;  // entries this warp wrote
   __syncwarp();
   for (u64 t = gw; t < A.n_tiles; t += G) {
-    const Tile T = tile_of(A, t);
-    const u32 rsteps = fill_mask(A, T, mask, lane);
+    const Tile T = tile_of<TW>(A, t);
+    const u32 rsteps = fill_mask<TW>(A, T, mask, lane);
     u32 carry = (T.a > T.sbase) ? A.ctx[T.a - 1] : NONE32;
     u64 tcarry = (T.a > T.sbase) ? A.ts[T.a - 1] : 0ull;  // timestamp before the step
     const u64 PR = A.tile_row_off[t], PE = A.tile_ent_off[t];
@@ -924,42 +935,53 @@ __global__ void k_compact_rows(const u64* __restrict__ slot_off, const u32* __re
 
 }  // namespace
 
-template <bool WRITE>
-static const void* tensor_kernel(int nw, bool bms) {
-  if (!WRITE) {
+template <u32 TW>
+static const void* tensor_kernel_tw(bool write, int nw, bool bms) {
+  if (!write) {
     switch (nw) {
-      case 4: return (const void*)k_tensor_count<4>;
-      case 16: return (const void*)k_tensor_count<16>;
-      default: return (const void*)k_tensor_count<8>;
+      case 4: return (const void*)k_tensor_count<4, TW>;
+      case 16: return (const void*)k_tensor_count<16, TW>;
+      default: return (const void*)k_tensor_count<8, TW>;
     }
   }
   switch (nw) {
-    case 4: return bms ? (const void*)k_tensor_write<4, true> : (const void*)k_tensor_write<4, false>;
+    case 4:
+      return bms ? (const void*)k_tensor_write<4, true, TW> : (const void*)k_tensor_write<4, false, TW>;
     case 16:
-      return bms ? (const void*)k_tensor_write<16, true> : (const void*)k_tensor_write<16, false>;
-    default: return bms ? (const void*)k_tensor_write<8, true> : (const void*)k_tensor_write<8, false>;
+      return bms ? (const void*)k_tensor_write<16, true, TW>
+                 : (const void*)k_tensor_write<16, false, TW>;
+    default:
+      return bms ? (const void*)k_tensor_write<8, true, TW> : (const void*)k_tensor_write<8, false, TW>;
   }
+}
+
+static const void* tensor_kernel(bool write, int nw, bool bms, int tile) {
+  return tile == 2048 ? tensor_kernel_tw<2048>(write, nw, bms)
+                      : tensor_kernel_tw<TW_DEFAULT>(write, nw, bms);
 }
 
 static void set_smem(const void* k, size_t smem) {
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
+// The bitmap goes to shared memory when it fits beside the default tile's
+// layout (the narrower tile's layout is smaller), so the choice does not
+// depend on the tile width.
 static bool tensor_bm_in_smem(u32 C) {
-  return WriteSmem::fixed + (size_t)bm_words(C) * 4 <= 14 * 1024;
+  return WriteSmem<TW_DEFAULT>::fixed + (size_t)bm_words(C) * 4 <= 14 * 1024;
 }
 
 // Dynamic shared memory of a pass (the count pass uses static memory only).
-static size_t tensor_smem(u32 C, bool write, int nw) {
+static size_t tensor_smem(u32 C, bool write, int nw, int tile) {
   if (!write) return 0;
   const size_t bm = tensor_bm_in_smem(C) ? (size_t)bm_words(C) * 4 : 0;
-  return (size_t)(WriteSmem::fixed + bm) * nw;
+  const size_t fixed = tile == 2048 ? WriteSmem<2048>::fixed : WriteSmem<TW_DEFAULT>::fixed;
+  return (fixed + bm) * nw;
 }
 
-int tensor_max_per_sm(u32 C, bool write, int nw) {
-  const void* k = write ? tensor_kernel<true>(nw, tensor_bm_in_smem(C))
-                        : tensor_kernel<false>(nw, false);
-  const size_t smem = tensor_smem(C, write, nw);
+int tensor_max_per_sm(u32 C, bool write, int nw, int tile) {
+  const void* k = tensor_kernel(write, nw, write && tensor_bm_in_smem(C), tile);
+  const size_t smem = tensor_smem(C, write, nw, tile);
   if (write) set_smem(k, smem);
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nw * 32, smem);
@@ -968,15 +990,15 @@ int tensor_max_per_sm(u32 C, bool write, int nw) {
 
 TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape) {
   TensorPlan P;
-  P.tile = TW;
+  P.tile = shape.tile == 2048 ? 2048 : (int)TW_DEFAULT;
   P.bm_in_smem = tensor_bm_in_smem(C);
   P.nw_count = shape.nw_count;
   P.nw_write = shape.nw_write;
-  P.smem_count = tensor_smem(C, false, P.nw_count);
-  P.smem = tensor_smem(C, true, P.nw_write);
-  const u64 n_tiles = std::max<u64>(1, (N + TW - 1) / TW);
+  P.smem_count = tensor_smem(C, false, P.nw_count, P.tile);
+  P.smem = tensor_smem(C, true, P.nw_write, P.tile);
+  const u64 n_tiles = std::max<u64>(1, (N + P.tile - 1) / P.tile);
   auto grid = [&](bool write, int nw, int per_sm) {
-    const int occ = tensor_max_per_sm(C, write, nw);
+    const int occ = tensor_max_per_sm(C, write, nw, P.tile);
     const int ps = per_sm > 0 ? std::min(per_sm, occ) : occ;
     return (int)std::max<u64>(1, std::min<u64>((u64)num_sms * ps, (n_tiles + nw - 1) / nw));
   };
@@ -988,8 +1010,8 @@ TensorPlan plan_tensor(u32 C, u64 N, int num_sms, const TensorShape& shape) {
 
 void launch_tensor_count(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
   void* args[] = {(void*)&A};
-  cudaLaunchKernel(tensor_kernel<false>(P.nw_count, false), P.grid_count, P.nw_count * 32, args,
-                   P.smem_count, L.stream);
+  cudaLaunchKernel(tensor_kernel(false, P.nw_count, false, P.tile), P.grid_count,
+                   P.nw_count * 32, args, P.smem_count, L.stream);
   L.count();
 }
 
@@ -1001,8 +1023,8 @@ void launch_tile_scan(const Launch& L, const TensorArgs& A) {
 
 void launch_tensor_write(const Launch& L, const TensorPlan& P, const TensorArgs& A) {
   void* args[] = {(void*)&A};
-  cudaLaunchKernel(tensor_kernel<true>(P.nw_write, P.bm_in_smem), P.grid_write, P.nw_write * 32,
-                   args, P.smem, L.stream);
+  cudaLaunchKernel(tensor_kernel(true, P.nw_write, P.bm_in_smem, P.tile), P.grid_write,
+                   P.nw_write * 32, args, P.smem, L.stream);
   L.count();
 }
 
