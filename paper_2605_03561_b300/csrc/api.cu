@@ -94,6 +94,30 @@ void ta::resolve_phases(ta_ctx* c) {
   c->pending.clear();
 }
 
+cudaStream_t ta::fork_aux(ta_ctx* c) {
+  if (!c->aux) {
+    if (cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (c->aux) cudaStreamDestroy(c->aux);
+      if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+      c->aux = nullptr;
+      c->fork_ev = c->join_ev = nullptr;
+      return nullptr;
+    }
+  }
+  cudaEventRecord(c->fork_ev, c->stream);
+  cudaStreamWaitEvent(c->aux, c->fork_ev, 0);
+  return c->aux;
+}
+
+void ta::join_aux(ta_ctx* c) {
+  if (!c->aux) return;
+  cudaEventRecord(c->join_ev, c->aux);
+  cudaStreamWaitEvent(c->stream, c->join_ev, 0);
+}
+
 ta_status ta::sync_check(ta_ctx* c, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(e, what);
@@ -163,6 +187,12 @@ ta_status ta_destroy(ta_ctx* c) {
   cudaStreamSynchronize(c->stream);
   resolve_phases(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->aux) {
+    cudaStreamSynchronize(c->aux);
+    cudaStreamDestroy(c->aux);
+    cudaEventDestroy(c->fork_ev);
+    cudaEventDestroy(c->join_ev);
+  }
   delete c;
   return TA_OK;
 }

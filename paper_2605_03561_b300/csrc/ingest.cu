@@ -302,19 +302,23 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
-      // the next batch's contexts are loaded before this batch is marked
+      // entries as 32-bit offsets from the rank's first (a rank holds fewer
+      // than 2^32 samples, so fewer entries); the next batch's contexts are
+      // loaded before this batch is marked
+      const u32* const cx = A.in_ctx + E0;
+      const u32 ne = (u32)(E1 - E0);
       u32 c[RU];
 #pragma unroll
       for (int u = 0; u < RU; ++u) {
-        const u64 j = E0 + 32 * u + lane;
-        c[u] = j < E1 ? A.in_ctx[j] : NONE32;
+        const u32 j = 32 * u + lane;
+        c[u] = j < ne ? cx[j] : NONE32;
       }
-      for (u64 j0 = E0; j0 < E1; j0 += 32 * RU) {
+      for (u32 j0 = 0; j0 < ne; j0 += 32 * RU) {
         u32 cn[RU];
 #pragma unroll
         for (int u = 0; u < RU; ++u) {
-          const u64 j = j0 + 32 * RU + 32 * u + lane;
-          cn[u] = j < E1 ? A.in_ctx[j] : NONE32;
+          const u32 j = j0 + 32 * RU + 32 * u + lane;
+          cn[u] = j < ne ? cx[j] : NONE32;
         }
 #pragma unroll
         for (int u = 0; u < RU; ++u)
@@ -379,20 +383,24 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       // two batches of RA entries per lane: the next is loaded while this
       // one is added
       constexpr int RA = RU / 2;
+      const u32* const cx = A.in_ctx + E0;
+      const u64* const tx = A.in_time + E0;
+      const u32* const nx = A.in_cnt + E0;
+      const u32 ne = (u32)(E1 - E0);
       u32 c[RA], n[RA];
       u64 t[RA];
-      auto load = [&](u64 j0, u32* cc, u64* tt, u32* nn) {
+      auto load = [&](u32 j0, u32* cc, u64* tt, u32* nn) {
 #pragma unroll
         for (int u = 0; u < RA; ++u) {
-          const u64 j = j0 + 32 * u + lane;
-          const bool ok = j < E1;
-          cc[u] = ok ? A.in_ctx[j] : NONE32;
-          tt[u] = ok ? A.in_time[j] : 0ull;
-          nn[u] = ok ? A.in_cnt[j] : 0u;
+          const u32 j = j0 + 32 * u + lane;
+          const bool ok = j < ne;
+          cc[u] = ok ? cx[j] : NONE32;
+          tt[u] = ok ? tx[j] : 0ull;
+          nn[u] = ok ? nx[j] : 0u;
         }
       };
-      load(E0, c, t, n);
-      for (u64 j0 = E0; j0 < E1; j0 += 32 * RA) {
+      load(0, c, t, n);
+      for (u32 j0 = 0; j0 < ne; j0 += 32 * RA) {
         u32 cn[RA], nn[RA];
         u64 tn[RA];
         load(j0 + 32 * RA, cn, tn, nn);
@@ -400,7 +408,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         for (int u = 0; u < RA; ++u) {
           if (c[u] == NONE32) continue;
           const u32 k = bm_rank(bm, c[u]);
-          atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t[u]);
+          atomic_add_u64_lo32((unsigned long long*)&st.time[k], (u64)t[u]);
           atomicAdd(&st.cnt[k], n[u]);
           st.ctx[k] = c[u];
         }
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
           for (int u = 0; u < 4; ++u) {
             if (a[u] == NONE32) continue;
             const u32 k = bm_rank(bm, a[u]);
-            atomicAdd((unsigned long long*)&st.time[k], (unsigned long long)t);
+            atomic_add_u64_lo32((unsigned long long*)&st.time[k], (u64)t);
             atomicAdd(&st.cnt[k], n);
             st.ctx[k] = a[u];
           }
@@ -480,7 +488,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
           for (u32 i = b0 + lane; i < b1; i += 32) {
             const u32 k = order[i];
             const u32 kp = st.par[k];
-            atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
+            atomic_add_u64_lo32((unsigned long long*)&st.time[kp], (u64)vld(&st.time[k]));
             atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
           }
           __syncwarp();
@@ -490,7 +498,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
           for (u32 k = lane; k < nnz; k += 32) {
             if (st.dep[k] == d) {
               const u32 kp = st.par[k];
-              atomicAdd((unsigned long long*)&st.time[kp], (unsigned long long)vld(&st.time[k]));
+              atomic_add_u64_lo32((unsigned long long*)&st.time[kp], (u64)vld(&st.time[k]));
               atomicAdd(&st.cnt[kp], vld(&st.cnt[k]));
             }
           }

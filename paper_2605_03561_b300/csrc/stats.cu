@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(SP_NW * 32)
       for (u32 u = 0; u < SP_U; ++u) {
         const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
         if (kk == NONE32) continue;
-        atomicAdd(&my_sum[kk], (unsigned long long)t[u]);
+        atomic_add_u64_lo32(&my_sum[kk], t[u]);
         atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t[u] * t[u]);
       }
 #pragma unroll
@@ -1027,8 +1027,12 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
     const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + SP_NW - 1) / SP_NW)));
     if (map_smem)
       cudaFuncSetAttribute(k_sp_within, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_smem);
+    // the within-rank terms and the cells read the same rows independently:
+    // the former runs on the auxiliary stream beside the latter
+    cudaStream_t ws = fork_aux(c);
+    if (!ws) ws = L.stream;
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
-      k_sp_within<<<grid, SP_NW * 32, map_smem, L.stream>>>(
+      k_sp_within<<<grid, SP_NW * 32, map_smem, ws>>>(
           dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
           std::min(SP_KC, nk - k0), I, cvw);
       L.count();
@@ -1048,6 +1052,7 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
         dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
         group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
     L.count();
+    if (ws != L.stream) join_aux(c);
   }
   double* cvw2;
   double*& wsum = sp.wsum;

@@ -25,6 +25,10 @@ struct ta_ctx {
   };
   std::vector<cudaEvent_t> ev_pool;
   std::vector<PendingPhase> pending;
+  // a second stream for independent kernels of one call (created on first
+  // use), forked from and joined back to `stream` by events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 };
 
 namespace ta {
@@ -55,6 +59,11 @@ struct Pool {
 };
 
 ta_status fail(ta_status s, const char* fmt, ...);
+// The context's auxiliary stream, made to wait for the work queued so far on
+// its stream; null if it could not be created (then use the stream alone).
+cudaStream_t fork_aux(ta_ctx* c);
+// The context's stream waits for the work queued so far on the auxiliary one.
+void join_aux(ta_ctx* c);
 ta_status cuda_fail(cudaError_t e, const char* what);
 void* dalloc(ta_ctx* c, size_t bytes);
 void dfree(ta_ctx* c, void* p, size_t bytes);

@@ -466,6 +466,18 @@ __device__ __forceinline__ bool is_outlier(long long D, u64 n, u128 M, u32 tn, u
 }
 
 // 128-bit accumulator updated with two 64-bit atomics (exact, any order).
+// Adds v to the 64-bit word at p with 32-bit atomics: the low half's old
+// value tells whether it wrapped, and the high half is touched only for a
+// high part or a carry (rare for durations below 2^32 ns).  Exact in any
+// order; the word is read only after every add (shared or global memory).
+__device__ __forceinline__ void atomic_add_u64_lo32(unsigned long long* p, u64 v) {
+  u32* w = reinterpret_cast<u32*>(p);
+  const u32 lo = (u32)v, hi = (u32)(v >> 32);
+  const u32 old = atomicAdd(&w[0], lo);
+  const u32 up = hi + ((u32)(old + lo) < old ? 1u : 0u);
+  if (up) atomicAdd(&w[1], up);
+}
+
 __device__ __forceinline__ void atomic_add_u128(u64* lo, u64* hi, u128 v) {
   const u64 vlo = (u64)v, vhi = (u64)(v >> 64);
   const u64 old = atomicAdd((unsigned long long*)lo, (unsigned long long)vlo);
