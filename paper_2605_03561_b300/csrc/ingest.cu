@@ -294,10 +294,30 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     gs.par = A.gst_par + gbase;
   }
   __syncwarp();
+  // inclusive through ancestor lists: a rank whose exclusive contexts equal
+  // the warp's previous rank's (ranks of one program mostly call the same)
+  // keeps that rank's closure bitmap and prefix counts
+  u64 pE0 = 0, pE1 = 0;
+  u32 p_cbase = NONE32, p_nnz = 0;
+  bool kept = false;  // the bitmap holds the previous rank's closure
   for (u64 r = gw; r < A.R; r += G) {
     if (MODE == 0 && WRITE && A.only_over && A.out_cnt[r] <= A.xs_cap) continue;
     // context ids are local to the rank's set; tree arrays are concatenated
     const u32 cbase = A.sets.S ? A.sets.set_ctx0[A.sets.rank_set[r]] : 0u;
+    bool same = false;
+    if (MODE == 2 && kept) {
+      const u64 q0 = A.in_off[r], q1 = A.in_off[r + 1];
+      if (q1 - q0 == pE1 - pE0 && cbase == p_cbase) {
+        bool eq = true;
+        for (u64 j = lane; j < q1 - q0; j += 32) eq = eq && A.in_ctx[q0 + j] == A.in_ctx[pE0 + j];
+        same = __all_sync(FULL, eq);
+      }
+      if (!same) {
+        bm_clear_warp(bm, lane);
+        __syncwarp();
+        kept = false;
+      }
+    }
     u64 E0, E1;
     if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
@@ -339,7 +359,7 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     } else {  // the closure: every ancestor of every exclusive context
       E0 = A.in_off[r];
       E1 = A.in_off[r + 1];
-      for (u64 j = E0 + lane; j < E1; j += 32) {
+      for (u64 j = E0 + lane; j < E1 && !same; j += 32) {
         const u32 x = A.in_ctx[j];
         const u64 a1 = A.anc_off[cbase + x + 1];
         for (u64 q = A.anc_off[cbase + x]; q < a1; q += 4) {
@@ -354,13 +374,21 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     }
     __syncwarp();
     if (!WRITE) {
-      const u32 n = bm_count_warp(bm, lane);
+      const u32 n = same ? p_nnz : bm_count_warp(bm, lane);
       if (lane == 0) A.out_cnt[r] = n;
-      bm_clear_warp(bm, lane);
+      if (MODE == 2) {
+        pE0 = E0;
+        pE1 = E1;
+        p_cbase = cbase;
+        p_nnz = n;
+        kept = true;
+      } else {
+        bm_clear_warp(bm, lane);
+      }
       __syncwarp();
       continue;
     }
-    const u32 nnz = bm_prefix_warp(bm, lane);
+    const u32 nnz = same ? p_nnz : bm_prefix_warp(bm, lane);
     const bool scratch = MODE == 0 && A.xs_cap && !A.only_over;
     if (scratch) {
       if (lane == 0) {
@@ -525,9 +553,18 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     };
     if (nnz <= (MODE == 2 ? RSR2 : RSR)) run(ss);
     else run(gs);
-    bm_clear_warp(bm, lane);
+    if (MODE == 2) {
+      pE0 = E0;
+      pE1 = E1;
+      p_cbase = cbase;
+      p_nnz = nnz;
+      kept = true;
+    } else {
+      bm_clear_warp(bm, lane);
+    }
     __syncwarp();
   }
+  if (MODE == 2 && kept) bm_clear_warp(bm, lane);  // leave a global bitmap clean
 }
 
 constexpr int RANK_NW = 8;

@@ -422,7 +422,7 @@ struct StatsRun {
 // Everything of ta_context_stats on device buffers.
 ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 n,
                     const u32* dK, u32 nk, u32 tn, u32 td, u64 cap, double* z_out,
-                    uint8_t* rank_flag, StatsRun& R) {
+                    uint8_t* rank_flag, StatsRun& R, bool count_outliers = true) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const Csr* m = metric_csr(e, metric);
@@ -469,6 +469,7 @@ ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 
                                         z_out, R.keys, R.zs, kcap, n_out, rank_flag, SetMap{}, 0);
   k_stats_argmax<<<blocks(ns), 256, 0, L.stream>>>(ns, P.argmax, R.stats);
   L.count(4);
+  if (!count_outliers) return TA_OK;  // the caller needs the flags only
   u64 h = 0;
   TRY(copy(c, &h, n_out, 8));
   TRY(sync_check(c, "context statistics"));
@@ -499,11 +500,13 @@ __device__ __forceinline__ u64 csr_lookup(const u64* off, const u32* ctx, const 
 
 __global__ void k_topo_nodes(const u32* S, u32 n, const u64* off, const u32* ctx, const u64* time,
                              u32 c, const uint8_t* rank_flag, const u32* node_of_rank,
-                             u32* node_out, unsigned long long* node_sum, u32* node_ranks) {
+                             u32* node_out, unsigned long long* node_sum, u32* node_ranks,
+                             u32 nn) {
   const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const u32 r = rank_at(S, i);
   const u32 nd = node_of_rank[r];
+  if (nd >= nn) return;  // reported by k_topo_check
   const u64 x = csr_lookup(off, ctx, time, r, c);
   if (rank_flag[r]) atomicAdd(&node_out[nd], 1u);
   atomicAdd(&node_sum[nd], (unsigned long long)x);
@@ -513,12 +516,13 @@ __global__ void k_topo_nodes(const u32* S, u32 n, const u64* off, const u32* ctx
 __global__ void k_topo_up(u32 nn, const u32* node_out, const unsigned long long* node_sum,
                           u32 min_ranks, const u32* rack, const u32* chassis, uint8_t* node_flag,
                           u32* ch_flag, u32* ch_nodes, unsigned long long* ch_sum, u32* rk_flag,
-                          u32* rk_nodes, unsigned long long* rk_sum) {
+                          u32* rk_nodes, unsigned long long* rk_sum, u32 nc, u32 nr) {
   const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nn) return;
   const u32 f = node_out[i] >= min_ranks ? 1u : 0u;
   node_flag[i] = (uint8_t)f;
   const u32 ch = chassis[i], rk = rack[i];
+  if (ch >= nc || rk >= nr) return;  // reported by k_topo_check
   atomicAdd(&ch_flag[ch], f);
   atomicAdd(&ch_nodes[ch], 1u);
   atomicAdd(&ch_sum[ch], node_sum[i]);
@@ -1162,13 +1166,10 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
   TRY(tmp.get_n(1, &status, "status"));
   TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
   cudaMemsetAsync(status, 0, 4, c->stream);
+  // ids out of range are reported at the end (the kernels below skip them)
   k_topo_check<<<blocks(std::max(e->R, nn)), 256, 0, L.stream>>>(dnode, e->R, nn, drack, nr, dch,
                                                                   nc, status);
   L.count();
-  u32 hs = 0;
-  TRY(copy(c, &hs, status, 4));
-  TRY(sync_check(c, "topology check"));
-  if (hs) return fail(TA_ERR_INVALID_ARG, "topology ids out of range");
   uint8_t* rank_flag;
   TRY(tmp.get_n(e->R, &rank_flag, "rank flags"));
   cudaMemsetAsync(rank_flag, 0, e->R, c->stream);
@@ -1176,7 +1177,8 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
   TRY(tmp.get_n(1, &dk, "ctx"));
   TRY(copy(c, dk, &a->ctx, 4));
   StatsRun R;
-  TRY(stats_run(e, tmp, a->metric, dS, n, dk, 1, a->tau_num, a->tau_den, 0, nullptr, rank_flag, R));
+  TRY(stats_run(e, tmp, a->metric, dS, n, dk, 1, a->tau_num, a->tau_den, 0, nullptr, rank_flag, R,
+                false));
   // outputs on the device (staged when the caller wants host memory)
   const bool dev = o->mem_kind == TA_MEM_DEVICE;
   u32 *no, *nrk, *cf, *cn, *rf, *rn, *fr, *cnt;
@@ -1213,13 +1215,14 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
   cudaMemsetAsync(rsum, 0, (size_t)nr * 8, c->stream);
   const Csr* m = metric_csr(e, a->metric);
   k_topo_nodes<<<blocks(n), 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, a->ctx, rank_flag,
-                                                dnode, no, nsum, nrk);
+                                                dnode, no, nsum, nrk, nn);
   k_topo_up<<<blocks(nn), 256, 0, L.stream>>>(nn, no, nsum, a->min_ranks, drack, dch, nf, cf, cn,
-                                              csum, rf, rn, rsum);
+                                              csum, rf, rn, rsum, nc, nr);
   k_topo_racks<<<1, 256, 0, L.stream>>>(nr, rf, fr, cnt);
   L.count(3);
-  u32 nfr = 0;
+  u32 nfr = 0, hs = 0;
   TRY(copy(c, &nfr, cnt, 4));
+  TRY(copy(c, &hs, status, 4));
   if (!dev) {
     if (o->node_outliers) TRY(copy(c, o->node_outliers, no, (size_t)nn * 4));
     if (o->node_sum) TRY(copy(c, o->node_sum, nsum, (size_t)nn * 8));
@@ -1234,6 +1237,7 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
     if (o->flagged_racks) TRY(copy(c, o->flagged_racks, fr, (size_t)nr * 4));
   }
   TRY(sync_check(c, "ta_topology_rollup"));
+  if (hs) return fail(TA_ERR_INVALID_ARG, "topology ids out of range");
   o->n_flagged_racks = nfr;
   return TA_OK;
 }
@@ -1840,7 +1844,7 @@ ta_status ta_topology_finalize(ta_ctx* c, const uint64_t* node_parts, const ta_t
       nn, o->node_outliers, (const unsigned long long*)o->node_sum, min_ranks, t->rack_of_node,
       t->chassis_of_node, o->node_flag, o->chassis_flagged, o->chassis_nodes,
       (unsigned long long*)o->chassis_sum, o->rack_flagged, o->rack_nodes,
-      (unsigned long long*)o->rack_sum);
+      (unsigned long long*)o->rack_sum, nc, nr);
   k_topo_racks<<<1, 1024, 0, L.stream>>>(nr, o->rack_flagged, o->flagged_racks, status + 1);
   L.count(3);
   u32 nf = 0;
