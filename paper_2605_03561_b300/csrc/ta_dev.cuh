@@ -22,8 +22,6 @@ enum : u32 {
   F_INTERNAL = 64u
 };
 
-// Bound on every device-side spin: polls with a short sleep in between.
-constexpr u32 SPIN_LIMIT = 1u << 24;
 
 __device__ __forceinline__ void flag(u32* status, u32 bits) { atomicOr(status, bits); }
 
@@ -281,138 +279,6 @@ __device__ __forceinline__ u64 head_time(const u64* __restrict__ ts, u64 b, u64 
   const u64 nx = b < re ? ts[b] : ts[b - 1];
   const u64 hi = min(nx, t1);
   return hi > t0 ? hi - t0 : 0ull;
-}
-
-// ----------------------------------------------- decoupled look-back ------
-// Ordered prefix of (rows, entries) over work units claimed in increasing
-// order from an atomic counter.  A unit publishes its own aggregate, walks
-// back over its predecessors (adding aggregates until it meets an inclusive
-// prefix), then publishes its inclusive prefix.  Units are claimed by running
-// CTAs in order, so every predecessor is owned by a CTA that is running or
-// done: the walk always ends.  Each poll is bounded all the same.
-struct alignas(16) UnitStatus {
-  u32 flag;  // 0 empty, 1 aggregate, 2 inclusive
-  u32 pad;
-  u64 agg_a, agg_b, inc_a, inc_b, pad2;
-};
-
-__device__ __forceinline__ void lookback(UnitStatus* S, u32 t, u64 a, u64 b, u64* pre_a,
-                                         u64* pre_b, u32* status) {
-  if (t == 0) {
-    S[0].inc_a = a;
-    S[0].inc_b = b;
-    __threadfence();
-    st_release(&S[0].flag, 2);
-    *pre_a = 0;
-    *pre_b = 0;
-    return;
-  }
-  S[t].agg_a = a;
-  S[t].agg_b = b;
-  __threadfence();
-  st_release(&S[t].flag, 1);
-  u64 sa = 0, sb = 0;
-  long long p = (long long)t - 1;
-  u32 spins = 0;
-  while (p >= 0) {
-    const u32 f = ld_acquire(&S[p].flag);
-    if (f == 2) {
-      sa += ld_relaxed(&S[p].inc_a);
-      sb += ld_relaxed(&S[p].inc_b);
-      break;
-    }
-    if (f == 1) {
-      sa += ld_relaxed(&S[p].agg_a);
-      sb += ld_relaxed(&S[p].agg_b);
-      --p;
-      continue;
-    }
-    if (++spins > SPIN_LIMIT) {
-      flag(status, F_TIMEOUT);
-      break;
-    }
-    __nanosleep(64);
-  }
-  S[t].inc_a = sa + a;
-  S[t].inc_b = sb + b;
-  __threadfence();
-  st_release(&S[t].flag, 2);
-  *pre_a = sa;
-  *pre_b = sb;
-}
-
-// Warp-cooperative look-back: all 32 lanes call it.  Lane 0 publishes the
-// unit's aggregate; the warp then inspects 32 predecessors per memory round
-// trip (lane i looks at unit t-1-i), adds the aggregates up to the nearest
-// predecessor that has an inclusive prefix, and lane 0 publishes its own
-// inclusive prefix.  Waiting happens only while a predecessor in the window
-// has not published anything yet; every wait is bounded.
-__device__ __forceinline__ void lookback_warp(UnitStatus* S, u32 t, u64 a, u64 b, u64* pre_a,
-                                              u64* pre_b, u32* status) {
-  const int lane = threadIdx.x & 31;
-  if (t == 0) {
-    if (lane == 0) {
-      S[0].inc_a = a;
-      S[0].inc_b = b;
-      __threadfence();
-      st_release(&S[0].flag, 2);
-    }
-    *pre_a = 0;
-    *pre_b = 0;
-    __syncwarp();
-    return;
-  }
-  if (lane == 0) {
-    S[t].agg_a = a;
-    S[t].agg_b = b;
-    __threadfence();
-    st_release(&S[t].flag, 1);
-  }
-  u64 sa = 0, sb = 0;
-  long long base = (long long)t - 1;
-  u32 spins = 0;
-  for (;;) {
-    const long long idx = base - lane;
-    const u32 f = idx >= 0 ? ld_acquire(&S[idx].flag) : 2u;
-    const u32 m2 = __ballot_sync(FULL, f == 2);
-    const u32 m0 = __ballot_sync(FULL, f == 0);
-    const int first2 = m2 ? __ffs(m2) - 1 : 32;
-    const u32 below = first2 >= 32 ? FULL : ((1u << first2) - 1u);
-    if (m0 & below) {  // a nearer predecessor has not published yet
-      if (++spins > SPIN_LIMIT) {
-        if (lane == 0) flag(status, F_TIMEOUT);
-        break;
-      }
-      __nanosleep(32);
-      continue;
-    }
-    u64 va = 0, vb = 0;
-    if (lane < first2) {
-      va = ld_relaxed(&S[idx].agg_a);
-      vb = ld_relaxed(&S[idx].agg_b);
-    } else if (lane == first2 && idx >= 0) {
-      va = ld_relaxed(&S[idx].inc_a);
-      vb = ld_relaxed(&S[idx].inc_b);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      va += __shfl_xor_sync(FULL, va, o);
-      vb += __shfl_xor_sync(FULL, vb, o);
-    }
-    sa += va;
-    sb += vb;
-    if (first2 < 32) break;
-    base -= 32;
-  }
-  if (lane == 0) {
-    S[t].inc_a = sa + a;
-    S[t].inc_b = sb + b;
-    __threadfence();
-    st_release(&S[t].flag, 2);
-  }
-  *pre_a = sa;
-  *pre_b = sb;
-  __syncwarp();
 }
 
 // ------------------------------------------- exact integer -> double ------
