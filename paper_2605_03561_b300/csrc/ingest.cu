@@ -249,6 +249,72 @@ struct RStage {
   u32* par;
 };
 
+// Exclusive fast path: the iteration rows of rank r (its rows after the
+// first) as one template block.  Returns true when every such row holds the
+// first one's contexts -- rows are context-sorted, so entry p of every row is
+// then the same context -- with at most 96 of them; tc holds them and tt / tn
+// each position's time and samples summed over the rows (lane l: positions
+// l, l + 32, l + 64; four rows' loads in flight, one vote per row).  The
+// rank's first row (its prologue) is [p0, p1), left to the caller.
+constexpr u32 XT_P = 3;  // positions per lane
+constexpr u32 XT_R = 4;  // rows in flight
+__device__ __forceinline__ bool excl_template(const RankCsrArgs& A, u64 r, int lane,
+                                              u32 (&tc)[XT_P], u64 (&tt)[XT_P],
+                                              u32 (&tn)[XT_P], u64& p0, u64& p1) {
+  const u64 R0 = A.row_off_of_rank[r], R1 = A.row_off_of_rank[r + 1];
+  if (R1 < R0 + 3) return false;  // fewer than two iteration rows: nothing to gain
+  p0 = A.entry_off[R0];
+  p1 = A.entry_off[R0 + 1];
+  const u64 b0 = p1;
+  const u64 L64 = A.entry_off[R0 + 2] - b0;
+  if (L64 == 0 || L64 > 32 * XT_P) return false;
+  const u32 L = (u32)L64;
+#pragma unroll
+  for (u32 q = 0; q < XT_P; ++q) {
+    const u32 p = (u32)lane + 32 * q;
+    tc[q] = p < L ? A.in_ctx[b0 + p] : NONE32;
+    tt[q] = 0;
+    tn[q] = 0;
+  }
+  const u64 nrow = R1 - R0 - 1;
+  for (u64 j0 = 0; j0 < nrow; j0 += 32) {
+    const u32 m = (u32)(nrow - j0 < 32 ? nrow - j0 : 32);
+    // every row of the block is L entries long: row j starts at b0 + j L
+    const bool okl = (u32)lane > m ||
+                     A.entry_off[R0 + 1 + j0 + lane] == b0 + (j0 + (u32)lane) * (u64)L;
+    if (!__all_sync(FULL, okl)) return false;
+    for (u32 w0 = 0; w0 < m; w0 += XT_R) {
+      u32 c[XT_R][XT_P], n[XT_R][XT_P];
+      u64 t[XT_R][XT_P];
+#pragma unroll
+      for (u32 w = 0; w < XT_R; ++w)
+#pragma unroll
+        for (u32 q = 0; q < XT_P; ++q) {
+          const u32 p = (u32)lane + 32 * q;
+          const bool live = w0 + w < m && p < L;
+          const u64 e = b0 + (j0 + w0 + w) * (u64)L + p;
+          c[w][q] = live ? A.in_ctx[e] : tc[q];
+          t[w][q] = live ? A.in_time[e] : 0ull;
+          n[w][q] = live ? A.in_cnt[e] : 0u;
+        }
+      bool ok = true;
+#pragma unroll
+      for (u32 w = 0; w < XT_R; ++w)
+#pragma unroll
+        for (u32 q = 0; q < XT_P; ++q) ok = ok && c[w][q] == tc[q];
+      if (!__all_sync(FULL, ok)) return false;
+#pragma unroll
+      for (u32 w = 0; w < XT_R; ++w)
+#pragma unroll
+        for (u32 q = 0; q < XT_P; ++q) {
+          tt[q] += t[w][q];
+          tn[q] += n[w][q];
+        }
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 template <int NW, int MODE, bool WRITE, bool BMS>
@@ -319,7 +385,22 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       }
     }
     u64 E0, E1;
-    if (MODE == 0) {
+    // exclusive: the iteration rows as a template block when they allow it
+    u32 xtc[XT_P];
+    u64 xtt[XT_P], xp0 = 0, xp1 = 0;
+    u32 xtn[XT_P];
+    const bool tmpl = MODE == 0 && WRITE && excl_template(A, r, lane, xtc, xtt, xtn, xp0, xp1);
+    if (MODE == 0 && tmpl) {  // marks: the template's contexts and the first row's
+      E0 = A.entry_off[A.row_off_of_rank[r]];
+      E1 = A.entry_off[A.row_off_of_rank[r + 1]];
+#pragma unroll
+      for (u32 q = 0; q < XT_P; ++q)
+        if (xtc[q] != NONE32 && !bm_has(bm, xtc[q])) bm_set(bm, xtc[q]);
+      for (u64 j = xp0 + lane; j < xp1; j += 32) {
+        const u32 c = A.in_ctx[j];
+        if (!bm_has(bm, c)) bm_set(bm, c);
+      }
+    } else if (MODE == 0) {
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
       // entries as 32-bit offsets from the rank's first (a rank holds fewer
@@ -407,7 +488,23 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
       st.cnt[k] = 0;
     }
     __syncwarp();
-    if (MODE == 0) {
+    if (MODE == 0 && tmpl) {  // the template block's sums, then the first row's entries
+#pragma unroll
+      for (u32 q = 0; q < XT_P; ++q) {
+        if (xtc[q] == NONE32) continue;
+        const u32 k = bm_rank(bm, xtc[q]);
+        atomic_add_u64_lo32((unsigned long long*)&st.time[k], xtt[q]);
+        atomicAdd(&st.cnt[k], xtn[q]);
+        st.ctx[k] = xtc[q];
+      }
+      for (u64 j = xp0 + lane; j < xp1; j += 32) {
+        const u32 c = A.in_ctx[j];
+        const u32 k = bm_rank(bm, c);
+        atomic_add_u64_lo32((unsigned long long*)&st.time[k], A.in_time[j]);
+        atomicAdd(&st.cnt[k], A.in_cnt[j]);
+        st.ctx[k] = c;
+      }
+    } else if (MODE == 0) {
       // two batches of RA entries per lane: the next is loaded while this
       // one is added
       constexpr int RA = RU / 2;
