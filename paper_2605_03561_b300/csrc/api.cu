@@ -456,6 +456,12 @@ ta_status excl_begin(ta_experiment* e, Pool& tmp, ExclPending* xq) {
   TRY(tmp.get_n((u64)R * cap, &A.xs_cnt, "exclusive scratch"));
   A.xs_cap = (u32)cap;
   A.n_over = (unsigned long long*)(meta + 2);
+  // iteration moments beside the entries (the speedup's within-rank terms
+  // read them instead of the rows)
+  TRY(tmp.get_n((u64)R * cap, &A.xs_m1, "exclusive scratch"));
+  TRY(tmp.get_n((u64)R * cap * 2, &A.xs_m2, "exclusive scratch"));
+  TRY(e->own(std::max<u32>(R, 1), (void**)&e->x_mom, "iteration moments"));
+  A.mom_ok = e->x_mom;
   {
     PhaseTimer timer(c, &c->prof.exclusive_ms);
     launch_excl_scratch(L, P, A);
@@ -483,6 +489,10 @@ ta_status excl_finish(ta_experiment* e, ExclPending& xq, const u64* h) {
   A.out_ctx = out.ctx;
   A.out_time = out.time;
   A.out_cnt_e = out.cnt;
+  TRY(e->own(n * 8, (void**)&e->x_m1, "iteration moments"));
+  TRY(e->own(n * 16, (void**)&e->x_m2, "iteration moments"));
+  A.out_m1 = e->x_m1;
+  A.out_m2 = e->x_m2;
   PhaseTimer timer(c, &c->prof.exclusive_ms);
   launch_excl_copy(L, A);
   if (h[2]) {

@@ -253,14 +253,16 @@ struct RStage {
 // first) as one template block.  Returns true when every such row holds the
 // first one's contexts -- rows are context-sorted, so entry p of every row is
 // then the same context -- with at most 96 of them; tc holds them and tt / tn
-// each position's time and samples summed over the rows (lane l: positions
-// l, l + 32, l + 64; four rows' loads in flight, one vote per row).  The
-// rank's first row (its prologue) is [p0, p1), left to the caller.
+// each position's time and samples summed over the rows, ql / qh the 128-bit
+// sum of the squared times (lane l: positions l, l + 32, l + 64; four rows'
+// loads in flight, one vote per row).  The rank's first row (its prologue)
+// is [p0, p1), left to the caller.
 constexpr u32 XT_P = 3;  // positions per lane
 constexpr u32 XT_R = 4;  // rows in flight
 __device__ __forceinline__ bool excl_template(const RankCsrArgs& A, u64 r, int lane,
                                               u32 (&tc)[XT_P], u64 (&tt)[XT_P],
-                                              u32 (&tn)[XT_P], u64& p0, u64& p1) {
+                                              u32 (&tn)[XT_P], u64 (&ql)[XT_P],
+                                              u64 (&qh)[XT_P], u64& p0, u64& p1) {
   const u64 R0 = A.row_off_of_rank[r], R1 = A.row_off_of_rank[r + 1];
   if (R1 < R0 + 3) return false;  // fewer than two iteration rows: nothing to gain
   p0 = A.entry_off[R0];
@@ -275,6 +277,8 @@ __device__ __forceinline__ bool excl_template(const RankCsrArgs& A, u64 r, int l
     tc[q] = p < L ? A.in_ctx[b0 + p] : NONE32;
     tt[q] = 0;
     tn[q] = 0;
+    ql[q] = 0;
+    qh[q] = 0;
   }
   const u64 nrow = R1 - R0 - 1;
   for (u64 j0 = 0; j0 < nrow; j0 += 32) {
@@ -309,6 +313,9 @@ __device__ __forceinline__ bool excl_template(const RankCsrArgs& A, u64 r, int l
         for (u32 q = 0; q < XT_P; ++q) {
           tt[q] += t[w][q];
           tn[q] += n[w][q];
+          const u64 lo = t[w][q] * t[w][q];
+          ql[q] += lo;
+          qh[q] += __umul64hi(t[w][q], t[w][q]) + (ql[q] < lo ? 1ull : 0ull);
         }
     }
   }
@@ -387,9 +394,10 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
     u64 E0, E1;
     // exclusive: the iteration rows as a template block when they allow it
     u32 xtc[XT_P];
-    u64 xtt[XT_P], xp0 = 0, xp1 = 0;
+    u64 xtt[XT_P], xql[XT_P], xqh[XT_P], xp0 = 0, xp1 = 0;
     u32 xtn[XT_P];
-    const bool tmpl = MODE == 0 && WRITE && excl_template(A, r, lane, xtc, xtt, xtn, xp0, xp1);
+    const bool tmpl =
+        MODE == 0 && WRITE && excl_template(A, r, lane, xtc, xtt, xtn, xql, xqh, xp0, xp1);
     if (MODE == 0 && tmpl) {  // marks: the template's contexts and the first row's
       E0 = A.entry_off[A.row_off_of_rank[r]];
       E1 = A.entry_off[A.row_off_of_rank[r + 1]];
@@ -647,6 +655,26 @@ __global__ void __launch_bounds__(NW * 32) k_rank_pass(const RankCsrArgs A) {
         A.out_cnt_e[eo + k] = vld(&st.cnt[k]);
       }
     }
+    if (MODE == 0 && A.mom_ok) {  // iteration moments: the template's, 0 elsewhere
+      if (lane == 0) A.mom_ok[r] = tmpl ? 1 : 0;
+      if (tmpl) {
+        const u64 eo = scratch ? r * (u64)A.xs_cap : A.out_off[r];
+        u64* const m1 = (scratch ? A.xs_m1 : A.out_m1) + eo;
+        ulonglong2* const m2 = reinterpret_cast<ulonglong2*>(scratch ? A.xs_m2 : A.out_m2) + eo;
+        for (u32 k = lane; k < nnz; k += 32) {
+          m1[k] = 0;
+          m2[k] = make_ulonglong2(0, 0);
+        }
+        __syncwarp();
+#pragma unroll
+        for (u32 q = 0; q < XT_P; ++q) {
+          if (xtc[q] == NONE32) continue;
+          const u32 k = bm_rank(bm, xtc[q]);
+          m1[k] = xtt[q];
+          m2[k] = make_ulonglong2(xql[q], xqh[q]);
+        }
+      }
+    }
     };
     if (nnz <= (MODE == 2 ? RSR2 : RSR)) run(ss);
     else run(gs);
@@ -735,6 +763,14 @@ __global__ void k_excl_copy(const RankCsrArgs A) {
       A.out_ctx[dst + k] = A.xs_ctx[src + k];
       A.out_time[dst + k] = A.xs_time[src + k];
       A.out_cnt_e[dst + k] = A.xs_cnt[src + k];
+    }
+    if (A.mom_ok && A.mom_ok[r]) {
+      const ulonglong2* m2s = reinterpret_cast<const ulonglong2*>(A.xs_m2) + src;
+      ulonglong2* m2d = reinterpret_cast<ulonglong2*>(A.out_m2) + dst;
+      for (u32 k = lane; k < n; k += 32) {
+        A.out_m1[dst + k] = A.xs_m1[src + k];
+        m2d[k] = m2s[k];
+      }
     }
   }
 }

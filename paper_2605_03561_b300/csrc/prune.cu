@@ -170,6 +170,11 @@ extern "C" ta_status ta_prune_profiles(ta_experiment* e, const ta_prune_args* a,
     m->cnt = cn;
     m->nnz = nnz;
   }
+  // the iteration moments follow the unpruned exclusive entries: dropped
+  for (void* p : {(void*)e->x_m1, (void*)e->x_m2, (void*)e->x_mom})
+    if (p) e->disown(p);
+  e->x_m1 = e->x_m2 = nullptr;
+  e->x_mom = nullptr;
   u32 h[2];
   TRY(copy(c, h, meta, 8));
   if (o->kept) TRY(copy(c, o->kept, kept, C));

@@ -621,12 +621,15 @@ struct KLookup {
 // (a) Within-rank CV terms: one warp per rank of S; over iterations i < I*,
 // per context of the chunk: sum and 128-bit sum of squares of t[r][i][k] in
 // warp-private shared memory (a context absent from a row adds 0), then the
-// CV term of (r, k).  The rank's rows are contiguous entries; two batches of
-// them are in flight while one is summed.
+// CV term of (r, k).  A rank with exactly I* iteration rows whose exclusive
+// entries carry their iteration moments (mom_ok) takes both sums from them,
+// one entry per context; any other rank reads its rows, which are contiguous
+// entries, two batches in flight while one is summed.
 __global__ void __launch_bounds__(SP_NW * 32)
     k_sp_within(const u32* S, u32 n, const u64* row_off, const u64* entry_off, const u32* e_ctx,
                 const u64* e_time, const u32* kset, const u32* kmap, u32 C, u32 k0, u32 nkc,
-                u32 I, double* cvw) {
+                u32 I, const u64* x_off, const u32* x_ctx, const u64* x_m1, const u64* x_m2,
+                const uint8_t* mom_ok, double* cvw) {
   __shared__ unsigned long long s_sum[SP_NW][SP_KC], s_lo[SP_NW][SP_KC], s_hi[SP_NW][SP_KC];
   extern __shared__ __align__(16) unsigned char kmap8[];
   const bool smap = C <= SP_SMAP;
@@ -642,35 +645,47 @@ __global__ void __launch_bounds__(SP_NW * 32)
   for (u32 ri = gw; ri < n; ri += nw) {
     const u32 r = rank_at(S, ri);
     const u64 row0 = row_off[r] + 1;  // skip the prologue row
-    const u64 E0 = entry_off[row0], E1 = entry_off[row0 + I];
-    u32 c[SP_U];
-    u64 t[SP_U];
-#pragma unroll
-    for (u32 u = 0; u < SP_U; ++u) {
-      const u64 j = E0 + u * 32 + lane;
-      c[u] = j < E1 ? e_ctx[j] : NONE32;
-      t[u] = j < E1 ? e_time[j] : 0ull;
-    }
-    for (u64 jb = E0; jb < E1; jb += 32 * SP_U) {
-      u32 cn[SP_U];
-      u64 tn[SP_U];
-#pragma unroll
-      for (u32 u = 0; u < SP_U; ++u) {  // the next batch
-        const u64 j = jb + 32 * SP_U + u * 32 + lane;
-        cn[u] = j < E1 ? e_ctx[j] : NONE32;
-        tn[u] = j < E1 ? e_time[j] : 0ull;
-      }
-#pragma unroll
-      for (u32 u = 0; u < SP_U; ++u) {
-        const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
+    if (mom_ok && mom_ok[r] && row_off[r + 1] - row_off[r] == (u64)I + 1) {
+      const ulonglong2* m2 = reinterpret_cast<const ulonglong2*>(x_m2);
+      for (u64 j = x_off[r] + lane; j < x_off[r + 1]; j += 32) {
+        const u32 kk = look(x_ctx[j]);
         if (kk == NONE32) continue;
-        atomic_add_u64_lo32(&my_sum[kk], t[u]);
-        atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t[u] * t[u]);
+        const ulonglong2 q = m2[j];
+        my_sum[kk] = x_m1[j];
+        my_lo[kk] = q.x;
+        my_hi[kk] = q.y;
       }
+    } else {
+      const u64 E0 = entry_off[row0], E1 = entry_off[row0 + I];
+      u32 c[SP_U];
+      u64 t[SP_U];
 #pragma unroll
       for (u32 u = 0; u < SP_U; ++u) {
-        c[u] = cn[u];
-        t[u] = tn[u];
+        const u64 j = E0 + u * 32 + lane;
+        c[u] = j < E1 ? e_ctx[j] : NONE32;
+        t[u] = j < E1 ? e_time[j] : 0ull;
+      }
+      for (u64 jb = E0; jb < E1; jb += 32 * SP_U) {
+        u32 cn[SP_U];
+        u64 tn[SP_U];
+#pragma unroll
+        for (u32 u = 0; u < SP_U; ++u) {  // the next batch
+          const u64 j = jb + 32 * SP_U + u * 32 + lane;
+          cn[u] = j < E1 ? e_ctx[j] : NONE32;
+          tn[u] = j < E1 ? e_time[j] : 0ull;
+        }
+#pragma unroll
+        for (u32 u = 0; u < SP_U; ++u) {
+          const u32 kk = (c[u] != NONE32) ? look(c[u]) : NONE32;
+          if (kk == NONE32) continue;
+          atomic_add_u64_lo32(&my_sum[kk], t[u]);
+          atomic_add_u128((u64*)&my_lo[kk], (u64*)&my_hi[kk], (u128)t[u] * t[u]);
+        }
+#pragma unroll
+        for (u32 u = 0; u < SP_U; ++u) {
+          c[u] = cn[u];
+          t[u] = tn[u];
+        }
       }
     }
     __syncwarp();
@@ -1038,7 +1053,7 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
       k_sp_within<<<grid, SP_NW * 32, map_smem, ws>>>(
           dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
-          std::min(SP_KC, nk - k0), I, cvw);
+          std::min(SP_KC, nk - k0), I, e->x.off, e->x.ctx, e->x_m1, e->x_m2, e->x_mom, cvw);
       L.count();
     }
     // cells: enough warps to fill the GPU, each with a sizeable group of ranks

@@ -127,6 +127,14 @@ struct ta_experiment {
   ta::u32* e_cnt = nullptr;
   ta::u64 rows = 0, nnz = 0;
   ta::Csr x, in;
+  // iteration moments of every exclusive entry (in x's order): the sum of its
+  // time over the rank's iteration rows (every row after the first) and the
+  // 128-bit sum of their squares (lo, hi pairs); set for the ranks whose
+  // iteration rows all hold the same contexts (x_mom[r] = 1).  Null when not
+  // built or no longer matching x.
+  ta::u64* x_m1 = nullptr;
+  ta::u64* x_m2 = nullptr;
+  uint8_t* x_mom = nullptr;
   bool has_incl = false;
   // first sample of every tensor row ([rows + 1], global sample index; built
   // by the first time-window call) and that call's last result

@@ -181,6 +181,16 @@ struct RankCsrArgs {
   u32 xs_cap;
   u32 only_over;
   unsigned long long* n_over;  // [1] ranks above xs_cap
+  // exclusive, optional (null: not written): per entry the iteration
+  // moments (time summed over the rank's rows after its first, and the
+  // 128-bit sum of squares as lo, hi), at out_off or in the scratch like
+  // the entries; mom_ok[r] = 1 where they were taken (every iteration row of
+  // the rank holds the same contexts), else 0
+  u64* out_m1;
+  u64* out_m2;
+  u64* xs_m1;
+  u64* xs_m2;
+  uint8_t* mom_ok;
 };
 // Kernels of the rank passes by variant: 0 exclusive, 1 inclusive by a
 // level-by-level sweep, 2 inclusive through ancestor lists.
