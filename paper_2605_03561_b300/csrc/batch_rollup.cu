@@ -78,14 +78,10 @@ __global__ void __launch_bounds__(BNW * 32) k_bsp_within(const BatchSpeedupArgs 
         }
       }
       __syncwarp();
+      const double cI = cv_coef(I);
       for (u32 kk = lane; kk < nkc; kk += 32) {
-        const u64 sm_ = ms[kk];
         const u128 q = ((u128)mh[kk] << 64) | ml[kk];
-        const double mean = u64_to_f64(sm_) / u64_to_f64(I);
-        const double sd = (I < 2) ? 0.0
-                                  : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
-                                         u64_to_f64((u64)I * (I - 1)));
-        P.cvw[P.cv0[s] + (u64)(kc0 + kk) * n + ri] = (mean == 0.0) ? 0.0 : sd / mean;
+        P.cvw[P.cv0[s] + (u64)(kc0 + kk) * n + ri] = cv_of_sums(ms[kk], q, I, cI);
         ms[kk] = ml[kk] = mh[kk] = 0;
       }
       __syncwarp();

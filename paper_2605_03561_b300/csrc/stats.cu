@@ -642,6 +642,7 @@ __global__ void __launch_bounds__(SP_NW * 32)
   for (u32 q = lane; q < SP_KC; q += 32) my_sum[q] = my_lo[q] = my_hi[q] = 0;
   __syncwarp();
   const u32 gw = blockIdx.x * SP_NW + warp, nw = gridDim.x * SP_NW;
+  const double cI = cv_coef(I);
   for (u32 ri = gw; ri < n; ri += nw) {
     const u32 r = rank_at(S, ri);
     const u64 row0 = row_off[r] + 1;  // skip the prologue row
@@ -690,13 +691,8 @@ __global__ void __launch_bounds__(SP_NW * 32)
     }
     __syncwarp();
     for (u32 kk = lane; kk < nkc; kk += 32) {
-      const u64 sm_ = my_sum[kk];
       const u128 q = ((u128)my_hi[kk] << 64) | my_lo[kk];
-      const double mean = u64_to_f64(sm_) / u64_to_f64(I);
-      const double sd = (I < 2) ? 0.0
-                                : sqrt(u128_to_f64((u128)I * q - (u128)sm_ * sm_) /
-                                       u64_to_f64((u64)I * (I - 1)));
-      cvw[(u64)(k0 + kk) * n + ri] = (mean == 0.0) ? 0.0 : sd / mean;
+      cvw[(u64)(k0 + kk) * n + ri] = cv_of_sums(my_sum[kk], q, I, cI);
       my_sum[kk] = my_lo[kk] = my_hi[kk] = 0;
     }
     __syncwarp();
@@ -910,8 +906,44 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
 // Sum of each context's per-rank CV terms (a column of n values of cvw,
 // context-major) in the fixed pairwise order of the definition: level by
 // level, element i of the next level is v[2i] + v[2i+1], an odd last element
-// moves up unchanged.  One CTA per context; levels ping-pong between cvw and
-// tmp.
+// moves up unchanged.  Element i of level l is the same rule applied to the
+// values [i 2^l, min((i + 1) 2^l, n)) alone (a pair adds two such ranges, a
+// carried element keeps its own), so the first PW_LEVELS levels are taken
+// per block of 2^PW_LEVELS values in shared memory by many CTAs, and the
+// rest by one CTA per context over the block values.
+constexpr u32 PW_LEVELS = 11;
+constexpr u32 PW_BLOCK = 1u << PW_LEVELS;
+
+// Level PW_LEVELS of each context: CTA (k, y) reduces values
+// [b PW_BLOCK, min((b + 1) PW_BLOCK, n)) of column k into blk[k nb + b] for
+// the blocks b = y, y + gridDim.y, ...
+__global__ void __launch_bounds__(256) k_sp_pair_blocks(const double* cvw, u32 n, u32 nb,
+                                                        double* blk) {
+  __shared__ double a[PW_BLOCK], b[PW_BLOCK];
+  const u32 k = blockIdx.x;
+  for (u32 bi = blockIdx.y; bi < nb; bi += gridDim.y) {
+    const u64 base = (u64)k * n + (u64)bi * PW_BLOCK;
+    u32 cnt = (u32)min((u64)PW_BLOCK, (u64)n - (u64)bi * PW_BLOCK);
+    for (u32 i = threadIdx.x; i < cnt; i += blockDim.x) a[i] = cvw[base + i];
+    __syncthreads();
+    double *src = a, *dst = b;
+    while (cnt > 1) {
+      const u32 m = cnt / 2;
+      for (u32 i = threadIdx.x; i < m; i += blockDim.x) dst[i] = src[2 * i] + src[2 * i + 1];
+      if ((cnt & 1) && threadIdx.x == 0) dst[m] = src[cnt - 1];
+      cnt = m + (cnt & 1);
+      double* x = src;
+      src = dst;
+      dst = x;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) blk[(u64)k * nb + bi] = src[0];
+    __syncthreads();  // a and b are refilled for the next block
+  }
+}
+
+// The remaining levels: one CTA per context over its n values of cvw (the
+// block values), ping-ponging between cvw and tmp.
 __global__ void __launch_bounds__(256) k_sp_pairwise(double* cvw, double* tmp, u32 n,
                                                      double* within) {
   const u32 k = blockIdx.x;
@@ -1046,16 +1078,11 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
     const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + SP_NW - 1) / SP_NW)));
     if (map_smem)
       cudaFuncSetAttribute(k_sp_within, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)map_smem);
-    // the within-rank terms and the cells read the same rows independently:
-    // the former runs on the auxiliary stream beside the latter
+    // the cells and the within-rank terms are independent: the latter run on
+    // the auxiliary stream, launched second so that they fill the SMs the
+    // cells' last wave leaves idle
     cudaStream_t ws = fork_aux(c);
     if (!ws) ws = L.stream;
-    for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
-      k_sp_within<<<grid, SP_NW * 32, map_smem, ws>>>(
-          dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
-          std::min(SP_KC, nk - k0), I, e->x.off, e->x.ctx, e->x_m1, e->x_m2, e->x_mom, cvw);
-      L.count();
-    }
     // cells: enough warps to fill the GPU, each with a sizeable group of ranks
     const u32 n_ib = (I + SP_IB - 1) / SP_IB, n_kb = (nk + 63) / 64;
     const u64 tiles = (u64)n_ib * n_kb;
@@ -1071,16 +1098,25 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
         dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
         group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
     L.count();
+    for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
+      k_sp_within<<<grid, SP_NW * 32, map_smem, ws>>>(
+          dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, k0,
+          std::min(SP_KC, nk - k0), I, e->x.off, e->x.ctx, e->x_m1, e->x_m2, e->x_mom, cvw);
+      L.count();
+    }
     if (ws != L.stream) join_aux(c);
   }
   double* cvw2;
   double*& wsum = sp.wsum;
-  TRY(tmp.get_n(std::max<u64>(1, (u64)n * nk), &cvw2, "cv terms"));
+  const u32 nb = (u32)(((u64)n + PW_BLOCK - 1) / PW_BLOCK);
+  TRY(tmp.get_n(std::max<u64>(1, 2ull * nk * nb), &cvw2, "cv block sums"));
   TRY(tmp.get_n(nk, &wsum, "within sums"));
   cudaMemsetAsync(wsum, 0, (size_t)nk * 8, c->stream);
-  if (I > 0) {
-    k_sp_pairwise<<<nk, 256, 0, L.stream>>>(cvw, cvw2, n, wsum);
-    L.count();
+  if (I > 0 && n > 0) {
+    double* blk = cvw2;  // [nk nb] block values, then [nk nb] of ping-pong space
+    k_sp_pair_blocks<<<dim3(nk, std::min(nb, 65535u)), 256, 0, L.stream>>>(cvw, n, nb, blk);
+    k_sp_pairwise<<<nk, 256, 0, L.stream>>>(blk, blk + (u64)nk * nb, nb, wsum);
+    L.count(2);
   }
   return TA_OK;
 }

@@ -297,6 +297,22 @@ __device__ __forceinline__ double u128_to_f64(u128 v) {
   return scalbn(d, s);
 }
 
+// Coefficient of variation (sample standard deviation over the mean) of m
+// values from their sum s and exact sum of squares q.  The definition's
+// mean = s / m and sd = sqrt((m q - s^2) / (m (m - 1))) give
+// sd / mean = c_m sqrt(m q - s^2) / s with c_m = sqrt(m / (m - 1)), taken
+// once per launch: one square root and one division per value instead of
+// three divisions and a square root (a few units in the last place from the
+// definition's rounding).  0 when the mean is 0 or m < 2.
+__device__ __forceinline__ double cv_coef(u32 m) {
+  return m < 2 ? 0.0 : sqrt(u64_to_f64(m) / u64_to_f64(m - 1));
+}
+__device__ __forceinline__ double cv_of_sums(u64 s, u128 q, u32 m, double c_m) {
+  if (s == 0 || m < 2) return 0.0;
+  const u128 d = (u128)m * q - (u128)s * s;
+  return c_m * sqrt(u128_to_f64(d)) / u64_to_f64(s);
+}
+
 // a * b exactly as 256 bits (little-endian limbs), a, b < 2^128.
 struct W256 {
   u64 w[4];
