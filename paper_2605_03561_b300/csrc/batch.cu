@@ -81,6 +81,11 @@ struct ta_batch {
   bool compact = false;
   TensorCompact TC{};
   Csr x, in;
+  // iteration moments of the exclusive entries (see the single-experiment
+  // load): time over the iteration rows and its 128-bit sum of squares
+  u64* x_m1 = nullptr;
+  u64* x_m2 = nullptr;
+  uint8_t* x_mom = nullptr;
   ta_ctx_stats* stats = nullptr;
   u64* keys = nullptr;
   double* zs = nullptr;
@@ -377,6 +382,11 @@ ta_status plan_rollups(ta_batch* b) {
     P.entry_off = b->entry_off;
     P.e_ctx = b->e_ctx;
     P.e_time = b->e_time;
+    P.x_off = b->x.off;
+    P.x_ctx = b->x.ctx;
+    P.x_m1 = b->x_m1;
+    P.x_m2 = b->x_m2;
+    P.mom_ok = b->x_mom;
     u32 *d_kmap = nullptr, *d_k0 = nullptr, *d_istar = nullptr;
     u64 *d_cell0 = nullptr, *d_cv0 = nullptr, *d_item0 = nullptr, *d_excl = nullptr,
         *d_tapp = nullptr;
@@ -843,6 +853,14 @@ ta_status create_impl(ta_batch* b, const ta_trace_desc* sets, u32 S) {
     X.out_ctx = out.ctx;
     X.out_time = out.time;
     X.out_cnt_e = out.cnt;
+    if (mode == 0) {
+      TRY(b->own_n(std::max<u64>(t, 1), &b->x_m1, "iteration moments"));
+      TRY(b->own_n(std::max<u64>(2 * t, 2), &b->x_m2, "iteration moments"));
+      TRY(b->own_n(std::max<u32>(b->R, 1), &b->x_mom, "iteration moments"));
+      X.out_m1 = b->x_m1;
+      X.out_m2 = b->x_m2;
+      X.mom_ok = b->x_mom;
+    }
     launch_rank_write(L, b->XP, X);
     TRY(check_flags(b, "ta_batch_plan"));
   }

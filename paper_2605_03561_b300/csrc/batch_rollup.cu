@@ -40,6 +40,8 @@ __device__ __forceinline__ u32 find_set32(const u32* prefix, u32 S, u32 v) {
 }
 
 // Within-rank CV terms: warp per rank of every set with a speedup request.
+// A rank with exactly I* iteration rows and iteration moments takes its sums
+// from its exclusive entries; any other rank reads its rows.
 __global__ void __launch_bounds__(BNW * 32) k_bsp_within(const BatchSpeedupArgs P) {
   __shared__ unsigned long long s_sum[BNW][BKC], s_lo[BNW][BKC], s_hi[BNW][BKC];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -57,9 +59,21 @@ __global__ void __launch_bounds__(BNW * 32) k_bsp_within(const BatchSpeedupArgs 
     const u32 cb = P.set_ctx0[s];
     const u64 row0 = P.row_off[r] + 1;
     const u64 E0 = P.entry_off[row0], E1 = P.entry_off[row0 + I];
+    const bool mom = P.mom_ok && P.mom_ok[r] && P.row_off[r + 1] - P.row_off[r] == (u64)I + 1;
     for (u32 kc0 = 0; kc0 < nk; kc0 += BKC) {
       const u32 nkc = min(BKC, nk - kc0);
-      for (u64 jb = E0; jb < E1; jb += 32 * BU) {
+      if (mom) {
+        const ulonglong2* m2 = reinterpret_cast<const ulonglong2*>(P.x_m2);
+        for (u64 j = P.x_off[r] + lane; j < P.x_off[r + 1]; j += 32) {
+          const u32 k = P.kmap[cb + P.x_ctx[j]];
+          if (k == NONE32 || k < kc0 || k >= kc0 + nkc) continue;
+          const ulonglong2 q = m2[j];
+          ms[k - kc0] = P.x_m1[j];
+          ml[k - kc0] = q.x;
+          mh[k - kc0] = q.y;
+        }
+      }
+      for (u64 jb = mom ? E1 : E0; jb < E1; jb += 32 * BU) {
         u32 c[BU];
         u64 t[BU];
 #pragma unroll

@@ -249,6 +249,12 @@ struct BatchSpeedupArgs {
   const u64* entry_off;
   const u32* e_ctx;
   const u64* e_time;
+  // exclusive entries with their iteration moments (mom_ok[r]: rank r's are set)
+  const u64* x_off;
+  const u32* x_ctx;
+  const u64* x_m1;
+  const u64* x_m2;
+  const uint8_t* mom_ok;
   const u32* kmap;
   const u32* k0;
   const u32* istar;
