@@ -441,6 +441,17 @@ def _np(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
+def _as_py_ints(a):
+    """A struct field column with the dtype np.array would give the same
+    values as Python numbers: integers as int64, or uint64 when one exceeds
+    int64's range; floats unchanged."""
+    if a.dtype.kind not in "ui":
+        return a.copy()
+    if a.dtype == np.uint64 and a.size and int(a.max()) > np.iinfo(np.int64).max:
+        return a.copy()
+    return a.astype(np.int64)
+
+
 class Columns:
     """The column operations of include/ta.h (ta_events_table, ta_col_*) on
     torch device tensors of this context's device."""
@@ -647,8 +658,8 @@ class Experiment:
         a.ranks, a.n_ranks_subset = _ptr(rk), 0 if ranks is None else len(ranks)
         a.ctxs, a.n_ctxs = _ptr(cx), 0 if ctxs is None else len(ctxs)
         a.tau_num, a.tau_den = tau
-        st = (CtxStats * max(k, 1))()
-        outl = (Outlier * max(outlier_cap, 1))()
+        st = np.zeros(max(k, 1), np.dtype(CtxStats))
+        outl = np.empty(max(outlier_cap, 1), np.dtype(Outlier))
         nnz = 0
         if want_z:
             v = CsrView()
@@ -663,23 +674,23 @@ class Experiment:
             dz = torch.zeros(max(nnz, 1), dtype=torch.float64, device="cuda") if want_z else None
             o.stats, o.outliers, o.z = dst.data_ptr(), dout.data_ptr(), _ptr(dz)
         else:
-            o.stats, o.outliers, o.z = C.addressof(st), C.addressof(outl), _ptr(z)
+            o.stats, o.outliers, o.z = st.ctypes.data, outl.ctypes.data, _ptr(z)
         o.outlier_cap = outlier_cap
         s = lib().ta_context_stats(self.h, C.byref(a), C.byref(o))
         n_out = int(o.n_outliers)
         if s not in (OK, CAPACITY):
             _check(s)
+        m = min(n_out, outlier_cap) if s == OK else 0
         if device:
-            C.memmove(st, dst.cpu().numpy().ctypes.data, max(k, 1) * C.sizeof(CtxStats))
-            C.memmove(outl, dout.cpu().numpy().ctypes.data, max(outlier_cap, 1) * C.sizeof(Outlier))
+            C.memmove(st.ctypes.data, dst.cpu().numpy().ctypes.data, max(k, 1) * C.sizeof(CtxStats))
+            if m:
+                C.memmove(outl.ctypes.data, dout[: m * C.sizeof(Outlier)].cpu().numpy().ctypes.data,
+                          m * C.sizeof(Outlier))
             if want_z:
                 z = dz.cpu().numpy()
-        stats = {f: np.array([getattr(x, f) for x in st[:k]]) for f, _ in CtxStats._fields_
-                 if f != "reserved"}
-        m = min(n_out, outlier_cap) if s == OK else 0
-        outliers = dict(ctx=np.array([x.ctx for x in outl[:m]], np.uint32),
-                        rank=np.array([x.rank for x in outl[:m]], np.uint32),
-                        z=np.array([x.z for x in outl[:m]], np.float64))
+        stats = {f: _as_py_ints(st[f][:k]) for f, _ in CtxStats._fields_ if f != "reserved"}
+        outliers = dict(ctx=outl["ctx"][:m].copy(), rank=outl["rank"][:m].copy(),
+                        z=outl["z"][:m].copy())
         if s == CAPACITY:
             raise TaError(s, f"{n_out} outliers exceed capacity {outlier_cap}")
         return stats, outliers, n_out, (z[:nnz] if want_z else None)
