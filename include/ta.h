@@ -168,6 +168,11 @@ typedef struct ta_trace_desc {
 /* Validate the traces (all of the rules above) and build the experiment's
  * resident products on the device: per-rank spans and iteration counts, the
  * iteration tensor, the exclusive CSR and (unless skipped) the inclusive CSR.
+ * Beside the exclusive CSR it keeps each entry's iteration moments: the time
+ * summed over the rank's iteration rows and the 128-bit sum of its squares.
+ * They are kept only for ranks whose iteration rows all hold the same
+ * contexts, and ta_potential_speedup reads them.  24 bytes per exclusive
+ * entry plus 1 per rank; ta_prune_profiles drops them.
  * Synchronous: returns after the device work, with the first error found in
  * the order INVALID_ARG, BAD_CCT, BAD_CTX, NOT_SORTED (then OOM, TIMEOUT,
  * CUDA).  Host inputs are copied to the device first.  The experiment is
@@ -359,7 +364,14 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
  *   cv_within = mean over r in S of (std/mean over i < I* of t[r][.][k]),
  * and totals: sum G, total reduction = sum G / n, t_app = app_time_ns or
  * (if 0) the longest rank span in S, speedup_fraction = sum G / (n t_app).
- * (Both CV sums run in ascending i / ascending r.) */
+ * cv_across sums its terms in ascending i.  cv_within sums its per-rank
+ * terms in a fixed pairwise order: level by level, v[2i] + v[2i+1], an odd
+ * last term moving up.  Each per-rank term is computed as
+ * sqrt(m / (m - 1)) sqrt(m q - s^2) / s from the exact sums s and q over
+ * m = I* iterations.  That equals std/mean up to a few units in the last
+ * place.  For ranks with exactly I* iterations whose iteration rows all hold
+ * the same contexts, s and q come from the load's iteration moments; other
+ * ranks read their tensor rows. */
 typedef struct ta_speedup_args {
   uint32_t mem_kind; /* of ctxs / ranks / outputs */
   uint32_t n_ctxs;
