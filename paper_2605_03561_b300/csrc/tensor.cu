@@ -229,8 +229,10 @@ __device__ __forceinline__ u32 from_mask8(u32 f, int lane) {
   return s <= 0 ? 0xFFu : (s >= (int)KC ? 0u : (0xFFu << s) & 0xFFu);
 }
 
+// 64 registers (32 warps per SM): the rotating buffers would take 74 and
+// leave room for 24.
 template <int NW, u32 TW>
-__global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
+__global__ void __launch_bounds__(NW * 32, 32 / NW) k_tensor_count(const TensorArgs A) {
   constexpr int D = DEPTH_COUNT;
   __shared__ u32 masks[NW][TileW<TW>::MASKW];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -243,22 +245,26 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
     u32 carry = (T.a > T.sbase) ? A.ctx[T.a - 1] : NONE32;
     u32 heads = 0, ms = 0, cmax = 0;
     bool open = false;  // a row of this tile has started
-    CStep ring[D + 1];
+    // three step buffers in turn (the step being read and the next two in
+    // flight): the loop body runs three times per iteration, so no buffer is
+    // copied from one step to the next
+    static_assert(D == 2, "three step buffers");
+    CStep r0, r1, r2;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const u64 qd = T.a + (u64)d * STEPC;
-      if (qd < A.N) load_c(A, qd, lane, ring[d]);
-    }
-    for (u64 q0 = T.a;; q0 += STEPC) {
+    for (int j = 0; j < (int)KC; ++j) r0.c[j] = r1.c[j] = r2.c[j] = NONE32;
+    if (T.a < A.N) load_c(A, T.a, lane, r0);
+    if (T.a + STEPC < A.N) load_c(A, T.a + STEPC, lane, r1);
+    u64 q0 = T.a;
+    // one step from cur, nxt taking the step D ahead; true: the tile is done
+    auto step = [&](CStep& cur, CStep& nxt) -> bool {
       const bool tile_step = q0 < T.b;
-      if (!tile_step && !open) break;
+      if (!tile_step && !open) return true;
       const u64 lim = tile_step ? T.b : T.qrank;
-      if (q0 >= lim) break;
+      if (q0 >= lim) return true;
       {
         const u64 qd = q0 + (u64)D * STEPC;
-        if (qd < A.N) load_c(A, qd, lane, ring[D]);
+        if (qd < A.N) load_c(A, qd, lane, nxt);
       }
-      const CStep& cur = ring[0];
       u32 pc0 = __shfl_up_sync(FULL, cur.c[KC - 1], 1);
       if (lane == 0) pc0 = carry;
       carry = __shfl_sync(FULL, cur.c[KC - 1], 31);
@@ -272,15 +278,16 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
 #pragma unroll
         for (int j = 0; j < (int)KC; ++j) {
           const u32 c = cur.c[j];
-          h += (u32)(c != prev);
-          s2 += (u32)(c == m && prev != m);
+          const u32 hd = (u32)(c != prev);
+          h += hd;
+          s2 += (u32)(c == m) & hd;  // a marker after another context is a head
           cm = max(cm, c);
           prev = c;
         }
         heads += h;
         ms += s2;
         cmax = max(cmax, cm);
-        if (q0 + STEPC >= T.b && T.b == T.N) break;  // the set's last tile
+        if (q0 + STEPC >= T.b && T.b == T.N) return true;  // the set's last tile
       } else {
         const u32 nvalid = (u32)min(lim - q0, (u64)STEPC);
         const u32 rel = (u32)(q0 - T.a) + KC * (u32)lane;
@@ -315,11 +322,16 @@ __global__ void __launch_bounds__(NW * 32) k_tensor_count(const TensorArgs A) {
           }
         }
         heads += __popc(take);
-        if (stop) break;
-        if (tile_step && q0 + STEPC >= T.b && T.b == T.N) break;  // the set's last tile
+        if (stop) return true;
+        if (tile_step && q0 + STEPC >= T.b && T.b == T.N) return true;  // the set's last tile
       }
-#pragma unroll
-      for (int d = 0; d < D; ++d) ring[d] = ring[d + 1];
+      q0 += STEPC;
+      return false;
+    };
+    for (;;) {
+      if (step(r0, r2)) break;
+      if (step(r1, r0)) break;
+      if (step(r2, r1)) break;
     }
     u32 fl = cmax >= T.C ? F_BAD_CTX : 0u;
     heads = __reduce_add_sync(FULL, heads);
