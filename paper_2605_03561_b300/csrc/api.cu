@@ -677,6 +677,9 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
   TRY(sync_check(c, "iteration tensor (write)"));
   TRY(tensor_finish(e, tmp, tq, ht));
   launch_n_iter(L, e->row_off, R, e->n_iter);
+  u64* isum;  // I*, sum n_iter, max span over all ranks, read at the final wait
+  TRY(tmp.get_n(4, &isum, "iteration summary"));
+  launch_iter_summary(L, R, e->n_iter, e->span, isum);
   TRY(excl_begin(e, tmp, &xq));  // from the finished tensor's rows
   TRY(copy(c, ht + 4, xq.meta, 3 * 8));
   TRY(sync_check(c, "exclusive (scratch)"));
@@ -688,12 +691,16 @@ ta_status load_impl(ta_ctx* c, const ta_trace_desc* d, ta_experiment* e, Pool& t
     e->has_incl = true;
   }
   // the status words left by the last passes, read at the one final wait
-  u64 fin[2] = {0, 0};
+  u64 fin[2] = {0, 0}, hi[3] = {0, 0, 0};
   TRY(copy(c, &fin[0], xq.meta, 8));
   if (incl_status) TRY(copy(c, &fin[1], incl_status, 8));
+  TRY(copy(c, hi, isum, sizeof hi));
   TRY(sync_check(c, "ta_load_traces"));
   TRY(status_from_flags((u32)fin[0], "exclusive"));
   TRY(status_from_flags((u32)fin[1], "inclusive"));
+  e->istar_all = (u32)hi[0];
+  e->sum_iter_all = hi[1];
+  e->has_iter_summary = true;
   // raw traces are not needed after ingestion unless kept for time windows
   if (e->owns_traces && !(d->flags & TA_LOAD_KEEP_TRACES)) {
     e->disown((void*)e->ts);

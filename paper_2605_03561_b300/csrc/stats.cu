@@ -598,7 +598,8 @@ __device__ __forceinline__ void build_kmap8(unsigned char* kmap8, u32 C, const u
   const uint4 ff = make_uint4(~0u, ~0u, ~0u, ~0u);
   for (u32 i = threadIdx.x; i < (C + 15) / 16; i += blockDim.x) w[i] = ff;
   __syncthreads();
-  for (u32 i = threadIdx.x; i < nkc; i += blockDim.x) kmap8[kset[k0 + i]] = (unsigned char)i;
+  for (u32 i = threadIdx.x; i < nkc; i += blockDim.x)
+    if (kset[k0 + i] < C) kmap8[kset[k0 + i]] = (unsigned char)i;  // checked later
   __syncthreads();
 }
 
@@ -1316,22 +1317,32 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
   const u32 *dS, *dK;
   TRY(to_device(c, tmp, a->ranks, a->ranks ? n : 0, a->mem_kind, &dS, "rank subset"));
   TRY(to_device(c, tmp, a->ctxs, nk, a->mem_kind, &dK, "ctx set"));
-  u32* status;
-  TRY(tmp.get_n(1, &status, "status"));
+  u32* status;  // [0] the cells kernel's stalled copies, [1] the context set's check
+  TRY(tmp.get_n(2, &status, "status"));
+  // rank ids index the tensor: checked before any kernel reads them
   TRY(check_subset(c, L, dS, n, e->R, status, "rank subset"));
-  TRY(check_subset(c, L, dK, nk, e->C, status, "ctx set"));
-  cudaMemsetAsync(status, 0, 4, c->stream);  // the cells kernel reports a stalled copy here
-  u64* meta;  // [0] istar, [1] sum n_iter, [2] max span
-  TRY(tmp.get_n(4, &meta, "speedup meta"));
-  cudaMemsetAsync(meta, 0, 32, c->stream);
-  cudaMemsetAsync(meta, 0xFF, 4, c->stream);
-  k_sp_istar<<<blocks(n), 256, 0, L.stream>>>(dS, n, e->n_iter, e->span, (u32*)meta,
-                                              (unsigned long long*)meta + 1,
-                                              (unsigned long long*)meta + 2);
+  cudaMemsetAsync(status, 0, 8, c->stream);
+  // context ids only select outputs (the maps skip ids >= C): checked on the
+  // device here, read at the final wait
+  k_check_sorted<<<blocks(nk), 256, 0, L.stream>>>(dK, nk, e->C, status + 1);
   L.count();
-  u64 h[3];
-  TRY(copy(c, h, meta, sizeof h));
-  TRY(sync_check(c, "speedup I*"));
+  u64 h[3];  // I*, sum n_iter, max span over S
+  if (!dS && e->has_iter_summary) {  // all ranks: kept from the load
+    h[0] = e->istar_all;
+    h[1] = e->sum_iter_all;
+    h[2] = e->max_span;
+  } else {
+    u64* meta;
+    TRY(tmp.get_n(4, &meta, "speedup meta"));
+    cudaMemsetAsync(meta, 0, 32, c->stream);
+    cudaMemsetAsync(meta, 0xFF, 4, c->stream);
+    k_sp_istar<<<blocks(n), 256, 0, L.stream>>>(dS, n, e->n_iter, e->span, (u32*)meta,
+                                                (unsigned long long*)meta + 1,
+                                                (unsigned long long*)meta + 2);
+    L.count();
+    TRY(copy(c, h, meta, sizeof h));
+    TRY(sync_check(c, "speedup I*"));
+  }
   const u32 I = (u32)h[0];
   const u64 excluded = h[1] - (u64)n * I;
   const u64 t_app = a->app_time_ns ? a->app_time_ns : h[2];
@@ -1355,10 +1366,11 @@ ta_status ta_potential_speedup(ta_experiment* e, const ta_speedup_args* a, ta_sp
     TRY(copy(c, o->per_ctx, dper, (size_t)nk * sizeof(ta_speedup_ctx)));
     TRY(copy(c, o->total, dtot, sizeof(ta_speedup_total)));
   }
-  u32 f = 0;
-  TRY(copy(c, &f, status, 4));
+  u32 f[2] = {0, 0};
+  TRY(copy(c, f, status, 8));
   TRY(sync_check(c, "ta_potential_speedup"));
-  return status_from_flags(f, "ta_potential_speedup");
+  if (f[1]) return fail(TA_ERR_INVALID_ARG, "ctx set must be sorted, unique and in range");
+  return status_from_flags(f[0], "ta_potential_speedup");
 }
 
 }  // extern "C"
@@ -2032,6 +2044,14 @@ __global__ void k_write_batch_outliers(const u64* keys, const double* zs, u64 n,
 namespace ta {
 
 // Shared with the other entry points (declared in ta_api_internal.h).
+void launch_iter_summary(const Launch& L, u32 R, const u32* n_iter, const u64* span, u64* meta) {
+  cudaMemsetAsync(meta, 0, 32, L.stream);
+  cudaMemsetAsync(meta, 0xFF, 4, L.stream);
+  k_sp_istar<<<blocks(R), 256, 0, L.stream>>>(nullptr, R, n_iter, span, (u32*)meta,
+                                              (unsigned long long*)meta + 1,
+                                              (unsigned long long*)meta + 2);
+  L.count();
+}
 void sort_u64_pairs(const Launch& L, u64* keys, double* vals, u64 n) { sort_pairs(L, keys, vals, n); }
 const Csr* csr_of_metric(const ta_experiment* e, u32 metric) { return metric_csr(e, metric); }
 ta_status rank_subset_to_device(ta_ctx* c, Pool& tmp, const Launch& L, const u32* src, u32 n,

@@ -135,6 +135,10 @@ struct ta_experiment {
   ta::u64* x_m1 = nullptr;
   ta::u64* x_m2 = nullptr;
   uint8_t* x_mom = nullptr;
+  // over all ranks (from the load): I* = min n_iter and the sum of n_iter
+  bool has_iter_summary = false;
+  ta::u32 istar_all = 0;
+  ta::u64 sum_iter_all = 0;
   bool has_incl = false;
   // first sample of every tensor row ([rows + 1], global sample index; built
   // by the first time-window call) and that call's last result
@@ -173,6 +177,9 @@ ta_status ensure_row_index(ta_experiment* e);
 // Bitonic sort of n (key, value) pairs ascending by key, in buffers of at
 // least next_pow2(n) entries (stats.cu).
 void sort_u64_pairs(const Launch& L, u64* keys, double* vals, u64 n);
+// I* (min n_iter, u32), the sum of n_iter and the longest span over all R
+// ranks into meta[0..2] (32 bytes of device scratch).
+void launch_iter_summary(const Launch& L, u32 R, const u32* n_iter, const u64* span, u64* meta);
 // The experiment's CSR of a metric, or null (inclusive not built).
 const Csr* csr_of_metric(const ta_experiment* e, u32 metric);
 // A caller rank subset on the device (null stays null), checked sorted,

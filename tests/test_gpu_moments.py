@@ -68,3 +68,21 @@ def test_many_ranks_and_prune():
     check_speedup(a, e, segs)
     e.prune(keep=(1, 100))  # the moments follow the unpruned entries: dropped
     check_speedup(a, e, segs)
+
+
+def test_speedup_argument_errors_then_valid():
+    # Context sets are checked on the device and reported at the call's end
+    # (the maps skip ids >= C meanwhile); rank subsets before any kernel.
+    d, extended, _ = _mixed(5)
+    tr, a, e = load_both(d)
+    C = len(d["parent"])
+    import paper_2605_03561_b300 as ta
+    for bad in ([3, 2], [2, 2], [1, C], [C + 1000]):
+        with pytest.raises(ta.TaError) as ei:
+            e.speedup(bad)
+        assert ei.value.status == ta.INVALID_ARG, bad
+    with pytest.raises(ta.TaError) as ei:
+        e.speedup([1, 2], ranks=np.array([5, 3], np.uint32))
+    assert ei.value.status == ta.INVALID_ARG
+    check_speedup(a, e, list(range(C)))
+    check_speedup(a, e, [1, 2], ranks=np.array(extended, np.uint32))
