@@ -584,7 +584,9 @@ def run_batched(args, ctx, local):
                        for x in sets], tau=(3, 1), outlier_cap=cap, set_args=set_args)
     plan_s = time.perf_counter() - t0
     info = b.info()
+    torch.cuda.nvtx.range_push("batched")  # lets a profiler take the replays alone
     batch_ms, batch_l, batch_clk = timed(b.run, args.steps, max(3, args.warmup))
+    torch.cuda.nvtx.range_pop()
     alg = 12 * N + 16 * info["tensor_nnz"] + 8 * info["n_rows"] + 8 * (R + len(sets))
     out = {"workload": BATCHED + (f" (rank scale {args.batch_scale})" if args.batch_scale != 1 else ""),
            "sets": len(sets), "records": N, "ranks": R, "tensor_entries": info["tensor_nnz"],
