@@ -140,6 +140,60 @@ __global__ void __launch_bounds__(STATS_NT)
   }
 }
 
+// Index of context k in the context-sorted entries [E0, E1), or ~0.
+__device__ __forceinline__ u64 find_ctx(const u32* __restrict__ ctx, u64 E0, u64 E1, u32 k) {
+  u64 lo = E0, hi = E1;  // first entry >= k
+  while (lo < hi) {
+    const u64 mid = lo + (hi - lo) / 2;
+    if (ctx[mid] < k) lo = mid + 1;
+    else hi = mid;
+  }
+  return (lo < E1 && ctx[lo] == k) ? lo : ~0ull;
+}
+
+// The partials of one context (slot 0): a thread per rank finds the rank's
+// entry by binary search (the entries are context-sorted) instead of a warp
+// reading all of them; warp sums, then one set of atomics per warp.
+__global__ void __launch_bounds__(STATS_NT)
+    k_stats_partial_one(const u32* __restrict__ S, u32 n, const u64* __restrict__ off,
+                        const u32* __restrict__ ctx, const u64* __restrict__ time, u32 k,
+                        Partials P) {
+  u32 pres = 0;
+  u64 mn = ~0ull, mx = 0, s1 = 0, s2lo = 0, s2hi = 0;
+  for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const u32 r = rank_at(S, i);
+    const u64 j = find_ctx(ctx, off[r], off[r + 1], k);
+    if (j == ~0ull) continue;
+    const u64 x = time[j];
+    const u128 x2 = (u128)x * x;
+    ++pres;
+    mn = min(mn, x);
+    mx = max(mx, x);
+    s1 += x;
+    const u64 lo = s2lo + (u64)x2;
+    s2hi += (u64)(x2 >> 64) + (lo < s2lo ? 1ull : 0ull);
+    s2lo = lo;
+  }
+  pres = __reduce_add_sync(FULL, pres);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, (u64)__shfl_xor_sync(FULL, mn, o));
+    mx = max(mx, (u64)__shfl_xor_sync(FULL, mx, o));
+    s1 += __shfl_xor_sync(FULL, s1, o);
+    const u64 ol = __shfl_xor_sync(FULL, s2lo, o), oh = __shfl_xor_sync(FULL, s2hi, o);
+    const u64 lo = s2lo + ol;
+    s2hi += oh + (lo < s2lo ? 1ull : 0ull);
+    s2lo = lo;
+  }
+  if ((threadIdx.x & 31) == 0 && pres) {
+    atomicAdd(&P.present[0], pres);
+    atomicMin((unsigned long long*)&P.mn[0], (unsigned long long)mn);
+    atomicMax((unsigned long long*)&P.mx[0], (unsigned long long)mx);
+    atomicAdd((unsigned long long*)&P.s1[0], (unsigned long long)s1);
+    atomic_add_u128(&P.s2lo[0], &P.s2hi[0], ((u128)s2hi << 64) | s2lo);
+  }
+}
+
 // Per slot: mean, std (ddof 1), cv, balance from the exact partials.
 __global__ void k_stats_finalize(u32 n_slots, u64 n_all, const u32* S, Partials P,
                                  ta_ctx_stats* out, SetMap sets) {
@@ -187,7 +241,35 @@ __global__ void k_stats_z(const u32* __restrict__ S, u32 n_all, const u64* __res
                           const u32* __restrict__ slot_of_ctx, Partials P, u32 tn, u32 td,
                           double* z_out, u64* keys, double* zs, u64 cap,
                           unsigned long long* n_out, uint8_t* rank_flag, SetMap sets,
-                          u64 n_stat) {
+                          u64 n_stat, u32 single) {
+  // entry j of rank r in slot `slot`, over n ranks
+  auto entry = [&](u64 j, u32 r, u32 slot, u64 n) {
+    const u64 x = time[j];
+    const u64 mx = P.mx[slot];
+    if (mx > 0 && x == mx) atomicMin(&P.argmax[slot], r);
+    const u64 s1 = P.s1[slot];
+    const u128 M = ((u128)P.Mhi[slot] << 64) | P.Mlo[slot];
+    const long long D = (long long)((u64)n * x) - (long long)s1;
+    const double z = (n < 2 || M == 0) ? 0.0 : i64_to_f64(D) / (u64_to_f64(n) * P.sd[slot]);
+    if (z_out) z_out[j] = z;
+    if (is_outlier(D, n, M, tn, td)) {
+      const unsigned long long q = atomicAdd(n_out, 1ull);
+      if (q < cap) {
+        keys[q] = ((u64)slot << 32) | r;
+        zs[q] = z;
+      }
+      if (rank_flag) rank_flag[r] = 1;
+    }
+  };
+  if (single != NONE32) {  // one context (slot 0), no sets: a thread per rank
+    const u64 n = n_stat ? n_stat : n_all;
+    for (u32 i = blockIdx.x * blockDim.x + threadIdx.x; i < n_all; i += gridDim.x * blockDim.x) {
+      const u32 r = rank_at(S, i);
+      const u64 j = find_ctx(ctx, off[r], off[r + 1], single);
+      if (j != ~0ull) entry(j, r, 0, n);
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const u32 gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const u32 nw = (gridDim.x * blockDim.x) >> 5;
@@ -205,22 +287,7 @@ __global__ void k_stats_z(const u32* __restrict__ S, u32 n_all, const u64* __res
       const u32 c = ctx[j];
       const u32 slot = sets.S ? cbase + c : slot_of_ctx[c];
       if (slot == NONE32) continue;
-      const u64 x = time[j];
-      const u64 mx = P.mx[slot];
-      if (mx > 0 && x == mx) atomicMin(&P.argmax[slot], r);
-      const u64 s1 = P.s1[slot];
-      const u128 M = ((u128)P.Mhi[slot] << 64) | P.Mlo[slot];
-      const long long D = (long long)((u64)n * x) - (long long)s1;
-      const double z = (n < 2 || M == 0) ? 0.0 : i64_to_f64(D) / (u64_to_f64(n) * P.sd[slot]);
-      if (z_out) z_out[j] = z;
-      if (is_outlier(D, n, M, tn, td)) {
-        const unsigned long long q = atomicAdd(n_out, 1ull);
-        if (q < cap) {
-          keys[q] = ((u64)slot << 32) | r;
-          zs[q] = z;
-        }
-        if (rank_flag) rank_flag[r] = 1;
-      }
+      entry(j, r, slot, n);
     }
   }
 }
@@ -422,7 +489,8 @@ struct StatsRun {
 // Everything of ta_context_stats on device buffers.
 ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 n,
                     const u32* dK, u32 nk, u32 tn, u32 td, u64 cap, double* z_out,
-                    uint8_t* rank_flag, StatsRun& R, bool count_outliers = true) {
+                    uint8_t* rank_flag, StatsRun& R, bool count_outliers = true,
+                    u32 single = NONE32) {
   ta_ctx* c = e->ctx;
   Launch L{c->stream, c->num_sms, &c->launches};
   const Csr* m = metric_csr(e, metric);
@@ -462,11 +530,18 @@ ta_status stats_run(ta_experiment* e, Pool& tmp, u32 metric, const u32* dS, u32 
   cudaMemsetAsync(n_out, 0, 8, c->stream);
   if (z_out) cudaMemsetAsync(z_out, 0, m->nnz * 8, c->stream);
   const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((n + 7) / 8)));
-  k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P,
-                                                   SetMap{});
+  // one context (given on the host): each rank's entry by binary search
+  if (nk != 1 || !dK) single = NONE32;
+  if (single != NONE32)
+    k_stats_partial_one<<<blocks(n), STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time,
+                                                              single, P);
+  else
+    k_stats_partial<<<grid, STATS_NT, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx,
+                                                     P, SetMap{});
   k_stats_finalize<<<blocks(ns), 256, 0, L.stream>>>(ns, n, dS, P, R.stats, SetMap{});
-  k_stats_z<<<grid, 256, 0, L.stream>>>(dS, n, m->off, m->ctx, m->time, slot_of_ctx, P, tn, td,
-                                        z_out, R.keys, R.zs, kcap, n_out, rank_flag, SetMap{}, 0);
+  k_stats_z<<<single != NONE32 ? blocks(n) : grid, 256, 0, L.stream>>>(
+      dS, n, m->off, m->ctx, m->time, slot_of_ctx, P, tn, td, z_out, R.keys, R.zs, kcap, n_out,
+      rank_flag, SetMap{}, 0, single);
   k_stats_argmax<<<blocks(ns), 256, 0, L.stream>>>(ns, P.argmax, R.stats);
   L.count(4);
   if (!count_outliers) return TA_OK;  // the caller needs the flags only
@@ -1162,8 +1237,11 @@ ta_status ta_context_stats(ta_experiment* e, const ta_stats_args* a, ta_stats_ou
     else TRY(tmp.get_n(std::max<u64>(m->nnz, 1), &dz, "z"));
   }
   StatsRun R;
+  // one context given on the host (already checked against n_ctx): the
+  // binary-search form
+  const u32 single = (a->ctxs && nk == 1 && a->mem_kind == TA_MEM_HOST) ? a->ctxs[0] : NONE32;
   TRY(stats_run(e, tmp, a->metric, dS, n, dK, a->ctxs ? nk : 0, a->tau_num, a->tau_den,
-                o->outlier_cap, dz, nullptr, R));
+                o->outlier_cap, dz, nullptr, R, true, single));
   o->n_outliers = R.n_out;
   const bool fits = R.n_out <= o->outlier_cap;
   ta_outlier* dout = nullptr;
@@ -1230,7 +1308,7 @@ ta_status ta_topology_rollup(ta_experiment* e, const ta_topology* t, const ta_to
   TRY(copy(c, dk, &a->ctx, 4));
   StatsRun R;
   TRY(stats_run(e, tmp, a->metric, dS, n, dk, 1, a->tau_num, a->tau_den, 0, nullptr, rank_flag, R,
-                false));
+                false, a->ctx));
   // outputs on the device (staged when the caller wants host memory)
   const bool dev = o->mem_kind == TA_MEM_DEVICE;
   u32 *no, *nrk, *cf, *cn, *rf, *rn, *fr, *cnt;
@@ -1548,7 +1626,7 @@ extern "C" ta_status ta_context_stats_noalloc(void* cuda_stream, const uint64_t*
   k_stats_partial<<<grid, STATS_NT, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, SetMap{});
   k_stats_finalize<<<blocks(C), 256, 0, st>>>((u32)C, n, ranks, P, stats, SetMap{});
   k_stats_z<<<grid, 256, 0, st>>>(ranks, n, off, ctx, time, slot_of_ctx, P, tau_num, tau_den,
-                                  nullptr, keys, zs, kcap, n_out, nullptr, SetMap{}, 0);
+                                  nullptr, keys, zs, kcap, n_out, nullptr, SetMap{}, 0, NONE32);
   k_stats_argmax<<<blocks(C), 256, 0, st>>>((u32)C, P.argmax, stats);
   L.count(5);
   err = cudaGetLastError();
@@ -1779,7 +1857,7 @@ ta_status ta_shard_stats_finalize(ta_experiment* e, const ta_shard_merged* mg,
   const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((e->R + 7) / 8)));
   k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, e->R, m->off, m->ctx, m->time, slot_of_ctx, P,
                                         mg->tau_num, mg->tau_den, nullptr, keys, zs, kcap, n_out,
-                                        nullptr, SetMap{}, mg->n_total);
+                                        nullptr, SetMap{}, mg->n_total, NONE32);
   k_shard_argmax<<<blocks(C), 256, 0, L.stream>>>(C, P.argmax, mg->rank_base, o->argmax,
                                                   o->stats);
   L.count(5);
@@ -1859,7 +1937,7 @@ ta_status ta_shard_topology_partials(ta_experiment* e, const ta_shard_merged* mg
   const int grid = std::max(1, std::min<int>(c->num_sms * 4, (int)((e->R + 7) / 8)));
   k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, e->R, m->off, m->ctx, m->time, slot_of_ctx, P,
                                         mg->tau_num, mg->tau_den, nullptr, keys, zs, 1, n_out,
-                                        rank_flag, SetMap{}, mg->n_total);
+                                        rank_flag, SetMap{}, mg->n_total, ctx);
   cudaMemsetAsync(node_parts, 0, (size_t)n_nodes * 24, c->stream);
   k_shard_nodes<<<blocks(e->R), 256, 0, L.stream>>>(e->R, m->off, m->ctx, m->time, ctx, rank_flag,
                                                     node_of_rank,
@@ -2099,7 +2177,7 @@ void launch_batch_stats(const Launch& L, u32 R, u32 Ctot, const u64* off, const 
   k_stats_finalize<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, R, nullptr, P, stats, sets);
   k_stats_z<<<grid, 256, 0, L.stream>>>(nullptr, R, off, ctx, time, nullptr, P, tau_num, tau_den,
                                         nullptr, keys, zs, std::max<u64>(cap, 1), n_out, nullptr,
-                                        sets, 0);
+                                        sets, 0, NONE32);
   k_stats_argmax<<<blocks(Ctot), 256, 0, L.stream>>>(Ctot, P.argmax, stats, sets);
   L.count(4);
 }
