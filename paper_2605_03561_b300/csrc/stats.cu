@@ -785,7 +785,11 @@ __global__ void __launch_bounds__(SP_NW * 32)
 // summed the next ones are on their way.  Each entry's time is scattered to
 // a per-warp buffer indexed by (row, context) -- a row holds each context
 // once, so plain stores suffice -- and every lane then folds its contexts'
-// values into its registers, absent ones reading 0.  A round too long for a
+// values into its registers, absent ones reading 0.  A rank whose iteration
+// rows all hold the same contexts (the load's mom_ok) has only its first
+// row's contexts copied: its values go to the buffer by position, through
+// the warp's template (contexts by position and each chunk slot's position),
+// rebuilt when a rank's first row differs from it.  A round too long for a
 // stage is read from global memory directly.  The group's cells go to the
 // global cells with one set of atomics per warp.
 constexpr u32 SP_IB = 4;      // iterations per warp (one contiguous read per rank)
@@ -805,8 +809,10 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
                const u64* __restrict__ e_time, const u32* __restrict__ kset,
                const u32* __restrict__ kmap, u32 C, u32 nk, u32 I, u32 n_ib, u32 n_kb, u32 group,
                u64 n_items, u32 map_bytes, u64* g_sum, u64* g_max, u64* g_sqlo, u64* g_sqhi,
-               u32* status) {
+               const uint8_t* __restrict__ mom_ok, u32* status) {
   __shared__ u64 rowbuf[SP_NW][SP_IB][64];
+  __shared__ u32 tctx[SP_NW][96];             // the warp's template contexts by position
+  __shared__ unsigned char pslot[SP_NW][64];  // and each chunk slot's position (0xFF: none)
   extern __shared__ __align__(16) unsigned char dsm[];
   unsigned char* kmap8 = dsm;  // [map_bytes]: one chunk of 64 contexts maps through it
   const bool smap = map_bytes > 0;
@@ -841,24 +847,34 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
   // stage is refilled without waiting on these loads
   constexpr u32 SPC_OB = 6;
   static_assert(SPC_OB * NB <= 32 && SPC_OB % SPC_ST == 0, "offset batch");
+  // bit 63 of a round's first bound: every iteration row of its rank holds
+  // the same contexts (mom_ok), so the stage copies the first row's contexts
+  // only and the round is read by position (entry offsets are below 2^63)
+  constexpr u64 TBIT = 1ull << 63;
   auto batch = [&](u32 rb0) -> u64 {
     const u32 p = (u32)lane / NB, q = (u32)lane % NB;
     u64 mine = 0;
     if (p < SPC_OB && rb0 + p < r_end) {
-      const u64 row = row_off[rank_at(S, rb0 + p)] + 1 + i0;
+      const u32 rk = rank_at(S, rb0 + p);
+      const u64 row = row_off[rk] + 1 + i0;
       mine = entry_off[row + min(q, nrow)];
+      if (q == 0 && mom_ok && mom_ok[rk]) mine |= TBIT;
     }
     return mine;
   };
+  u32 tp = 0;  // the template: L (bits 0-7, 0: none), slot positions (8-15, 16-23)
   // stage s takes round rb (its bounds in lanes p NB .. p NB + SP_IB of ob)
   u32 phase = 0;      // bit s: parity of stage s's next completion
   u32 staged = 0;     // bit s: stage s holds a copy in flight
   u64 sbase[SPC_ST];  // first entry of each stage's range
   auto issue = [&](u32 s, u32 rb, u64 ob, u32 p) {
-    const u64 e0 = __shfl_sync(FULL, ob, p * NB), e1 = __shfl_sync(FULL, ob, p * NB + nrow);
+    const u64 e0t = __shfl_sync(FULL, ob, p * NB), e1 = __shfl_sync(FULL, ob, p * NB + nrow);
+    const u64 r1 = __shfl_sync(FULL, ob, p * NB + 1);  // end of the round's first row
+    const u64 e0 = e0t & ~TBIT;
     staged &= ~(1u << s);
     if (rb >= r_end || e1 <= e0 || e1 - e0 > SPC_CAP) return;
-    const u64 c0 = e0 & ~(u64)3, c1 = (e1 + 3) & ~(u64)3;  // 16-byte rounded ranges
+    const u64 ce = (e0t & TBIT) ? r1 : e1;  // contexts: the first row only for a template rank
+    const u64 c0 = e0 & ~(u64)3, c1 = (ce + 3) & ~(u64)3;  // 16-byte rounded ranges
     const u64 t0 = e0 & ~(u64)1, t1 = (e1 + 1) & ~(u64)1;
     sbase[s] = e0;
     staged |= 1u << s;
@@ -883,6 +899,8 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
       u64 bnd[NB];
 #pragma unroll
       for (u32 q = 0; q < NB; ++q) bnd[q] = __shfl_sync(FULL, ob0, p * NB + q);
+      const bool trank = (bnd[0] & TBIT) != 0;
+      bnd[0] &= ~TBIT;
       const u64 total = bnd[SP_IB] - bnd[0];
       if ((staged >> s) & 1u) {
         if (!mbar_wait(&bar[s], (phase >> s) & 1u)) {
@@ -893,26 +911,58 @@ __global__ void __launch_bounds__(SP_NW * 32, 2)
         const unsigned char* st = ws + s * SPC_STAGE_BYTES;
         const u32* sctx = reinterpret_cast<const u32*>(st) + (sbase[s] & 3);
         const u64* stime = reinterpret_cast<const u64*>(st + SPC_CTX_BYTES) + (sbase[s] & 1);
-        // all of the stage's loads first (independent), then the lookups,
-        // then the scatter: no chain of dependent shared-memory loads
-        constexpr u32 SPC_U = SPC_CAP / 32;
-        u32 kk[SPC_U];
+        if (trank) {  // every row is the first row's contexts: values by position
+          const u32 L = (u32)(bnd[1] - bnd[0]);
+          const bool h0 = (u32)lane < L, h1 = (u32)lane + 32 < L, h2 = (u32)lane + 64 < L;
+          const u32 c0 = h0 ? sctx[lane] : NONE32, c1 = h1 ? sctx[lane + 32] : NONE32,
+                    c2 = h2 ? sctx[lane + 64] : NONE32;
+          bool same = (tp & 0xFFu) == L;
+          if (same)
+            same = c0 == tctx[warp][lane] && c1 == tctx[warp][lane + 32] &&
+                   c2 == tctx[warp][lane + 64];
+          if (!__all_sync(FULL, same)) {  // a new template: its contexts and slot positions
+            tctx[warp][lane] = c0;
+            tctx[warp][lane + 32] = c1;
+            tctx[warp][lane + 64] = c2;
+            pslot[warp][lane] = pslot[warp][lane + 32] = 0xFF;
+            __syncwarp();
+            const u32 k0s = h0 ? look(c0) : NONE32, k1s = h1 ? look(c1) : NONE32,
+                      k2s = h2 ? look(c2) : NONE32;
+            if (k0s != NONE32) pslot[warp][k0s] = (unsigned char)lane;
+            if (k1s != NONE32) pslot[warp][k1s] = (unsigned char)(lane + 32);
+            if (k2s != NONE32) pslot[warp][k2s] = (unsigned char)(lane + 64);
+            __syncwarp();
+            tp = L | (u32)pslot[warp][lane] << 8 | (u32)pslot[warp][lane + 32] << 16;
+          }
+          const u32 src0 = (tp >> 8) & 0xFFu, src1 = tp >> 16;
 #pragma unroll
-        for (u32 u = 0; u < SPC_U; ++u) {
-          const u32 v = (u32)lane + 32 * u;
-          kk[u] = v < (u32)total ? sctx[v] : NONE32;
-        }
+          for (u32 il = 0; il < SP_IB; ++il) {
+            if (il >= nrow) continue;
+            if (src0 != 0xFFu) buf[il * 64 + lane] = stime[il * L + src0];
+            if (src1 != 0xFFu) buf[il * 64 + lane + 32] = stime[il * L + src1];
+          }
+        } else {
+          // all of the stage's loads first (independent), then the lookups,
+          // then the scatter: no chain of dependent shared-memory loads
+          constexpr u32 SPC_U = SPC_CAP / 32;
+          u32 kk[SPC_U];
 #pragma unroll
-        for (u32 u = 0; u < SPC_U; ++u) kk[u] = kk[u] != NONE32 ? look(kk[u]) : NONE32;
+          for (u32 u = 0; u < SPC_U; ++u) {
+            const u32 v = (u32)lane + 32 * u;
+            kk[u] = v < (u32)total ? sctx[v] : NONE32;
+          }
 #pragma unroll
-        for (u32 u = 0; u < SPC_U; ++u) {
-          const u32 v = (u32)lane + 32 * u;
-          if (kk[u] == NONE32) continue;
-          const u64 jj = bnd[0] + v;
-          u32 il = 0;
+          for (u32 u = 0; u < SPC_U; ++u) kk[u] = kk[u] != NONE32 ? look(kk[u]) : NONE32;
 #pragma unroll
-          for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bnd[q]) ? 1u : 0u;
-          buf[il * 64 + kk[u]] = stime[v];
+          for (u32 u = 0; u < SPC_U; ++u) {
+            const u32 v = (u32)lane + 32 * u;
+            if (kk[u] == NONE32) continue;
+            const u64 jj = bnd[0] + v;
+            u32 il = 0;
+#pragma unroll
+            for (u32 q = 1; q < SP_IB; ++q) il += (jj >= bnd[q]) ? 1u : 0u;
+            buf[il * 64 + kk[u]] = stime[v];
+          }
         }
       } else {
         for (u64 vb = 0; vb < total; vb += 32 * SP_CU) {
@@ -1172,7 +1222,7 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
     cudaFuncSetAttribute(k_sp_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cells_smem);
     k_sp_cells<<<(unsigned)((n_items + SP_NW - 1) / SP_NW), SP_NW * 32, cells_smem, L.stream>>>(
         dS, n, e->row_off, e->entry_off, e->e_ctx, e->e_time, dK, kmap, e->C, nk, I, n_ib, n_kb,
-        group, n_items, (u32)cmap_smem, gs, gm, gl, gh, status);
+        group, n_items, (u32)cmap_smem, gs, gm, gl, gh, e->x_mom, status);
     L.count();
     for (u32 k0 = 0; k0 < nk; k0 += SP_KC) {
       k_sp_within<<<grid, SP_NW * 32, map_smem, ws>>>(
