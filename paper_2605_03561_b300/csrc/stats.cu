@@ -1212,8 +1212,10 @@ ta_status speedup_parts(ta_experiment* e, Pool& tmp, const Launch& L, const u32*
     // cells: enough warps to fill the GPU, each with a sizeable group of ranks
     const u32 n_ib = (I + SP_IB - 1) / SP_IB, n_kb = (nk + 63) / 64;
     const u64 tiles = (u64)n_ib * n_kb;
+    // at most `want` warps: three full waves of two 8-warp CTAs per SM (one
+    // more item than that would start a fourth wave of a few CTAs)
     const u64 want = (u64)c->num_sms * 48;
-    u64 groups = std::max<u64>(1, std::min<u64>((want + tiles - 1) / tiles, (n + 63) / 64));
+    u64 groups = std::max<u64>(1, std::min<u64>(want / tiles, (n + 63) / 64));
     const u32 group = (u32)((n + groups - 1) / groups);
     groups = (n + group - 1) / group;
     const u64 n_items = tiles * groups;
