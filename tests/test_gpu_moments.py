@@ -86,3 +86,28 @@ def test_speedup_argument_errors_then_valid():
     assert ei.value.status == ta.INVALID_ARG
     check_speedup(a, e, list(range(C)))
     check_speedup(a, e, [1, 2], ranks=np.array(extended, np.uint32))
+
+
+def test_alternating_templates():
+    # Odd ranks move one segment context's samples to the prologue context in
+    # every iteration: they keep one context list across their iterations (so
+    # both the moments and the cells' by-position reading apply), but a list
+    # different from the even ranks', so a warp's template is rebuilt as it
+    # goes from rank to rank.
+    g = synth.generate(synth.preset(1, seed=13, n_ranks=200))
+    ro, ts, cx, m = g["rank_off"], g["ts"], g["ctx"].copy(), int(g["marker"])
+    pro = int(g["info"].prologue_ctx)
+    for r in range(1, len(ro) - 1, 2):
+        a, b = int(ro[r]), int(ro[r + 1])
+        starts = np.flatnonzero(cx[a:b] == m)
+        if not len(starts):
+            continue
+        it = cx[a + int(starts[0]):b]
+        seg = [x for x in np.unique(it) if x != m and x != pro]
+        if seg:
+            it[it == seg[0]] = pro
+    d = dict(rank_off=ro, ts=ts, ctx=cx, parent=g["parent"], marker=m)
+    tr, a, e = load_both(d)
+    check_products(tr, a, e)
+    check_speedup(a, e, list(range(len(d["parent"]))))
+    check_speedup(a, e, sorted(set(int(x) for x in cx[:3000])), ranks=np.arange(0, 200, 3, dtype=np.uint32))
